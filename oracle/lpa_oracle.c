@@ -1,0 +1,324 @@
+/*
+ * lpa_oracle.c -- plain, slow, single-threaded CPU oracle for GVE-LPA
+ * (Sahu, "GVE-LPA: Fast Label Propagation Algorithm (LPA) for Community
+ * Detection in Shared Memory Setting", arXiv 2312.08140).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this file.  The product path
+ * (the CUDA library) never calls it and shares no code with it.
+ *
+ * What it computes, in the paper's order and notation:
+ *   - oracle_pick:       the label update rule (Eq. 3, Section 3.3): the
+ *                        label c maximising K_{i->c}, the summed weight of
+ *                        i's neighbours j != i with C_j = c, as the
+ *                        scanCommunities step of Algorithm 1 accumulates it
+ *                        (self-loops skipped).  Ties go to the smallest label
+ *                        id (strict LPA, Section 4.1.5 and Section 2).
+ *                        A vertex with no neighbour other than itself keeps
+ *                        its label.  Sums are taken in fp64 in CSR order.
+ *   - oracle_lpa_sync:   a synchronous (Jacobi) reading of Algorithm 1: every
+ *                        vertex of sweep t reads the labels of sweep t-1; no
+ *                        pruning.  Stops after the sweep whose changed count
+ *                        satisfies dN/N <= tau, or after max_iters sweeps
+ *                        (Section 4.1.2, 4.1.3).
+ *   - oracle_lpa_async:  Algorithm 1 run by one thread in ascending vertex
+ *                        order: labels updated in place, a vertex is marked
+ *                        processed when visited and, when its label changes,
+ *                        all of its neighbours other than itself are marked
+ *                        unprocessed (vertex pruning, Section 4.1.4).
+ *   - oracle_modularity: Eq. 1 (Section 3.2) in its community form, all sums
+ *                        in fp64.
+ *   - checkers used by the tests on any output (labels inside the vertex's
+ *     connected component; count of vertices not at a local maximum).
+ *
+ * The per-vertex accumulator is the paper's collision-free table
+ * (Section 4.1.6): a list of touched keys plus a value array of size |V|
+ * indexed by label, reset through the key list after each vertex.
+ *
+ * Every function returns a negative value on invalid input and never aborts.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_BAD_ARG (-1)
+#define ORACLE_NO_MEM  (-2)
+
+/* Collision-free accumulator of Section 4.1.6: keys[] lists the labels seen
+ * for the current vertex, val[] (size n) holds their summed weights and
+ * seen[] (size n) marks whether a label is already in keys[]. */
+typedef struct {
+    int64_t  n;
+    int32_t *keys;
+    int64_t  nkeys;
+    double  *val;
+    uint8_t *seen;
+} kv_table;
+
+static int kv_init(kv_table *t, int64_t n) {
+    t->n = n;
+    t->nkeys = 0;
+    t->keys = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    t->val = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    t->seen = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    if (!t->keys || !t->val || !t->seen) {
+        free(t->keys); free(t->val); free(t->seen);
+        return ORACLE_NO_MEM;
+    }
+    return 0;
+}
+
+static void kv_free(kv_table *t) {
+    free(t->keys); free(t->val); free(t->seen);
+}
+
+static void kv_add(kv_table *t, int32_t key, double w) {
+    if (!t->seen[key]) {
+        t->seen[key] = 1;
+        t->keys[t->nkeys++] = key;
+    }
+    t->val[key] += w;
+}
+
+static void kv_clear(kv_table *t) {
+    for (int64_t k = 0; k < t->nkeys; ++k) {
+        t->val[t->keys[k]] = 0.0;
+        t->seen[t->keys[k]] = 0;
+    }
+    t->nkeys = 0;
+}
+
+static double edge_weight(const float *w, int64_t e) {
+    return w ? (double)w[e] : 1.0;
+}
+
+/* scanCommunities of Algorithm 1: for every CSR entry (j, w) of row i with
+ * j != i, H[C[j]] += w.  Returns the number of entries accumulated. */
+static int64_t scan_communities(kv_table *H, const int64_t *off, const int32_t *idx,
+                                const float *w, const int32_t *C, int64_t i) {
+    int64_t used = 0;
+    for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+        int32_t j = idx[e];
+        if ((int64_t)j == i) continue;            /* self-loops are skipped */
+        kv_add(H, C[j], edge_weight(w, e));
+        ++used;
+    }
+    return used;
+}
+
+/* The most weighted label in H (Eq. 3); ties go to the smallest label id. */
+static int32_t most_weighted_label(const kv_table *H) {
+    int32_t best = -1;
+    double best_w = 0.0;
+    for (int64_t k = 0; k < H->nkeys; ++k) {
+        int32_t c = H->keys[k];
+        double v = H->val[c];
+        if (best < 0 || v > best_w || (v == best_w && c < best)) {
+            best = c;
+            best_w = v;
+        }
+    }
+    return best;
+}
+
+static int32_t pick(kv_table *H, const int64_t *off, const int32_t *idx, const float *w,
+                    const int32_t *C, int64_t i) {
+    int64_t used = scan_communities(H, off, idx, w, C, i);
+    int32_t c = used ? most_weighted_label(H) : C[i];
+    kv_clear(H);
+    return c;
+}
+
+static int check_csr(int64_t n, const int64_t *off, const int32_t *idx) {
+    if (n < 0 || !off) return ORACLE_BAD_ARG;
+    if (off[0] != 0) return ORACLE_BAD_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (off[i + 1] < off[i]) return ORACLE_BAD_ARG;
+    if (off[n] > 0 && !idx) return ORACLE_BAD_ARG;
+    for (int64_t e = 0; e < off[n]; ++e)
+        if (idx[e] < 0 || (int64_t)idx[e] >= n) return ORACLE_BAD_ARG;
+    return 0;
+}
+
+/* Convergence test of Algorithm 1: dN / N <= tau, in fp64. */
+static int converged(int64_t dN, int64_t n, double tau) {
+    return (double)dN / (double)n <= tau;
+}
+
+/* One label for vertex i given labels C (Eq. 3 with the strict tie-break). */
+int32_t oracle_pick(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                    const int32_t *C, int64_t i) {
+    if (check_csr(n, off, idx) || i < 0 || i >= n || !C) return ORACLE_BAD_ARG;
+    kv_table H;
+    if (kv_init(&H, n)) return ORACLE_NO_MEM;
+    int32_t c = pick(&H, off, idx, w, C, i);
+    kv_free(&H);
+    return c;
+}
+
+/* One synchronous sweep: C_out[i] = pick(i, C_in) for every i.  Returns dN,
+ * the number of vertices whose label changed. */
+int64_t oracle_sync_sweep(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                          const int32_t *C_in, int32_t *C_out) {
+    if (check_csr(n, off, idx) || !C_in || !C_out) return ORACLE_BAD_ARG;
+    kv_table H;
+    if (kv_init(&H, n)) return ORACLE_NO_MEM;
+    int64_t dN = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        C_out[i] = pick(&H, off, idx, w, C_in, i);
+        dN += (C_out[i] != C_in[i]);
+    }
+    kv_free(&H);
+    return dN;
+}
+
+/* Synchronous LPA.  C_out: int32[n]; changed_hist (nullable): int64[max_iters]
+ * receives dN of each sweep.  Returns the number of sweeps performed. */
+int64_t oracle_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                        double tau, int64_t max_iters, int32_t *C_out, int64_t *changed_hist) {
+    if (check_csr(n, off, idx) || !C_out || max_iters < 0 || !(tau >= 0.0)) return ORACLE_BAD_ARG;
+    for (int64_t i = 0; i < n; ++i) C_out[i] = (int32_t)i;          /* C <- [0 .. |V|) */
+    if (n == 0) return 0;
+    int32_t *prev = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!prev) return ORACLE_NO_MEM;
+    kv_table H;
+    if (kv_init(&H, n)) { free(prev); return ORACLE_NO_MEM; }
+    int64_t it = 0;
+    while (it < max_iters) {
+        memcpy(prev, C_out, (size_t)n * sizeof(int32_t));
+        int64_t dN = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            C_out[i] = pick(&H, off, idx, w, prev, i);
+            dN += (C_out[i] != prev[i]);
+        }
+        if (changed_hist) changed_hist[it] = dN;
+        ++it;
+        if (converged(dN, n, tau)) break;
+    }
+    kv_free(&H);
+    free(prev);
+    return it;
+}
+
+/* Algorithm 1 (lpa / lpaMove / scanCommunities) run by a single thread that
+ * visits vertices in ascending order.  Returns the number of sweeps. */
+int64_t oracle_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                         double tau, int64_t max_iters, int32_t *C_out, int64_t *changed_hist) {
+    if (check_csr(n, off, idx) || !C_out || max_iters < 0 || !(tau >= 0.0)) return ORACLE_BAD_ARG;
+    for (int64_t i = 0; i < n; ++i) C_out[i] = (int32_t)i;          /* C <- [0 .. |V|) */
+    if (n == 0) return 0;
+    uint8_t *unprocessed = (uint8_t *)malloc((size_t)n);
+    if (!unprocessed) return ORACLE_NO_MEM;
+    memset(unprocessed, 1, (size_t)n);                               /* all unprocessed */
+    kv_table H;
+    if (kv_init(&H, n)) { free(unprocessed); return ORACLE_NO_MEM; }
+    int64_t it = 0;
+    while (it < max_iters) {
+        int64_t dN = 0;                                              /* lpaMove */
+        for (int64_t i = 0; i < n; ++i) {
+            if (!unprocessed[i]) continue;
+            unprocessed[i] = 0;                                      /* prune */
+            int32_t c = pick(&H, off, idx, w, C_out, i);
+            if (c == C_out[i]) continue;
+            C_out[i] = c;
+            ++dN;
+            for (int64_t e = off[i]; e < off[i + 1]; ++e)            /* re-mark neighbours */
+                if ((int64_t)idx[e] != i) unprocessed[idx[e]] = 1;
+        }
+        if (changed_hist) changed_hist[it] = dN;
+        ++it;
+        if (converged(dN, n, tau)) break;
+    }
+    kv_free(&H);
+    free(unprocessed);
+    return it;
+}
+
+/* Modularity, Eq. 1 in community form: Q = sum_c [sigma_c/2m - (Sigma_c/2m)^2]
+ * with 2m = sum of all stored entries' weights, sigma_c = weight of entries
+ * (i,j) with C_i = C_j = c and Sigma_c = sum of K_i over i in c.
+ * Returns 0 when the graph has no weight (2m == 0).  *q_out receives Q. */
+int oracle_modularity(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                      const int32_t *C, double *q_out) {
+    if (check_csr(n, off, idx) || !C || !q_out) return ORACLE_BAD_ARG;
+    for (int64_t i = 0; i < n; ++i)
+        if (C[i] < 0 || (int64_t)C[i] >= n) return ORACLE_BAD_ARG;
+    double two_m = 0.0, sigma = 0.0;
+    double *Sigma = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!Sigma) return ORACLE_NO_MEM;
+    for (int64_t i = 0; i < n; ++i) {
+        double K_i = 0.0;
+        for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+            double wij = edge_weight(w, e);
+            K_i += wij;
+            if (C[idx[e]] == C[i]) sigma += wij;
+        }
+        two_m += K_i;
+        Sigma[C[i]] += K_i;
+    }
+    double q = 0.0;
+    if (two_m > 0.0) {
+        double null_term = 0.0;
+        for (int64_t c = 0; c < n; ++c) null_term += (Sigma[c] / two_m) * (Sigma[c] / two_m);
+        q = sigma / two_m - null_term;
+    }
+    free(Sigma);
+    *q_out = q;
+    return 0;
+}
+
+/* ---- checkers (properties any correct output has) ---------------------- */
+
+static int64_t uf_find(int64_t *parent, int64_t x) {
+    while (parent[x] != x) {
+        parent[x] = parent[parent[x]];
+        x = parent[x];
+    }
+    return x;
+}
+
+/* Number of vertices i whose label C[i] is not a vertex of i's connected
+ * component (labels only travel along edges, so a correct run returns 0).
+ * Also fails labels outside [0, n). */
+int64_t oracle_count_labels_outside_component(int64_t n, const int64_t *off, const int32_t *idx,
+                                              const int32_t *C) {
+    if (check_csr(n, off, idx) || !C) return ORACLE_BAD_ARG;
+    int64_t *parent = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!parent) return ORACLE_NO_MEM;
+    for (int64_t i = 0; i < n; ++i) parent[i] = i;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t e = off[i]; e < off[i + 1]; ++e) {
+            int64_t a = uf_find(parent, i), b = uf_find(parent, idx[e]);
+            if (a != b) parent[a < b ? b : a] = (a < b ? a : b);
+        }
+    int64_t bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (C[i] < 0 || (int64_t)C[i] >= n) { ++bad; continue; }
+        if (uf_find(parent, i) != uf_find(parent, C[i])) ++bad;
+    }
+    free(parent);
+    return bad;
+}
+
+/* Number of vertices not at a local maximum: K_{i->C_i} < max_c K_{i->c}
+ * (tie-insensitive).  Vertices with no neighbour other than themselves count
+ * as at a maximum. */
+int64_t oracle_count_not_local_max(int64_t n, const int64_t *off, const int32_t *idx,
+                                   const float *w, const int32_t *C) {
+    if (check_csr(n, off, idx) || !C) return ORACLE_BAD_ARG;
+    kv_table H;
+    if (kv_init(&H, n)) return ORACLE_NO_MEM;
+    int64_t bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (C[i] < 0 || (int64_t)C[i] >= n) { ++bad; continue; }
+        int64_t used = scan_communities(&H, off, idx, w, C, i);
+        if (used) {
+            int32_t best = most_weighted_label(&H);
+            double own = H.seen[C[i]] ? H.val[C[i]] : 0.0;
+            if (own < H.val[best]) ++bad;
+        }
+        kv_clear(&H);
+    }
+    kv_free(&H);
+    return bad;
+}
