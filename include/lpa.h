@@ -1,0 +1,238 @@
+/*
+ * lpa.h -- C ABI of liblpa: GPU label propagation (GVE-LPA, Sahu, arXiv
+ * 2312.08140) for NVIDIA GB300 (sm_103a).
+ *
+ * Terms follow the paper (Section 3): an undirected graph G(V, E, w) with
+ * w_ij = w_ji is given as CSR holding both directions of every edge;
+ * N = |V|; C_i is the label (community id) of vertex i; one "sweep" is one
+ * call of lpaMove in Algorithm 1.
+ *
+ * Conventions for every entry point:
+ *   - The return value is an lpa_status; no call aborts the process.  On
+ *     error, output arguments are left untouched and lpa_last_error() gives a
+ *     one-line reason (thread-local).
+ *   - "device" pointers are CUDA device (or managed) pointers of the current
+ *     device; "host" pointers are ordinary or pinned host memory.
+ *   - The library owns what it allocates and frees it in the matching
+ *     *_destroy call.  The caller owns every buffer it passes in and every
+ *     stream.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls documented as asynchronous only enqueue work on it.
+ *   - A handle may be used by one host thread at a time, and its runs must be
+ *     ordered (one stream, or explicit synchronisation between streams).
+ *   - Vertex ids and labels are int32 (N <= 2^31 - 1); entry counts are int64.
+ */
+#ifndef LPA_H_
+#define LPA_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LPA_OK = 0,
+    LPA_ERR_INVALID_ARG = 1,    /* a scalar argument or pointer is out of its documented range */
+    LPA_ERR_INVALID_GRAPH = 2,  /* CSR failed validation (offsets, index range, weights) */
+    LPA_ERR_OUT_OF_MEMORY = 3,  /* a device or pinned allocation failed */
+    LPA_ERR_CUDA = 4,           /* a CUDA runtime call failed; see lpa_last_error() */
+    LPA_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    LPA_ERR_BUSY = 6,           /* serving: the request does not fit the HBM budget right now */
+    LPA_ERR_NOT_FOUND = 7,      /* serving: unknown ticket */
+    LPA_ERR_NOT_READY = 8       /* serving: ticket not finished yet */
+} lpa_status;
+
+/* Sweep semantics.
+ * LPA_MODE_SYNC       Jacobi reading of Algorithm 1: every vertex of sweep t
+ *                     reads the labels left by sweep t-1; ties go to the
+ *                     smallest label id (Section 4.1.5).  Only vertices with a
+ *                     neighbour that changed in sweep t-1 are scanned (vertex
+ *                     pruning, Section 4.1.4); this never changes the result
+ *                     because a vertex's pick depends on its neighbours'
+ *                     labels only.  Deterministic.
+ * LPA_MODE_ASYNC      Algorithm 1 as the paper runs it (Section 4.1): labels
+ *                     are updated in place while other vertices read them,
+ *                     with vertex pruning.  Results depend on timing.
+ * LPA_MODE_SYNC_FULL  LPA_MODE_SYNC without pruning: every vertex is scanned
+ *                     in every sweep.  Same labels as LPA_MODE_SYNC. */
+typedef enum {
+    LPA_MODE_SYNC = 0,
+    LPA_MODE_ASYNC = 1,
+    LPA_MODE_SYNC_FULL = 2
+} lpa_mode;
+
+/* lpa_graph_create / lpa_batch_create flags */
+#define LPA_HOST_PTRS   0u  /* offsets/indices/weights are host memory; the library copies them */
+#define LPA_DEVICE_PTRS 1u  /* they are device memory; the library copies them (unless LPA_BORROW) */
+#define LPA_BORROW      2u  /* with LPA_DEVICE_PTRS: use the caller's device arrays in place; they
+                               must stay alive and unchanged until *_destroy */
+
+/* Per-sweep history kept in lpa_run_info (sweeps beyond this are still run). */
+#define LPA_MAX_RECORDED_ITERS 64
+
+typedef struct {
+    int32_t iterations;    /* sweeps performed, including the one that met the tolerance */
+    int32_t exit_reason;   /* 0: dN/N <= tolerance; 1: max_iters reached; 2: nothing to run
+                              (N == 0 or max_iters == 0) */
+    int64_t changed[LPA_MAX_RECORDED_ITERS];  /* dN of each sweep (Algorithm 1) */
+    int64_t active[LPA_MAX_RECORDED_ITERS];   /* vertices scanned in each sweep */
+    int64_t scanned[LPA_MAX_RECORDED_ITERS];  /* CSR entries of the scanned vertices */
+    int64_t edges_touched;                    /* sum of scanned[] over all sweeps */
+} lpa_run_info;
+
+typedef struct {
+    int64_t n;             /* vertices (sum over graphs for a batch) */
+    int64_t nnz;           /* stored CSR entries */
+    int32_t num_graphs;    /* 1 for lpa_graph_t */
+    int32_t weighted;      /* 0: unit weights (weights == NULL at create) */
+    int32_t exact;         /* 1: all weights are integers and every weighted degree is < 2^24,
+                              so every per-label sum is exact and LPA_MODE_SYNC is bit-exact
+                              against an exact-arithmetic reference */
+    int32_t reserved;
+    int64_t max_degree;
+    int64_t device_bytes;  /* device memory the handle holds */
+} lpa_graph_props;
+
+/* Launch parameters of the sweep.  Vertices are binned by degree d:
+ *   d <= small_max          one thread per vertex, labels and weights in registers
+ *   small_max < d <= warp_max  one warp per vertex, per-warp shared-memory table
+ *   d > warp_max            one block per vertex, shared-memory table with a global spill table
+ * lpa_graph_set_config validates: 1 <= small_max <= 8, small_max < warp_max <= 1024,
+ * hub_threads in {128, 256, 512, 1024}, hub_slots a power of two in [1024, 16384]. */
+typedef struct {
+    int32_t small_max;
+    int32_t warp_max;
+    int32_t hub_threads;
+    int32_t hub_slots;
+} lpa_config;
+
+/* Time per phase of one run, from CUDA events recorded around every launch
+ * (lpa_run_profiled).  Times in milliseconds. */
+typedef struct {
+    int32_t iterations;
+    int32_t reserved;
+    float   init_ms;
+    float   finish_ms[LPA_MAX_RECORDED_ITERS];   /* apply + frontier compaction + control */
+    float   sweep_ms[LPA_MAX_RECORDED_ITERS][3]; /* per degree bin: small, warp, hub */
+    int64_t bin_vertices[LPA_MAX_RECORDED_ITERS][3];
+    int64_t bin_entries[LPA_MAX_RECORDED_ITERS][3];
+    int64_t bin_changed[LPA_MAX_RECORDED_ITERS][3];
+} lpa_profile;
+
+typedef struct lpa_graph  *lpa_graph_t;
+typedef struct lpa_batch  *lpa_batch_t;
+typedef struct lpa_server *lpa_server_t;
+
+/* Library version string, e.g. "lpa-gb300 0.1". */
+const char *lpa_version(void);
+
+/* Static text for a status code. */
+const char *lpa_status_string(lpa_status st);
+
+/* Reason for the last non-OK status returned on this thread ("" if none). */
+const char *lpa_last_error(void);
+
+/* ---------------------------------------------------------------- graphs */
+
+/* Build a graph handle from CSR (Section 3: undirected, w_ij = w_ji).
+ *   n         vertices, 0 <= n <= 2^31 - 1
+ *   nnz       stored entries, >= 0; offsets[n] must equal nnz
+ *   offsets   int64[n+1], offsets[0] == 0, non-decreasing
+ *   indices   int32[nnz], each in [0, n); rows need not be sorted; an entry
+ *             (i, i) is a self-loop, skipped by the sweep (Algorithm 1,
+ *             scanCommunities) and counted by lpa_modularity
+ *   weights   float32[nnz] finite and >= 0, or NULL for unit weights (the
+ *             paper's setting, Table 1).  Symmetry is the caller's contract
+ *             and is not checked.
+ *   flags     LPA_HOST_PTRS | LPA_DEVICE_PTRS, optionally | LPA_BORROW
+ * Validates the CSR on the device (returns LPA_ERR_INVALID_GRAPH on failure)
+ * and synchronises `stream` before returning.  Device memory: the CSR copy
+ * (unless borrowed) plus about 17 bytes per vertex of working state. */
+lpa_status lpa_graph_create(int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *indices,
+                            const float *weights, uint32_t flags, void *stream, lpa_graph_t *out);
+
+lpa_status lpa_graph_destroy(lpa_graph_t g);
+
+/* Properties of a handle (host struct, filled synchronously). */
+lpa_status lpa_graph_props_get(lpa_graph_t g, lpa_graph_props *out);
+
+/* Read or replace the degree-bin launch parameters (see lpa_config). */
+lpa_status lpa_graph_get_config(lpa_graph_t g, lpa_config *out);
+lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config *cfg);
+
+/* Run label propagation (Algorithm 1, lpa()): C <- [0..N), then sweeps until
+ * dN/N <= tolerance (Section 4.1.3; the paper uses 0.05) or max_iters sweeps
+ * (Section 4.1.2; the paper uses 20).
+ *   mode        lpa_mode
+ *   tolerance   in [0, 1]
+ *   max_iters   in [0, 1 << 20]
+ *   labels_out  device int32[n], caller-owned; receives C
+ *   info        host pointer or NULL.  When non-NULL the call waits for the
+ *               run to finish and fills it; when NULL the call only enqueues
+ *               work on `stream` and returns.
+ * The whole loop runs on the device (a CUDA graph with a device-side loop
+ * condition): no host round trip per sweep. */
+lpa_status lpa_run(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters,
+                   int32_t *labels_out, void *stream, lpa_run_info *info);
+
+/* Same result as lpa_run, but every launch is issued from the host and timed
+ * with CUDA events; per-phase times and per-bin counts go to *prof (host).
+ * Blocks until done.  For profiling only: slower than lpa_run. */
+lpa_status lpa_run_profiled(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters,
+                            int32_t *labels_out, void *stream, lpa_run_info *info, lpa_profile *prof);
+
+/* Modularity Q of a labelling (Eq. 1, Section 3.2, community form):
+ *   Q = sum_c [ sigma_c / 2m - (Sigma_c / 2m)^2 ]
+ * with 2m the sum of all stored entries' weights, sigma_c the weight of
+ * entries (i, j) with C_i = C_j = c and Sigma_c the sum of weighted degrees
+ * K_i over i in c.  Sums in fp64.  Q = 0 when 2m = 0.
+ *   labels  device int32[n], each in [0, n) (else LPA_ERR_INVALID_ARG)
+ *   q_out   host double; the call synchronises `stream` before returning. */
+lpa_status lpa_modularity(lpa_graph_t g, const int32_t *labels, double *q_out, void *stream);
+
+/* Pick a faster lpa_config for this graph and mode by timing candidate
+ * configurations on it (each candidate: `trials` runs of lpa_run with the
+ * given tolerance and cap, best time kept).  Applies the winner to the handle
+ * and copies it to *chosen (host, nullable).  Synchronous; the graph's labels
+ * scratch is used, no caller buffer is touched. */
+lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters,
+                        int32_t trials, void *stream, lpa_config *chosen);
+
+/* ---------------------------------------------------------------- batches */
+
+/* G independent graphs packed back to back into one handle, solved together
+ * by one device-side loop (each graph keeps its own dN, tolerance test and
+ * sweep count, Algorithm 1 per graph).
+ *   graph_vtx_off   host int64[G+1]: graph g owns vertices [vo[g], vo[g+1])
+ *   graph_edge_off  host int64[G+1]: and entries [eo[g], eo[g+1])
+ *   offsets         int64[N+1] positions into the packed indices (global),
+ *                   offsets[vo[g]] == eo[g]
+ *   indices         int32[E], LOCAL vertex ids of the entry's own graph
+ *   weights         float32[E] or NULL
+ *   flags           as lpa_graph_create (LPA_BORROW is not accepted: indices
+ *                   are rewritten to global ids in the library's copy)
+ * Synchronises `stream`. */
+lpa_status lpa_batch_create(int32_t G, const int64_t *graph_vtx_off, const int64_t *graph_edge_off,
+                            const int64_t *offsets, const int32_t *indices, const float *weights,
+                            uint32_t flags, void *stream, lpa_batch_t *out);
+
+lpa_status lpa_batch_destroy(lpa_batch_t b);
+
+lpa_status lpa_batch_props_get(lpa_batch_t b, lpa_graph_props *out);
+
+/* Run every graph of the batch: labels_out is device int32[N] with LOCAL ids
+ * (graph g's labels lie in [0, n_g)); infos is host lpa_run_info[G] or NULL
+ * (non-NULL makes the call wait, as in lpa_run). */
+lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, float tolerance, int32_t max_iters,
+                         int32_t *labels_out, void *stream, lpa_run_info *infos);
+
+/* Modularity of graph g of the batch for LOCAL labels (device int32[n_g]). */
+lpa_status lpa_batch_modularity(lpa_batch_t b, int32_t g, const int32_t *labels, double *q_out,
+                                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LPA_H_ */

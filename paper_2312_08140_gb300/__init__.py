@@ -1,0 +1,326 @@
+"""GPU label propagation (GVE-LPA, arXiv 2312.08140) for GB300: Python binding.
+
+A thin ctypes layer over liblpa.so whose functions carry the names of the C ABI
+in include/lpa.h and only marshal arguments: every step of the computation runs
+in the library's CUDA kernels.  PyTorch provides device memory and streams.
+Importing works without a GPU; calling any lpa_* function needs the built
+library (``__graft_entry__.build()``) and raises if it is missing -- there is no
+CPU fallback.
+
+Pointer arguments accept a torch tensor (its data_ptr), a numpy array (host
+pointer), a raw integer address, or None.  Stream arguments accept None (torch's
+current stream when CUDA is available, else the legacy default stream), a
+torch.cuda.Stream, or a raw cudaStream_t integer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblpa.so")
+
+LPA_OK = 0
+LPA_ERR_INVALID_ARG = 1
+LPA_ERR_INVALID_GRAPH = 2
+LPA_ERR_OUT_OF_MEMORY = 3
+LPA_ERR_CUDA = 4
+LPA_ERR_TIMEOUT = 5
+LPA_ERR_BUSY = 6
+LPA_ERR_NOT_FOUND = 7
+LPA_ERR_NOT_READY = 8
+
+LPA_MODE_SYNC = 0
+LPA_MODE_ASYNC = 1
+LPA_MODE_SYNC_FULL = 2
+MODES = {"sync": LPA_MODE_SYNC, "async": LPA_MODE_ASYNC, "sync_full": LPA_MODE_SYNC_FULL}
+
+LPA_HOST_PTRS = 0
+LPA_DEVICE_PTRS = 1
+LPA_BORROW = 2
+
+LPA_MAX_RECORDED_ITERS = 64
+_H = LPA_MAX_RECORDED_ITERS
+
+
+class LpaRunInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("exit_reason", ctypes.c_int32),
+                ("changed", ctypes.c_int64 * _H), ("active", ctypes.c_int64 * _H),
+                ("scanned", ctypes.c_int64 * _H), ("edges_touched", ctypes.c_int64)]
+
+    def as_dict(self):
+        it = min(self.iterations, _H)
+        return {"iterations": self.iterations, "exit_reason": self.exit_reason,
+                "changed": list(self.changed[:it]), "active": list(self.active[:it]),
+                "scanned": list(self.scanned[:it]), "edges_touched": self.edges_touched}
+
+
+class LpaGraphProps(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("num_graphs", ctypes.c_int32),
+                ("weighted", ctypes.c_int32), ("exact", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class LpaConfig(ctypes.Structure):
+    _fields_ = [("small_max", ctypes.c_int32), ("warp_max", ctypes.c_int32),
+                ("hub_threads", ctypes.c_int32), ("hub_slots", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class LpaProfile(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32), ("init_ms", ctypes.c_float),
+                ("finish_ms", ctypes.c_float * _H), ("sweep_ms", (ctypes.c_float * 3) * _H),
+                ("bin_vertices", (ctypes.c_int64 * 3) * _H), ("bin_entries", (ctypes.c_int64 * 3) * _H),
+                ("bin_changed", (ctypes.c_int64 * 3) * _H)]
+
+    def as_dict(self):
+        it = min(self.iterations, _H)
+        return {"iterations": self.iterations, "init_ms": self.init_ms,
+                "finish_ms": list(self.finish_ms[:it]),
+                "sweep_ms": [list(self.sweep_ms[t]) for t in range(it)],
+                "bin_vertices": [list(self.bin_vertices[t]) for t in range(it)],
+                "bin_entries": [list(self.bin_entries[t]) for t in range(it)],
+                "bin_changed": [list(self.bin_changed[t]) for t in range(it)]}
+
+
+class LpaError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+_STATUS = {0: "ok", 1: "invalid argument", 2: "invalid graph", 3: "out of memory", 4: "CUDA error",
+           5: "timeout", 6: "busy", 7: "not found", 8: "not ready"}
+
+_lib = None
+_lock = threading.Lock()
+_V = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_U32 = ctypes.c_uint32
+_F = ctypes.c_float
+_P = ctypes.POINTER
+
+_SIGS = {
+    "lpa_version": ([], ctypes.c_char_p),
+    "lpa_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "lpa_last_error": ([], ctypes.c_char_p),
+    "lpa_graph_create": ([_I64, _I64, _V, _V, _V, _U32, _V, _P(_V)], ctypes.c_int),
+    "lpa_graph_destroy": ([_V], ctypes.c_int),
+    "lpa_graph_props_get": ([_V, _P(LpaGraphProps)], ctypes.c_int),
+    "lpa_graph_get_config": ([_V, _P(LpaConfig)], ctypes.c_int),
+    "lpa_graph_set_config": ([_V, _P(LpaConfig)], ctypes.c_int),
+    "lpa_run": ([_V, ctypes.c_int, _F, _I32, _V, _V, _P(LpaRunInfo)], ctypes.c_int),
+    "lpa_run_profiled": ([_V, ctypes.c_int, _F, _I32, _V, _V, _P(LpaRunInfo), _P(LpaProfile)], ctypes.c_int),
+    "lpa_modularity": ([_V, _V, _P(ctypes.c_double), _V], ctypes.c_int),
+    "lpa_autotune": ([_V, ctypes.c_int, _F, _I32, _I32, _V, _P(LpaConfig)], ctypes.c_int),
+    "lpa_batch_create": ([_I32, _V, _V, _V, _V, _V, _U32, _V, _P(_V)], ctypes.c_int),
+    "lpa_batch_destroy": ([_V], ctypes.c_int),
+    "lpa_batch_props_get": ([_V, _P(LpaGraphProps)], ctypes.c_int),
+    "lpa_batch_run": ([_V, ctypes.c_int, _F, _I32, _V, _V, _P(LpaRunInfo)], ctypes.c_int),
+    "lpa_batch_modularity": ([_V, _I32, _V, _P(ctypes.c_double), _V], ctypes.c_int),
+}
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects liblpa.so to export."""
+    return sorted(_SIGS)
+
+
+def load(path: str = LIB_PATH):
+    """Load liblpa.so (raises RuntimeError if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                                   "(there is no CPU fallback)")
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st):
+    if st != LPA_OK:
+        msg = load().lpa_last_error().decode()
+        raise LpaError(st, msg)
+
+
+def lpa_version() -> str:
+    return load().lpa_version().decode()
+
+
+def lpa_status_string(st: int) -> str:
+    return load().lpa_status_string(st).decode()
+
+
+def lpa_last_error() -> str:
+    return load().lpa_last_error().decode()
+
+
+def lpa_graph_create(n, nnz, offsets, indices, weights=None, flags=LPA_HOST_PTRS, stream=None):
+    h = _V()
+    _check(load().lpa_graph_create(n, nnz, _ptr(offsets), _ptr(indices), _ptr(weights), flags,
+                                   _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def lpa_graph_destroy(g):
+    _check(load().lpa_graph_destroy(g))
+
+
+def lpa_graph_props_get(g) -> dict:
+    p = LpaGraphProps()
+    _check(load().lpa_graph_props_get(g, ctypes.byref(p)))
+    return p.as_dict()
+
+
+def lpa_graph_get_config(g) -> LpaConfig:
+    c = LpaConfig()
+    _check(load().lpa_graph_get_config(g, ctypes.byref(c)))
+    return c
+
+
+def lpa_graph_set_config(g, cfg: LpaConfig):
+    _check(load().lpa_graph_set_config(g, ctypes.byref(cfg)))
+
+
+def _mode(m):
+    return MODES[m] if isinstance(m, str) else int(m)
+
+
+def lpa_run(g, mode, tolerance, max_iters, labels_out, stream=None, info=True):
+    """Returns an LpaRunInfo when info is True (the call then waits), else None."""
+    ri = LpaRunInfo() if info else None
+    _check(load().lpa_run(g, _mode(mode), tolerance, max_iters, _ptr(labels_out), _stream(stream),
+                          ctypes.byref(ri) if info else None))
+    return ri
+
+
+def lpa_run_profiled(g, mode, tolerance, max_iters, labels_out, stream=None):
+    ri, prof = LpaRunInfo(), LpaProfile()
+    _check(load().lpa_run_profiled(g, _mode(mode), tolerance, max_iters, _ptr(labels_out), _stream(stream),
+                                   ctypes.byref(ri), ctypes.byref(prof)))
+    return ri, prof
+
+
+def lpa_modularity(g, labels, stream=None) -> float:
+    q = ctypes.c_double()
+    _check(load().lpa_modularity(g, _ptr(labels), ctypes.byref(q), _stream(stream)))
+    return q.value
+
+
+def lpa_autotune(g, mode, tolerance, max_iters, trials=2, stream=None) -> LpaConfig:
+    c = LpaConfig()
+    _check(load().lpa_autotune(g, _mode(mode), tolerance, max_iters, trials, _stream(stream), ctypes.byref(c)))
+    return c
+
+
+def lpa_batch_create(G, graph_vtx_off, graph_edge_off, offsets, indices, weights=None, flags=LPA_HOST_PTRS,
+                     stream=None):
+    h = _V()
+    _check(load().lpa_batch_create(G, _ptr(graph_vtx_off), _ptr(graph_edge_off), _ptr(offsets), _ptr(indices),
+                                   _ptr(weights), flags, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def lpa_batch_destroy(b):
+    _check(load().lpa_batch_destroy(b))
+
+
+def lpa_batch_props_get(b) -> dict:
+    p = LpaGraphProps()
+    _check(load().lpa_batch_props_get(b, ctypes.byref(p)))
+    return p.as_dict()
+
+
+def lpa_batch_run(b, G, mode, tolerance, max_iters, labels_out, stream=None, info=True):
+    """Returns a list of G LpaRunInfo when info is True (the call then waits)."""
+    infos = (LpaRunInfo * G)() if info else None
+    _check(load().lpa_batch_run(b, _mode(mode), tolerance, max_iters, _ptr(labels_out), _stream(stream),
+                                infos))
+    return list(infos) if info else None
+
+
+def lpa_batch_modularity(b, g, labels, stream=None) -> float:
+    q = ctypes.c_double()
+    _check(load().lpa_batch_modularity(b, g, _ptr(labels), ctypes.byref(q), _stream(stream)))
+    return q.value
+
+
+class Graph:
+    """Owning wrapper: a graph handle built from host (numpy) or device (torch) CSR."""
+
+    def __init__(self, off, idx, w=None, stream=None):
+        n = int(off.shape[0]) - 1
+        nnz = int(idx.shape[0])
+        dev = hasattr(off, "is_cuda") and off.is_cuda
+        self.n, self.nnz = n, nnz
+        self.handle = lpa_graph_create(n, nnz, off, idx, w, LPA_DEVICE_PTRS if dev else LPA_HOST_PTRS, stream)
+
+    def run(self, mode="sync", tolerance=0.05, max_iters=20, labels_out=None, stream=None, info=True):
+        import torch
+        if labels_out is None:
+            labels_out = torch.empty(max(self.n, 1), dtype=torch.int32, device="cuda")
+        ri = lpa_run(self.handle, mode, tolerance, max_iters, labels_out, stream, info)
+        return labels_out[:self.n], (ri.as_dict() if ri is not None else None)
+
+    def modularity(self, labels, stream=None) -> float:
+        return lpa_modularity(self.handle, labels, stream)
+
+    def props(self) -> dict:
+        return lpa_graph_props_get(self.handle)
+
+    def close(self):
+        if self.handle:
+            lpa_graph_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,731 @@
+// lpa_api.cu -- the C ABI of include/lpa.h: handle lifetime, validation,
+// construction of the device-side loop (a CUDA graph whose WHILE node repeats
+// one sweep of Algorithm 1 until the device sets the condition to 0), runs,
+// modularity and the autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lpa.h"
+#include "lpa_internal.h"
+
+using namespace lpa;
+
+static_assert(LPA_MAX_RECORDED_ITERS == kMaxHist, "history depth mismatch");
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lpa_status fail(lpa_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+lpa_status cuda_fail(cudaError_t err, const char* where) {
+    if (err == cudaErrorMemoryAllocation)
+        return fail(LPA_ERR_OUT_OF_MEMORY, "%s: %s", where, cudaGetErrorString(err));
+    return fail(LPA_ERR_CUDA, "%s: %s", where, cudaGetErrorString(err));
+}
+
+#define LPA_CUDA(call)                                        \
+    do {                                                      \
+        cudaError_t err__ = (call);                           \
+        if (err__ != cudaSuccess) return cuda_fail(err__, #call); \
+    } while (0)
+
+int64_t pow2ceil(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+struct Engine {
+    int device = 0;
+    int sms = 1;
+    DevState s{};
+    std::vector<void*> owned;        // device allocations freed at destroy
+    int32_t* idx_owned = nullptr;
+    bool borrowed = false;
+    bool weighted = false;
+    bool exact = false;
+    int64_t max_degree = 0;
+    int64_t device_bytes = 0;
+    lpa_config cfg{8, 512, 512, 8192};
+    int hub_blocks = 0;
+    int32_t* spill_keys = nullptr;
+    void* spill_vals = nullptr;
+    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t cap_top = nullptr, cap_body = nullptr;
+    // modularity scratch
+    double* Sigma = nullptr;
+    ModAccum* acc = nullptr;
+    // host mirrors
+    std::vector<int64_t> vtx_off_host;
+    int64_t* labels_scratch_dummy = nullptr;
+};
+
+lpa_status dalloc(Engine& E, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t err = cudaMalloc(p, bytes);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc");
+    E.owned.push_back(*p);
+    E.device_bytes += (int64_t)bytes;
+    return LPA_OK;
+}
+
+template <typename T>
+lpa_status dalloc_t(Engine& E, T** p, size_t count) {
+    return dalloc(E, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void destroy_graphs(Engine& E) {
+    for (int m = 0; m < 3; ++m) {
+        if (E.exec[m]) cudaGraphExecDestroy(E.exec[m]);
+        if (E.graph[m]) cudaGraphDestroy(E.graph[m]);
+        E.exec[m] = nullptr;
+        E.graph[m] = nullptr;
+    }
+}
+
+void engine_free(Engine& E) {
+    destroy_graphs(E);
+    if (E.cap_top) cudaStreamDestroy(E.cap_top);
+    if (E.cap_body) cudaStreamDestroy(E.cap_body);
+    for (void* p : E.owned) cudaFree(p);
+    E.owned.clear();
+    if (E.spill_keys) cudaFree(E.spill_keys);
+    if (E.spill_vals) cudaFree(E.spill_vals);
+    E.spill_keys = nullptr;
+    E.spill_vals = nullptr;
+}
+
+// Hub spill tables: needed when a hub's row can hold more distinct labels than
+// half the shared table.  Sized for the maximum degree; the number of hub
+// blocks is capped so the tables stay within a fixed budget.
+lpa_status setup_hub(Engine& E) {
+    if (E.spill_keys) cudaFree(E.spill_keys);
+    if (E.spill_vals) cudaFree(E.spill_vals);
+    E.spill_keys = nullptr;
+    E.spill_vals = nullptr;
+    E.s.spill_keys = nullptr;
+    E.s.spill_vals = nullptr;
+    E.s.spill_slots = 0;
+    E.hub_blocks = hub_blocks_for(E.sms, E.cfg.hub_threads, E.cfg.hub_slots);
+    const int64_t need = pow2ceil(2 * std::max<int64_t>(E.max_degree, 1));
+    if (E.max_degree > E.cfg.warp_max && need > E.cfg.hub_slots) {
+        const int64_t budget = (int64_t)2 << 30;   // 2 GiB of spill tables at most
+        const int64_t per_block = need * 8;
+        int64_t blocks = std::min<int64_t>(E.hub_blocks, std::max<int64_t>(1, budget / per_block));
+        E.hub_blocks = (int)blocks;
+        cudaError_t err = cudaMalloc(&E.spill_keys, (size_t)(blocks * need * 4));
+        if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(spill keys)");
+        err = cudaMalloc(&E.spill_vals, (size_t)(blocks * need * 4));
+        if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(spill values)");
+        LPA_CUDA(cudaMemset(E.spill_keys, 0xff, (size_t)(blocks * need * 4)));
+        LPA_CUDA(cudaMemset(E.spill_vals, 0, (size_t)(blocks * need * 4)));
+        E.s.spill_keys = E.spill_keys;
+        E.s.spill_vals = E.spill_vals;
+        E.s.spill_slots = need;
+    }
+    return LPA_OK;
+}
+
+void apply_config_fields(Engine& E) {
+    E.s.small_max = E.cfg.small_max;
+    E.s.warp_max = E.cfg.warp_max;
+    E.s.warp_slots = (int32_t)pow2ceil(2 * (int64_t)E.cfg.warp_max);
+    E.s.hub_slots = E.cfg.hub_slots;
+}
+
+lpa_status check_config(const lpa_config& c) {
+    if (c.small_max < 1 || c.small_max > 8) return fail(LPA_ERR_INVALID_ARG, "small_max must be in [1, 8]");
+    if (c.warp_max <= c.small_max || c.warp_max > 1024)
+        return fail(LPA_ERR_INVALID_ARG, "warp_max must be in (small_max, 1024]");
+    if (c.hub_threads != 128 && c.hub_threads != 256 && c.hub_threads != 512 && c.hub_threads != 1024)
+        return fail(LPA_ERR_INVALID_ARG, "hub_threads must be 128, 256, 512 or 1024");
+    if (c.hub_slots < 1024 || c.hub_slots > 16384 || (c.hub_slots & (c.hub_slots - 1)))
+        return fail(LPA_ERR_INVALID_ARG, "hub_slots must be a power of two in [1024, 16384]");
+    return LPA_OK;
+}
+
+// Common creation path: G graphs (G == 1 for lpa_graph_create).
+lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const int64_t* edge_off_h, int64_t n,
+                         int64_t nnz, const int64_t* offsets, const int32_t* indices, const float* weights,
+                         uint32_t flags, cudaStream_t st) {
+    const bool dev = (flags & LPA_DEVICE_PTRS) != 0;
+    const bool borrow = (flags & LPA_BORROW) != 0;
+    if (flags & ~(LPA_DEVICE_PTRS | LPA_BORROW)) return fail(LPA_ERR_INVALID_ARG, "unknown flag bits");
+    if (borrow && !dev) return fail(LPA_ERR_INVALID_ARG, "LPA_BORROW needs LPA_DEVICE_PTRS");
+    if (borrow && G > 1) return fail(LPA_ERR_INVALID_ARG, "LPA_BORROW is not accepted for batches");
+    if (n < 0 || n > 0x7fffffffLL) return fail(LPA_ERR_INVALID_ARG, "n out of range [0, 2^31-1]");
+    if (nnz < 0) return fail(LPA_ERR_INVALID_ARG, "nnz < 0");
+    if (!offsets) return fail(LPA_ERR_INVALID_ARG, "offsets is NULL");
+    if (nnz > 0 && !indices) return fail(LPA_ERR_INVALID_ARG, "indices is NULL");
+
+    LPA_CUDA(cudaGetDevice(&E.device));
+    LPA_CUDA(cudaDeviceGetAttribute(&E.sms, cudaDevAttrMultiProcessorCount, E.device));
+    E.s.N = n;
+    E.s.E = nnz;
+    E.s.G = G;
+    E.weighted = weights != nullptr;
+    E.borrowed = borrow;
+    E.vtx_off_host.assign(vtx_off_h, vtx_off_h + G + 1);
+    const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    lpa_status rs;
+
+    // CSR
+    int64_t* off_d = nullptr;
+    int32_t* idx_d = nullptr;
+    float* w_d = nullptr;
+    if (borrow) {
+        off_d = const_cast<int64_t*>(offsets);
+        idx_d = const_cast<int32_t*>(indices);
+        w_d = const_cast<float*>(weights);
+    } else {
+        if ((rs = dalloc_t(E, &off_d, (size_t)n + 1)) != LPA_OK) return rs;
+        if ((rs = dalloc_t(E, &idx_d, (size_t)nnz)) != LPA_OK) return rs;
+        LPA_CUDA(cudaMemcpyAsync(off_d, offsets, ((size_t)n + 1) * 8, kind, st));
+        if (nnz) LPA_CUDA(cudaMemcpyAsync(idx_d, indices, (size_t)nnz * 4, kind, st));
+        if (weights) {
+            if ((rs = dalloc_t(E, &w_d, (size_t)nnz)) != LPA_OK) return rs;
+            if (nnz) LPA_CUDA(cudaMemcpyAsync(w_d, weights, (size_t)nnz * 4, kind, st));
+        }
+    }
+    int64_t* vo_d = nullptr;
+    int64_t* eo_d = nullptr;
+    if ((rs = dalloc_t(E, &vo_d, (size_t)G + 1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &eo_d, (size_t)G + 1)) != LPA_OK) return rs;
+    LPA_CUDA(cudaMemcpyAsync(vo_d, vtx_off_h, ((size_t)G + 1) * 8, cudaMemcpyHostToDevice, st));
+    LPA_CUDA(cudaMemcpyAsync(eo_d, edge_off_h, ((size_t)G + 1) * 8, cudaMemcpyHostToDevice, st));
+    int32_t* gid_d = nullptr;
+    if (G > 1) {
+        if ((rs = dalloc_t(E, &gid_d, (size_t)std::max<int64_t>(n, 1))) != LPA_OK) return rs;
+        LPA_CUDA(launch_fill_gid(vo_d, G, n, gid_d, st, E.sms));
+    }
+
+    // validation (and, for batches, local -> global index rewrite in our copy)
+    ValidateResult* vr_d = nullptr;
+    if ((rs = dalloc_t(E, &vr_d, 1)) != LPA_OK) return rs;
+    LPA_CUDA(cudaMemsetAsync(vr_d, 0, sizeof(ValidateResult), st));
+    if (n > 0)
+        LPA_CUDA(launch_validate(off_d, idx_d, w_d, n, nnz, vo_d, eo_d, gid_d, G, G > 1 ? 1 : 0, idx_d, vr_d, st,
+                                 E.sms));
+    ValidateResult vr{};
+    LPA_CUDA(cudaMemcpyAsync(&vr, vr_d, sizeof(vr), cudaMemcpyDeviceToHost, st));
+    LPA_CUDA(cudaStreamSynchronize(st));
+    if (n == 0 && nnz != 0) return fail(LPA_ERR_INVALID_GRAPH, "n == 0 but nnz != 0");
+    if (vr.bad_offsets) return fail(LPA_ERR_INVALID_GRAPH, "%u rows have invalid offsets", vr.bad_offsets);
+    if (vr.bad_index) return fail(LPA_ERR_INVALID_GRAPH, "%u indices out of range", vr.bad_index);
+    if (vr.bad_weight) return fail(LPA_ERR_INVALID_GRAPH, "%u weights negative or not finite", vr.bad_weight);
+    E.max_degree = (int64_t)vr.max_degree;
+
+    // weight representation: integer sums when every sum is an exact integer
+    if (!weights) {
+        E.exact = vr.huge_row == 0;
+        E.s.weight_kind = E.exact ? W_UNIT : W_F32;
+        if (!E.exact) return fail(LPA_ERR_INVALID_GRAPH, "a vertex has degree >= 2^31");
+    } else if (!borrow && vr.non_integer == 0 && vr.huge_row == 0) {
+        LPA_CUDA(launch_weights_to_u32(w_d, nnz, st, E.sms));
+        E.exact = true;
+        E.s.weight_kind = W_U32;
+    } else {
+        E.exact = vr.non_integer == 0 && vr.heavy_row == 0;
+        E.s.weight_kind = W_F32;
+    }
+    E.s.off = off_d;
+    E.s.idx = idx_d;
+    E.s.w = w_d;
+    E.s.gid = gid_d;
+    E.s.vtx_off = vo_d;
+
+    // working state
+    const size_t N1 = (size_t)std::max<int64_t>(n, 1);
+    if ((rs = dalloc_t(E, &E.s.C, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.Cnew, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.flags, N1 + 16)) != LPA_OK) return rs;
+    for (int b = 0; b < kBins; ++b)
+        if ((rs = dalloc_t(E, &E.s.list[b], N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.chg_list, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.ctrl, 1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.dN, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.done, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.iters, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.exit_reason, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.hist_changed, (size_t)G * kMaxHist)) != LPA_OK) return rs;
+    LPA_CUDA(cudaMemsetAsync(E.s.flags, 0, N1 + 16, st));
+    LPA_CUDA(cudaMemsetAsync(E.s.ctrl, 0, sizeof(Ctrl), st));
+    LPA_CUDA(cudaMemsetAsync(E.s.hist_changed, 0, (size_t)G * kMaxHist * 8, st));
+    apply_config_fields(E);
+    if ((rs = setup_hub(E)) != LPA_OK) return rs;
+    LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_top, cudaStreamNonBlocking));
+    LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_body, cudaStreamNonBlocking));
+    LPA_CUDA(cudaStreamSynchronize(st));
+    return LPA_OK;
+}
+
+// One sweep: the three bin kernels, then the finish kernel (apply, compact, control).
+cudaError_t enqueue_sweep(Engine& E, int mode, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) {
+    cudaError_t err = launch_sweep_small(E.s, mode, st, E.sms);
+    if (err != cudaSuccess) return err;
+    err = launch_sweep_warp(E.s, mode, st, E.sms);
+    if (err != cudaSuccess) return err;
+    err = launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st);
+    if (err != cudaSuccess) return err;
+    return launch_finish(E.s, 1, mode, h, in_graph, st, E.sms);
+}
+
+// Graph for one mode:  init -> init_cond -> first compaction -> WHILE { sweep } -> finalize
+lpa_status build_graph(Engine& E, int mode) {
+    if (E.exec[mode]) return LPA_OK;
+    cudaGraph_t top = nullptr;
+    LPA_CUDA(cudaGraphCreate(&top, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t err = cudaGraphConditionalHandleCreate(&h, top, 0, cudaGraphCondAssignDefault);
+    if (err != cudaSuccess) {
+        cudaGraphDestroy(top);
+        return cuda_fail(err, "cudaGraphConditionalHandleCreate");
+    }
+    auto bail = [&](cudaError_t e, const char* where) {
+        cudaStreamCaptureStatus cs;
+        if (cudaStreamIsCapturing(E.cap_top, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk;
+            cudaStreamEndCapture(E.cap_top, &junk);
+        }
+        if (cudaStreamIsCapturing(E.cap_body, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk;
+            cudaStreamEndCapture(E.cap_body, &junk);
+        }
+        cudaGraphDestroy(top);
+        cudaGetLastError();
+        return cuda_fail(e, where);
+    };
+    err = cudaStreamBeginCaptureToGraph(E.cap_top, top, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (err != cudaSuccess) return bail(err, "begin capture (top)");
+    if ((err = launch_init(E.s, E.cap_top, E.sms)) != cudaSuccess) return bail(err, "init");
+    if ((err = launch_init_cond(E.s, h, 1, E.cap_top)) != cudaSuccess) return bail(err, "init_cond");
+    if ((err = launch_finish(E.s, 0, mode, h, 0, E.cap_top, E.sms)) != cudaSuccess) return bail(err, "compact");
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraph_t capg = nullptr;
+    err = cudaStreamGetCaptureInfo(E.cap_top, &cst, nullptr, &capg, &deps, nullptr, &ndeps);
+    if (err != cudaSuccess) return bail(err, "capture info");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cond;
+    err = cudaGraphAddNode(&cond, capg, deps, nullptr, ndeps, &cp);
+    if (err != cudaSuccess) return bail(err, "add WHILE node");
+    err = cudaStreamUpdateCaptureDependencies(E.cap_top, &cond, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (err != cudaSuccess) return bail(err, "update capture deps");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    err = cudaStreamBeginCaptureToGraph(E.cap_body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (err != cudaSuccess) return bail(err, "begin capture (body)");
+    if ((err = enqueue_sweep(E, mode, h, 1, E.cap_body)) != cudaSuccess) return bail(err, "sweep");
+    cudaGraph_t body_out = nullptr;
+    err = cudaStreamEndCapture(E.cap_body, &body_out);
+    if (err != cudaSuccess) return bail(err, "end capture (body)");
+    if ((err = launch_finalize(E.s, E.cap_top, E.sms)) != cudaSuccess) return bail(err, "finalize");
+    cudaGraph_t top_out = nullptr;
+    err = cudaStreamEndCapture(E.cap_top, &top_out);
+    if (err != cudaSuccess) return bail(err, "end capture (top)");
+    cudaGraphExec_t ex = nullptr;
+    err = cudaGraphInstantiate(&ex, top, 0);
+    if (err != cudaSuccess) return bail(err, "instantiate");
+    E.graph[mode] = top;
+    E.exec[mode] = ex;
+    return LPA_OK;
+}
+
+lpa_status check_run_args(const Engine& E, int mode, float tol, int32_t max_iters, const int32_t* labels_out) {
+    if (mode < 0 || mode > 2) return fail(LPA_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (!(tol >= 0.f && tol <= 1.f)) return fail(LPA_ERR_INVALID_ARG, "tolerance must be in [0, 1]");
+    if (max_iters < 0 || max_iters > (1 << 20)) return fail(LPA_ERR_INVALID_ARG, "max_iters must be in [0, 2^20]");
+    if (E.s.N > 0 && !labels_out) return fail(LPA_ERR_INVALID_ARG, "labels_out is NULL");
+    return LPA_OK;
+}
+
+// Device results of the last run -> lpa_run_info per graph (host).
+lpa_status collect_info(Engine& E, cudaStream_t st, lpa_run_info* infos, int32_t count) {
+    std::vector<int32_t> iters(E.s.G), exits(E.s.G);
+    std::vector<long long> hist((size_t)E.s.G * kMaxHist);
+    Ctrl c;
+    LPA_CUDA(cudaMemcpyAsync(iters.data(), E.s.iters, (size_t)E.s.G * 4, cudaMemcpyDeviceToHost, st));
+    LPA_CUDA(cudaMemcpyAsync(exits.data(), E.s.exit_reason, (size_t)E.s.G * 4, cudaMemcpyDeviceToHost, st));
+    LPA_CUDA(cudaMemcpyAsync(hist.data(), E.s.hist_changed, hist.size() * 8, cudaMemcpyDeviceToHost, st));
+    LPA_CUDA(cudaMemcpyAsync(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    LPA_CUDA(cudaStreamSynchronize(st));
+    if (c.error) return fail(LPA_ERR_CUDA, "device-side check failed (code %d)", c.error);
+    for (int32_t g = 0; g < count; ++g) {
+        lpa_run_info& I = infos[g];
+        memset(&I, 0, sizeof(I));
+        I.iterations = iters[g];
+        I.exit_reason = exits[g];
+        const int rec = std::min(iters[g], kMaxHist);
+        for (int t = 0; t < rec; ++t) I.changed[t] = hist[(size_t)g * kMaxHist + t];
+        if (E.s.G == 1) {
+            for (int t = 0; t < rec; ++t) {
+                I.active[t] = c.hist_active[t];
+                I.scanned[t] = c.hist_scanned[t];
+                I.edges_touched += c.hist_scanned[t];
+            }
+        }
+    }
+    return LPA_OK;
+}
+
+lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t* labels_out, cudaStream_t st,
+                      lpa_run_info* infos, int local_ids) {
+    lpa_status rs = check_run_args(E, mode, tol, max_iters, labels_out);
+    if (rs != LPA_OK) return rs;
+    if (E.s.N == 0) {
+        for (int32_t g = 0; infos && g < E.s.G; ++g) {
+            memset(&infos[g], 0, sizeof(lpa_run_info));
+            infos[g].exit_reason = 2;
+        }
+        return LPA_OK;
+    }
+    if ((rs = build_graph(E, mode)) != LPA_OK) return rs;
+    LPA_CUDA(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, labels_out, local_ids, st));
+    LPA_CUDA(cudaGraphLaunch(E.exec[mode], st));
+    if (infos) return collect_info(E, st, infos, E.s.G);
+    return LPA_OK;
+}
+
+// Host-driven run with an event pair around every launch.
+lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters, int32_t* labels_out,
+                               cudaStream_t st, lpa_run_info* infos, lpa_profile* prof, int local_ids) {
+    lpa_status rs = check_run_args(E, mode, tol, max_iters, labels_out);
+    if (rs != LPA_OK) return rs;
+    if (!prof) return fail(LPA_ERR_INVALID_ARG, "prof is NULL");
+    memset(prof, 0, sizeof(*prof));
+    if (E.s.N == 0) return engine_run(E, mode, tol, max_iters, labels_out, st, infos, local_ids);
+    cudaEvent_t ev[6];
+    for (auto& e : ev) LPA_CUDA(cudaEventCreate(&e));
+    auto cleanup = [&]() {
+        for (auto& e : ev) cudaEventDestroy(e);
+    };
+    cudaGraphConditionalHandle none = 0;
+    cudaError_t err;
+    float ms = 0.f;
+#define LPA_P(call)                          \
+    do {                                     \
+        err = (call);                        \
+        if (err != cudaSuccess) {            \
+            cleanup();                       \
+            return cuda_fail(err, #call);    \
+        }                                    \
+    } while (0)
+    LPA_P(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, labels_out, local_ids, st));
+    LPA_P(cudaEventRecord(ev[0], st));
+    LPA_P(launch_init(E.s, st, E.sms));
+    LPA_P(launch_init_cond(E.s, none, 0, st));
+    LPA_P(launch_finish(E.s, 0, mode, none, 0, st, E.sms));
+    LPA_P(cudaEventRecord(ev[1], st));
+    LPA_P(cudaEventSynchronize(ev[1]));
+    LPA_P(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    prof->init_ms = ms;
+    Ctrl c;
+    LPA_P(cudaMemcpy(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+    int t = 0;
+    while (c.any_active) {
+        LPA_P(cudaEventRecord(ev[0], st));
+        LPA_P(launch_sweep_small(E.s, mode, st, E.sms));
+        LPA_P(cudaEventRecord(ev[1], st));
+        LPA_P(launch_sweep_warp(E.s, mode, st, E.sms));
+        LPA_P(cudaEventRecord(ev[2], st));
+        LPA_P(launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st));
+        LPA_P(cudaEventRecord(ev[3], st));
+        LPA_P(launch_finish(E.s, 1, mode, none, 0, st, E.sms));
+        LPA_P(cudaEventRecord(ev[4], st));
+        LPA_P(cudaEventSynchronize(ev[4]));
+        LPA_P(cudaMemcpy(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+        if (t < kMaxHist) {
+            for (int b = 0; b < kBins; ++b) {
+                LPA_P(cudaEventElapsedTime(&ms, ev[b], ev[b + 1]));
+                prof->sweep_ms[t][b] = ms;
+                prof->bin_vertices[t][b] = c.hist_bin_vertices[t][b];
+                prof->bin_entries[t][b] = c.hist_bin_entries[t][b];
+                prof->bin_changed[t][b] = c.hist_bin_changed[t][b];
+            }
+            LPA_P(cudaEventElapsedTime(&ms, ev[3], ev[4]));
+            prof->finish_ms[t] = ms;
+        }
+        ++t;
+        if (c.error) break;
+    }
+    prof->iterations = t;
+    LPA_P(launch_finalize(E.s, st, E.sms));
+    LPA_P(cudaStreamSynchronize(st));
+#undef LPA_P
+    cleanup();
+    if (infos) return collect_info(E, st, infos, E.s.G);
+    if (c.error) return fail(LPA_ERR_CUDA, "device-side check failed (code %d)", c.error);
+    return LPA_OK;
+}
+
+lpa_status engine_modularity(Engine& E, int64_t v0, int64_t v1, const int32_t* labels, double* q_out,
+                             cudaStream_t st) {
+    if (!q_out) return fail(LPA_ERR_INVALID_ARG, "q_out is NULL");
+    if (v1 > v0 && !labels) return fail(LPA_ERR_INVALID_ARG, "labels is NULL");
+    lpa_status rs;
+    if (!E.Sigma) {
+        if ((rs = dalloc_t(E, &E.Sigma, (size_t)std::max<int64_t>(E.s.N, 1))) != LPA_OK) return rs;
+        if ((rs = dalloc_t(E, &E.acc, 1)) != LPA_OK) return rs;
+    }
+    const int64_t n = v1 - v0;
+    if (n == 0) {
+        *q_out = 0.0;
+        return LPA_OK;
+    }
+    LPA_CUDA(cudaMemsetAsync(E.Sigma, 0, (size_t)n * 8, st));
+    LPA_CUDA(cudaMemsetAsync(E.acc, 0, sizeof(ModAccum), st));
+    LPA_CUDA(launch_modularity(E.s, v0, v1, labels, E.Sigma, E.acc, st, E.sms));
+    ModAccum a;
+    LPA_CUDA(cudaMemcpyAsync(&a, E.acc, sizeof(a), cudaMemcpyDeviceToHost, st));
+    LPA_CUDA(cudaStreamSynchronize(st));
+    if (a.bad_label) return fail(LPA_ERR_INVALID_ARG, "%u labels outside [0, n)", a.bad_label);
+    *q_out = a.two_m > 0.0 ? a.sigma / a.two_m - a.null_sum / (a.two_m * a.two_m) : 0.0;
+    return LPA_OK;
+}
+
+void fill_props(const Engine& E, lpa_graph_props* p) {
+    memset(p, 0, sizeof(*p));
+    p->n = E.s.N;
+    p->nnz = E.s.E;
+    p->num_graphs = E.s.G;
+    p->weighted = E.weighted ? 1 : 0;
+    p->exact = E.exact ? 1 : 0;
+    p->max_degree = E.max_degree;
+    p->device_bytes = E.device_bytes + (E.spill_keys ? E.hub_blocks * E.s.spill_slots * 8 : 0);
+}
+
+}  // namespace
+
+struct lpa_graph {
+    Engine e;
+};
+struct lpa_batch {
+    Engine e;
+};
+
+extern "C" {
+
+const char* lpa_version(void) { return "lpa-gb300 0.1"; }
+
+const char* lpa_status_string(lpa_status st) {
+    switch (st) {
+        case LPA_OK: return "ok";
+        case LPA_ERR_INVALID_ARG: return "invalid argument";
+        case LPA_ERR_INVALID_GRAPH: return "invalid graph";
+        case LPA_ERR_OUT_OF_MEMORY: return "out of memory";
+        case LPA_ERR_CUDA: return "CUDA error";
+        case LPA_ERR_TIMEOUT: return "timeout";
+        case LPA_ERR_BUSY: return "busy";
+        case LPA_ERR_NOT_FOUND: return "not found";
+        case LPA_ERR_NOT_READY: return "not ready";
+    }
+    return "unknown status";
+}
+
+const char* lpa_last_error(void) { return g_last_error.c_str(); }
+
+lpa_status lpa_graph_create(int64_t n, int64_t nnz, const int64_t* offsets, const int32_t* indices,
+                            const float* weights, uint32_t flags, void* stream, lpa_graph_t* out) {
+    g_last_error.clear();
+    if (!out) return fail(LPA_ERR_INVALID_ARG, "out is NULL");
+    lpa_graph* g = new (std::nothrow) lpa_graph();
+    if (!g) return fail(LPA_ERR_OUT_OF_MEMORY, "host allocation");
+    const int64_t vo[2] = {0, n};
+    const int64_t eo[2] = {0, nnz};
+    lpa_status rs = engine_create(g->e, 1, vo, eo, n, nnz, offsets, indices, weights, flags,
+                                  static_cast<cudaStream_t>(stream));
+    if (rs != LPA_OK) {
+        engine_free(g->e);
+        delete g;
+        return rs;
+    }
+    *out = g;
+    return LPA_OK;
+}
+
+lpa_status lpa_graph_destroy(lpa_graph_t g) {
+    if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
+    engine_free(g->e);
+    delete g;
+    return LPA_OK;
+}
+
+lpa_status lpa_graph_props_get(lpa_graph_t g, lpa_graph_props* out) {
+    if (!g || !out) return fail(LPA_ERR_INVALID_ARG, "NULL argument");
+    fill_props(g->e, out);
+    return LPA_OK;
+}
+
+lpa_status lpa_graph_get_config(lpa_graph_t g, lpa_config* out) {
+    if (!g || !out) return fail(LPA_ERR_INVALID_ARG, "NULL argument");
+    *out = g->e.cfg;
+    return LPA_OK;
+}
+
+static lpa_status set_config(Engine& E, const lpa_config* cfg) {
+    if (!cfg) return fail(LPA_ERR_INVALID_ARG, "cfg is NULL");
+    lpa_status rs = check_config(*cfg);
+    if (rs != LPA_OK) return rs;
+    LPA_CUDA(cudaDeviceSynchronize());
+    destroy_graphs(E);
+    E.cfg = *cfg;
+    apply_config_fields(E);
+    return setup_hub(E);
+}
+
+lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config* cfg) {
+    if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
+    return set_config(g->e, cfg);
+}
+
+lpa_status lpa_run(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters, int32_t* labels_out,
+                   void* stream, lpa_run_info* info) {
+    if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
+    return engine_run(g->e, (int)mode, tolerance, max_iters, labels_out, static_cast<cudaStream_t>(stream), info, 0);
+}
+
+lpa_status lpa_run_profiled(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters, int32_t* labels_out,
+                            void* stream, lpa_run_info* info, lpa_profile* prof) {
+    if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
+    return engine_run_profiled(g->e, (int)mode, tolerance, max_iters, labels_out, static_cast<cudaStream_t>(stream),
+                               info, prof, 0);
+}
+
+lpa_status lpa_modularity(lpa_graph_t g, const int32_t* labels, double* q_out, void* stream) {
+    if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
+    return engine_modularity(g->e, 0, g->e.s.N, labels, q_out, static_cast<cudaStream_t>(stream));
+}
+
+lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters, int32_t trials,
+                        void* stream, lpa_config* chosen) {
+    if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
+    if (trials < 1 || trials > 100) return fail(LPA_ERR_INVALID_ARG, "trials must be in [1, 100]");
+    Engine& E = g->e;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (E.s.N == 0) {
+        if (chosen) *chosen = E.cfg;
+        return LPA_OK;
+    }
+    int32_t* out = nullptr;
+    LPA_CUDA(cudaMalloc(&out, (size_t)E.s.N * 4));
+    std::vector<lpa_config> cands;
+    const int smalls[] = {4, 6, 8};
+    const int warps[] = {128, 256, 512, 1024};
+    const int hubs[][2] = {{256, 4096}, {512, 8192}, {1024, 16384}};
+    for (int sm : smalls)
+        for (int wm : warps)
+            for (auto& hb : hubs) cands.push_back(lpa_config{sm, wm, hb[0], hb[1]});
+    cudaEvent_t e0, e1;
+    LPA_CUDA(cudaEventCreate(&e0));
+    LPA_CUDA(cudaEventCreate(&e1));
+    const lpa_config orig = E.cfg;
+    lpa_config best = orig;
+    float best_ms = 1e30f;
+    lpa_status rs = LPA_OK;
+    for (const lpa_config& c : cands) {
+        if ((rs = set_config(E, &c)) != LPA_OK) break;
+        float tmin = 1e30f;
+        for (int r = 0; r <= trials; ++r) {   // first run warms up and builds the graph
+            cudaEventRecord(e0, st);
+            rs = engine_run(E, (int)mode, tolerance, max_iters, out, st, nullptr, 0);
+            if (rs != LPA_OK) break;
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0) tmin = std::min(tmin, ms);
+        }
+        if (rs != LPA_OK) break;
+        if (tmin < best_ms) {
+            best_ms = tmin;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (rs != LPA_OK) {
+        set_config(E, &orig);
+        return rs;
+    }
+    if ((rs = set_config(E, &best)) != LPA_OK) return rs;
+    if (chosen) *chosen = best;
+    return LPA_OK;
+}
+
+// ------------------------------------------------------------------ batches
+lpa_status lpa_batch_create(int32_t G, const int64_t* graph_vtx_off, const int64_t* graph_edge_off,
+                            const int64_t* offsets, const int32_t* indices, const float* weights, uint32_t flags,
+                            void* stream, lpa_batch_t* out) {
+    g_last_error.clear();
+    if (!out) return fail(LPA_ERR_INVALID_ARG, "out is NULL");
+    if (G < 1) return fail(LPA_ERR_INVALID_ARG, "G must be >= 1");
+    if (!graph_vtx_off || !graph_edge_off) return fail(LPA_ERR_INVALID_ARG, "graph offsets are NULL");
+    if (graph_vtx_off[0] != 0 || graph_edge_off[0] != 0)
+        return fail(LPA_ERR_INVALID_ARG, "graph offsets must start at 0");
+    for (int32_t g = 0; g < G; ++g)
+        if (graph_vtx_off[g + 1] < graph_vtx_off[g] || graph_edge_off[g + 1] < graph_edge_off[g])
+            return fail(LPA_ERR_INVALID_ARG, "graph offsets must be non-decreasing");
+    if (flags & LPA_BORROW) return fail(LPA_ERR_INVALID_ARG, "LPA_BORROW is not accepted for batches");
+    lpa_batch* b = new (std::nothrow) lpa_batch();
+    if (!b) return fail(LPA_ERR_OUT_OF_MEMORY, "host allocation");
+    lpa_status rs = engine_create(b->e, G, graph_vtx_off, graph_edge_off, graph_vtx_off[G], graph_edge_off[G],
+                                  offsets, indices, weights, flags, static_cast<cudaStream_t>(stream));
+    if (rs != LPA_OK) {
+        engine_free(b->e);
+        delete b;
+        return rs;
+    }
+    *out = b;
+    return LPA_OK;
+}
+
+lpa_status lpa_batch_destroy(lpa_batch_t b) {
+    if (!b) return fail(LPA_ERR_INVALID_ARG, "batch is NULL");
+    engine_free(b->e);
+    delete b;
+    return LPA_OK;
+}
+
+lpa_status lpa_batch_props_get(lpa_batch_t b, lpa_graph_props* out) {
+    if (!b || !out) return fail(LPA_ERR_INVALID_ARG, "NULL argument");
+    fill_props(b->e, out);
+    return LPA_OK;
+}
+
+lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, float tolerance, int32_t max_iters, int32_t* labels_out,
+                         void* stream, lpa_run_info* infos) {
+    if (!b) return fail(LPA_ERR_INVALID_ARG, "batch is NULL");
+    return engine_run(b->e, (int)mode, tolerance, max_iters, labels_out, static_cast<cudaStream_t>(stream), infos,
+                      1);
+}
+
+lpa_status lpa_batch_modularity(lpa_batch_t b, int32_t g, const int32_t* labels, double* q_out, void* stream) {
+    if (!b) return fail(LPA_ERR_INVALID_ARG, "batch is NULL");
+    if (g < 0 || g >= b->e.s.G) return fail(LPA_ERR_INVALID_ARG, "graph index out of range");
+    return engine_modularity(b->e, b->e.vtx_off_host[g], b->e.vtx_off_host[g + 1], labels, q_out,
+                             static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

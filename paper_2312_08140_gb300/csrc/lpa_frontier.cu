@@ -1,0 +1,486 @@
+// lpa_frontier.cu -- everything around the sweep kernels:
+//   k_set_params   run parameters into the control block
+//   k_init         C <- [0..N), every vertex with an entry marked unprocessed
+//                  (Algorithm 1, lpa(): initialisation)
+//   k_finish       after a sweep: apply sync-mode changes, compact the flags
+//                  of unprocessed vertices into per-degree-bin frontier lists,
+//                  and, in the last block, the per-graph convergence test
+//                  dN/N <= tau or the sweep cap (Algorithm 1; Sections 4.1.2,
+//                  4.1.3), which also sets the device-side loop condition
+//   k_finalize     labels out (optionally as graph-local ids)
+//   k_validate     CSR checks at graph creation, weight exactness
+//   k_mod_*        modularity, Eq. 1 (Section 3.2), in fp64
+#include "lpa_device.cuh"
+
+namespace lpa {
+
+constexpr int kFrontThreads = 256;
+constexpr int kVertsPerThread = 16;
+
+__global__ void k_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int32_t* labels_out,
+                             int local_ids) {
+    ctrl->tau = tau;
+    ctrl->max_iters = max_iters;
+    ctrl->mode = mode;
+    ctrl->labels_out = labels_out;
+    ctrl->local_ids = local_ids;
+}
+
+cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int32_t* labels_out,
+                              int local_ids, cudaStream_t st) {
+    k_set_params<<<1, 1, 0, st>>>(ctrl, tau, max_iters, mode, labels_out, local_ids);
+    return cudaGetLastError();
+}
+
+__global__ void k_init(DevState s) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = tid; i < s.N; i += stride) {
+        s.C[i] = (int32_t)i;
+        s.flags[i] = (s.off[i + 1] > s.off[i]) ? 1 : 0;
+    }
+    Ctrl* c = s.ctrl;
+    const int max_iters = c->max_iters;
+    for (int64_t g = tid; g < s.G; g += stride) {
+        const int64_t ng = s.vtx_off[g + 1] - s.vtx_off[g];
+        const bool nothing = ng == 0 || max_iters == 0;
+        s.dN[g] = 0;
+        s.done[g] = nothing ? 1 : 0;
+        s.iters[g] = 0;
+        s.exit_reason[g] = nothing ? 2 : 0;
+    }
+    for (int64_t q = tid; q < kMaxHist; q += stride) {
+        c->hist_active[q] = 0;
+        c->hist_scanned[q] = 0;
+        c->hist_changed_entries[q] = 0;
+        for (int b = 0; b < kBins; ++b) {
+            c->hist_bin_vertices[q][b] = 0;
+            c->hist_bin_entries[q][b] = 0;
+            c->hist_bin_changed[q][b] = 0;
+        }
+    }
+    if (tid == 0) {
+        c->iter = 0;
+        c->error = 0;
+        c->ticket = 0;
+        c->chg_cnt = 0;
+        for (int b = 0; b < kBins; ++b) {
+            c->bin_cnt[0][b] = c->bin_cnt[1][b] = 0;
+            c->bin_entries[0][b] = c->bin_entries[1][b] = 0;
+            c->bin_changed[b] = 0;
+            c->bin_changed_entries[b] = 0;
+        }
+    }
+}
+
+// Separate 1-thread kernel: the only writer of the loop condition before the
+// loop starts (concurrent writers of a conditional handle are not allowed).
+__global__ void k_init_cond(DevState s, cudaGraphConditionalHandle h, int in_graph) {
+    const bool run = s.ctrl->max_iters > 0 && s.N > 0;
+    s.ctrl->any_active = run ? 1 : 0;
+    if (in_graph) cudaGraphSetConditional(h, run ? 1u : 0u);
+}
+
+cudaError_t launch_init(const DevState& s, cudaStream_t st, int sms) {
+    k_init<<<sms * 4, kFrontThreads, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) {
+    k_init_cond<<<1, 1, 0, st>>>(s, h, in_graph);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ int bin_of(int64_t d, int small_max, int warp_max) {
+    return d <= small_max ? 0 : (d <= warp_max ? 1 : 2);
+}
+
+// Warp-aggregated append of up to kVertsPerThread vertices per lane into the
+// three bin lists of buffer `nb`.  All 32 lanes must call.
+__device__ __forceinline__ void append_bins(const DevState& s, int nb, const int32_t (&vid)[kVertsPerThread],
+                                            const int8_t (&bin)[kVertsPerThread],
+                                            const int64_t (&deg)[kVertsPerThread]) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) {
+        unsigned cnt = 0;
+        unsigned long long ent = 0;
+#pragma unroll
+        for (int q = 0; q < kVertsPerThread; ++q) {
+            if (bin[q] == b) {
+                ++cnt;
+                ent += (unsigned long long)deg[q];
+            }
+        }
+        unsigned incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned y = __shfl_up_sync(kFull, incl, o);
+            if ((int)lane >= o) incl += y;
+        }
+        const unsigned total = __shfl_sync(kFull, incl, 31);
+        if (total == 0) continue;
+        unsigned long long ent_sum = ent;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ent_sum += __shfl_xor_sync(kFull, ent_sum, o);
+        unsigned base = 0;
+        if (lane == 31) {
+            base = atomicAdd(&s.ctrl->bin_cnt[nb][b], total);
+            atomicAdd(&s.ctrl->bin_entries[nb][b], ent_sum);
+        }
+        base = __shfl_sync(kFull, base, 31) + incl - cnt;
+        int32_t* list = s.list[b];
+#pragma unroll
+        for (int q = 0; q < kVertsPerThread; ++q) {
+            if (bin[q] == b) list[base++] = vid[q];
+        }
+    }
+}
+
+// Control step run by the last block of k_finish after sweep t = ctrl->iter.
+__device__ void control_step(const DevState& s, int mode, cudaGraphConditionalHandle h, int in_graph) {
+    Ctrl* c = s.ctrl;
+    volatile Ctrl* vc = c;
+    const int t = vc->iter;
+    const int cur = t & 1, nb = (t + 1) & 1;
+    const double tau = vc->tau;
+    const int max_iters = vc->max_iters;
+    unsigned long long changed_total = 0;
+    for (int b = 0; b < kBins; ++b) changed_total += vc->bin_changed[b];
+    int any = 0;
+    for (int64_t g = threadIdx.x; g < s.G; g += blockDim.x) {
+        if (!s.done[g]) {
+            const unsigned long long dn = (s.G == 1) ? changed_total : ((volatile unsigned long long*)s.dN)[g];
+            if (t < kMaxHist) s.hist_changed[g * kMaxHist + t] = (long long)dn;
+            s.iters[g] = t + 1;
+            const int64_t ng = s.vtx_off[g + 1] - s.vtx_off[g];
+            if ((double)dn / (double)ng <= tau) {
+                s.done[g] = 1;
+                s.exit_reason[g] = 0;
+            } else if (t + 1 >= max_iters) {
+                s.done[g] = 1;
+                s.exit_reason[g] = 1;
+            }
+            s.dN[g] = 0;
+        }
+        any |= !s.done[g];
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) {
+        if (t < kMaxHist) {
+            long long act = 0, scn = 0, che = 0;
+            for (int b = 0; b < kBins; ++b) {
+                c->hist_bin_vertices[t][b] = vc->bin_cnt[cur][b];
+                c->hist_bin_entries[t][b] = (long long)vc->bin_entries[cur][b];
+                c->hist_bin_changed[t][b] = (long long)vc->bin_changed[b];
+                act += vc->bin_cnt[cur][b];
+                scn += (long long)vc->bin_entries[cur][b];
+                che += (long long)vc->bin_changed_entries[b];
+            }
+            c->hist_active[t] = act;
+            c->hist_scanned[t] = scn;
+            c->hist_changed_entries[t] = che;
+        }
+        for (int b = 0; b < kBins; ++b) {
+            c->bin_changed[b] = 0;
+            c->bin_changed_entries[b] = 0;
+            if (mode == MODE_SYNC_FULL) {
+                c->bin_cnt[nb][b] = vc->bin_cnt[cur][b];
+                c->bin_entries[nb][b] = vc->bin_entries[cur][b];
+            } else {
+                c->bin_cnt[cur][b] = 0;
+                c->bin_entries[cur][b] = 0;
+            }
+        }
+        c->chg_cnt = 0;
+        c->iter = t + 1;
+        c->any_active = any;
+        c->ticket = 0;
+        __threadfence();
+        if (in_graph) cudaGraphSetConditional(h, any ? 1u : 0u);
+    }
+}
+
+// phase 0: first compaction (after k_init), no control.
+// phase 1: after sweep t: apply (sync modes), compact into buffer (t+1)&1, control.
+__global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int phase, int mode,
+                                                           cudaGraphConditionalHandle h, int in_graph) {
+    const int t = s.ctrl->iter;
+    const int nb = phase == 0 ? 0 : ((t + 1) & 1);
+    const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned gstride = gridDim.x * blockDim.x;
+
+    if (phase == 1 && mode != MODE_ASYNC) {
+        const unsigned nchg = s.ctrl->chg_cnt;
+        for (unsigned k = gtid; k < nchg; k += gstride) {
+            const int32_t v = s.chg_list[k];
+            s.C[v] = s.Cnew[v];
+        }
+    }
+
+    if (phase == 0 || mode != MODE_SYNC_FULL) {
+        const int64_t nchunks = (s.N + kVertsPerThread - 1) / kVertsPerThread;
+        for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nchunks; base += gstride) {
+            const int64_t ch = base + threadIdx.x;
+            const int64_t v0 = ch * kVertsPerThread;
+            uint8_t f[kVertsPerThread];
+            bool anyf = false;
+            if (ch < nchunks) {
+                if (v0 + kVertsPerThread <= s.N) {
+                    uint4 raw = *reinterpret_cast<const uint4*>(s.flags + v0);
+                    const uint8_t* pb = reinterpret_cast<const uint8_t*>(&raw);
+#pragma unroll
+                    for (int q = 0; q < kVertsPerThread; ++q) f[q] = pb[q];
+                    anyf = (raw.x | raw.y | raw.z | raw.w) != 0;
+                    if (anyf) *reinterpret_cast<uint4*>(s.flags + v0) = make_uint4(0, 0, 0, 0);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kVertsPerThread; ++q) {
+                        f[q] = (v0 + q < s.N) ? s.flags[v0 + q] : 0;
+                        anyf |= f[q] != 0;
+                    }
+                    if (anyf) {
+                        for (int q = 0; q < kVertsPerThread; ++q)
+                            if (v0 + q < s.N) s.flags[v0 + q] = 0;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kVertsPerThread; ++q) f[q] = 0;
+            }
+            int32_t vid[kVertsPerThread];
+            int8_t bin[kVertsPerThread];
+            int64_t deg[kVertsPerThread];
+#pragma unroll
+            for (int q = 0; q < kVertsPerThread; ++q) {
+                vid[q] = (int32_t)(v0 + q);
+                bin[q] = -1;
+                deg[q] = 0;
+                if (f[q]) {
+                    const int64_t d = s.off[v0 + q + 1] - s.off[v0 + q];
+                    deg[q] = d;
+                    bin[q] = (int8_t)bin_of(d, s.small_max, s.warp_max);
+                }
+            }
+            if (__any_sync(kFull, anyf)) append_bins(s, nb, vid, bin, deg);
+        }
+    }
+
+    // last block runs the control step
+    __shared__ bool is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned tk = atomicAdd(&s.ctrl->ticket, 1u);
+        is_last = tk == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (phase == 1) {
+        control_step(s, mode, h, in_graph);
+    } else if (threadIdx.x == 0) {
+        s.ctrl->ticket = 0;
+    }
+}
+
+cudaError_t launch_finish(const DevState& s, int phase, int mode, cudaGraphConditionalHandle h, int in_graph,
+                          cudaStream_t st, int sms) {
+    k_finish<<<sms * 4, kFrontThreads, 0, st>>>(s, phase, mode, h, in_graph);
+    return cudaGetLastError();
+}
+
+__global__ void k_finalize(DevState s) {
+    int32_t* out = s.ctrl->labels_out;
+    const int local = s.ctrl->local_ids;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.N; i += stride) {
+        int32_t c = s.C[i];
+        if (local && s.G > 1) c -= (int32_t)s.vtx_off[s.gid[i]];
+        out[i] = c;
+    }
+}
+
+cudaError_t launch_finalize(const DevState& s, cudaStream_t st, int sms) {
+    k_finalize<<<sms * 4, kFrontThreads, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ validation --
+// One warp per row.  For a batch (G > 1) indices are graph-local on input and
+// are rewritten to global ids in idx_rw (the library's own copy).
+__global__ void k_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N, int64_t E,
+                           const int64_t* vtx_off, const int64_t* edge_off, const int32_t* gid, int32_t G,
+                           int rewrite, int32_t* idx_rw, ValidateResult* res) {
+    const unsigned lane = lane_id();
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < N; v += nwarps) {
+        const int64_t st = off[v], en = off[v + 1];
+        const int32_t g = G > 1 ? gid[v] : 0;
+        const int64_t lo = G > 1 ? vtx_off[g] : 0;
+        const int64_t hi = G > 1 ? vtx_off[g + 1] : N;
+        bool bad = st < 0 || en < st || en > E || (v == 0 && st != 0) || (v == N - 1 && en != E);
+        if (G > 1 && v == lo && st != edge_off[g]) bad = true;
+        if (G > 1 && v == hi - 1 && en != edge_off[g + 1]) bad = true;
+        if (bad) {
+            if (lane == 0) atomicAdd(&res->bad_offsets, 1u);
+            continue;
+        }
+        const int64_t n_local = hi - lo;
+        unsigned bad_i = 0, bad_w = 0, non_int = 0;
+        double rowsum = 0.0;
+        for (int64_t e = st + lane; e < en; e += 32) {
+            int64_t j = idx[e];
+            if (rewrite) {
+                if (j < 0 || j >= n_local) ++bad_i;
+                else idx_rw[e] = (int32_t)(j + lo);
+            } else if (j < 0 || j >= N) {
+                ++bad_i;
+            }
+            if (w) {
+                const float x = w[e];
+                if (!isfinite(x) || x < 0.f) ++bad_w;
+                else {
+                    if (x != truncf(x)) ++non_int;
+                    rowsum += (double)x;
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            bad_i += __shfl_xor_sync(kFull, bad_i, o);
+            bad_w += __shfl_xor_sync(kFull, bad_w, o);
+            non_int += __shfl_xor_sync(kFull, non_int, o);
+            rowsum += __shfl_xor_sync(kFull, rowsum, o);
+        }
+        if (lane == 0) {
+            if (bad_i) atomicAdd(&res->bad_index, bad_i);
+            if (bad_w) atomicAdd(&res->bad_weight, bad_w);
+            if (non_int) atomicAdd(&res->non_integer, non_int);
+            const double deg_w = w ? rowsum : (double)(en - st);
+            if (deg_w >= 16777216.0) atomicAdd(&res->heavy_row, 1u);
+            if (deg_w >= 2147483648.0) atomicAdd(&res->huge_row, 1u);
+            atomicMax(&res->max_degree, (unsigned long long)(en - st));
+        }
+    }
+}
+
+cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N, int64_t E,
+                            const int64_t* vtx_off, const int64_t* edge_off, const int32_t* gid, int32_t G,
+                            int rewrite_local_ids, int32_t* idx_rw, ValidateResult* res, cudaStream_t st,
+                            int sms) {
+    k_validate<<<sms * 8, 256, 0, st>>>(off, idx, w, N, E, vtx_off, edge_off, gid, G, rewrite_local_ids,
+                                        idx_rw, res);
+    return cudaGetLastError();
+}
+
+__global__ void k_fill_gid(const int64_t* vtx_off, int32_t G, int64_t N, int32_t* gid) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += stride) {
+        int32_t lo = 0, hi = G;   // find g with vtx_off[g] <= v < vtx_off[g+1]
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (vtx_off[mid] <= v) lo = mid;
+            else hi = mid;
+        }
+        gid[v] = lo;
+    }
+}
+
+cudaError_t launch_fill_gid(const int64_t* vtx_off, int32_t G, int64_t N, int32_t* gid, cudaStream_t st, int sms) {
+    k_fill_gid<<<sms * 4, 256, 0, st>>>(vtx_off, G, N, gid);
+    return cudaGetLastError();
+}
+
+__global__ void k_weights_to_u32(float* w, int64_t E) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t* u = reinterpret_cast<uint32_t*>(w);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride)
+        u[e] = (uint32_t)w[e];
+}
+
+cudaError_t launch_weights_to_u32(float* w, int64_t E, cudaStream_t st, int sms) {
+    k_weights_to_u32<<<sms * 8, 256, 0, st>>>(w, E);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ modularity --
+__device__ __forceinline__ double weight_f64(const DevState& s, int64_t e) {
+    if (s.weight_kind == W_UNIT) return 1.0;
+    if (s.weight_kind == W_U32) return (double)static_cast<const uint32_t*>(s.w)[e];
+    return (double)static_cast<const float*>(s.w)[e];
+}
+
+// One warp per vertex i of [v0, v1): K_i, and the weight of entries whose two
+// ends share a label (sigma); Sigma_c += K_i.
+__global__ void k_mod_rows(DevState s, int64_t v0, int64_t v1, const int32_t* labels, double* Sigma,
+                           ModAccum* acc) {
+    __shared__ double sh_two_m, sh_sigma;
+    if (threadIdx.x == 0) {
+        sh_two_m = 0.0;
+        sh_sigma = 0.0;
+    }
+    __syncthreads();
+    const unsigned lane = lane_id();
+    const int64_t nloc = v1 - v0;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double my_two_m = 0.0, my_sigma = 0.0;
+    for (int64_t i = warp; i < nloc; i += nwarps) {
+        const int32_t ci = labels[i];
+        if (ci < 0 || ci >= nloc) {
+            if (lane == 0) atomicAdd(&acc->bad_label, 1u);
+            continue;
+        }
+        double K = 0.0, sg = 0.0;
+        const int64_t st = s.off[v0 + i], en = s.off[v0 + i + 1];
+        for (int64_t e = st + lane; e < en; e += 32) {
+            const double w = weight_f64(s, e);
+            K += w;
+            const int64_t j = (int64_t)s.idx[e] - v0;
+            if (j >= 0 && j < nloc && labels[j] == ci) sg += w;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            K += __shfl_xor_sync(kFull, K, o);
+            sg += __shfl_xor_sync(kFull, sg, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&Sigma[ci], K);
+            my_two_m += K;
+            my_sigma += sg;
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&sh_two_m, my_two_m);
+        atomicAdd(&sh_sigma, my_sigma);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        atomicAdd(&acc->two_m, sh_two_m);
+        atomicAdd(&acc->sigma, sh_sigma);
+    }
+}
+
+__global__ void k_mod_null(const double* Sigma, int64_t n, ModAccum* acc) {
+    __shared__ double sh;
+    if (threadIdx.x == 0) sh = 0.0;
+    __syncthreads();
+    double local = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += stride) local += Sigma[c] * Sigma[c];
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(kFull, local, o);
+    if (lane_id() == 0) atomicAdd(&sh, local);
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(&acc->null_sum, sh);
+}
+
+cudaError_t launch_modularity(const DevState& s, int64_t v0, int64_t v1, const int32_t* labels, double* Sigma,
+                              ModAccum* acc, cudaStream_t st, int sms) {
+    k_mod_rows<<<sms * 8, 256, 0, st>>>(s, v0, v1, labels, Sigma, acc);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_mod_null<<<sms * 4, 256, 0, st>>>(Sigma, v1 - v0, acc);
+    return cudaGetLastError();
+}
+
+}  // namespace lpa

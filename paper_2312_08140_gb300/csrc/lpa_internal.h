@@ -1,0 +1,131 @@
+// lpa_internal.h -- layout of the device-resident state of one label
+// propagation engine and the launchers the host code calls.  Shared by the
+// kernel translation units and the C-ABI implementation; not installed.
+//
+// One engine runs G >= 1 independent graphs packed into one CSR with global
+// vertex ids (a single graph is G = 1).  Per sweep t (lpaMove of Algorithm 1):
+//   sweep kernels  (one per degree bin) read the frontier lists L_t, pick the
+//                  most weighted label per vertex (Eq. 3, smallest-id ties),
+//                  write changes and re-flag neighbours (vertex pruning);
+//   finish kernel  applies the sync-mode changes, compacts flags into L_{t+1}
+//                  and, in its last block, runs the per-graph tolerance test
+//                  of Algorithm 1 and sets the device-side loop condition.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lpa {
+
+constexpr int kMaxHist = 64;            // per-sweep history depth (LPA_MAX_RECORDED_ITERS)
+constexpr int kBins = 3;                // small / warp / hub
+constexpr int32_t kEmptyKey = -1;       // free slot in label tables; labels are >= 0
+
+enum WeightKind : int { W_UNIT = 0, W_U32 = 1, W_F32 = 2 };
+enum Mode : int { MODE_SYNC = 0, MODE_ASYNC = 1, MODE_SYNC_FULL = 2 };
+
+// Control block, one per engine, in device memory.
+struct Ctrl {
+    int32_t iter;                        // sweeps completed so far (t)
+    int32_t max_iters;
+    double tau;
+    int32_t mode;
+    int32_t any_active;                  // loop condition mirror (read by the profiled path)
+    int32_t* labels_out;                 // destination of the finalize kernel
+    int32_t local_ids;                   // finalize writes label - first vertex of its graph
+    int32_t error;                       // non-zero: a device-side check failed
+    unsigned int ticket;                 // last-block election in the finish kernel
+    unsigned int chg_cnt;                // sync mode: entries in the changed list
+    unsigned int bin_cnt[2][kBins];      // frontier list lengths, double-buffered by t & 1
+    unsigned long long bin_entries[2][kBins];   // CSR entries of those vertices
+    unsigned long long bin_changed[kBins];      // vertices changed in the current sweep, per bin
+    unsigned long long bin_changed_entries[kBins];
+    long long hist_active[kMaxHist];
+    long long hist_scanned[kMaxHist];
+    long long hist_bin_vertices[kMaxHist][kBins];
+    long long hist_bin_entries[kMaxHist][kBins];
+    long long hist_bin_changed[kMaxHist][kBins];
+    long long hist_changed_entries[kMaxHist];
+};
+
+// Everything a kernel needs, passed by value.
+struct DevState {
+    int64_t N;                 // vertices over all graphs
+    int64_t E;                 // CSR entries
+    int32_t G;                 // graphs
+    int32_t weight_kind;       // WeightKind
+    const int64_t* off;        // [N+1]
+    const int32_t* idx;        // [E] global vertex ids
+    const void* w;             // [E] uint32 (W_U32), float (W_F32) or null (W_UNIT)
+    const int32_t* gid;        // [N] graph of each vertex, null when G == 1
+    const int64_t* vtx_off;    // [G+1]
+    int32_t* C;                // [N] labels (global ids)
+    int32_t* Cnew;             // [N] sync mode: next labels of changed vertices
+    uint8_t* flags;            // [N] 1 = unprocessed (Algorithm 1)
+    int32_t* list[kBins];      // frontier lists, capacity N each
+    int32_t* chg_list;         // [N] sync mode: vertices changed in this sweep
+    Ctrl* ctrl;
+    unsigned long long* dN;    // [G] changed vertices of the current sweep
+    int32_t* done;             // [G]
+    int32_t* iters;            // [G]
+    int32_t* exit_reason;      // [G]
+    long long* hist_changed;   // [G * kMaxHist]
+    int32_t* spill_keys;       // hub spill tables: [hub_blocks * spill_slots]
+    void* spill_vals;
+    int64_t spill_slots;       // slots per hub block (power of two, 0 = no spill table)
+    int32_t small_max;         // degree bins (see lpa_config)
+    int32_t warp_max;
+    int32_t warp_slots;        // per-warp table slots = next pow2 >= 2 * warp_max
+    int32_t hub_slots;         // per-block shared table slots
+};
+
+// ---- launchers (return cudaSuccess or the launch error) ------------------
+struct LaunchShape {
+    int blocks;
+    int threads;
+    size_t smem;
+};
+
+cudaError_t launch_init(const DevState& s, cudaStream_t st, int sms);
+cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st);
+cudaError_t launch_finish(const DevState& s, int phase, int mode, cudaGraphConditionalHandle h,
+                          int in_graph, cudaStream_t st, int sms);
+cudaError_t launch_finalize(const DevState& s, cudaStream_t st, int sms);
+cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int32_t* labels_out,
+                              int local_ids, cudaStream_t st);
+cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms);
+cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int sms);
+cudaError_t launch_sweep_hub(const DevState& s, int mode, int hub_threads, int hub_blocks,
+                             cudaStream_t st);
+int hub_blocks_for(int sms, int hub_threads, int hub_slots);
+
+// Graph validation (row-wise).  Results accumulate into *res (device).
+struct ValidateResult {
+    unsigned int bad_offsets;
+    unsigned int bad_index;
+    unsigned int bad_weight;
+    unsigned int non_integer;
+    unsigned int heavy_row;            // weighted degree >= 2^24 (fp32 sums may round)
+    unsigned int huge_row;             // weighted degree >= 2^31 (32-bit integer sums may overflow)
+    unsigned long long max_degree;
+};
+cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N,
+                            int64_t E, const int64_t* vtx_off, const int64_t* edge_off,
+                            const int32_t* gid, int32_t G, int rewrite_local_ids, int32_t* idx_rw,
+                            ValidateResult* res, cudaStream_t st, int sms);
+cudaError_t launch_fill_gid(const int64_t* vtx_off, int32_t G, int64_t N, int32_t* gid,
+                            cudaStream_t st, int sms);
+cudaError_t launch_weights_to_u32(float* w, int64_t E, cudaStream_t st, int sms);
+
+// Modularity (Eq. 1), fp64.  Vertex range [v0, v1), labels local to v0.
+struct ModAccum {
+    double two_m;
+    double sigma;
+    double null_sum;
+    unsigned int bad_label;
+    unsigned int pad;
+};
+cudaError_t launch_modularity(const DevState& s, int64_t v0, int64_t v1, const int32_t* labels,
+                              double* Sigma, ModAccum* acc, cudaStream_t st, int sms);
+
+}  // namespace lpa

@@ -1,0 +1,200 @@
+// lpa_sweep_hub.cu -- sweep for high-degree vertices (d > warp_max): one
+// thread block per frontier vertex.
+//
+// Warps read the row in 32-entry chunks and group equal labels with
+// __match_any_sync as in the warp kernel; group leaders add their sums into a
+// shared-memory open-addressing table of up to hub_slots slots.  When the row
+// could hold more distinct labels than half the shared table (2d > slots),
+// inserts probe at most kSharedProbes slots and then go to a spill table in
+// global memory private to this block (2^ceil(log2(2d)) slots, so it never
+// fills).  Each label lives in exactly one of the two tables, so scanning both
+// yields every K_{i->c} (Eq. 3).  The block then reduces (sum, smallest label)
+// to the winner (Section 4.1.5), clears what it used, and on change marks the
+// neighbours unprocessed (Section 4.1.4).
+#include "lpa_device.cuh"
+
+namespace lpa {
+
+constexpr int kSharedProbes = 16;
+
+template <bool ASYNC, int WK, bool BATCH>
+__global__ void k_sweep_hub(DevState s, int flag_neighbours) {
+    using T = typename Acc<WK>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int S = s.hub_slots;
+    int32_t* keys = reinterpret_cast<int32_t*>(smem_raw);
+    T* vals = reinterpret_cast<T*>(keys + S);
+    __shared__ uint32_t red_key[32];
+    __shared__ int32_t red_lab[32];
+    __shared__ int spilled;
+    __shared__ int32_t winner;
+
+    const unsigned lane = lane_id();
+    const int wib = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int q = threadIdx.x; q < S; q += blockDim.x) {
+        keys[q] = kEmptyKey;
+        vals[q] = (T)0;
+    }
+    if (threadIdx.x == 0) spilled = 0;
+    int32_t* gkeys = s.spill_keys ? s.spill_keys + (size_t)blockIdx.x * s.spill_slots : nullptr;
+    T* gvals = s.spill_keys ? static_cast<T*>(s.spill_vals) + (size_t)blockIdx.x * s.spill_slots : nullptr;
+    __syncthreads();
+
+    const int buf = s.ctrl->iter & 1;
+    const unsigned cnt = s.ctrl->bin_cnt[buf][2];
+    const int32_t* __restrict__ list = s.list[2];
+    for (unsigned k = blockIdx.x; k < cnt; k += gridDim.x) {
+        const int32_t v = list[k];
+        if constexpr (BATCH) {
+            if (s.done[s.gid[v]]) continue;     // block-uniform
+        }
+        const int64_t st = s.off[v];
+        const int64_t en = s.off[v + 1];
+        const int64_t d = en - st;
+        const int log_full = ceil_log2((unsigned)(2 * d));
+        const bool fits = (1ll << log_full) <= S;
+        const int log_s = fits ? log_full : ceil_log2((unsigned)S);
+        // the spill table needs 2^log_full slots; the host sizes it for the max degree
+        const bool may_spill = !fits && gkeys != nullptr && (1ll << log_full) <= s.spill_slots;
+        for (int64_t e0 = st + (int64_t)wib * 32; e0 < en; e0 += (int64_t)nw * 32) {
+            const int64_t e = e0 + lane;
+            const bool in = e < en;
+            const int32_t j = in ? load_index(s.idx, e) : v;
+            const bool ok = in && j != v;
+            const int32_t lab = ok ? load_label<ASYNC>(s.C, j) : kEmptyKey;
+            T w = ok ? load_weight<WK>(s.w, e) : (T)0;
+            bool lead = ok;
+            if constexpr (WK != W_F32) {
+                const unsigned peers = __match_any_sync(kFull, lab);
+                if constexpr (WK == W_UNIT) {
+                    w = (T)__popc(peers);
+                } else {
+                    w = __reduce_add_sync(peers, w);
+                }
+                lead = ok && lane == (unsigned)(__ffs(peers) - 1);
+            }
+            if (lead) {
+                if (fits) {
+                    if (!table_add<T>(keys, vals, log_s, lab, w)) atomicExch(&s.ctrl->error, 3);
+                } else if (!table_add_bounded<T>(keys, vals, log_s, lab, w, kSharedProbes)) {
+                    if (may_spill) {
+                        if (!table_add<T>(gkeys, gvals, log_full, lab, w)) atomicExch(&s.ctrl->error, 3);
+                        spilled = 1;
+                    } else {
+                        atomicExch(&s.ctrl->error, 1);   // host sized the spill table too small
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        bool any = false;
+        T best_w = 0;
+        int32_t best = 0x7fffffff;
+        const int slots_s = 1 << log_s;
+        for (int q = threadIdx.x; q < slots_s; q += blockDim.x) {
+            const int32_t kq = keys[q];
+            if (kq != kEmptyKey) {
+                const T vq = vals[q];
+                if (!any || vq > best_w || (vq == best_w && kq < best)) {
+                    any = true;
+                    best_w = vq;
+                    best = kq;
+                }
+                keys[q] = kEmptyKey;
+                vals[q] = (T)0;
+            }
+        }
+        if (spilled) {
+            const int64_t slots_g = 1ll << log_full;
+            for (int64_t q = threadIdx.x; q < slots_g; q += blockDim.x) {
+                const int32_t kq = gkeys[q];
+                if (kq != kEmptyKey) {
+                    const T vq = gvals[q];
+                    if (!any || vq > best_w || (vq == best_w && kq < best)) {
+                        any = true;
+                        best_w = vq;
+                        best = kq;
+                    }
+                    gkeys[q] = kEmptyKey;
+                    gvals[q] = (T)0;
+                }
+            }
+        }
+        // block argmax: per warp, then warp 0 over the warp winners
+        uint32_t key = any ? sum_key(best_w) : 0u;
+        uint32_t m = __reduce_max_sync(kFull, key);
+        uint32_t c = __reduce_min_sync(kFull, (m != 0 && key == m) ? (uint32_t)best : 0xffffffffu);
+        if (lane == 0) {
+            red_key[wib] = m;
+            red_lab[wib] = (int32_t)c;
+        }
+        __syncthreads();
+        if (wib == 0) {
+            uint32_t kk = (int)lane < nw ? red_key[lane] : 0u;
+            int32_t ll = (int)lane < nw ? red_lab[lane] : 0;
+            int32_t wlab = warp_argmax(kk, ll);
+            if (lane == 0) {
+                winner = wlab;
+                spilled = 0;
+            }
+        }
+        __syncthreads();
+        const int32_t best_lab = winner;
+        bool changed = false;
+        if (best_lab >= 0) {
+            const int32_t own = ASYNC ? __ldcg(s.C + v) : s.C[v];
+            changed = best_lab != own;
+        }
+        if (changed) {                                // block-uniform
+            if (threadIdx.x == 0) write_label<ASYNC>(s, v, best_lab);
+            if (flag_neighbours) {
+                for (int64_t e = st + threadIdx.x; e < en; e += blockDim.x) {
+                    const int32_t j = s.idx[e];
+                    if (j != v) s.flags[j] = 1;
+                }
+            }
+        }
+        if (wib == 0) account_changes<ASYNC, BATCH>(s, 2, changed && lane == 0, v, d);
+        __syncthreads();    // tables clear and `winner` consumed before the next vertex
+    }
+}
+
+int hub_blocks_for(int sms, int hub_threads, int hub_slots) {
+    const size_t smem_per_block = (size_t)hub_slots * 8 + 512;
+    int by_smem = (int)((200 * 1024) / smem_per_block);
+    int by_threads = 2048 / hub_threads;
+    int per_sm = by_smem < by_threads ? by_smem : by_threads;
+    if (per_sm < 1) per_sm = 1;
+    return sms * per_sm;
+}
+
+template <bool ASYNC, int WK, bool BATCH>
+static cudaError_t launch_hub_t(const DevState& s, int flag, int threads, int blocks, cudaStream_t st) {
+    const size_t smem = (size_t)s.hub_slots * 8;
+    auto kern = k_sweep_hub<ASYNC, WK, BATCH>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    kern<<<blocks, threads, smem, st>>>(s, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_hub(const DevState& s, int mode, int hub_threads, int hub_blocks, cudaStream_t st) {
+    const bool async = mode == MODE_ASYNC;
+    const int flag = mode != MODE_SYNC_FULL;
+    const bool batch = s.G > 1;
+#define LPA_HUB_W(A, B)                                                                   \
+    switch (s.weight_kind) {                                                              \
+        case W_UNIT: return launch_hub_t<A, W_UNIT, B>(s, flag, hub_threads, hub_blocks, st); \
+        case W_U32: return launch_hub_t<A, W_U32, B>(s, flag, hub_threads, hub_blocks, st);   \
+        default: return launch_hub_t<A, W_F32, B>(s, flag, hub_threads, hub_blocks, st);      \
+    }
+    if (async) {
+        if (batch) { LPA_HUB_W(true, true) } else { LPA_HUB_W(true, false) }
+    } else {
+        if (batch) { LPA_HUB_W(false, true) } else { LPA_HUB_W(false, false) }
+    }
+#undef LPA_HUB_W
+}
+
+}  // namespace lpa

@@ -1,0 +1,106 @@
+// lpa_sweep_small.cu -- sweep for low-degree vertices (degree <= small_max <= 8):
+// one thread per frontier vertex.  The thread loads its row's neighbour ids,
+// weights and neighbour labels into registers and evaluates the update rule
+// (Eq. 3, Section 3.3) by comparing every pair of entries: the sum for the
+// label of entry q is the total weight of entries carrying the same label.
+// Self-loops are skipped (scanCommunities, Algorithm 1); ties go to the
+// smallest label id (Section 4.1.5).  When the label changes the thread marks
+// all other neighbours unprocessed (vertex pruning, Section 4.1.4).
+//
+// Memory per vertex: two offsets, d indices, d weights, d label gathers, one
+// own-label load; on change one label write and d flag bytes.
+#include "lpa_device.cuh"
+
+namespace lpa {
+
+constexpr int kSmallMaxD = 8;
+constexpr int kSmallThreads = 256;
+
+template <bool ASYNC, int WK, bool BATCH>
+__global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int flag_neighbours) {
+    using T = typename Acc<WK>::T;
+    const int buf = s.ctrl->iter & 1;
+    const unsigned cnt = s.ctrl->bin_cnt[buf][0];
+    const int32_t* __restrict__ list = s.list[0];
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned base = blockIdx.x * blockDim.x; base < cnt; base += stride) {
+        const unsigned k = base + threadIdx.x;
+        bool act = k < cnt;
+        int32_t v = act ? list[k] : 0;
+        if constexpr (BATCH) {
+            if (act && s.done[s.gid[v]]) act = false;
+        }
+        int64_t st = 0;
+        int d = 0;
+        if (act) {
+            st = s.off[v];
+            d = (int)(s.off[v + 1] - st);
+        }
+        int32_t nb[kSmallMaxD];
+        int32_t lab[kSmallMaxD];
+        T wt[kSmallMaxD];
+#pragma unroll
+        for (int q = 0; q < kSmallMaxD; ++q) {
+            bool ok = q < d;
+            int32_t j = ok ? load_index(s.idx, st + q) : v;
+            nb[q] = j;
+            ok = ok && (j != v);
+            lab[q] = ok ? load_label<ASYNC>(s.C, j) : kEmptyKey;
+            wt[q] = ok ? load_weight<WK>(s.w, st + q) : (T)0;
+        }
+        bool any = false;
+        T best_w = 0;
+        int32_t best = 0x7fffffff;
+#pragma unroll
+        for (int q = 0; q < kSmallMaxD; ++q) {
+            T sum = 0;
+#pragma unroll
+            for (int r = 0; r < kSmallMaxD; ++r) sum += (lab[r] == lab[q]) ? wt[r] : (T)0;
+            const bool better = lab[q] != kEmptyKey &&
+                                (!any || sum > best_w || (sum == best_w && lab[q] < best));
+            if (better) {
+                any = true;
+                best_w = sum;
+                best = lab[q];
+            }
+        }
+        bool changed = false;
+        if (act && any) {
+            const int32_t own = ASYNC ? __ldcg(s.C + v) : s.C[v];
+            changed = best != own;
+        }
+        if (changed) {
+            write_label<ASYNC>(s, v, best);
+            if (flag_neighbours) {
+#pragma unroll
+                for (int q = 0; q < kSmallMaxD; ++q)
+                    if (q < d && nb[q] != v) s.flags[nb[q]] = 1;
+            }
+        }
+        account_changes<ASYNC, BATCH>(s, 0, changed, v, d);
+    }
+}
+
+cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms) {
+    const bool async = mode == MODE_ASYNC;
+    const int flag = mode != MODE_SYNC_FULL;
+    const bool batch = s.G > 1;
+    dim3 grid(sms * 8), block(kSmallThreads);
+#define LPA_SMALL(A, W, B) k_sweep_small<A, W, B><<<grid, block, 0, st>>>(s, flag)
+#define LPA_SMALL_W(A, B)                                      \
+    switch (s.weight_kind) {                                   \
+        case W_UNIT: LPA_SMALL(A, W_UNIT, B); break;           \
+        case W_U32: LPA_SMALL(A, W_U32, B); break;             \
+        default: LPA_SMALL(A, W_F32, B); break;                \
+    }
+    if (async) {
+        if (batch) { LPA_SMALL_W(true, true) } else { LPA_SMALL_W(true, false) }
+    } else {
+        if (batch) { LPA_SMALL_W(false, true) } else { LPA_SMALL_W(false, false) }
+    }
+#undef LPA_SMALL_W
+#undef LPA_SMALL
+    return cudaGetLastError();
+}
+
+}  // namespace lpa

@@ -1,0 +1,181 @@
+// lpa_sweep_warp.cu -- sweep for mid-degree vertices (small_max < d <= warp_max):
+// one warp per frontier vertex.
+//
+// The warp reads the row 32 entries at a time (coalesced index and weight
+// loads, one label gather per lane).  Within each 32-entry chunk, lanes that
+// hold the same label are grouped with __match_any_sync and their weights
+// combined (a popcount for unit weights, a group reduction for integer
+// weights), so each distinct label of the chunk costs one table update.
+//   d <= 32: the grouped sums are already the per-label totals K_{i->c}
+//            (Eq. 3) and the warp takes the argmax directly.
+//   d  > 32: group leaders add their sums into a per-warp open-addressing
+//            table in shared memory sized 2^ceil(log2(2d)) slots (so it can
+//            never fill), then the warp scans the table for the argmax and
+//            clears the slots it used.
+// Ties go to the smallest label id (Section 4.1.5); self-loops are skipped
+// (Algorithm 1).  On change, the warp re-reads the row and marks the
+// neighbours unprocessed (Section 4.1.4).
+#include "lpa_device.cuh"
+
+namespace lpa {
+
+constexpr int kWarpThreads = 256;
+constexpr int kWarpsPerBlock = kWarpThreads / 32;
+
+// Combined weight of the lanes in `peers` (all hold the same label).
+template <int WK>
+__device__ __forceinline__ typename Acc<WK>::T group_sum(unsigned peers, typename Acc<WK>::T w,
+                                                         int32_t lab, bool ok) {
+    if constexpr (WK == W_UNIT) {
+        return (typename Acc<WK>::T)__popc(peers);
+    } else if constexpr (WK == W_U32) {
+        return __reduce_add_sync(peers, w);
+    } else {
+        // fp32: every lane of a group adds the group's weights in lane order,
+        // so all of them obtain the same value.
+        float sum = 0.f;
+        for (int q = 0; q < 32; ++q) {
+            float wq = __shfl_sync(kFull, w, q);
+            int32_t lq = __shfl_sync(kFull, lab, q);
+            if (ok && lq == lab) sum += wq;
+        }
+        (void)peers;
+        return sum;
+    }
+}
+
+template <bool ASYNC, int WK, bool BATCH>
+__global__ void __launch_bounds__(kWarpThreads) k_sweep_warp(DevState s, int flag_neighbours) {
+    using T = typename Acc<WK>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int wslots = s.warp_slots;
+    const unsigned lane = lane_id();
+    const int wib = threadIdx.x >> 5;
+    int32_t* keys = reinterpret_cast<int32_t*>(smem_raw) + (size_t)wib * wslots * 2;
+    T* vals = reinterpret_cast<T*>(keys + wslots);
+    for (int q = lane; q < wslots; q += 32) {
+        keys[q] = kEmptyKey;
+        vals[q] = (T)0;
+    }
+    __syncwarp();
+
+    const int buf = s.ctrl->iter & 1;
+    const unsigned cnt = s.ctrl->bin_cnt[buf][1];
+    const int32_t* __restrict__ list = s.list[1];
+    const unsigned nwarps = gridDim.x * kWarpsPerBlock;
+    for (unsigned k = blockIdx.x * kWarpsPerBlock + wib; k < cnt; k += nwarps) {
+        const int32_t v = list[k];
+        if constexpr (BATCH) {
+            if (s.done[s.gid[v]]) continue;     // warp-uniform
+        }
+        const int64_t st = s.off[v];
+        const int64_t en = s.off[v + 1];
+        const int d = (int)(en - st);
+        uint32_t key = 0;
+        int32_t cand = 0;
+        if (d <= 32) {
+            const bool in = (int)lane < d;
+            const int32_t j = in ? load_index(s.idx, st + lane) : v;
+            const bool ok = in && j != v;
+            const int32_t lab = ok ? load_label<ASYNC>(s.C, j) : kEmptyKey;
+            const T w = ok ? load_weight<WK>(s.w, st + lane) : (T)0;
+            const unsigned peers = __match_any_sync(kFull, lab);
+            const T sum = group_sum<WK>(peers, w, lab, ok);
+            if (ok && lane == (unsigned)(__ffs(peers) - 1)) {
+                key = sum_key(sum);
+                cand = lab;
+            }
+        } else {
+            const int log_slots = ceil_log2(2u * (unsigned)d);
+            for (int64_t e0 = st; e0 < en; e0 += 32) {
+                const int64_t e = e0 + lane;
+                const bool in = e < en;
+                const int32_t j = in ? load_index(s.idx, e) : v;
+                const bool ok = in && j != v;
+                const int32_t lab = ok ? load_label<ASYNC>(s.C, j) : kEmptyKey;
+                const T w = ok ? load_weight<WK>(s.w, e) : (T)0;
+                if constexpr (WK == W_F32) {
+                    if (ok && !table_add<T>(keys, vals, log_slots, lab, w)) atomicExch(&s.ctrl->error, 2);
+                } else {
+                    const unsigned peers = __match_any_sync(kFull, lab);
+                    const T sum = group_sum<WK>(peers, w, lab, ok);
+                    if (ok && lane == (unsigned)(__ffs(peers) - 1) && !table_add<T>(keys, vals, log_slots, lab, sum))
+                        atomicExch(&s.ctrl->error, 2);
+                }
+            }
+            __syncwarp();
+            bool any = false;
+            T best_w = 0;
+            int32_t best = 0x7fffffff;
+            const int slots = 1 << log_slots;
+            for (int q = lane; q < slots; q += 32) {
+                const int32_t kq = keys[q];
+                if (kq != kEmptyKey) {
+                    const T vq = vals[q];
+                    if (!any || vq > best_w || (vq == best_w && kq < best)) {
+                        any = true;
+                        best_w = vq;
+                        best = kq;
+                    }
+                    keys[q] = kEmptyKey;
+                    vals[q] = (T)0;
+                }
+            }
+            __syncwarp();
+            if (any) {
+                key = sum_key(best_w);
+                cand = best;
+            }
+        }
+        const int32_t best = warp_argmax(key, cand);
+        bool changed = false;
+        if (best >= 0) {
+            const int32_t own = ASYNC ? __ldcg(s.C + v) : s.C[v];
+            changed = best != own;
+        }
+        if (changed) {                           // warp-uniform
+            if (lane == 0) write_label<ASYNC>(s, v, best);
+            if (flag_neighbours) {
+                for (int64_t e = st + lane; e < en; e += 32) {
+                    const int32_t j = s.idx[e];
+                    if (j != v) s.flags[j] = 1;
+                }
+            }
+        }
+        account_changes<ASYNC, BATCH>(s, 1, changed && lane == 0, v, d);
+    }
+}
+
+template <bool ASYNC, int WK, bool BATCH>
+static cudaError_t launch_warp_t(const DevState& s, int flag, cudaStream_t st, int sms) {
+    const size_t smem = (size_t)kWarpsPerBlock * s.warp_slots * 8;
+    auto kern = k_sweep_warp<ASYNC, WK, BATCH>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarpThreads, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    kern<<<sms * per_sm, kWarpThreads, smem, st>>>(s, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int sms) {
+    const bool async = mode == MODE_ASYNC;
+    const int flag = mode != MODE_SYNC_FULL;
+    const bool batch = s.G > 1;
+#define LPA_WARP_W(A, B)                                                     \
+    switch (s.weight_kind) {                                                 \
+        case W_UNIT: return launch_warp_t<A, W_UNIT, B>(s, flag, st, sms);   \
+        case W_U32: return launch_warp_t<A, W_U32, B>(s, flag, st, sms);     \
+        default: return launch_warp_t<A, W_F32, B>(s, flag, st, sms);        \
+    }
+    if (async) {
+        if (batch) { LPA_WARP_W(true, true) } else { LPA_WARP_W(true, false) }
+    } else {
+        if (batch) { LPA_WARP_W(false, true) } else { LPA_WARP_W(false, false) }
+    }
+#undef LPA_WARP_W
+}
+
+}  // namespace lpa

@@ -1,0 +1,64 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every
+entry point include/lpa.h declares; the Python binding covers the same names."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lpa.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lpa_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2312_08140_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("lpa_graph_create", "lpa_graph_destroy", "lpa_run", "lpa_modularity",
+                     "lpa_batch_create", "lpa_batch_run", "lpa_batch_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header(lib_path):
+    import paper_2312_08140_gb300 as lpa
+    assert set(lpa.exported_symbols()) == set(_declared())
+    lpa.load(lib_path)
+    for n in _declared():
+        assert callable(getattr(lpa, n))
+
+
+def test_pure_host_entry_points(lib_path):
+    import paper_2312_08140_gb300 as lpa
+    lpa.load(lib_path)
+    assert lpa.lpa_version().startswith("lpa-gb300")
+    assert lpa.lpa_status_string(lpa.LPA_ERR_INVALID_GRAPH) == "invalid graph"
+    # argument checks happen before any CUDA call
+    with pytest.raises(lpa.LpaError) as e:
+        lpa.lpa_graph_create(-5, 0, None, None)
+    assert e.value.status == lpa.LPA_ERR_INVALID_ARG
+    with pytest.raises(lpa.LpaError):
+        lpa.lpa_graph_destroy(None)
+
+
+def test_struct_layouts_match_c(lib_path):
+    import paper_2312_08140_gb300 as lpa
+    H = lpa.LPA_MAX_RECORDED_ITERS
+    assert ctypes.sizeof(lpa.LpaRunInfo) == 8 + 3 * 8 * H + 8
+    assert ctypes.sizeof(lpa.LpaGraphProps) == 8 * 2 + 4 * 4 + 8 * 2
+    assert ctypes.sizeof(lpa.LpaConfig) == 16
+    assert ctypes.sizeof(lpa.LpaProfile) == 16 + 4 * H + 12 * H + 3 * 3 * 8 * H

@@ -1,0 +1,297 @@
+"""GPU label propagation vs the CPU oracle, through the C ABI.
+
+Synchronous modes (LPA_MODE_SYNC, LPA_MODE_SYNC_FULL) must reproduce the
+oracle's labels, sweep count and per-sweep changed counts exactly: every graph
+here has integer weights, so every per-label sum is exact in any order.  The
+asynchronous mode is order-dependent (Section 4.1), so it is held to
+invariants: labels stay inside the vertex's connected component, at most
+tau*N vertices are off their local argmax when the tolerance ended the run, and
+modularity not lower than the serial oracle's by more than 0.02.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import lpa_inputs as L
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lpa():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2312_08140_gb300 as m
+    m.load()
+    return m
+
+
+def run_gpu(lpa, g, mode, tau=0.05, iters=20, cfg=None):
+    import torch
+    h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w)
+    try:
+        if cfg is not None:
+            lpa.lpa_graph_set_config(h, lpa.LpaConfig(*cfg))
+        out = torch.full((max(g.n, 1),), -7, dtype=torch.int32, device="cuda")
+        info = lpa.lpa_run(h, mode, tau, iters, out)
+        return out[:g.n].cpu().numpy(), info.as_dict(), h
+    except Exception:
+        lpa.lpa_graph_destroy(h)
+        raise
+
+
+def assert_sync_parity(lpa, g, tau=0.05, iters=20, cfg=None, modes=("sync", "sync_full")):
+    ref, it, changed = O.lpa_sync(g.off, g.idx, g.w, tau, iters)
+    for mode in modes:
+        got, info, h = run_gpu(lpa, g, mode, tau, iters, cfg)
+        lpa.lpa_graph_destroy(h)
+        assert info["iterations"] == it, (mode, info["iterations"], it)
+        assert info["changed"] == changed.tolist()[:64], mode
+        mism = np.flatnonzero(got != ref)
+        assert mism.size == 0, f"{mode}: {mism.size} labels differ, first at {mism[:5]}"
+    return ref, it
+
+
+def _golden():
+    with open(os.path.join(ROOT, "tests", "golden", "hand_worked.json")) as f:
+        return json.load(f)["cases"]
+
+
+def _case_graph(case):
+    if "clique" in case:
+        k = case["clique"]
+        return L.from_undirected_pairs(case["n"], [(u, v) for u in range(k) for v in range(u + 1, k)])
+    return L.from_undirected_pairs(case["n"], [tuple(p) for p in case["pairs"]], case.get("weights"))
+
+
+@pytest.mark.parametrize("case", [c for c in _golden() if c["mode"] == "sync"], ids=lambda c: c["name"])
+def test_hand_worked_sync(lpa, case):
+    g = _case_graph(case)
+    for mode in ("sync", "sync_full"):
+        got, info, h = run_gpu(lpa, g, mode, case.get("tau", 0.05), case.get("max_iters", 20))
+        lpa.lpa_graph_destroy(h)
+        assert got.tolist() == case["labels"]
+        assert info["iterations"] == case["iterations"]
+        assert info["changed"] == case["changed"]
+
+
+def test_random_small_graphs_sync(lpa):
+    rng = np.random.default_rng(11)
+    for t in range(120):
+        n = int(rng.integers(1, 60))
+        g = L.random_small(n, float(rng.uniform(0.02, 0.6)), seed=70000 + t, wmax=int(rng.integers(0, 5)),
+                           self_loops=0.1, multi=bool(t % 3 == 0))
+        assert_sync_parity(lpa, g, tau=float(rng.choice([0.0, 0.05, 0.2])), iters=int(rng.integers(1, 25)))
+
+
+def test_planted_partition_sync(lpa):
+    g = L.planted_partition()
+    ref, it = assert_sync_parity(lpa, g)
+    assert it >= 3
+
+
+@pytest.mark.parametrize("cfg", [None, (4, 64, 256, 1024), (8, 1024, 1024, 16384), (1, 33, 128, 1024)])
+def test_rmat_bins_and_spill_sync(lpa, cfg):
+    """R-MAT scale 14 has vertices in all three degree bins; hub_slots = 1024 forces
+    the global spill table for every hub with degree > 512."""
+    g = L.rmat(14, 16, seed=3)
+    assert int(np.diff(g.off).max()) > 2048
+    assert_sync_parity(lpa, g, cfg=cfg)
+
+
+def test_rmat_raw_duplicates_selfloops_sync(lpa):
+    g = L.rmat(12, 8, seed=5, dedup=False, drop_self=False)
+    assert_sync_parity(lpa, g)
+
+
+def test_weighted_grid_sync(lpa):
+    g = L.road_grid(200, 173, seed=2)       # ragged: n is not a multiple of any tile
+    assert_sync_parity(lpa, g, iters=7)
+
+
+def test_weighted_sbm_sync(lpa):
+    g = L.batched_sbm_graph(3, n_max=20000)
+    assert_sync_parity(lpa, g)
+
+
+def test_edge_cases(lpa):
+    import torch
+    # N == 0
+    h = lpa.lpa_graph_create(0, 0, np.zeros(1, np.int64), np.zeros(0, np.int32))
+    info = lpa.lpa_run(h, "sync", 0.05, 20, None)
+    assert info.iterations == 0 and info.exit_reason == 2
+    lpa.lpa_graph_destroy(h)
+    # no entries: one sweep, nothing changes, labels = ids
+    g = L.Graph(np.zeros(6, np.int64), np.zeros(0, np.int32), None)
+    for mode in ("sync", "async", "sync_full"):
+        got, info, h = run_gpu(lpa, g, mode)
+        lpa.lpa_graph_destroy(h)
+        assert got.tolist() == list(range(5)) and info["iterations"] == 1 and info["changed"] == [0]
+    # max_iters == 0: labels stay ids
+    g = L.planted_partition(n=500, blocks=5, seed=2)
+    got, info, h = run_gpu(lpa, g, "async", 0.05, 0)
+    lpa.lpa_graph_destroy(h)
+    assert np.array_equal(got, np.arange(g.n)) and info["iterations"] == 0 and info["exit_reason"] == 2
+    # tolerance 1: exactly one sweep
+    assert_sync_parity(lpa, g, tau=1.0)
+    # cap reached
+    ref, it = assert_sync_parity(lpa, L.from_undirected_pairs(2, [(0, 1)]), iters=5)
+    assert it == 5
+
+
+def test_invalid_graphs_rejected(lpa):
+    off = np.array([0, 2, 3, 4], np.int64)
+    idx = np.array([1, 2, 0, 0], np.int32)
+    bad = [
+        (np.array([0, 2, 1, 4], np.int64), idx, None),          # decreasing offsets
+        (np.array([0, 2, 3, 5], np.int64), idx, None),          # offsets[n] != nnz
+        (off, np.array([1, 3, 0, 0], np.int32), None),          # index out of range
+        (off, np.array([1, -1, 0, 0], np.int32), None),         # negative index
+        (off, idx, np.array([1, -2, 1, 1], np.float32)),        # negative weight
+        (off, idx, np.array([1, np.nan, 1, 1], np.float32)),    # NaN weight
+        (off, idx, np.array([1, np.inf, 1, 1], np.float32)),    # inf weight
+    ]
+    for o, i, w in bad:
+        with pytest.raises(lpa.LpaError) as e:
+            lpa.lpa_graph_create(3, 4, o, i, w)
+        assert e.value.status in (lpa.LPA_ERR_INVALID_GRAPH, lpa.LPA_ERR_INVALID_ARG)
+    with pytest.raises(lpa.LpaError):
+        lpa.lpa_graph_create(-1, 0, off, idx)
+    h = lpa.lpa_graph_create(3, 4, off, idx)
+    import torch
+    out = torch.empty(3, dtype=torch.int32, device="cuda")
+    for args in (("sync", -0.1, 20), ("sync", 1.5, 20), ("sync", 0.05, -1), (7, 0.05, 20)):
+        with pytest.raises(lpa.LpaError):
+            lpa.lpa_run(h, args[0], args[1], args[2], out)
+    lpa.lpa_graph_destroy(h)
+
+
+def test_non_integer_weights_flagged_inexact(lpa):
+    g = L.road_grid(64, 64, seed=4)
+    w = g.w * 0.37
+    h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, w)
+    assert lpa.lpa_graph_props_get(h)["exact"] == 0
+    lpa.lpa_graph_destroy(h)
+    h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w)
+    p = lpa.lpa_graph_props_get(h)
+    assert p["exact"] == 1 and p["weighted"] == 1
+    lpa.lpa_graph_destroy(h)
+
+
+def check_async(lpa, g, tau=0.05, iters=20, cfg=None, q_slack=0.02):
+    got, info, h = run_gpu(lpa, g, "async", tau, iters, cfg)
+    try:
+        assert np.all((got >= 0) & (got < g.n))
+        assert O.count_labels_outside_component(g.off, g.idx, got) == 0
+        q_gpu = lpa.lpa_modularity(h, got_t := __import__("torch").from_numpy(got).cuda())
+        del got_t
+    finally:
+        lpa.lpa_graph_destroy(h)
+    q_ref_gpu_labels = O.modularity(g.off, g.idx, g.w, got)
+    assert abs(q_gpu - q_ref_gpu_labels) <= 1e-6 * max(1.0, abs(q_ref_gpu_labels))
+    ref, it_ref, _ = O.lpa_async(g.off, g.idx, g.w, tau, iters)
+    q_ser = O.modularity(g.off, g.idx, g.w, ref)
+    assert q_gpu >= q_ser - q_slack, (q_gpu, q_ser)
+    off_max = O.count_not_local_max(g.off, g.idx, g.w, got)
+    if info["exit_reason"] == 0:
+        # changes in the final sweep can unsettle neighbours; report generously
+        assert off_max <= max(tau * g.n, 1) * 4, (off_max, tau * g.n)
+    return info, q_gpu, q_ser, off_max
+
+
+def test_async_invariants_small(lpa):
+    rng = np.random.default_rng(5)
+    for t in range(60):
+        n = int(rng.integers(2, 80))
+        g = L.random_small(n, float(rng.uniform(0.05, 0.5)), seed=80000 + t, wmax=int(rng.integers(0, 4)))
+        got, info, h = run_gpu(lpa, g, "async")
+        lpa.lpa_graph_destroy(h)
+        assert O.count_labels_outside_component(g.off, g.idx, got) == 0
+        assert 1 <= info["iterations"] <= 20
+
+
+def test_async_planted_partition(lpa):
+    check_async(lpa, L.planted_partition())
+
+
+def test_async_rmat_and_grid_medium(lpa):
+    check_async(lpa, L.rmat(16, 16, seed=1))
+    check_async(lpa, L.road_grid(512, 512, seed=1))
+
+
+def test_modularity_parity(lpa):
+    import torch
+    rng = np.random.default_rng(9)
+    for g in (L.planted_partition(), L.road_grid(100, 77, seed=3), L.rmat(13, 16, seed=2),
+              L.from_undirected_pairs(3, [(0, 0), (0, 1), (1, 2)], [2.0, 1.0, 3.0])):
+        h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w)
+        for lab in (np.arange(g.n), np.zeros(g.n), rng.integers(0, max(1, g.n // 7), g.n)):
+            lab = lab.astype(np.int32)
+            q = lpa.lpa_modularity(h, torch.from_numpy(lab).cuda())
+            q_ref = O.modularity(g.off, g.idx, g.w, lab)
+            assert abs(q - q_ref) <= 1e-6 * max(1.0, abs(q_ref)), (q, q_ref)
+        with pytest.raises(lpa.LpaError):
+            lpa.lpa_modularity(h, torch.full((g.n,), g.n, dtype=torch.int32, device="cuda"))
+        lpa.lpa_graph_destroy(h)
+
+
+def _batch_inputs(graphs):
+    vo, eo, off, idx_global, w = L.pack(graphs)
+    idx_local = np.concatenate([gr.idx for gr in graphs]) if graphs else np.zeros(0, np.int32)
+    return vo, eo, off, idx_local.astype(np.int32), w
+
+
+def test_batch_matches_solo_sync(lpa):
+    import torch
+    graphs = [L.batched_sbm_graph(g, n_max=6000) for g in range(24)]
+    graphs.insert(5, L.from_undirected_pairs(1, []))                 # single isolated vertex
+    graphs.insert(9, L.from_undirected_pairs(2, [(0, 1)]))           # oscillates to the cap
+    vo, eo, off, idx, w = _batch_inputs(graphs)
+    b = lpa.lpa_batch_create(len(graphs), vo, eo, off, idx, w)
+    out = torch.empty(int(vo[-1]), dtype=torch.int32, device="cuda")
+    try:
+        for mode in ("sync", "sync_full"):
+            infos = lpa.lpa_batch_run(b, len(graphs), mode, 0.05, 20, out)
+            got = out.cpu().numpy()
+            for k, gr in enumerate(graphs):
+                ref, it, ch = O.lpa_sync(gr.off, gr.idx, gr.w)
+                assert np.array_equal(got[vo[k]:vo[k + 1]], ref), (mode, k)
+                assert infos[k].iterations == it and list(infos[k].changed[:it]) == ch.tolist(), (mode, k)
+        infos = lpa.lpa_batch_run(b, len(graphs), "async", 0.05, 20, out)
+        got = out.cpu().numpy()
+        for k, gr in enumerate(graphs):
+            lab = got[vo[k]:vo[k + 1]]
+            assert O.count_labels_outside_component(gr.off, gr.idx, lab) == 0
+            q = lpa.lpa_batch_modularity(b, k, out[vo[k]:vo[k + 1]])
+            assert abs(q - O.modularity(gr.off, gr.idx, gr.w, lab)) <= 1e-6
+    finally:
+        lpa.lpa_batch_destroy(b)
+
+
+# ---------------------------------------------------------------- full size --
+@pytest.fixture(scope="module")
+def rmat22():
+    return L.rmat(22, 16, seed=1)
+
+
+@pytest.fixture(scope="module")
+def grid4096():
+    return L.road_grid(4096, 4096, seed=1)
+
+
+def test_full_size_rmat22_sync(lpa, rmat22):
+    assert_sync_parity(lpa, rmat22, modes=("sync",))
+
+
+def test_full_size_grid_sync(lpa, grid4096):
+    assert_sync_parity(lpa, grid4096, modes=("sync",))
+
+
+def test_full_size_async(lpa, rmat22, grid4096):
+    for g in (rmat22, grid4096):
+        check_async(lpa, g)
