@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Label propagation throughput on one GB300 (or N replicas under torchrun).
+
+Workload (default "rmat22+grid4096"): R-MAT scale 22, edge factor 16,
+(a,b,c,d) = (.57,.19,.19,.05), symmetrised, de-duplicated, self-loops removed,
+unit weights; and a 4096 x 4096 4-neighbour lattice with 10% of edges dropped,
+0.1% random shortcuts and integer weights 1..8.  One step = four runs of the
+whole hot path (initialisation, sweeps with pruning until dN/N <= 0.05 or 20
+sweeps, labels out): each graph in the synchronous and the asynchronous mode.
+
+Metric: LPA edges/s = sum over runs of nnz x sweeps / time.  Every rank runs
+the same workload on its own GPU (replicas, no collective on the data path);
+value = all ranks' edges / the slowest rank's time.
+
+Also reported:
+  e2e          the same metric through the public C ABI from pinned host
+               buffers: graph creation (H2D copy + validation), both runs,
+               labels copied back, all inside the timed region;
+  roofline     algorithmic bytes of the dominant kernel per launch / its mean
+               launch time, from CUDA events around every launch of the
+               profiled run path, against the measured HBM copy bandwidth;
+  cpu_baseline the single-threaded CPU oracle on a bounded sample;
+  clocks       nvidia-smi samples taken during the timed region.
+
+--impl reference times the CPU oracle (the reference arm of this method) on
+the same workload: each step is one oracle sweep of one (graph, mode) pair.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LPA edges/s (|E| x iterations / time)"
+UNIT = "edges/s"
+TAU = 0.05
+MAX_ITERS = 20
+MODES = ("sync", "async")
+HBM_FALLBACK_GBS = 6800.0
+
+
+def workload(name):
+    import lpa_inputs as L
+    if name == "rmat22+grid4096":
+        return [("rmat22", lambda: L.rmat(22, 16, seed=1)), ("grid4096", lambda: L.road_grid(4096, 4096, seed=1))]
+    if name == "rmat18+grid1024":
+        return [("rmat18", lambda: L.rmat(18, 16, seed=1)), ("grid1024", lambda: L.road_grid(1024, 1024, seed=1))]
+    raise SystemExit(f"unknown workload {name}")
+
+
+WORKLOAD_TEXT = {
+    "rmat22+grid4096": "R-MAT scale 22 edge factor 16 (a,b,c,d=.57,.19,.19,.05; symmetrised, deduplicated, "
+                       "no self-loops; unit weights) + 4096x4096 road-like grid (10% edges dropped, 0.1% "
+                       "shortcuts, integer weights 1..8); sync and async-with-pruning; tau=0.05, cap 20",
+    "rmat18+grid1024": "R-MAT scale 18 + 1024x1024 road-like grid (small profiling case of the same "
+                       "generators); sync and async-with-pruning; tau=0.05, cap 20",
+}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- oracle arm
+def oracle_sample(graphs, pairs):
+    """Times one oracle sweep per (graph, mode) pair; returns (edges, seconds)."""
+    import oracle as O
+    edges, secs = 0, 0.0
+    for gi, mode in pairs:
+        g = graphs[gi]
+        fn = O.lpa_sync if mode == "sync" else O.lpa_async
+        t0 = time.perf_counter()
+        _, it, _ = fn(g.off, g.idx, g.w, TAU, 1)
+        secs += time.perf_counter() - t0
+        edges += g.nnz * it
+    return edges, secs
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    wl = workload(args.workload)
+    graphs = [make() for _, make in wl]
+    pairs = [(gi, m) for gi in range(len(graphs)) for m in MODES]
+    for s in range(args.warmup):
+        oracle_sample(graphs, [pairs[s % len(pairs)]])
+    edges, secs = 0, 0.0
+    t_all = time.perf_counter()
+    for s in range(args.steps):
+        e, t = oracle_sample(graphs, [pairs[s % len(pairs)]])
+        edges += e
+        secs += t
+    wall = time.perf_counter() - t_all
+    value = edges / secs
+    sample = (f"each step: one CPU-oracle sweep of one (graph, mode) pair, rotating over "
+              f"{[(wl[g][0], m) for g, m in pairs]}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_TEXT[args.workload]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+def kernel_bytes(prof, wbytes, sync):
+    """Algorithmic bytes per sweep-kernel launch from the per-bin counts:
+    per scanned vertex 16 B offsets + 4 B own label + 4 B frontier id; per
+    scanned entry 4 B index + wbytes weight + 4 B gathered label; per changed
+    vertex 4 B label write (+4 B changed-list entry in sync mode) and 1 B flag
+    per entry of its row."""
+    out = {b: {"bytes": 0.0, "ms": 0.0, "launches": 0} for b in ("small", "warp", "hub")}
+    for t in range(min(prof["iterations"], 64)):
+        for bi, b in enumerate(("small", "warp", "hub")):
+            v = prof["bin_vertices"][t][bi]
+            e = prof["bin_entries"][t][bi]
+            c = prof["bin_changed"][t][bi]
+            ce = prof["bin_changed_entries"][t][bi]
+            by = v * 24 + e * (8 + wbytes) + c * (8 if sync else 4) + ce
+            out[b]["bytes"] += by
+            out[b]["ms"] += prof["sweep_ms"][t][bi]
+            out[b]["launches"] += 1
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gvelpa", choices=["gvelpa", "reference"])
+    ap.add_argument("--workload", default="rmat22+grid4096", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true", help="skip the event-timed roofline pass")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    import paper_2312_08140_gb300 as lpa
+    lpa.load()
+
+    wl = workload(args.workload)
+    graphs = [make() for _, make in wl]
+    stream = torch.cuda.current_stream()
+    handles = [lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS, stream) for g in graphs]
+    outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+
+    def step():
+        for h, g, o in zip(handles, graphs, outs):
+            for m in MODES:
+                lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    before = [lpa.lpa_graph_props_get(h) for h in handles]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    after = [lpa.lpa_graph_props_get(h) for h in handles]
+    sweeps = [a["sweeps_total"] - b["sweeps_total"] for a, b in zip(after, before)]
+    edges = sum(g.nnz * s for g, s in zip(graphs, sweeps))
+    touched = sum(a["scanned_total"] - b["scanned_total"] for a, b in zip(after, before))
+    runs = args.steps * len(graphs) * len(MODES)
+    launches = runs * 5 + 4 * sum(sweeps)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        u = torch.tensor([edges, touched, launches], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        edges, touched, launches = (float(x) for x in u.tolist())
+    value = edges / (ms / 1e3)
+
+    # per-run detail (one run each, with info) for the record
+    per_run = []
+    for (name, _), h, g, o in zip(wl, handles, graphs, outs):
+        for m in MODES:
+            ri = lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=True)
+            per_run.append({"graph": name, "mode": m, "n": g.n, "nnz": g.nnz, "iterations": ri.iterations,
+                            "exit_reason": ri.exit_reason, "scanned": ri.edges_touched})
+
+    # e2e through the public API from pinned host memory
+    pinned = []
+    for g in graphs:
+        t_off = torch.from_numpy(g.off).pin_memory()
+        t_idx = torch.from_numpy(g.idx).pin_memory()
+        t_w = torch.from_numpy(g.w).pin_memory() if g.w is not None else None
+        t_lab = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        pinned.append((t_off, t_idx, t_w, t_lab))
+    h2d = sum(g.off.nbytes + g.idx.nbytes + (g.w.nbytes if g.w is not None else 0) for g in graphs)
+    d2h = sum(4 * g.n * len(MODES) for g in graphs)
+
+    def e2e_step():
+        e = 0
+        for g, (t_off, t_idx, t_w, t_lab), o in zip(graphs, pinned, outs):
+            h = lpa.lpa_graph_create(g.n, g.nnz, t_off, t_idx, t_w, lpa.LPA_HOST_PTRS, stream)
+            for m in MODES:
+                lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
+                t_lab.copy_(o, non_blocking=True)
+            e += g.nnz * lpa.lpa_graph_props_get(h)["sweeps_total"]   # waits for the device
+            lpa.lpa_graph_destroy(h)
+        return e
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_edges = sum(e2e_step() for _ in range(args.e2e_steps))
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        u = torch.tensor([e2e_edges], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        e2e_edges = float(u.item())
+
+    # roofline: event-timed profiled runs, same kernels and launch shapes
+    roofline, kernels = None, None
+    hbm, hbm_kind = peaks()
+    if not args.no_profile:
+        agg = {}
+        for g, h, o in zip(graphs, handles, outs):
+            wbytes = 0 if g.w is None else 4
+            for m in MODES:
+                _, prof = lpa.lpa_run_profiled(h, m, TAU, MAX_ITERS, o, stream)
+                for b, d in kernel_bytes(prof.as_dict(), wbytes, m == "sync").items():
+                    a = agg.setdefault(b, {"bytes": 0.0, "ms": 0.0, "launches": 0})
+                    for k in a:
+                        a[k] += d[k]
+        kernels = {}
+        for b, a in agg.items():
+            if a["launches"] and a["ms"] > 0:
+                kernels[f"k_sweep_{b}"] = {"launches_per_step": a["launches"], "ms_per_step": a["ms"],
+                                           "GB_per_s": a["bytes"] / (a["ms"] / 1e3) / 1e9,
+                                           "bytes_per_launch": a["bytes"] / a["launches"]}
+        dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+        d = kernels[dom]
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": d["GB_per_s"], "peak": hbm, "unit": "GB/s",
+                    "frac": d["GB_per_s"] / hbm, "peak_kind": hbm_kind, "traffic": None,
+                    "bytes_per_launch": d["bytes_per_launch"],
+                    "mean_launch_ms": d["ms_per_step"] / d["launches_per_step"]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pairs = [(gi, m) for gi in range(len(graphs)) for m in MODES]
+        e, s = oracle_sample(graphs, pairs + pairs)
+        cpu = {"value": e / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "CPU oracle, one sweep of each (graph, mode) pair of the workload, twice "
+                         f"({s:.1f} s of single-thread CPU work)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+                "config": {"workload": WORKLOAD_TEXT[args.workload], "inputs_larger_than_l2": True,
+                           "parallelism": f"replicas x{world}", "tau": TAU, "max_iters": MAX_ITERS},
+                "touched_edges_per_s": touched / (ms / 1e3),
+                "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
+                "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline, "kernels": kernels,
+                "cpu_baseline": cpu, "per_run": per_run}
+        print(json.dumps(line), flush=True)
+    for h in handles:
+        lpa.lpa_graph_destroy(h)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -86,12 +86,16 @@ typedef struct {
     int64_t nnz;           /* stored CSR entries */
     int32_t num_graphs;    /* 1 for lpa_graph_t */
     int32_t weighted;      /* 0: unit weights (weights == NULL at create) */
-    int32_t exact;         /* 1: all weights are integers and every weighted degree is < 2^24,
-                              so every per-label sum is exact and LPA_MODE_SYNC is bit-exact
-                              against an exact-arithmetic reference */
+    int32_t exact;         /* 1: every per-label sum is computed exactly, so LPA_MODE_SYNC is
+                              bit-exact against an exact-arithmetic reference: all weights are
+                              integers (or unit) and every weighted degree is < 2^31 (the
+                              library's own copy, summed in 32-bit integers) or < 2^24
+                              (borrowed weights, summed in fp32) */
     int32_t reserved;
     int64_t max_degree;
     int64_t device_bytes;  /* device memory the handle holds */
+    int64_t sweeps_total;  /* sweeps run on this handle since creation (all runs) */
+    int64_t scanned_total; /* CSR entries scanned by those sweeps */
 } lpa_graph_props;
 
 /* Launch parameters of the sweep.  Vertices are binned by degree d:
@@ -118,6 +122,7 @@ typedef struct {
     int64_t bin_vertices[LPA_MAX_RECORDED_ITERS][3];
     int64_t bin_entries[LPA_MAX_RECORDED_ITERS][3];
     int64_t bin_changed[LPA_MAX_RECORDED_ITERS][3];
+    int64_t bin_changed_entries[LPA_MAX_RECORDED_ITERS][3];  /* CSR entries of the changed vertices */
 } lpa_profile;
 
 typedef struct lpa_graph  *lpa_graph_t;
@@ -154,7 +159,8 @@ lpa_status lpa_graph_create(int64_t n, int64_t nnz, const int64_t *offsets, cons
 
 lpa_status lpa_graph_destroy(lpa_graph_t g);
 
-/* Properties of a handle (host struct, filled synchronously). */
+/* Properties of a handle (host struct).  Waits for all work on the device
+ * (cudaDeviceSynchronize) so that the cumulative counters are current. */
 lpa_status lpa_graph_props_get(lpa_graph_t g, lpa_graph_props *out);
 
 /* Read or replace the degree-bin launch parameters (see lpa_config). */

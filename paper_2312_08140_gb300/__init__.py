@@ -59,7 +59,8 @@ class LpaRunInfo(ctypes.Structure):
 class LpaGraphProps(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("num_graphs", ctypes.c_int32),
                 ("weighted", ctypes.c_int32), ("exact", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("sweeps_total", ctypes.c_int64), ("scanned_total", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -77,7 +78,7 @@ class LpaProfile(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32), ("init_ms", ctypes.c_float),
                 ("finish_ms", ctypes.c_float * _H), ("sweep_ms", (ctypes.c_float * 3) * _H),
                 ("bin_vertices", (ctypes.c_int64 * 3) * _H), ("bin_entries", (ctypes.c_int64 * 3) * _H),
-                ("bin_changed", (ctypes.c_int64 * 3) * _H)]
+                ("bin_changed", (ctypes.c_int64 * 3) * _H), ("bin_changed_entries", (ctypes.c_int64 * 3) * _H)]
 
     def as_dict(self):
         it = min(self.iterations, _H)
@@ -86,7 +87,8 @@ class LpaProfile(ctypes.Structure):
                 "sweep_ms": [list(self.sweep_ms[t]) for t in range(it)],
                 "bin_vertices": [list(self.bin_vertices[t]) for t in range(it)],
                 "bin_entries": [list(self.bin_entries[t]) for t in range(it)],
-                "bin_changed": [list(self.bin_changed[t]) for t in range(it)]}
+                "bin_changed": [list(self.bin_changed[t]) for t in range(it)],
+                "bin_changed_entries": [list(self.bin_changed_entries[t]) for t in range(it)]}
 
 
 class LpaError(RuntimeError):

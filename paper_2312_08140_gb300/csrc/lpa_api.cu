@@ -462,6 +462,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
                 prof->bin_vertices[t][b] = c.hist_bin_vertices[t][b];
                 prof->bin_entries[t][b] = c.hist_bin_entries[t][b];
                 prof->bin_changed[t][b] = c.hist_bin_changed[t][b];
+                prof->bin_changed_entries[t][b] = c.hist_bin_changed_entries[t][b];
             }
             LPA_P(cudaEventElapsedTime(&ms, ev[3], ev[4]));
             prof->finish_ms[t] = ms;
@@ -504,8 +505,13 @@ lpa_status engine_modularity(Engine& E, int64_t v0, int64_t v1, const int32_t* l
     return LPA_OK;
 }
 
-void fill_props(const Engine& E, lpa_graph_props* p) {
+lpa_status fill_props(const Engine& E, lpa_graph_props* p) {
+    Ctrl c;
+    LPA_CUDA(cudaDeviceSynchronize());
+    LPA_CUDA(cudaMemcpy(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
     memset(p, 0, sizeof(*p));
+    p->sweeps_total = c.total_sweeps;
+    p->scanned_total = c.total_scanned;
     p->n = E.s.N;
     p->nnz = E.s.E;
     p->num_graphs = E.s.G;
@@ -513,6 +519,7 @@ void fill_props(const Engine& E, lpa_graph_props* p) {
     p->exact = E.exact ? 1 : 0;
     p->max_degree = E.max_degree;
     p->device_bytes = E.device_bytes + (E.spill_keys ? E.hub_blocks * E.s.spill_slots * 8 : 0);
+    return LPA_OK;
 }
 
 }  // namespace
@@ -573,8 +580,7 @@ lpa_status lpa_graph_destroy(lpa_graph_t g) {
 
 lpa_status lpa_graph_props_get(lpa_graph_t g, lpa_graph_props* out) {
     if (!g || !out) return fail(LPA_ERR_INVALID_ARG, "NULL argument");
-    fill_props(g->e, out);
-    return LPA_OK;
+    return fill_props(g->e, out);
 }
 
 lpa_status lpa_graph_get_config(lpa_graph_t g, lpa_config* out) {
@@ -710,8 +716,7 @@ lpa_status lpa_batch_destroy(lpa_batch_t b) {
 
 lpa_status lpa_batch_props_get(lpa_batch_t b, lpa_graph_props* out) {
     if (!b || !out) return fail(LPA_ERR_INVALID_ARG, "NULL argument");
-    fill_props(b->e, out);
-    return LPA_OK;
+    return fill_props(b->e, out);
 }
 
 lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, float tolerance, int32_t max_iters, int32_t* labels_out,

@@ -57,6 +57,7 @@ __global__ void k_init(DevState s) {
             c->hist_bin_vertices[q][b] = 0;
             c->hist_bin_entries[q][b] = 0;
             c->hist_bin_changed[q][b] = 0;
+            c->hist_bin_changed_entries[q][b] = 0;
         }
     }
     if (tid == 0) {
@@ -167,20 +168,25 @@ __device__ void control_step(const DevState& s, int mode, cudaGraphConditionalHa
     }
     any = __syncthreads_or(any);
     if (threadIdx.x == 0) {
+        long long act = 0, scn = 0, che = 0;
+        for (int b = 0; b < kBins; ++b) {
+            act += vc->bin_cnt[cur][b];
+            scn += (long long)vc->bin_entries[cur][b];
+            che += (long long)vc->bin_changed_entries[b];
+        }
         if (t < kMaxHist) {
-            long long act = 0, scn = 0, che = 0;
             for (int b = 0; b < kBins; ++b) {
                 c->hist_bin_vertices[t][b] = vc->bin_cnt[cur][b];
                 c->hist_bin_entries[t][b] = (long long)vc->bin_entries[cur][b];
                 c->hist_bin_changed[t][b] = (long long)vc->bin_changed[b];
-                act += vc->bin_cnt[cur][b];
-                scn += (long long)vc->bin_entries[cur][b];
-                che += (long long)vc->bin_changed_entries[b];
+                c->hist_bin_changed_entries[t][b] = (long long)vc->bin_changed_entries[b];
             }
             c->hist_active[t] = act;
             c->hist_scanned[t] = scn;
             c->hist_changed_entries[t] = che;
         }
+        c->total_sweeps += 1;
+        c->total_scanned += scn;
         for (int b = 0; b < kBins; ++b) {
             c->bin_changed[b] = 0;
             c->bin_changed_entries[b] = 0;

@@ -46,6 +46,9 @@ struct Ctrl {
     long long hist_bin_entries[kMaxHist][kBins];
     long long hist_bin_changed[kMaxHist][kBins];
     long long hist_changed_entries[kMaxHist];
+    long long hist_bin_changed_entries[kMaxHist][kBins];
+    long long total_sweeps;              // cumulative over all runs (never reset)
+    long long total_scanned;
 };
 
 // Everything a kernel needs, passed by value.

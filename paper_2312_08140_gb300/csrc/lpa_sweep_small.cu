@@ -7,6 +7,14 @@
 // smallest label id (Section 4.1.5).  When the label changes the thread marks
 // all other neighbours unprocessed (vertex pruning, Section 4.1.4).
 //
+// Asynchronous mode: each thread takes a run of kAsyncRun consecutive
+// frontier entries and processes them one after another, so a vertex reads the
+// labels its predecessors in the run have just written -- the GPU counterpart
+// of the paper's threads walking contiguous chunks of vertices (Section 4.1,
+// 4.1.1).  One vertex per thread would make every thread of a sweep read the
+// labels left by the previous sweep, which turns the sweep into a Jacobi
+// update that oscillates on bipartite structure such as lattices.
+//
 // Memory per vertex: two offsets, d indices, d weights, d label gathers, one
 // own-label load; on change one label write and d flag bytes.
 #include "lpa_device.cuh"
@@ -15,6 +23,7 @@ namespace lpa {
 
 constexpr int kSmallMaxD = 8;
 constexpr int kSmallThreads = 256;
+constexpr int kAsyncRun = 32;
 
 template <bool ASYNC, int WK, bool BATCH>
 __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int flag_neighbours) {
@@ -23,9 +32,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
     const unsigned cnt = s.ctrl->bin_cnt[buf][0];
     const int32_t* __restrict__ list = s.list[0];
     const unsigned stride = gridDim.x * blockDim.x;
-    for (unsigned base = blockIdx.x * blockDim.x; base < cnt; base += stride) {
-        const unsigned k = base + threadIdx.x;
-        bool act = k < cnt;
+    constexpr int RUN = ASYNC ? kAsyncRun : 1;
+    const unsigned nruns = (cnt + RUN - 1) / RUN;
+    for (unsigned rbase = blockIdx.x * blockDim.x; rbase < nruns; rbase += stride)
+    for (int step = 0; step < RUN; ++step) {
+        const unsigned run = rbase + threadIdx.x;
+        const unsigned k = run * RUN + step;
+        bool act = run < nruns && k < cnt;
         int32_t v = act ? list[k] : 0;
         if constexpr (BATCH) {
             if (act && s.done[s.gid[v]]) act = false;
