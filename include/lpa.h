@@ -102,13 +102,21 @@ typedef struct {
  *   d <= small_max          one thread per vertex, labels and weights in registers
  *   small_max < d <= warp_max  one warp per vertex, per-warp shared-memory table
  *   d > warp_max            one block per vertex, shared-memory table with a global spill table
+ * A sweep is "dense" (every vertex with an entry is scanned, no frontier
+ * compaction) when the changed vertices of the previous sweep hold at least
+ * dense_permille / 1000 of all entries; the first sweep is always dense
+ * (Algorithm 1 starts with every vertex unprocessed); 1001 = never otherwise.
+ * Scanning a vertex whose neighbours did not change never changes its label
+ * in LPA_MODE_SYNC, so this choice affects speed only.
  * lpa_graph_set_config validates: 1 <= small_max <= 8, small_max < warp_max <= 1024,
- * hub_threads in {128, 256, 512, 1024}, hub_slots a power of two in [1024, 16384]. */
+ * hub_threads in {128, 256, 512, 1024}, hub_slots a power of two in [1024, 16384],
+ * 0 <= dense_permille <= 1001. */
 typedef struct {
     int32_t small_max;
     int32_t warp_max;
     int32_t hub_threads;
     int32_t hub_slots;
+    int32_t dense_permille;
 } lpa_config;
 
 /* Time per phase of one run, from CUDA events recorded around every launch

@@ -68,7 +68,8 @@ class LpaGraphProps(ctypes.Structure):
 
 class LpaConfig(ctypes.Structure):
     _fields_ = [("small_max", ctypes.c_int32), ("warp_max", ctypes.c_int32),
-                ("hub_threads", ctypes.c_int32), ("hub_slots", ctypes.c_int32)]
+                ("hub_threads", ctypes.c_int32), ("hub_slots", ctypes.c_int32),
+                ("dense_permille", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

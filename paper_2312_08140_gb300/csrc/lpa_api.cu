@@ -62,7 +62,7 @@ struct Engine {
     bool exact = false;
     int64_t max_degree = 0;
     int64_t device_bytes = 0;
-    lpa_config cfg{8, 512, 512, 8192};
+    lpa_config cfg{8, 512, 512, 8192, 500};
     int hub_blocks = 0;
     int32_t* spill_keys = nullptr;
     void* spill_vals = nullptr;
@@ -148,6 +148,7 @@ void apply_config_fields(Engine& E) {
     E.s.warp_max = E.cfg.warp_max;
     E.s.warp_slots = (int32_t)pow2ceil(2 * (int64_t)E.cfg.warp_max);
     E.s.hub_slots = E.cfg.hub_slots;
+    E.s.dense_permille = E.cfg.dense_permille;
 }
 
 lpa_status check_config(const lpa_config& c) {
@@ -158,6 +159,8 @@ lpa_status check_config(const lpa_config& c) {
         return fail(LPA_ERR_INVALID_ARG, "hub_threads must be 128, 256, 512 or 1024");
     if (c.hub_slots < 1024 || c.hub_slots > 16384 || (c.hub_slots & (c.hub_slots - 1)))
         return fail(LPA_ERR_INVALID_ARG, "hub_slots must be a power of two in [1024, 16384]");
+    if (c.dense_permille < 0 || c.dense_permille > 1001)
+        return fail(LPA_ERR_INVALID_ARG, "dense_permille must be in [0, 1001]");
     return LPA_OK;
 }
 
@@ -256,9 +259,9 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     if ((rs = dalloc_t(E, &E.s.C, N1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.Cnew, N1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.flags, N1 + 16)) != LPA_OK) return rs;
-    for (int b = 0; b < kBins; ++b)
-        if ((rs = dalloc_t(E, &E.s.list[b], N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.chg_list, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.slist, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.flist, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.chg, N1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.ctrl, 1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.dN, (size_t)G)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.done, (size_t)G)) != LPA_OK) return rs;
@@ -270,6 +273,7 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     LPA_CUDA(cudaMemsetAsync(E.s.hist_changed, 0, (size_t)G * kMaxHist * 8, st));
     apply_config_fields(E);
     if ((rs = setup_hub(E)) != LPA_OK) return rs;
+    LPA_CUDA(build_static_lists(E.s, st));
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_top, cudaStreamNonBlocking));
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_body, cudaStreamNonBlocking));
     LPA_CUDA(cudaStreamSynchronize(st));
@@ -284,10 +288,10 @@ cudaError_t enqueue_sweep(Engine& E, int mode, cudaGraphConditionalHandle h, int
     if (err != cudaSuccess) return err;
     err = launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st);
     if (err != cudaSuccess) return err;
-    return launch_finish(E.s, 1, mode, h, in_graph, st, E.sms);
+    return launch_finish(E.s, mode, h, in_graph, st, E.sms);
 }
 
-// Graph for one mode:  init -> init_cond -> first compaction -> WHILE { sweep } -> finalize
+// Graph for one mode:  init -> init_cond -> WHILE { sweep } -> finalize
 lpa_status build_graph(Engine& E, int mode) {
     if (E.exec[mode]) return LPA_OK;
     cudaGraph_t top = nullptr;
@@ -316,7 +320,6 @@ lpa_status build_graph(Engine& E, int mode) {
     if (err != cudaSuccess) return bail(err, "begin capture (top)");
     if ((err = launch_init(E.s, E.cap_top, E.sms)) != cudaSuccess) return bail(err, "init");
     if ((err = launch_init_cond(E.s, h, 1, E.cap_top)) != cudaSuccess) return bail(err, "init_cond");
-    if ((err = launch_finish(E.s, 0, mode, h, 0, E.cap_top, E.sms)) != cudaSuccess) return bail(err, "compact");
     cudaStreamCaptureStatus cst;
     const cudaGraphNode_t* deps = nullptr;
     size_t ndeps = 0;
@@ -435,7 +438,6 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
     LPA_P(cudaEventRecord(ev[0], st));
     LPA_P(launch_init(E.s, st, E.sms));
     LPA_P(launch_init_cond(E.s, none, 0, st));
-    LPA_P(launch_finish(E.s, 0, mode, none, 0, st, E.sms));
     LPA_P(cudaEventRecord(ev[1], st));
     LPA_P(cudaEventSynchronize(ev[1]));
     LPA_P(cudaEventElapsedTime(&ms, ev[0], ev[1]));
@@ -451,7 +453,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
         LPA_P(cudaEventRecord(ev[2], st));
         LPA_P(launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st));
         LPA_P(cudaEventRecord(ev[3], st));
-        LPA_P(launch_finish(E.s, 1, mode, none, 0, st, E.sms));
+        LPA_P(launch_finish(E.s, mode, none, 0, st, E.sms));
         LPA_P(cudaEventRecord(ev[4], st));
         LPA_P(cudaEventSynchronize(ev[4]));
         LPA_P(cudaMemcpy(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
@@ -597,7 +599,10 @@ static lpa_status set_config(Engine& E, const lpa_config* cfg) {
     destroy_graphs(E);
     E.cfg = *cfg;
     apply_config_fields(E);
-    return setup_hub(E);
+    lpa_status rs2 = setup_hub(E);
+    if (rs2 != LPA_OK) return rs2;
+    LPA_CUDA(build_static_lists(E.s, 0));
+    return LPA_OK;
 }
 
 lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config* cfg) {
@@ -636,12 +641,14 @@ lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t m
     int32_t* out = nullptr;
     LPA_CUDA(cudaMalloc(&out, (size_t)E.s.N * 4));
     std::vector<lpa_config> cands;
-    const int smalls[] = {4, 6, 8};
-    const int warps[] = {128, 256, 512, 1024};
+    const int smalls[] = {4, 8};
+    const int warps[] = {128, 512, 1024};
     const int hubs[][2] = {{256, 4096}, {512, 8192}, {1024, 16384}};
+    const int denses[] = {300, 600, 1001};
     for (int sm : smalls)
         for (int wm : warps)
-            for (auto& hb : hubs) cands.push_back(lpa_config{sm, wm, hb[0], hb[1]});
+            for (auto& hb : hubs)
+                for (int dp : denses) cands.push_back(lpa_config{sm, wm, hb[0], hb[1], dp});
     cudaEvent_t e0, e1;
     LPA_CUDA(cudaEventCreate(&e0));
     LPA_CUDA(cudaEventCreate(&e1));

@@ -141,34 +141,65 @@ __device__ __forceinline__ bool table_add_bounded(int32_t* keys, T* vals, int lo
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
 
-// Per-warp bookkeeping of one processed slot per lane: dN (per graph when
-// batched), per-bin changed counts and, in sync mode, the changed list.
-// All 32 lanes must call.
-template <bool ASYNC, bool BATCH>
-__device__ __forceinline__ void account_changes(const DevState& s, int bin, bool changed, int32_t v,
-                                                int64_t deg) {
-    const unsigned lane = lane_id();
-    const unsigned m = __ballot_sync(kFull, changed);
-    if (m == 0) return;
-    const unsigned leader = __ffs(m) - 1;
-    unsigned long long deg_sum = __reduce_add_sync(kFull, changed ? (unsigned)deg : 0u);
-    if (lane == leader) {
-        atomicAdd(&s.ctrl->bin_changed[bin], (unsigned long long)__popc(m));
-        atomicAdd(&s.ctrl->bin_changed_entries[bin], deg_sum);
-    }
+// Batched runs: dN of each graph, aggregated over the lanes of a warp that
+// changed a vertex of the same graph.  All 32 lanes must call.
+template <bool BATCH>
+__device__ __forceinline__ void count_graph_changes(const DevState& s, bool changed, int32_t v) {
     if constexpr (BATCH) {
+        const unsigned m = __ballot_sync(kFull, changed);
         if (changed) {
-            int32_t g = s.gid[v];
-            unsigned peers = __match_any_sync(m, g);
-            if (lane == __ffs(peers) - 1) atomicAdd(&s.dN[g], (unsigned long long)__popc(peers));
+            const int32_t g = s.gid[v];
+            const unsigned peers = __match_any_sync(m, g);
+            if (lane_id() == (unsigned)(__ffs(peers) - 1)) atomicAdd(&s.dN[g], (unsigned long long)__popc(peers));
         }
     }
-    if constexpr (!ASYNC) {
-        unsigned base = 0;
-        if (lane == leader) base = atomicAdd(&s.ctrl->chg_cnt, (unsigned)__popc(m));
-        base = __shfl_sync(kFull, base, leader);
-        if (changed) s.chg_list[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+// Per-thread counts of changed vertices (and their CSR entries) are summed
+// over the block and added to the bin's counters with one atomic each.  All
+// threads of the block must call, once, at the end of the kernel.
+__device__ __forceinline__ void flush_bin_counts(const DevState& s, int bin, unsigned long long changed,
+                                                 unsigned long long changed_entries) {
+    __shared__ unsigned long long red[2][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        changed += __shfl_xor_sync(kFull, changed, o);
+        changed_entries += __shfl_xor_sync(kFull, changed_entries, o);
     }
+    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane_id() == 0) {
+        red[0][w] = changed;
+        red[1][w] = changed_entries;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long a = 0, b = 0;
+        for (int q = 0; q < nw; ++q) {
+            a += red[0][q];
+            b += red[1][q];
+        }
+        if (a) {
+            atomicAdd(&s.ctrl->bin_changed[bin], a);
+            atomicAdd(&s.ctrl->bin_changed_entries[bin], b);
+        }
+    }
+}
+
+// Frontier of bin b for the current sweep: the static list when the sweep is
+// dense, else the compacted list; both live in the bin's slot region.
+struct BinView {
+    const int32_t* list;   // already offset to the bin's region
+    int32_t* chg;          // sync-mode change marks, same offset
+    unsigned cnt;
+};
+
+__device__ __forceinline__ BinView bin_view(const DevState& s, int b) {
+    const int buf = s.ctrl->iter & 1;
+    BinView bv;
+    const int64_t base = s.bin_base[b];
+    bv.list = (s.ctrl->dense[buf] ? s.slist : s.flist) + base;
+    bv.chg = s.chg + base;
+    bv.cnt = s.ctrl->bin_cnt[buf][b];
+    return bv;
 }
 
 // Result write for a vertex whose label changed.

@@ -10,6 +10,8 @@
 //   k_finalize     labels out (optionally as graph-local ids)
 //   k_validate     CSR checks at graph creation, weight exactness
 //   k_mod_*        modularity, Eq. 1 (Section 3.2), in fp64
+#include <vector>
+
 #include "lpa_device.cuh"
 
 namespace lpa {
@@ -37,7 +39,7 @@ __global__ void k_init(DevState s) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = tid; i < s.N; i += stride) {
         s.C[i] = (int32_t)i;
-        s.flags[i] = (s.off[i + 1] > s.off[i]) ? 1 : 0;
+        s.flags[i] = 0;
     }
     Ctrl* c = s.ctrl;
     const int max_iters = c->max_iters;
@@ -61,13 +63,17 @@ __global__ void k_init(DevState s) {
         }
     }
     if (tid == 0) {
+        // Algorithm 1 marks every vertex unprocessed: the first sweep is dense
         c->iter = 0;
         c->error = 0;
         c->ticket = 0;
-        c->chg_cnt = 0;
+        c->dense[0] = 1;
+        c->dense[1] = 0;
         for (int b = 0; b < kBins; ++b) {
-            c->bin_cnt[0][b] = c->bin_cnt[1][b] = 0;
-            c->bin_entries[0][b] = c->bin_entries[1][b] = 0;
+            c->bin_cnt[0][b] = s.bin_static[b];
+            c->bin_entries[0][b] = s.bin_static_entries[b];
+            c->bin_cnt[1][b] = 0;
+            c->bin_entries[1][b] = 0;
             c->bin_changed[b] = 0;
             c->bin_changed_entries[b] = 0;
         }
@@ -96,50 +102,228 @@ __device__ __forceinline__ int bin_of(int64_t d, int small_max, int warp_max) {
     return d <= small_max ? 0 : (d <= warp_max ? 1 : 2);
 }
 
-// Warp-aggregated append of up to kVertsPerThread vertices per lane into the
-// three bin lists of buffer `nb`.  All 32 lanes must call.
-__device__ __forceinline__ void append_bins(const DevState& s, int nb, const int32_t (&vid)[kVertsPerThread],
-                                            const int8_t (&bin)[kVertsPerThread],
-                                            const int64_t (&deg)[kVertsPerThread]) {
+// Block-wide ordered append of up to kVertsPerThread vertices per thread into
+// the three bin regions of `list`; `cursor[b]` is the running length of bin b
+// (device counter when `atomic`, otherwise a block-private running offset kept
+// by the caller in shared memory).  Entries keep ascending thread order.  All
+// threads of the block must call.
+template <bool ATOMIC>
+__device__ __forceinline__ void block_append(const int64_t (&base)[kBins], int32_t* list, unsigned* cursor,
+                                             unsigned long long* entries, const int32_t (&vid)[kVertsPerThread],
+                                             const int8_t (&bin)[kVertsPerThread],
+                                             const int64_t (&deg)[kVertsPerThread]) {
+    __shared__ unsigned wcnt[kBins][32];
+    __shared__ unsigned long long went[kBins][32];
+    __shared__ unsigned bbase[kBins];
     const unsigned lane = lane_id();
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned cnt[kBins], excl[kBins];
 #pragma unroll
     for (int b = 0; b < kBins; ++b) {
-        unsigned cnt = 0;
+        unsigned c = 0;
         unsigned long long ent = 0;
 #pragma unroll
-        for (int q = 0; q < kVertsPerThread; ++q) {
+        for (int q = 0; q < kVertsPerThread; ++q)
             if (bin[q] == b) {
-                ++cnt;
+                ++c;
                 ent += (unsigned long long)deg[q];
             }
-        }
-        unsigned incl = cnt;
+        unsigned incl = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            unsigned y = __shfl_up_sync(kFull, incl, o);
+            const unsigned y = __shfl_up_sync(kFull, incl, o);
             if ((int)lane >= o) incl += y;
         }
-        const unsigned total = __shfl_sync(kFull, incl, 31);
-        if (total == 0) continue;
-        unsigned long long ent_sum = ent;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ent_sum += __shfl_xor_sync(kFull, ent_sum, o);
-        unsigned base = 0;
+        for (int o = 16; o > 0; o >>= 1) ent += __shfl_xor_sync(kFull, ent, o);
+        cnt[b] = c;
+        excl[b] = incl - c;
         if (lane == 31) {
-            base = atomicAdd(&s.ctrl->bin_cnt[nb][b], total);
-            atomicAdd(&s.ctrl->bin_entries[nb][b], ent_sum);
+            wcnt[b][w] = incl;
+            went[b][w] = ent;
         }
-        base = __shfl_sync(kFull, base, 31) + incl - cnt;
-        int32_t* list = s.list[b];
+    }
+    __syncthreads();
+    if (threadIdx.x < kBins) {
+        const int b = threadIdx.x;
+        unsigned run = 0;
+        unsigned long long ent = 0;
+        for (int q = 0; q < nw; ++q) {
+            const unsigned x = wcnt[b][q];
+            wcnt[b][q] = run;
+            run += x;
+            ent += went[b][q];
+        }
+        if (ATOMIC) {
+            bbase[b] = run ? atomicAdd(&cursor[b], run) : 0u;
+            if (run) atomicAdd(&entries[b], ent);
+        } else {
+            bbase[b] = cursor[b];
+            cursor[b] += run;
+            entries[b] += ent;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) {
+        unsigned pos = bbase[b] + wcnt[b][w] + excl[b];
+        if (cnt[b] == 0) continue;
+        int32_t* out = list + base[b];
+#pragma unroll
+        for (int q = 0; q < kVertsPerThread; ++q)
+            if (bin[q] == b) out[pos++] = vid[q];
+    }
+    __syncthreads();
+}
+
+// Loads the flags of vertices [v0, v0 + kVertsPerThread) (zeros past N) and
+// clears them when `clear`.  Returns true if any is set.
+__device__ __forceinline__ bool load_flags(uint8_t* flags, int64_t N, int64_t v0, bool clear,
+                                           uint8_t (&f)[kVertsPerThread]) {
+    bool anyf = false;
+    if (v0 + kVertsPerThread <= N) {
+        uint4 raw = *reinterpret_cast<const uint4*>(flags + v0);
+        const uint8_t* pb = reinterpret_cast<const uint8_t*>(&raw);
+#pragma unroll
+        for (int q = 0; q < kVertsPerThread; ++q) f[q] = pb[q];
+        anyf = (raw.x | raw.y | raw.z | raw.w) != 0;
+        if (anyf && clear) *reinterpret_cast<uint4*>(flags + v0) = make_uint4(0, 0, 0, 0);
+    } else {
 #pragma unroll
         for (int q = 0; q < kVertsPerThread; ++q) {
-            if (bin[q] == b) list[base++] = vid[q];
+            f[q] = (v0 + q < N) ? flags[v0 + q] : 0;
+            anyf |= f[q] != 0;
+        }
+        if (anyf && clear)
+            for (int q = 0; q < kVertsPerThread; ++q)
+                if (v0 + q < N) flags[v0 + q] = 0;
+    }
+    return anyf;
+}
+
+// ------------------------------------------------------------ static lists --
+// Every vertex with at least one entry, grouped by degree bin, ascending.
+// Two passes over blocks of 4096 vertices: count, then ordered scatter from
+// per-block bases computed on the host.
+constexpr int kStaticChunk = kFrontThreads * kVertsPerThread;
+
+__device__ __forceinline__ void static_chunk(const DevState& s, int64_t v0, int32_t (&vid)[kVertsPerThread],
+                                             int8_t (&bin)[kVertsPerThread], int64_t (&deg)[kVertsPerThread]) {
+#pragma unroll
+    for (int q = 0; q < kVertsPerThread; ++q) {
+        const int64_t v = v0 + q;
+        vid[q] = (int32_t)v;
+        bin[q] = -1;
+        deg[q] = 0;
+        if (v < s.N) {
+            const int64_t d = s.off[v + 1] - s.off[v];
+            if (d > 0) {
+                deg[q] = d;
+                bin[q] = (int8_t)bin_of(d, s.small_max, s.warp_max);
+            }
         }
     }
 }
 
+__global__ void __launch_bounds__(kFrontThreads) k_static_count(DevState s, unsigned* counts,
+                                                                 unsigned long long* ents) {
+    const int64_t v0 = (int64_t)blockIdx.x * kStaticChunk + (int64_t)threadIdx.x * kVertsPerThread;
+    int32_t vid[kVertsPerThread];
+    int8_t bin[kVertsPerThread];
+    int64_t deg[kVertsPerThread];
+    static_chunk(s, v0, vid, bin, deg);
+    __shared__ unsigned c[kBins];
+    __shared__ unsigned long long e[kBins];
+    if (threadIdx.x < kBins) {
+        c[threadIdx.x] = 0;
+        e[threadIdx.x] = 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kVertsPerThread; ++q)
+        if (bin[q] >= 0) {
+            atomicAdd(&c[bin[q]], 1u);
+            atomicAdd(&e[bin[q]], (unsigned long long)deg[q]);
+        }
+    __syncthreads();
+    if (threadIdx.x < kBins) {
+        counts[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = c[threadIdx.x];
+        ents[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = e[threadIdx.x];
+    }
+}
+
+__global__ void __launch_bounds__(kFrontThreads) k_static_scatter(DevState s, const unsigned* block_base) {
+    const int64_t v0 = (int64_t)blockIdx.x * kStaticChunk + (int64_t)threadIdx.x * kVertsPerThread;
+    int32_t vid[kVertsPerThread];
+    int8_t bin[kVertsPerThread];
+    int64_t deg[kVertsPerThread];
+    static_chunk(s, v0, vid, bin, deg);
+    __shared__ unsigned cursor[kBins];
+    __shared__ unsigned long long ent[kBins];
+    if (threadIdx.x < kBins) {
+        cursor[threadIdx.x] = block_base[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+        ent[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    block_append<false>(s.bin_base, s.slist, cursor, ent, vid, bin, deg);
+}
+
+cudaError_t build_static_lists(DevState& s, cudaStream_t st) {
+    const int64_t nblk = (s.N + kStaticChunk - 1) / kStaticChunk;
+    for (int b = 0; b < kBins; ++b) {
+        s.bin_base[b] = 0;
+        s.bin_static[b] = 0;
+        s.bin_static_entries[b] = 0;
+    }
+    s.active_entries = 0;
+    if (nblk == 0) return cudaSuccess;
+    unsigned* counts = nullptr;
+    unsigned long long* ents = nullptr;
+    cudaError_t err = cudaMalloc(&counts, (size_t)nblk * kBins * sizeof(unsigned));
+    if (err != cudaSuccess) return err;
+    err = cudaMalloc(&ents, (size_t)nblk * kBins * sizeof(unsigned long long));
+    if (err != cudaSuccess) {
+        cudaFree(counts);
+        return err;
+    }
+    std::vector<unsigned> hc((size_t)nblk * kBins);
+    std::vector<unsigned long long> he((size_t)nblk * kBins);
+    k_static_count<<<(unsigned)nblk, kFrontThreads, 0, st>>>(s, counts, ents);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaMemcpyAsync(hc.data(), counts, hc.size() * 4, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(he.data(), ents, he.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err == cudaSuccess) {
+        int64_t base = 0;
+        for (int b = 0; b < kBins; ++b) {
+            s.bin_base[b] = base;
+            unsigned run = 0;
+            unsigned long long e = 0;
+            for (int64_t k = 0; k < nblk; ++k) {
+                const unsigned x = hc[(size_t)b * nblk + k];
+                hc[(size_t)b * nblk + k] = run;
+                run += x;
+                e += he[(size_t)b * nblk + k];
+            }
+            s.bin_static[b] = run;
+            s.bin_static_entries[b] = e;
+            s.active_entries += (int64_t)e;
+            base += run;
+        }
+        err = cudaMemcpyAsync(counts, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice, st);
+    }
+    if (err == cudaSuccess) {
+        k_static_scatter<<<(unsigned)nblk, kFrontThreads, 0, st>>>(s, counts);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    cudaFree(counts);
+    cudaFree(ents);
+    return err;
+}
+
 // Control step run by the last block of k_finish after sweep t = ctrl->iter.
-__device__ void control_step(const DevState& s, int mode, cudaGraphConditionalHandle h, int in_graph) {
+__device__ void control_step(const DevState& s, int dense_next, cudaGraphConditionalHandle h, int in_graph) {
     Ctrl* c = s.ctrl;
     volatile Ctrl* vc = c;
     const int t = vc->iter;
@@ -155,7 +339,7 @@ __device__ void control_step(const DevState& s, int mode, cudaGraphConditionalHa
             if (t < kMaxHist) s.hist_changed[g * kMaxHist + t] = (long long)dn;
             s.iters[g] = t + 1;
             const int64_t ng = s.vtx_off[g + 1] - s.vtx_off[g];
-            if ((double)dn / (double)ng <= tau) {
+            if ((double)dn / (double)ng <= tau) {            // Algorithm 1: dN / N <= tau
                 s.done[g] = 1;
                 s.exit_reason[g] = 0;
             } else if (t + 1 >= max_iters) {
@@ -190,15 +374,14 @@ __device__ void control_step(const DevState& s, int mode, cudaGraphConditionalHa
         for (int b = 0; b < kBins; ++b) {
             c->bin_changed[b] = 0;
             c->bin_changed_entries[b] = 0;
-            if (mode == MODE_SYNC_FULL) {
-                c->bin_cnt[nb][b] = vc->bin_cnt[cur][b];
-                c->bin_entries[nb][b] = vc->bin_entries[cur][b];
-            } else {
-                c->bin_cnt[cur][b] = 0;
-                c->bin_entries[cur][b] = 0;
+            if (dense_next) {
+                c->bin_cnt[nb][b] = s.bin_static[b];
+                c->bin_entries[nb][b] = s.bin_static_entries[b];
             }
+            c->bin_cnt[cur][b] = 0;
+            c->bin_entries[cur][b] = 0;
         }
-        c->chg_cnt = 0;
+        c->dense[nb] = dense_next;
         c->iter = t + 1;
         c->any_active = any;
         c->ticket = 0;
@@ -207,49 +390,54 @@ __device__ void control_step(const DevState& s, int mode, cudaGraphConditionalHa
     }
 }
 
-// phase 0: first compaction (after k_init), no control.
-// phase 1: after sweep t: apply (sync modes), compact into buffer (t+1)&1, control.
-__global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int phase, int mode,
-                                                           cudaGraphConditionalHandle h, int in_graph) {
+// After sweep t: (1) sync modes apply the marked changes C[v] = Cnew[v];
+// (2) the next sweep is dense (static lists, every vertex) when the entries
+// of the changed vertices reach dense_permille of all entries -- then the
+// flags are simply cleared -- else the flags are compacted into per-bin
+// frontier lists; (3) the last block runs the control step.
+__global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, cudaGraphConditionalHandle h,
+                                                           int in_graph) {
     const int t = s.ctrl->iter;
-    const int nb = phase == 0 ? 0 : ((t + 1) & 1);
+    const int cur = t & 1, nb = (t + 1) & 1;
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned gstride = gridDim.x * blockDim.x;
 
-    if (phase == 1 && mode != MODE_ASYNC) {
-        const unsigned nchg = s.ctrl->chg_cnt;
-        for (unsigned k = gtid; k < nchg; k += gstride) {
-            const int32_t v = s.chg_list[k];
-            s.C[v] = s.Cnew[v];
+    if (mode != MODE_ASYNC) {
+        for (int b = 0; b < kBins; ++b) {
+            const unsigned cnt = s.ctrl->bin_cnt[cur][b];
+            const int32_t* chg = s.chg + s.bin_base[b];
+            for (unsigned k = gtid; k < cnt; k += gstride) {
+                const int32_t v = chg[k];
+                if (v >= 0) s.C[v] = s.Cnew[v];
+            }
         }
     }
 
-    if (phase == 0 || mode != MODE_SYNC_FULL) {
-        const int64_t nchunks = (s.N + kVertsPerThread - 1) / kVertsPerThread;
+    unsigned long long che = 0;
+    for (int b = 0; b < kBins; ++b) che += ((volatile Ctrl*)s.ctrl)->bin_changed_entries[b];
+    const int dense = mode == MODE_SYNC_FULL ||
+                      (double)che * 1000.0 >= (double)s.dense_permille * (double)s.active_entries;
+
+    const int64_t nchunks = (s.N + kVertsPerThread - 1) / kVertsPerThread;
+    if (dense) {
+        if (mode != MODE_SYNC_FULL) {
+            for (int64_t ch = gtid; ch < nchunks; ch += gstride) {
+                const int64_t v0 = ch * kVertsPerThread;
+                if (v0 + kVertsPerThread <= s.N) {
+                    *reinterpret_cast<uint4*>(s.flags + v0) = make_uint4(0, 0, 0, 0);
+                } else {
+                    for (int64_t v = v0; v < s.N; ++v) s.flags[v] = 0;
+                }
+            }
+        }
+    } else {
         for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nchunks; base += gstride) {
             const int64_t ch = base + threadIdx.x;
             const int64_t v0 = ch * kVertsPerThread;
             uint8_t f[kVertsPerThread];
             bool anyf = false;
             if (ch < nchunks) {
-                if (v0 + kVertsPerThread <= s.N) {
-                    uint4 raw = *reinterpret_cast<const uint4*>(s.flags + v0);
-                    const uint8_t* pb = reinterpret_cast<const uint8_t*>(&raw);
-#pragma unroll
-                    for (int q = 0; q < kVertsPerThread; ++q) f[q] = pb[q];
-                    anyf = (raw.x | raw.y | raw.z | raw.w) != 0;
-                    if (anyf) *reinterpret_cast<uint4*>(s.flags + v0) = make_uint4(0, 0, 0, 0);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < kVertsPerThread; ++q) {
-                        f[q] = (v0 + q < s.N) ? s.flags[v0 + q] : 0;
-                        anyf |= f[q] != 0;
-                    }
-                    if (anyf) {
-                        for (int q = 0; q < kVertsPerThread; ++q)
-                            if (v0 + q < s.N) s.flags[v0 + q] = 0;
-                    }
-                }
+                anyf = load_flags(s.flags, s.N, v0, true, f);
             } else {
 #pragma unroll
                 for (int q = 0; q < kVertsPerThread; ++q) f[q] = 0;
@@ -264,11 +452,15 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int phase,
                 deg[q] = 0;
                 if (f[q]) {
                     const int64_t d = s.off[v0 + q + 1] - s.off[v0 + q];
-                    deg[q] = d;
-                    bin[q] = (int8_t)bin_of(d, s.small_max, s.warp_max);
+                    if (d > 0) {
+                        deg[q] = d;
+                        bin[q] = (int8_t)bin_of(d, s.small_max, s.warp_max);
+                    }
                 }
             }
-            if (__any_sync(kFull, anyf)) append_bins(s, nb, vid, bin, deg);
+            if (__syncthreads_or(anyf))
+                block_append<true>(s.bin_base, s.flist, s.ctrl->bin_cnt[nb], s.ctrl->bin_entries[nb], vid, bin,
+                                   deg);
         }
     }
 
@@ -283,16 +475,12 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int phase,
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    if (phase == 1) {
-        control_step(s, mode, h, in_graph);
-    } else if (threadIdx.x == 0) {
-        s.ctrl->ticket = 0;
-    }
+    control_step(s, dense, h, in_graph);
 }
 
-cudaError_t launch_finish(const DevState& s, int phase, int mode, cudaGraphConditionalHandle h, int in_graph,
+cudaError_t launch_finish(const DevState& s, int mode, cudaGraphConditionalHandle h, int in_graph,
                           cudaStream_t st, int sms) {
-    k_finish<<<sms * 4, kFrontThreads, 0, st>>>(s, phase, mode, h, in_graph);
+    k_finish<<<sms * 4, kFrontThreads, 0, st>>>(s, mode, h, in_graph);
     return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ struct Ctrl {
     int32_t local_ids;                   // finalize writes label - first vertex of its graph
     int32_t error;                       // non-zero: a device-side check failed
     unsigned int ticket;                 // last-block election in the finish kernel
-    unsigned int chg_cnt;                // sync mode: entries in the changed list
+    int32_t dense[2];                    // sweep reads the static bin lists (all vertices), by t & 1
     unsigned int bin_cnt[2][kBins];      // frontier list lengths, double-buffered by t & 1
     unsigned long long bin_entries[2][kBins];   // CSR entries of those vertices
     unsigned long long bin_changed[kBins];      // vertices changed in the current sweep, per bin
@@ -65,8 +65,13 @@ struct DevState {
     int32_t* C;                // [N] labels (global ids)
     int32_t* Cnew;             // [N] sync mode: next labels of changed vertices
     uint8_t* flags;            // [N] 1 = unprocessed (Algorithm 1)
-    int32_t* list[kBins];      // frontier lists, capacity N each
-    int32_t* chg_list;         // [N] sync mode: vertices changed in this sweep
+    int32_t* slist;            // [N] static lists: vertices with an entry, by bin, ascending
+    int32_t* flist;            // [N] frontier lists of the sparse sweeps, same bin regions
+    int32_t* chg;              // [N] sync mode, aligned with list slots: vertex if changed, else -1
+    int64_t bin_base[kBins];   // first slot of each bin's region in slist / flist / chg
+    unsigned int bin_static[kBins];            // vertices of each bin (static list lengths)
+    unsigned long long bin_static_entries[kBins];
+    int64_t active_entries;    // entries of all vertices with an entry (= E)
     Ctrl* ctrl;
     unsigned long long* dN;    // [G] changed vertices of the current sweep
     int32_t* done;             // [G]
@@ -80,6 +85,7 @@ struct DevState {
     int32_t warp_max;
     int32_t warp_slots;        // per-warp table slots = next pow2 >= 2 * warp_max
     int32_t hub_slots;         // per-block shared table slots
+    int32_t dense_permille;    // dense sweep when entries of changed vertices >= this / 1000 of E
 };
 
 // ---- launchers (return cudaSuccess or the launch error) ------------------
@@ -90,9 +96,12 @@ struct LaunchShape {
 };
 
 cudaError_t launch_init(const DevState& s, cudaStream_t st, int sms);
+// Static bin lists (slist, bin_base, bin_static*, active_entries) from the
+// degrees and the bin limits in s.  Synchronises `st`.
+cudaError_t build_static_lists(DevState& s, cudaStream_t st);
 cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st);
-cudaError_t launch_finish(const DevState& s, int phase, int mode, cudaGraphConditionalHandle h,
-                          int in_graph, cudaStream_t st, int sms);
+cudaError_t launch_finish(const DevState& s, int mode, cudaGraphConditionalHandle h, int in_graph,
+                          cudaStream_t st, int sms);
 cudaError_t launch_finalize(const DevState& s, cudaStream_t st, int sms);
 cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int32_t* labels_out,
                               int local_ids, cudaStream_t st);

@@ -41,13 +41,16 @@ __global__ void k_sweep_hub(DevState s, int flag_neighbours) {
     T* gvals = s.spill_keys ? static_cast<T*>(s.spill_vals) + (size_t)blockIdx.x * s.spill_slots : nullptr;
     __syncthreads();
 
-    const int buf = s.ctrl->iter & 1;
-    const unsigned cnt = s.ctrl->bin_cnt[buf][2];
-    const int32_t* __restrict__ list = s.list[2];
+    const BinView bv = bin_view(s, 2);
+    const unsigned cnt = bv.cnt;
+    unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned k = blockIdx.x; k < cnt; k += gridDim.x) {
-        const int32_t v = list[k];
+        const int32_t v = bv.list[k];
         if constexpr (BATCH) {
-            if (s.done[s.gid[v]]) continue;     // block-uniform
+            if (s.done[s.gid[v]]) {             // block-uniform
+                if (!ASYNC && threadIdx.x == 0) bv.chg[k] = -1;
+                continue;
+            }
         }
         const int64_t st = s.off[v];
         const int64_t en = s.off[v + 1];
@@ -147,7 +150,11 @@ __global__ void k_sweep_hub(DevState s, int flag_neighbours) {
             changed = best_lab != own;
         }
         if (changed) {                                // block-uniform
-            if (threadIdx.x == 0) write_label<ASYNC>(s, v, best_lab);
+            if (threadIdx.x == 0) {
+                write_label<ASYNC>(s, v, best_lab);
+                ++my_changed;
+                my_changed_entries += (unsigned long long)d;
+            }
             if (flag_neighbours) {
                 for (int64_t e = st + threadIdx.x; e < en; e += blockDim.x) {
                     const int32_t j = s.idx[e];
@@ -155,9 +162,15 @@ __global__ void k_sweep_hub(DevState s, int flag_neighbours) {
                 }
             }
         }
-        if (wib == 0) account_changes<ASYNC, BATCH>(s, 2, changed && lane == 0, v, d);
+        if (threadIdx.x == 0) {
+            if constexpr (!ASYNC) bv.chg[k] = changed ? v : -1;
+            if constexpr (BATCH) {
+                if (changed) atomicAdd(&s.dN[s.gid[v]], 1ull);
+            }
+        }
         __syncthreads();    // tables clear and `winner` consumed before the next vertex
     }
+    flush_bin_counts(s, 2, my_changed, my_changed_entries);
 }
 
 int hub_blocks_for(int sms, int hub_threads, int hub_slots) {

@@ -21,25 +21,25 @@
 
 namespace lpa {
 
-constexpr int kSmallMaxD = 8;
 constexpr int kSmallThreads = 256;
 constexpr int kAsyncRun = 32;
 
-template <bool ASYNC, int WK, bool BATCH>
+template <bool ASYNC, int WK, bool BATCH, int MAXD>
 __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
-    const int buf = s.ctrl->iter & 1;
-    const unsigned cnt = s.ctrl->bin_cnt[buf][0];
-    const int32_t* __restrict__ list = s.list[0];
+    const BinView bv = bin_view(s, 0);
+    const unsigned cnt = bv.cnt;
     const unsigned stride = gridDim.x * blockDim.x;
     constexpr int RUN = ASYNC ? kAsyncRun : 1;
     const unsigned nruns = (cnt + RUN - 1) / RUN;
+    unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned rbase = blockIdx.x * blockDim.x; rbase < nruns; rbase += stride)
     for (int step = 0; step < RUN; ++step) {
         const unsigned run = rbase + threadIdx.x;
         const unsigned k = run * RUN + step;
-        bool act = run < nruns && k < cnt;
-        int32_t v = act ? list[k] : 0;
+        const bool slot = run < nruns && k < cnt;
+        bool act = slot;
+        const int32_t v = slot ? bv.list[k] : 0;
         if constexpr (BATCH) {
             if (act && s.done[s.gid[v]]) act = false;
         }
@@ -49,13 +49,13 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
             st = s.off[v];
             d = (int)(s.off[v + 1] - st);
         }
-        int32_t nb[kSmallMaxD];
-        int32_t lab[kSmallMaxD];
-        T wt[kSmallMaxD];
+        int32_t nb[MAXD];
+        int32_t lab[MAXD];
+        T wt[MAXD];
 #pragma unroll
-        for (int q = 0; q < kSmallMaxD; ++q) {
+        for (int q = 0; q < MAXD; ++q) {
             bool ok = q < d;
-            int32_t j = ok ? load_index(s.idx, st + q) : v;
+            const int32_t j = ok ? load_index(s.idx, st + q) : v;
             nb[q] = j;
             ok = ok && (j != v);
             lab[q] = ok ? load_label<ASYNC>(s.C, j) : kEmptyKey;
@@ -65,10 +65,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
         T best_w = 0;
         int32_t best = 0x7fffffff;
 #pragma unroll
-        for (int q = 0; q < kSmallMaxD; ++q) {
+        for (int q = 0; q < MAXD; ++q) {
             T sum = 0;
 #pragma unroll
-            for (int r = 0; r < kSmallMaxD; ++r) sum += (lab[r] == lab[q]) ? wt[r] : (T)0;
+            for (int r = 0; r < MAXD; ++r) sum += (lab[r] == lab[q]) ? wt[r] : (T)0;
             const bool better = lab[q] != kEmptyKey &&
                                 (!any || sum > best_w || (sum == best_w && lab[q] < best));
             if (better) {
@@ -86,20 +86,31 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
             write_label<ASYNC>(s, v, best);
             if (flag_neighbours) {
 #pragma unroll
-                for (int q = 0; q < kSmallMaxD; ++q)
+                for (int q = 0; q < MAXD; ++q)
                     if (q < d && nb[q] != v) s.flags[nb[q]] = 1;
             }
+            ++my_changed;
+            my_changed_entries += (unsigned)d;
         }
-        account_changes<ASYNC, BATCH>(s, 0, changed, v, d);
+        if constexpr (!ASYNC) {
+            if (slot) bv.chg[k] = changed ? v : -1;
+        }
+        count_graph_changes<BATCH>(s, changed, v);
     }
+    flush_bin_counts(s, 0, my_changed, my_changed_entries);
 }
 
 cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms) {
     const bool async = mode == MODE_ASYNC;
     const int flag = mode != MODE_SYNC_FULL;
     const bool batch = s.G > 1;
+    const bool four = s.small_max <= 4;
     dim3 grid(sms * 8), block(kSmallThreads);
-#define LPA_SMALL(A, W, B) k_sweep_small<A, W, B><<<grid, block, 0, st>>>(s, flag)
+#define LPA_SMALL(A, W, B)                                                          \
+    do {                                                                            \
+        if (four) k_sweep_small<A, W, B, 4><<<grid, block, 0, st>>>(s, flag);       \
+        else k_sweep_small<A, W, B, 8><<<grid, block, 0, st>>>(s, flag);            \
+    } while (0)
 #define LPA_SMALL_W(A, B)                                      \
     switch (s.weight_kind) {                                   \
         case W_UNIT: LPA_SMALL(A, W_UNIT, B); break;           \

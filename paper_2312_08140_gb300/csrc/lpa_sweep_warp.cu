@@ -59,14 +59,17 @@ __global__ void __launch_bounds__(kWarpThreads) k_sweep_warp(DevState s, int fla
     }
     __syncwarp();
 
-    const int buf = s.ctrl->iter & 1;
-    const unsigned cnt = s.ctrl->bin_cnt[buf][1];
-    const int32_t* __restrict__ list = s.list[1];
+    const BinView bv = bin_view(s, 1);
+    const unsigned cnt = bv.cnt;
     const unsigned nwarps = gridDim.x * kWarpsPerBlock;
+    unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned k = blockIdx.x * kWarpsPerBlock + wib; k < cnt; k += nwarps) {
-        const int32_t v = list[k];
+        const int32_t v = bv.list[k];
         if constexpr (BATCH) {
-            if (s.done[s.gid[v]]) continue;     // warp-uniform
+            if (s.done[s.gid[v]]) {             // warp-uniform
+                if (!ASYNC && lane == 0) bv.chg[k] = -1;
+                continue;
+            }
         }
         const int64_t st = s.off[v];
         const int64_t en = s.off[v + 1];
@@ -134,7 +137,11 @@ __global__ void __launch_bounds__(kWarpThreads) k_sweep_warp(DevState s, int fla
             changed = best != own;
         }
         if (changed) {                           // warp-uniform
-            if (lane == 0) write_label<ASYNC>(s, v, best);
+            if (lane == 0) {
+                write_label<ASYNC>(s, v, best);
+                ++my_changed;
+                my_changed_entries += (unsigned)d;
+            }
             if (flag_neighbours) {
                 for (int64_t e = st + lane; e < en; e += 32) {
                     const int32_t j = s.idx[e];
@@ -142,8 +149,14 @@ __global__ void __launch_bounds__(kWarpThreads) k_sweep_warp(DevState s, int fla
                 }
             }
         }
-        account_changes<ASYNC, BATCH>(s, 1, changed && lane == 0, v, d);
+        if constexpr (!ASYNC) {
+            if (lane == 0) bv.chg[k] = changed ? v : -1;
+        }
+        if constexpr (BATCH) {
+            if (changed && lane == 0) atomicAdd(&s.dN[s.gid[v]], 1ull);
+        }
     }
+    flush_bin_counts(s, 1, my_changed, my_changed_entries);
 }
 
 template <bool ASYNC, int WK, bool BATCH>

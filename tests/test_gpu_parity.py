@@ -95,7 +95,8 @@ def test_planted_partition_sync(lpa):
     assert it >= 3
 
 
-@pytest.mark.parametrize("cfg", [None, (4, 64, 256, 1024), (8, 1024, 1024, 16384), (1, 33, 128, 1024)])
+@pytest.mark.parametrize("cfg", [None, (4, 64, 256, 1024, 0), (8, 1024, 1024, 16384, 1001),
+                                 (1, 33, 128, 1024, 200)])
 def test_rmat_bins_and_spill_sync(lpa, cfg):
     """R-MAT scale 14 has vertices in all three degree bins; hub_slots = 1024 forces
     the global spill table for every hub with degree > 512."""
