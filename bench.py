@@ -49,8 +49,8 @@ def workload(name):
     import lpa_inputs as L
     if name == "rmat22+grid4096":
         return [("rmat22", lambda: L.rmat(22, 16, seed=1)), ("grid4096", lambda: L.road_grid(4096, 4096, seed=1))]
-    if name == "rmat18+grid1024":
-        return [("rmat18", lambda: L.rmat(18, 16, seed=1)), ("grid1024", lambda: L.road_grid(1024, 1024, seed=1))]
+    if name == "rmat21+grid2048":
+        return [("rmat21", lambda: L.rmat(21, 16, seed=1)), ("grid2048", lambda: L.road_grid(2048, 2048, seed=1))]
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -58,8 +58,8 @@ WORKLOAD_TEXT = {
     "rmat22+grid4096": "R-MAT scale 22 edge factor 16 (a,b,c,d=.57,.19,.19,.05; symmetrised, deduplicated, "
                        "no self-loops; unit weights) + 4096x4096 road-like grid (10% edges dropped, 0.1% "
                        "shortcuts, integer weights 1..8); sync and async-with-pruning; tau=0.05, cap 20",
-    "rmat18+grid1024": "R-MAT scale 18 + 1024x1024 road-like grid (small profiling case of the same "
-                       "generators); sync and async-with-pruning; tau=0.05, cap 20",
+    "rmat21+grid2048": "R-MAT scale 21 + 2048x2048 road-like grid (smaller profiling case of the same "
+                       "generators, still larger than L2); sync and async-with-pruning; tau=0.05, cap 20",
 }
 
 
