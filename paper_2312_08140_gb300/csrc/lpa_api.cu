@@ -62,7 +62,7 @@ struct Engine {
     bool exact = false;
     int64_t max_degree = 0;
     int64_t device_bytes = 0;
-    lpa_config cfg{8, 512, 512, 8192, 500};
+    lpa_config cfg{4, 128, 256, 4096, 500};
     int hub_blocks = 0;
     int32_t* spill_keys = nullptr;
     void* spill_vals = nullptr;
@@ -256,8 +256,8 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
 
     // working state
     const size_t N1 = (size_t)std::max<int64_t>(n, 1);
-    if ((rs = dalloc_t(E, &E.s.C, N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.Cnew, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.lab[0], N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.lab[1], N1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.flags, N1 + 16)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.slist, N1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.flist, N1)) != LPA_OK) return rs;

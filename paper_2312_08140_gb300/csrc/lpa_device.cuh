@@ -49,6 +49,8 @@ __device__ __forceinline__ int32_t load_index(const int32_t* idx, int64_t e) {
 
 // Sync mode reads labels that no thread writes during the sweep (read-only
 // path); async mode reads labels other SMs update in place, so it bypasses L1.
+// A vertex's own label is written only by the thread that scans it, so it may
+// be read at any point of the sweep.
 template <bool ASYNC>
 __device__ __forceinline__ int32_t load_label(const int32_t* C, int32_t j) {
     if constexpr (ASYNC) {
@@ -202,13 +204,39 @@ __device__ __forceinline__ BinView bin_view(const DevState& s, int b) {
     return bv;
 }
 
-// Result write for a vertex whose label changed.
+// Label buffers of the current sweep: C (read) and Cn (sync modes write it;
+// async mode updates C in place).
+struct Labels {
+    int32_t* C;
+    int32_t* Cn;
+    bool dense;
+};
+
+__device__ __forceinline__ Labels labels_of(const DevState& s) {
+    const int cb = s.ctrl->cbuf;
+    Labels L;
+    L.C = s.lab[cb];
+    L.Cn = s.lab[cb ^ 1];
+    L.dense = s.ctrl->dense[s.ctrl->iter & 1] != 0;
+    return L;
+}
+
+// Outcome of one scanned vertex.  Async: in-place write on change.  Sync,
+// dense sweep: the next buffer receives every scanned vertex's label (the
+// buffers flip after the sweep).  Sync, sparse sweep: only changed vertices
+// are written and their list slot is marked for the apply step.
 template <bool ASYNC>
-__device__ __forceinline__ void write_label(const DevState& s, int32_t v, int32_t c) {
+__device__ __forceinline__ void record_label(const Labels& L, int32_t* chg_slot, int32_t v, int32_t own,
+                                             int32_t best, bool changed) {
     if constexpr (ASYNC) {
-        s.C[v] = c;
+        if (changed) L.C[v] = best;
     } else {
-        s.Cnew[v] = c;
+        if (L.dense) {
+            L.Cn[v] = changed ? best : own;
+        } else {
+            if (changed) L.Cn[v] = best;
+            *chg_slot = changed ? v : -1;
+        }
     }
 }
 

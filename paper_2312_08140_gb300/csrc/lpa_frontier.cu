@@ -38,7 +38,8 @@ __global__ void k_init(DevState s) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = tid; i < s.N; i += stride) {
-        s.C[i] = (int32_t)i;
+        s.lab[0][i] = (int32_t)i;      // C <- [0 .. |V|) (Algorithm 1), in both buffers
+        s.lab[1][i] = (int32_t)i;
         s.flags[i] = 0;
     }
     Ctrl* c = s.ctrl;
@@ -67,6 +68,7 @@ __global__ void k_init(DevState s) {
         c->iter = 0;
         c->error = 0;
         c->ticket = 0;
+        c->cbuf = 0;
         c->dense[0] = 1;
         c->dense[1] = 0;
         for (int b = 0; b < kBins; ++b) {
@@ -323,7 +325,8 @@ cudaError_t build_static_lists(DevState& s, cudaStream_t st) {
 }
 
 // Control step run by the last block of k_finish after sweep t = ctrl->iter.
-__device__ void control_step(const DevState& s, int dense_next, cudaGraphConditionalHandle h, int in_graph) {
+__device__ void control_step(const DevState& s, int mode, int dense_next, cudaGraphConditionalHandle h,
+                             int in_graph) {
     Ctrl* c = s.ctrl;
     volatile Ctrl* vc = c;
     const int t = vc->iter;
@@ -381,6 +384,8 @@ __device__ void control_step(const DevState& s, int dense_next, cudaGraphConditi
             c->bin_cnt[cur][b] = 0;
             c->bin_entries[cur][b] = 0;
         }
+        // a dense sync sweep wrote every scanned vertex into the other buffer
+        if (mode != MODE_ASYNC && vc->dense[cur]) c->cbuf ^= 1;
         c->dense[nb] = dense_next;
         c->iter = t + 1;
         c->any_active = any;
@@ -390,7 +395,9 @@ __device__ void control_step(const DevState& s, int dense_next, cudaGraphConditi
     }
 }
 
-// After sweep t: (1) sync modes apply the marked changes C[v] = Cnew[v];
+// After sweep t: (1) after a sparse sync sweep, apply the marked changes
+// (current buffer <- next buffer at the marked vertices; a dense sync sweep
+// instead flips the buffers in the control step);
 // (2) the next sweep is dense (static lists, every vertex) when the entries
 // of the changed vertices reach dense_permille of all entries -- then the
 // flags are simply cleared -- else the flags are compacted into per-bin
@@ -402,13 +409,23 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned gstride = gridDim.x * blockDim.x;
 
-    if (mode != MODE_ASYNC) {
+    if (mode != MODE_ASYNC && !s.ctrl->dense[cur]) {
+        const int cb = s.ctrl->cbuf;
+        int32_t* C = s.lab[cb];
+        const int32_t* Cn = s.lab[cb ^ 1];
         for (int b = 0; b < kBins; ++b) {
             const unsigned cnt = s.ctrl->bin_cnt[cur][b];
             const int32_t* chg = s.chg + s.bin_base[b];
-            for (unsigned k = gtid; k < cnt; k += gstride) {
-                const int32_t v = chg[k];
-                if (v >= 0) s.C[v] = s.Cnew[v];
+            for (unsigned k0 = gtid * 4u; k0 < cnt; k0 += gstride * 4u) {
+                int32_t v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = (k0 + q < cnt) ? chg[k0 + q] : -1;
+                int32_t c[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) c[q] = v[q] >= 0 ? Cn[v[q]] : 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (v[q] >= 0) C[v[q]] = c[q];
             }
         }
     }
@@ -475,7 +492,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    control_step(s, dense, h, in_graph);
+    control_step(s, mode, dense, h, in_graph);
 }
 
 cudaError_t launch_finish(const DevState& s, int mode, cudaGraphConditionalHandle h, int in_graph,
@@ -487,9 +504,10 @@ cudaError_t launch_finish(const DevState& s, int mode, cudaGraphConditionalHandl
 __global__ void k_finalize(DevState s) {
     int32_t* out = s.ctrl->labels_out;
     const int local = s.ctrl->local_ids;
+    const int32_t* C = s.lab[s.ctrl->cbuf];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.N; i += stride) {
-        int32_t c = s.C[i];
+        int32_t c = C[i];
         if (local && s.G > 1) c -= (int32_t)s.vtx_off[s.gid[i]];
         out[i] = c;
     }

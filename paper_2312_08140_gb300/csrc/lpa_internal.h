@@ -36,6 +36,7 @@ struct Ctrl {
     int32_t error;                       // non-zero: a device-side check failed
     unsigned int ticket;                 // last-block election in the finish kernel
     int32_t dense[2];                    // sweep reads the static bin lists (all vertices), by t & 1
+    int32_t cbuf;                        // labels of the current sweep are lab[cbuf]
     unsigned int bin_cnt[2][kBins];      // frontier list lengths, double-buffered by t & 1
     unsigned long long bin_entries[2][kBins];   // CSR entries of those vertices
     unsigned long long bin_changed[kBins];      // vertices changed in the current sweep, per bin
@@ -62,8 +63,9 @@ struct DevState {
     const void* w;             // [E] uint32 (W_U32), float (W_F32) or null (W_UNIT)
     const int32_t* gid;        // [N] graph of each vertex, null when G == 1
     const int64_t* vtx_off;    // [G+1]
-    int32_t* C;                // [N] labels (global ids)
-    int32_t* Cnew;             // [N] sync mode: next labels of changed vertices
+    int32_t* lab[2];           // [N] label buffers (global ids): current lab[cbuf]; sync sweeps write
+                               // the other one (every scanned vertex in dense sweeps, then the
+                               // buffers flip; only changed vertices in sparse sweeps, then applied)
     uint8_t* flags;            // [N] 1 = unprocessed (Algorithm 1)
     int32_t* slist;            // [N] static lists: vertices with an entry, by bin, ascending
     int32_t* flist;            // [N] frontier lists of the sparse sweeps, same bin regions

@@ -42,13 +42,15 @@ __global__ void k_sweep_hub(DevState s, int flag_neighbours) {
     __syncthreads();
 
     const BinView bv = bin_view(s, 2);
+    const Labels L = labels_of(s);
     const unsigned cnt = bv.cnt;
     unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned k = blockIdx.x; k < cnt; k += gridDim.x) {
         const int32_t v = bv.list[k];
+        const int32_t own = ASYNC ? __ldcg(L.C + v) : L.C[v];
         if constexpr (BATCH) {
             if (s.done[s.gid[v]]) {             // block-uniform
-                if (!ASYNC && threadIdx.x == 0) bv.chg[k] = -1;
+                if (threadIdx.x == 0) record_label<ASYNC>(L, bv.chg + k, v, own, own, false);
                 continue;
             }
         }
@@ -65,7 +67,7 @@ __global__ void k_sweep_hub(DevState s, int flag_neighbours) {
             const bool in = e < en;
             const int32_t j = in ? load_index(s.idx, e) : v;
             const bool ok = in && j != v;
-            const int32_t lab = ok ? load_label<ASYNC>(s.C, j) : kEmptyKey;
+            const int32_t lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
             T w = ok ? load_weight<WK>(s.w, e) : (T)0;
             bool lead = ok;
             if constexpr (WK != W_F32) {
@@ -144,14 +146,10 @@ __global__ void k_sweep_hub(DevState s, int flag_neighbours) {
         }
         __syncthreads();
         const int32_t best_lab = winner;
-        bool changed = false;
-        if (best_lab >= 0) {
-            const int32_t own = ASYNC ? __ldcg(s.C + v) : s.C[v];
-            changed = best_lab != own;
-        }
-        if (changed) {                                // block-uniform
+        const bool changed = best_lab >= 0 && best_lab != own;   // block-uniform
+        if (threadIdx.x == 0) record_label<ASYNC>(L, bv.chg + k, v, own, best_lab, changed);
+        if (changed) {
             if (threadIdx.x == 0) {
-                write_label<ASYNC>(s, v, best_lab);
                 ++my_changed;
                 my_changed_entries += (unsigned long long)d;
             }
@@ -162,11 +160,8 @@ __global__ void k_sweep_hub(DevState s, int flag_neighbours) {
                 }
             }
         }
-        if (threadIdx.x == 0) {
-            if constexpr (!ASYNC) bv.chg[k] = changed ? v : -1;
-            if constexpr (BATCH) {
-                if (changed) atomicAdd(&s.dN[s.gid[v]], 1ull);
-            }
+        if constexpr (BATCH) {
+            if (threadIdx.x == 0 && changed) atomicAdd(&s.dN[s.gid[v]], 1ull);
         }
         __syncthreads();    // tables clear and `winner` consumed before the next vertex
     }

@@ -28,6 +28,7 @@ template <bool ASYNC, int WK, bool BATCH, int MAXD>
 __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     const BinView bv = bin_view(s, 0);
+    const Labels L = labels_of(s);
     const unsigned cnt = bv.cnt;
     const unsigned stride = gridDim.x * blockDim.x;
     constexpr int RUN = ASYNC ? kAsyncRun : 1;
@@ -45,6 +46,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
         }
         int64_t st = 0;
         int d = 0;
+        int32_t own = 0;
+        if (slot) own = ASYNC ? __ldcg(L.C + v) : L.C[v];
         if (act) {
             st = s.off[v];
             d = (int)(s.off[v + 1] - st);
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
             const int32_t j = ok ? load_index(s.idx, st + q) : v;
             nb[q] = j;
             ok = ok && (j != v);
-            lab[q] = ok ? load_label<ASYNC>(s.C, j) : kEmptyKey;
+            lab[q] = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
             wt[q] = ok ? load_weight<WK>(s.w, st + q) : (T)0;
         }
         bool any = false;
@@ -77,13 +80,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
                 best = lab[q];
             }
         }
-        bool changed = false;
-        if (act && any) {
-            const int32_t own = ASYNC ? __ldcg(s.C + v) : s.C[v];
-            changed = best != own;
-        }
+        const bool changed = act && any && best != own;
+        if (slot) record_label<ASYNC>(L, bv.chg + k, v, own, best, changed);
         if (changed) {
-            write_label<ASYNC>(s, v, best);
             if (flag_neighbours) {
 #pragma unroll
                 for (int q = 0; q < MAXD; ++q)
@@ -91,9 +90,6 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
             }
             ++my_changed;
             my_changed_entries += (unsigned)d;
-        }
-        if constexpr (!ASYNC) {
-            if (slot) bv.chg[k] = changed ? v : -1;
         }
         count_graph_changes<BATCH>(s, changed, v);
     }

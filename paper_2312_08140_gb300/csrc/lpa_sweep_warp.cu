@@ -60,100 +60,118 @@ __global__ void __launch_bounds__(kWarpThreads) k_sweep_warp(DevState s, int fla
     __syncwarp();
 
     const BinView bv = bin_view(s, 1);
+    const Labels L = labels_of(s);
     const unsigned cnt = bv.cnt;
     const unsigned nwarps = gridDim.x * kWarpsPerBlock;
     unsigned long long my_changed = 0, my_changed_entries = 0;
-    for (unsigned k = blockIdx.x * kWarpsPerBlock + wib; k < cnt; k += nwarps) {
-        const int32_t v = bv.list[k];
-        if constexpr (BATCH) {
-            if (s.done[s.gid[v]]) {             // warp-uniform
-                if (!ASYNC && lane == 0) bv.chg[k] = -1;
-                continue;
+    for (unsigned base = (blockIdx.x * kWarpsPerBlock + wib) * 32u; base < cnt; base += nwarps * 32u) {
+        // Metadata of up to 32 consecutive frontier entries, one per lane, loaded
+        // together so their latencies overlap.
+        const unsigned kl = base + lane;
+        const bool okl = kl < cnt;
+        const int32_t vl = okl ? bv.list[kl] : 0;
+        int64_t stl = 0, enl = 0;
+        int32_t ownl = 0;
+        int actl = okl;
+        if (okl) {
+            stl = s.off[vl];
+            enl = s.off[vl + 1];
+            ownl = ASYNC ? __ldcg(L.C + vl) : L.C[vl];
+            if constexpr (BATCH) {
+                if (s.done[s.gid[vl]]) actl = 0;
             }
         }
-        const int64_t st = s.off[v];
-        const int64_t en = s.off[v + 1];
-        const int d = (int)(en - st);
-        uint32_t key = 0;
-        int32_t cand = 0;
-        if (d <= 32) {
-            const bool in = (int)lane < d;
-            const int32_t j = in ? load_index(s.idx, st + lane) : v;
-            const bool ok = in && j != v;
-            const int32_t lab = ok ? load_label<ASYNC>(s.C, j) : kEmptyKey;
-            const T w = ok ? load_weight<WK>(s.w, st + lane) : (T)0;
-            const unsigned peers = __match_any_sync(kFull, lab);
-            const T sum = group_sum<WK>(peers, w, lab, ok);
-            if (ok && lane == (unsigned)(__ffs(peers) - 1)) {
-                key = sum_key(sum);
-                cand = lab;
+        const unsigned nv = min(32u, cnt - base);
+        // indices of the first chunk of the next vertex are fetched one vertex ahead
+        int32_t jpre = kEmptyKey;
+        {
+            const int64_t st0 = __shfl_sync(kFull, stl, 0), en0 = __shfl_sync(kFull, enl, 0);
+            if (__shfl_sync(kFull, actl, 0) && st0 + lane < en0) jpre = load_index(s.idx, st0 + lane);
+        }
+        for (unsigned i = 0; i < nv; ++i) {
+            const int32_t v = __shfl_sync(kFull, vl, i);
+            const int64_t st = __shfl_sync(kFull, stl, i);
+            const int64_t en = __shfl_sync(kFull, enl, i);
+            const int32_t own = __shfl_sync(kFull, ownl, i);
+            const int act = __shfl_sync(kFull, actl, i);
+            const int d = (int)(en - st);
+            int32_t j = jpre;
+            {
+                const unsigned i2 = (i + 1) & 31u;
+                const int64_t st2 = __shfl_sync(kFull, stl, i2), en2 = __shfl_sync(kFull, enl, i2);
+                const int a2 = __shfl_sync(kFull, actl, i2) && (i + 1 < nv);
+                jpre = (a2 && st2 + lane < en2) ? load_index(s.idx, st2 + lane) : kEmptyKey;
             }
-        } else {
-            const int log_slots = ceil_log2(2u * (unsigned)d);
-            for (int64_t e0 = st; e0 < en; e0 += 32) {
-                const int64_t e = e0 + lane;
-                const bool in = e < en;
-                const int32_t j = in ? load_index(s.idx, e) : v;
-                const bool ok = in && j != v;
-                const int32_t lab = ok ? load_label<ASYNC>(s.C, j) : kEmptyKey;
-                const T w = ok ? load_weight<WK>(s.w, e) : (T)0;
-                if constexpr (WK == W_F32) {
-                    if (ok && !table_add<T>(keys, vals, log_slots, lab, w)) atomicExch(&s.ctrl->error, 2);
-                } else {
-                    const unsigned peers = __match_any_sync(kFull, lab);
-                    const T sum = group_sum<WK>(peers, w, lab, ok);
-                    if (ok && lane == (unsigned)(__ffs(peers) - 1) && !table_add<T>(keys, vals, log_slots, lab, sum))
-                        atomicExch(&s.ctrl->error, 2);
+            uint32_t key = 0;
+            int32_t cand = 0;
+            if (act && d <= 32) {
+                const bool ok = (int)lane < d && j != v;
+                const int32_t lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
+                const T w = ok ? load_weight<WK>(s.w, st + lane) : (T)0;
+                const unsigned peers = __match_any_sync(kFull, lab);
+                const T sum = group_sum<WK>(peers, w, lab, ok);
+                if (ok && lane == (unsigned)(__ffs(peers) - 1)) {
+                    key = sum_key(sum);
+                    cand = lab;
                 }
-            }
-            __syncwarp();
-            bool any = false;
-            T best_w = 0;
-            int32_t best = 0x7fffffff;
-            const int slots = 1 << log_slots;
-            for (int q = lane; q < slots; q += 32) {
-                const int32_t kq = keys[q];
-                if (kq != kEmptyKey) {
-                    const T vq = vals[q];
-                    if (!any || vq > best_w || (vq == best_w && kq < best)) {
-                        any = true;
-                        best_w = vq;
-                        best = kq;
+            } else if (act) {
+                const int log_slots = ceil_log2(2u * (unsigned)d);
+                for (int64_t e0 = st; e0 < en; e0 += 32) {
+                    const int64_t e = e0 + lane;
+                    const int32_t jn = (e + 32 < en) ? load_index(s.idx, e + 32) : kEmptyKey;
+                    const bool ok = e < en && j != v;
+                    const int32_t lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
+                    const T w = ok ? load_weight<WK>(s.w, e) : (T)0;
+                    if constexpr (WK == W_F32) {
+                        if (ok && !table_add<T>(keys, vals, log_slots, lab, w)) atomicExch(&s.ctrl->error, 2);
+                    } else {
+                        const unsigned peers = __match_any_sync(kFull, lab);
+                        const T sum = group_sum<WK>(peers, w, lab, ok);
+                        if (ok && lane == (unsigned)(__ffs(peers) - 1) && !table_add<T>(keys, vals, log_slots, lab, sum))
+                            atomicExch(&s.ctrl->error, 2);
                     }
-                    keys[q] = kEmptyKey;
-                    vals[q] = (T)0;
+                    j = jn;
+                }
+                __syncwarp();
+                bool any = false;
+                T best_w = 0;
+                int32_t best = 0x7fffffff;
+                const int slots = 1 << log_slots;
+                for (int q = lane; q < slots; q += 32) {
+                    const int32_t kq = keys[q];
+                    if (kq != kEmptyKey) {
+                        const T vq = vals[q];
+                        if (!any || vq > best_w || (vq == best_w && kq < best)) {
+                            any = true;
+                            best_w = vq;
+                            best = kq;
+                        }
+                        keys[q] = kEmptyKey;
+                        vals[q] = (T)0;
+                    }
+                }
+                __syncwarp();
+                if (any) {
+                    key = sum_key(best_w);
+                    cand = best;
                 }
             }
-            __syncwarp();
-            if (any) {
-                key = sum_key(best_w);
-                cand = best;
-            }
-        }
-        const int32_t best = warp_argmax(key, cand);
-        bool changed = false;
-        if (best >= 0) {
-            const int32_t own = ASYNC ? __ldcg(s.C + v) : s.C[v];
-            changed = best != own;
-        }
-        if (changed) {                           // warp-uniform
-            if (lane == 0) {
-                write_label<ASYNC>(s, v, best);
-                ++my_changed;
-                my_changed_entries += (unsigned)d;
-            }
-            if (flag_neighbours) {
-                for (int64_t e = st + lane; e < en; e += 32) {
-                    const int32_t j = s.idx[e];
-                    if (j != v) s.flags[j] = 1;
+            const int32_t best = warp_argmax(key, cand);
+            const bool changed = act && best >= 0 && best != own;   // warp-uniform
+            if (lane == 0) record_label<ASYNC>(L, bv.chg + base + i, v, own, best, changed);
+            if (changed) {
+                if (flag_neighbours) {
+                    for (int64_t e = st + lane; e < en; e += 32) {
+                        const int32_t jj = s.idx[e];
+                        if (jj != v) s.flags[jj] = 1;
+                    }
+                }
+                if (lane == 0) {
+                    ++my_changed;
+                    my_changed_entries += (unsigned)d;
+                    if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
                 }
             }
-        }
-        if constexpr (!ASYNC) {
-            if (lane == 0) bv.chg[k] = changed ? v : -1;
-        }
-        if constexpr (BATCH) {
-            if (changed && lane == 0) atomicAdd(&s.dN[s.gid[v]], 1ull);
         }
     }
     flush_bin_counts(s, 1, my_changed, my_changed_entries);
