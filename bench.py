@@ -170,7 +170,7 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------- GPU arm
-def kernel_bytes(prof, wbytes, sync):
+def kernel_bytes(prof, wbytes, sync, passes):
     """Algorithmic bytes per sweep-kernel launch from the per-bin counts:
     per scanned vertex 16 B offsets + 4 B own label + 4 B frontier id; per
     scanned entry 4 B index + wbytes weight + 4 B gathered label; per changed
@@ -186,7 +186,7 @@ def kernel_bytes(prof, wbytes, sync):
             by = v * 24 + e * (8 + wbytes) + c * (8 if sync else 4) + ce
             out[b]["bytes"] += by
             out[b]["ms"] += prof["sweep_ms"][t][bi]
-            out[b]["launches"] += 1
+            out[b]["launches"] += passes
     return out
 
 
@@ -259,8 +259,7 @@ def main():
     sweeps = [a["sweeps_total"] - b["sweeps_total"] for a, b in zip(after, before)]
     edges = sum(g.nnz * s for g, s in zip(graphs, sweeps))
     touched = sum(a["scanned_total"] - b["scanned_total"] for a, b in zip(after, before))
-    runs = args.steps * len(graphs) * len(MODES)
-    launches = runs * 5 + 4 * sum(sweeps)
+    launches = sum(a["launches_total"] - b["launches_total"] for a, b in zip(after, before))
     if dist:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -325,7 +324,7 @@ def main():
             wbytes = 0 if g.w is None else 4
             for m in MODES:
                 _, prof = lpa.lpa_run_profiled(h, m, TAU, MAX_ITERS, o, stream)
-                for b, d in kernel_bytes(prof.as_dict(), wbytes, m == "sync").items():
+                for b, d in kernel_bytes(prof.as_dict(), wbytes, m == "sync", 1 if m == "sync" else 2).items():
                     a = agg.setdefault(b, {"bytes": 0.0, "ms": 0.0, "launches": 0})
                     for k in a:
                         a[k] += d[k]

@@ -53,7 +53,11 @@ typedef enum {
  *                     labels only.  Deterministic.
  * LPA_MODE_ASYNC      Algorithm 1 as the paper runs it (Section 4.1): labels
  *                     are updated in place while other vertices read them,
- *                     with vertex pruning.  Results depend on timing.
+ *                     with vertex pruning.  Each sweep scans the unprocessed
+ *                     vertices, then once more the vertices re-marked during
+ *                     that scan (as the serial loop scans a re-marked vertex
+ *                     again later in the same sweep); dN counts both.  Results
+ *                     depend on timing.
  * LPA_MODE_SYNC_FULL  LPA_MODE_SYNC without pruning: every vertex is scanned
  *                     in every sweep.  Same labels as LPA_MODE_SYNC. */
 typedef enum {
@@ -96,6 +100,7 @@ typedef struct {
     int64_t device_bytes;  /* device memory the handle holds */
     int64_t sweeps_total;  /* sweeps run on this handle since creation (all runs) */
     int64_t scanned_total; /* CSR entries scanned by those sweeps */
+    int64_t launches_total;/* kernel launches of the lpa_run calls on this handle */
 } lpa_graph_props;
 
 /* Launch parameters of the sweep.  Vertices are binned by degree d:

@@ -74,7 +74,7 @@ struct Engine {
     ModAccum* acc = nullptr;
     // host mirrors
     std::vector<int64_t> vtx_off_host;
-    int64_t* labels_scratch_dummy = nullptr;
+    int64_t runs_total = 0;          // lpa_run calls that launched the device loop
 };
 
 lpa_status dalloc(Engine& E, void** p, size_t bytes) {
@@ -280,15 +280,30 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     return LPA_OK;
 }
 
-// One sweep: the three bin kernels, then the finish kernel (apply, compact, control).
-cudaError_t enqueue_sweep(Engine& E, int mode, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) {
+cudaError_t enqueue_pass(Engine& E, int mode, cudaStream_t st) {
     cudaError_t err = launch_sweep_small(E.s, mode, st, E.sms);
     if (err != cudaSuccess) return err;
     err = launch_sweep_warp(E.s, mode, st, E.sms);
     if (err != cudaSuccess) return err;
-    err = launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st);
+    return launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st);
+}
+
+// One sweep (lpaMove of Algorithm 1).  Sync modes: one pass over the frontier,
+// then the finish kernel (apply, compaction, control).  Async mode: a main
+// pass, a compaction of the vertices it re-marked, and a catch-up pass over
+// them within the same sweep -- the parallel counterpart of the serial loop,
+// where a vertex re-marked by an earlier vertex is scanned again later in the
+// same sweep -- then the finish kernel.
+cudaError_t enqueue_sweep(Engine& E, int mode, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) {
+    cudaError_t err = enqueue_pass(E, mode, st);
     if (err != cudaSuccess) return err;
-    return launch_finish(E.s, mode, h, in_graph, st, E.sms);
+    if (mode == MODE_ASYNC) {
+        err = launch_finish(E.s, mode, 1, h, in_graph, st, E.sms);
+        if (err != cudaSuccess) return err;
+        err = enqueue_pass(E, mode, st);
+        if (err != cudaSuccess) return err;
+    }
+    return launch_finish(E.s, mode, 0, h, in_graph, st, E.sms);
 }
 
 // Graph for one mode:  init -> init_cond -> WHILE { sweep } -> finalize
@@ -406,6 +421,7 @@ lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t
     if ((rs = build_graph(E, mode)) != LPA_OK) return rs;
     LPA_CUDA(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, labels_out, local_ids, st));
     LPA_CUDA(cudaGraphLaunch(E.exec[mode], st));
+    ++E.runs_total;
     if (infos) return collect_info(E, st, infos, E.s.G);
     return LPA_OK;
 }
@@ -446,28 +462,36 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
     LPA_P(cudaMemcpy(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
     int t = 0;
     while (c.any_active) {
-        LPA_P(cudaEventRecord(ev[0], st));
-        LPA_P(launch_sweep_small(E.s, mode, st, E.sms));
-        LPA_P(cudaEventRecord(ev[1], st));
-        LPA_P(launch_sweep_warp(E.s, mode, st, E.sms));
-        LPA_P(cudaEventRecord(ev[2], st));
-        LPA_P(launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st));
-        LPA_P(cudaEventRecord(ev[3], st));
-        LPA_P(launch_finish(E.s, mode, none, 0, st, E.sms));
-        LPA_P(cudaEventRecord(ev[4], st));
-        LPA_P(cudaEventSynchronize(ev[4]));
+        float sweep_ms[3] = {0.f, 0.f, 0.f}, fin_ms = 0.f;
+        const int passes = mode == MODE_ASYNC ? 2 : 1;
+        for (int p = 0; p < passes; ++p) {
+            LPA_P(cudaEventRecord(ev[0], st));
+            LPA_P(launch_sweep_small(E.s, mode, st, E.sms));
+            LPA_P(cudaEventRecord(ev[1], st));
+            LPA_P(launch_sweep_warp(E.s, mode, st, E.sms));
+            LPA_P(cudaEventRecord(ev[2], st));
+            LPA_P(launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st));
+            LPA_P(cudaEventRecord(ev[3], st));
+            LPA_P(launch_finish(E.s, mode, p + 1 < passes ? 1 : 0, none, 0, st, E.sms));
+            LPA_P(cudaEventRecord(ev[4], st));
+            LPA_P(cudaEventSynchronize(ev[4]));
+            for (int b = 0; b < kBins; ++b) {
+                LPA_P(cudaEventElapsedTime(&ms, ev[b], ev[b + 1]));
+                sweep_ms[b] += ms;
+            }
+            LPA_P(cudaEventElapsedTime(&ms, ev[3], ev[4]));
+            fin_ms += ms;
+        }
         LPA_P(cudaMemcpy(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
         if (t < kMaxHist) {
             for (int b = 0; b < kBins; ++b) {
-                LPA_P(cudaEventElapsedTime(&ms, ev[b], ev[b + 1]));
-                prof->sweep_ms[t][b] = ms;
+                prof->sweep_ms[t][b] = sweep_ms[b];
                 prof->bin_vertices[t][b] = c.hist_bin_vertices[t][b];
                 prof->bin_entries[t][b] = c.hist_bin_entries[t][b];
                 prof->bin_changed[t][b] = c.hist_bin_changed[t][b];
                 prof->bin_changed_entries[t][b] = c.hist_bin_changed_entries[t][b];
             }
-            LPA_P(cudaEventElapsedTime(&ms, ev[3], ev[4]));
-            prof->finish_ms[t] = ms;
+            prof->finish_ms[t] = fin_ms;
         }
         ++t;
         if (c.error) break;
@@ -514,6 +538,7 @@ lpa_status fill_props(const Engine& E, lpa_graph_props* p) {
     memset(p, 0, sizeof(*p));
     p->sweeps_total = c.total_sweeps;
     p->scanned_total = c.total_scanned;
+    p->launches_total = E.runs_total * 4 + c.total_sweep_launches;
     p->n = E.s.N;
     p->nnz = E.s.E;
     p->num_graphs = E.s.G;

@@ -182,6 +182,7 @@ __device__ __forceinline__ void flush_bin_counts(const DevState& s, int bin, uns
         if (a) {
             atomicAdd(&s.ctrl->bin_changed[bin], a);
             atomicAdd(&s.ctrl->bin_changed_entries[bin], b);
+            atomicAdd(&s.ctrl->pass_changed_entries, b);
         }
     }
 }
@@ -195,7 +196,7 @@ struct BinView {
 };
 
 __device__ __forceinline__ BinView bin_view(const DevState& s, int b) {
-    const int buf = s.ctrl->iter & 1;
+    const int buf = s.ctrl->rd;
     BinView bv;
     const int64_t base = s.bin_base[b];
     bv.list = (s.ctrl->dense[buf] ? s.slist : s.flist) + base;
@@ -217,7 +218,7 @@ __device__ __forceinline__ Labels labels_of(const DevState& s) {
     Labels L;
     L.C = s.lab[cb];
     L.Cn = s.lab[cb ^ 1];
-    L.dense = s.ctrl->dense[s.ctrl->iter & 1] != 0;
+    L.dense = s.ctrl->dense[s.ctrl->rd] != 0;
     return L;
 }
 

@@ -69,8 +69,10 @@ __global__ void k_init(DevState s) {
         c->error = 0;
         c->ticket = 0;
         c->cbuf = 0;
+        c->rd = 0;
         c->dense[0] = 1;
         c->dense[1] = 0;
+        c->pass_changed_entries = 0;
         for (int b = 0; b < kBins; ++b) {
             c->bin_cnt[0][b] = s.bin_static[b];
             c->bin_entries[0][b] = s.bin_static_entries[b];
@@ -78,6 +80,8 @@ __global__ void k_init(DevState s) {
             c->bin_entries[1][b] = 0;
             c->bin_changed[b] = 0;
             c->bin_changed_entries[b] = 0;
+            c->sweep_bin_vertices[b] = 0;
+            c->sweep_bin_entries[b] = 0;
         }
     }
 }
@@ -324,47 +328,59 @@ cudaError_t build_static_lists(DevState& s, cudaStream_t st) {
     return err;
 }
 
-// Control step run by the last block of k_finish after sweep t = ctrl->iter.
-__device__ void control_step(const DevState& s, int mode, int dense_next, cudaGraphConditionalHandle h,
+// Run by the last block of k_finish once every block is done.  `rd` is the
+// buffer the pass just consumed; `wr` = rd ^ 1 received the next frontier
+// (or is dense).  For role 0 (end of sweep t) it also runs the per-graph
+// convergence test of Algorithm 1 and sets the loop condition.
+__device__ void control_step(const DevState& s, int mode, int role, int dense_next, cudaGraphConditionalHandle h,
                              int in_graph) {
     Ctrl* c = s.ctrl;
     volatile Ctrl* vc = c;
     const int t = vc->iter;
-    const int cur = t & 1, nb = (t + 1) & 1;
-    const double tau = vc->tau;
-    const int max_iters = vc->max_iters;
-    unsigned long long changed_total = 0;
-    for (int b = 0; b < kBins; ++b) changed_total += vc->bin_changed[b];
+    const int rd = vc->rd, wr = rd ^ 1;
     int any = 0;
-    for (int64_t g = threadIdx.x; g < s.G; g += blockDim.x) {
-        if (!s.done[g]) {
-            const unsigned long long dn = (s.G == 1) ? changed_total : ((volatile unsigned long long*)s.dN)[g];
-            if (t < kMaxHist) s.hist_changed[g * kMaxHist + t] = (long long)dn;
-            s.iters[g] = t + 1;
-            const int64_t ng = s.vtx_off[g + 1] - s.vtx_off[g];
-            if ((double)dn / (double)ng <= tau) {            // Algorithm 1: dN / N <= tau
-                s.done[g] = 1;
-                s.exit_reason[g] = 0;
-            } else if (t + 1 >= max_iters) {
-                s.done[g] = 1;
-                s.exit_reason[g] = 1;
+    if (role == 0) {
+        const double tau = vc->tau;
+        const int max_iters = vc->max_iters;
+        unsigned long long changed_total = 0;
+        for (int b = 0; b < kBins; ++b) changed_total += vc->bin_changed[b];
+        for (int64_t g = threadIdx.x; g < s.G; g += blockDim.x) {
+            if (!s.done[g]) {
+                const unsigned long long dn =
+                    (s.G == 1) ? changed_total : ((volatile unsigned long long*)s.dN)[g];
+                if (t < kMaxHist) s.hist_changed[g * kMaxHist + t] = (long long)dn;
+                s.iters[g] = t + 1;
+                const int64_t ng = s.vtx_off[g + 1] - s.vtx_off[g];
+                if ((double)dn / (double)ng <= tau) {            // Algorithm 1: dN / N <= tau
+                    s.done[g] = 1;
+                    s.exit_reason[g] = 0;
+                } else if (t + 1 >= max_iters) {
+                    s.done[g] = 1;
+                    s.exit_reason[g] = 1;
+                }
+                s.dN[g] = 0;
             }
-            s.dN[g] = 0;
+            any |= !s.done[g];
         }
-        any |= !s.done[g];
+        any = __syncthreads_or(any);
     }
-    any = __syncthreads_or(any);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x != 0) return;
+    // the pass that just ended scanned buffer rd
+    for (int b = 0; b < kBins; ++b) {
+        c->sweep_bin_vertices[b] += vc->bin_cnt[rd][b];
+        c->sweep_bin_entries[b] += (long long)vc->bin_entries[rd][b];
+    }
+    if (role == 0) {
         long long act = 0, scn = 0, che = 0;
         for (int b = 0; b < kBins; ++b) {
-            act += vc->bin_cnt[cur][b];
-            scn += (long long)vc->bin_entries[cur][b];
+            act += vc->sweep_bin_vertices[b];
+            scn += vc->sweep_bin_entries[b];
             che += (long long)vc->bin_changed_entries[b];
         }
         if (t < kMaxHist) {
             for (int b = 0; b < kBins; ++b) {
-                c->hist_bin_vertices[t][b] = vc->bin_cnt[cur][b];
-                c->hist_bin_entries[t][b] = (long long)vc->bin_entries[cur][b];
+                c->hist_bin_vertices[t][b] = vc->sweep_bin_vertices[b];
+                c->hist_bin_entries[t][b] = vc->sweep_bin_entries[b];
                 c->hist_bin_changed[t][b] = (long long)vc->bin_changed[b];
                 c->hist_bin_changed_entries[t][b] = (long long)vc->bin_changed_entries[b];
             }
@@ -374,47 +390,54 @@ __device__ void control_step(const DevState& s, int mode, int dense_next, cudaGr
         }
         c->total_sweeps += 1;
         c->total_scanned += scn;
+        c->total_sweep_launches += mode == MODE_ASYNC ? 8 : 4;
         for (int b = 0; b < kBins; ++b) {
             c->bin_changed[b] = 0;
             c->bin_changed_entries[b] = 0;
-            if (dense_next) {
-                c->bin_cnt[nb][b] = s.bin_static[b];
-                c->bin_entries[nb][b] = s.bin_static_entries[b];
-            }
-            c->bin_cnt[cur][b] = 0;
-            c->bin_entries[cur][b] = 0;
+            c->sweep_bin_vertices[b] = 0;
+            c->sweep_bin_entries[b] = 0;
         }
         // a dense sync sweep wrote every scanned vertex into the other buffer
-        if (mode != MODE_ASYNC && vc->dense[cur]) c->cbuf ^= 1;
-        c->dense[nb] = dense_next;
+        if (mode != MODE_ASYNC && vc->dense[rd]) c->cbuf ^= 1;
         c->iter = t + 1;
         c->any_active = any;
-        c->ticket = 0;
-        __threadfence();
-        if (in_graph) cudaGraphSetConditional(h, any ? 1u : 0u);
     }
+    for (int b = 0; b < kBins; ++b) {
+        if (dense_next) {
+            c->bin_cnt[wr][b] = s.bin_static[b];
+            c->bin_entries[wr][b] = s.bin_static_entries[b];
+        }
+        c->bin_cnt[rd][b] = 0;
+        c->bin_entries[rd][b] = 0;
+    }
+    c->dense[wr] = dense_next;
+    c->rd = wr;
+    c->pass_changed_entries = 0;
+    c->ticket = 0;
+    __threadfence();
+    if (role == 0 && in_graph) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
-// After sweep t: (1) after a sparse sync sweep, apply the marked changes
-// (current buffer <- next buffer at the marked vertices; a dense sync sweep
-// instead flips the buffers in the control step);
-// (2) the next sweep is dense (static lists, every vertex) when the entries
-// of the changed vertices reach dense_permille of all entries -- then the
-// flags are simply cleared -- else the flags are compacted into per-bin
-// frontier lists; (3) the last block runs the control step.
-__global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, cudaGraphConditionalHandle h,
-                                                           int in_graph) {
-    const int t = s.ctrl->iter;
-    const int cur = t & 1, nb = (t + 1) & 1;
+// After a pass over buffer rd: (1) at the end of a sparse sync sweep, apply
+// the marked changes (current label buffer <- next buffer at the marked
+// vertices; after a dense sync sweep the control step flips the buffers
+// instead); (2) the next pass is dense (static lists, every vertex) when the
+// vertices changed since the last compaction hold at least dense_permille of
+// all entries -- then the flags are only cleared -- else the flags are
+// compacted into the per-bin frontier lists of buffer rd ^ 1; (3) the last
+// block runs the control step.
+__global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, int role,
+                                                           cudaGraphConditionalHandle h, int in_graph) {
+    const int rd = s.ctrl->rd, wr = rd ^ 1;
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned gstride = gridDim.x * blockDim.x;
 
-    if (mode != MODE_ASYNC && !s.ctrl->dense[cur]) {
+    if (role == 0 && mode != MODE_ASYNC && !s.ctrl->dense[rd]) {
         const int cb = s.ctrl->cbuf;
         int32_t* C = s.lab[cb];
         const int32_t* Cn = s.lab[cb ^ 1];
         for (int b = 0; b < kBins; ++b) {
-            const unsigned cnt = s.ctrl->bin_cnt[cur][b];
+            const unsigned cnt = s.ctrl->bin_cnt[rd][b];
             const int32_t* chg = s.chg + s.bin_base[b];
             for (unsigned k0 = gtid * 4u; k0 < cnt; k0 += gstride * 4u) {
                 int32_t v[4];
@@ -430,8 +453,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
         }
     }
 
-    unsigned long long che = 0;
-    for (int b = 0; b < kBins; ++b) che += ((volatile Ctrl*)s.ctrl)->bin_changed_entries[b];
+    const unsigned long long che = ((volatile Ctrl*)s.ctrl)->pass_changed_entries;
     const int dense = mode == MODE_SYNC_FULL ||
                       (double)che * 1000.0 >= (double)s.dense_permille * (double)s.active_entries;
 
@@ -476,7 +498,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
                 }
             }
             if (__syncthreads_or(anyf))
-                block_append<true>(s.bin_base, s.flist, s.ctrl->bin_cnt[nb], s.ctrl->bin_entries[nb], vid, bin,
+                block_append<true>(s.bin_base, s.flist, s.ctrl->bin_cnt[wr], s.ctrl->bin_entries[wr], vid, bin,
                                    deg);
         }
     }
@@ -492,12 +514,12 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    control_step(s, mode, dense, h, in_graph);
+    control_step(s, mode, role, dense, h, in_graph);
 }
 
-cudaError_t launch_finish(const DevState& s, int mode, cudaGraphConditionalHandle h, int in_graph,
+cudaError_t launch_finish(const DevState& s, int mode, int role, cudaGraphConditionalHandle h, int in_graph,
                           cudaStream_t st, int sms) {
-    k_finish<<<sms * 4, kFrontThreads, 0, st>>>(s, mode, h, in_graph);
+    k_finish<<<sms * 4, kFrontThreads, 0, st>>>(s, mode, role, h, in_graph);
     return cudaGetLastError();
 }
 

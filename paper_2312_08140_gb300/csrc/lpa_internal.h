@@ -35,12 +35,17 @@ struct Ctrl {
     int32_t local_ids;                   // finalize writes label - first vertex of its graph
     int32_t error;                       // non-zero: a device-side check failed
     unsigned int ticket;                 // last-block election in the finish kernel
-    int32_t dense[2];                    // sweep reads the static bin lists (all vertices), by t & 1
+    int32_t rd;                          // frontier buffer the sweep kernels read (flipped by
+                                         // every compaction, which writes buffer rd ^ 1)
+    int32_t dense[2];                    // buffer holds the static bin lists (every vertex)
     int32_t cbuf;                        // labels of the current sweep are lab[cbuf]
-    unsigned int bin_cnt[2][kBins];      // frontier list lengths, double-buffered by t & 1
+    unsigned int bin_cnt[2][kBins];      // frontier list lengths per buffer
     unsigned long long bin_entries[2][kBins];   // CSR entries of those vertices
     unsigned long long bin_changed[kBins];      // vertices changed in the current sweep, per bin
     unsigned long long bin_changed_entries[kBins];
+    unsigned long long pass_changed_entries;    // entries of vertices changed since the last compaction
+    long long sweep_bin_vertices[kBins];        // scanned in the current sweep (all passes)
+    long long sweep_bin_entries[kBins];
     long long hist_active[kMaxHist];
     long long hist_scanned[kMaxHist];
     long long hist_bin_vertices[kMaxHist][kBins];
@@ -50,6 +55,7 @@ struct Ctrl {
     long long hist_bin_changed_entries[kMaxHist][kBins];
     long long total_sweeps;              // cumulative over all runs (never reset)
     long long total_scanned;
+    long long total_sweep_launches;      // kernel launches of those sweeps
 };
 
 // Everything a kernel needs, passed by value.
@@ -102,7 +108,10 @@ cudaError_t launch_init(const DevState& s, cudaStream_t st, int sms);
 // degrees and the bin limits in s.  Synchronises `st`.
 cudaError_t build_static_lists(DevState& s, cudaStream_t st);
 cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st);
-cudaError_t launch_finish(const DevState& s, int mode, cudaGraphConditionalHandle h, int in_graph,
+// role 0: end of a sweep (apply, compaction for the next sweep, control);
+// role 1: inside an asynchronous sweep, compaction of the vertices re-marked by
+// the main pass for the catch-up pass.
+cudaError_t launch_finish(const DevState& s, int mode, int role, cudaGraphConditionalHandle h, int in_graph,
                           cudaStream_t st, int sms);
 cudaError_t launch_finalize(const DevState& s, cudaStream_t st, int sms);
 cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int32_t* labels_out,
