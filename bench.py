@@ -42,6 +42,7 @@ UNIT = "edges/s"
 TAU = 0.05
 MAX_ITERS = 20
 MODES = ("sync", "async")
+BIN_KERNELS = ("k_sweep_small", "k_sweep_warp", "k_sweep_block128", "k_sweep_block256", "k_sweep_block512")
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -176,9 +177,9 @@ def kernel_bytes(prof, wbytes, sync, passes):
     scanned entry 4 B index + wbytes weight + 4 B gathered label; per changed
     vertex 4 B label write (+4 B changed-list entry in sync mode) and 1 B flag
     per entry of its row."""
-    out = {b: {"bytes": 0.0, "ms": 0.0, "launches": 0} for b in ("small", "warp", "hub")}
+    out = {b: {"bytes": 0.0, "ms": 0.0, "launches": 0} for b in BIN_KERNELS}
     for t in range(min(prof["iterations"], 64)):
-        for bi, b in enumerate(("small", "warp", "hub")):
+        for bi, b in enumerate(BIN_KERNELS):
             v = prof["bin_vertices"][t][bi]
             e = prof["bin_entries"][t][bi]
             c = prof["bin_changed"][t][bi]
@@ -331,7 +332,7 @@ def main():
         kernels = {}
         for b, a in agg.items():
             if a["launches"] and a["ms"] > 0:
-                kernels[f"k_sweep_{b}"] = {"launches_per_step": a["launches"], "ms_per_step": a["ms"],
+                kernels[b] = {"launches_per_step": a["launches"], "ms_per_step": a["ms"],
                                            "GB_per_s": a["bytes"] / (a["ms"] / 1e3) / 1e9,
                                            "bytes_per_launch": a["bytes"] / a["launches"]}
         dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])

@@ -74,6 +74,8 @@ typedef enum {
 
 /* Per-sweep history kept in lpa_run_info (sweeps beyond this are still run). */
 #define LPA_MAX_RECORDED_ITERS 64
+/* Degree bins of lpa_config (thread, warp, three block sizes). */
+#define LPA_BINS 5
 
 typedef struct {
     int32_t iterations;    /* sweeps performed, including the one that met the tolerance */
@@ -104,23 +106,26 @@ typedef struct {
 } lpa_graph_props;
 
 /* Launch parameters of the sweep.  Vertices are binned by degree d:
- *   d <= small_max          one thread per vertex, labels and weights in registers
- *   small_max < d <= warp_max  one warp per vertex, per-warp shared-memory table
- *   d > warp_max            one block per vertex, shared-memory table with a global spill table
+ *   d <= small_max                  one thread per vertex, row held in registers
+ *   small_max < d <= warp_max       one warp per vertex, per-warp shared-memory table
+ *   warp_max  < d <= mid_max        one 128-thread block per vertex, shared table
+ *   mid_max   < d <= large_max      one 256-thread block per vertex, shared table
+ *   d > large_max                   one 512-thread block per vertex, 8192-slot shared
+ *                                   table spilling to a global table
  * A sweep is "dense" (every vertex with an entry is scanned, no frontier
- * compaction) when the changed vertices of the previous sweep hold at least
- * dense_permille / 1000 of all entries; the first sweep is always dense
- * (Algorithm 1 starts with every vertex unprocessed); 1001 = never otherwise.
- * Scanning a vertex whose neighbours did not change never changes its label
- * in LPA_MODE_SYNC, so this choice affects speed only.
- * lpa_graph_set_config validates: 1 <= small_max <= 8, small_max < warp_max <= 1024,
- * hub_threads in {128, 256, 512, 1024}, hub_slots a power of two in [1024, 16384],
+ * compaction) when the vertices changed since the previous compaction hold
+ * at least dense_permille / 1000 of all entries; the first sweep is always
+ * dense (Algorithm 1 starts with every vertex unprocessed); 1001 = never
+ * otherwise.  Scanning a vertex whose neighbours did not change never
+ * changes its label in LPA_MODE_SYNC, so this choice affects speed only.
+ * lpa_graph_set_config validates: 1 <= small_max <= 8, small_max < warp_max
+ * <= 256, warp_max < mid_max <= 2048, mid_max < large_max <= 4096,
  * 0 <= dense_permille <= 1001. */
 typedef struct {
     int32_t small_max;
     int32_t warp_max;
-    int32_t hub_threads;
-    int32_t hub_slots;
+    int32_t mid_max;
+    int32_t large_max;
     int32_t dense_permille;
 } lpa_config;
 
@@ -130,12 +135,12 @@ typedef struct {
     int32_t iterations;
     int32_t reserved;
     float   init_ms;
-    float   finish_ms[LPA_MAX_RECORDED_ITERS];   /* apply + frontier compaction + control */
-    float   sweep_ms[LPA_MAX_RECORDED_ITERS][3]; /* per degree bin: small, warp, hub */
-    int64_t bin_vertices[LPA_MAX_RECORDED_ITERS][3];
-    int64_t bin_entries[LPA_MAX_RECORDED_ITERS][3];
-    int64_t bin_changed[LPA_MAX_RECORDED_ITERS][3];
-    int64_t bin_changed_entries[LPA_MAX_RECORDED_ITERS][3];  /* CSR entries of the changed vertices */
+    float   finish_ms[LPA_MAX_RECORDED_ITERS];          /* apply + frontier compaction + control */
+    float   sweep_ms[LPA_MAX_RECORDED_ITERS][LPA_BINS]; /* per degree bin of lpa_config */
+    int64_t bin_vertices[LPA_MAX_RECORDED_ITERS][LPA_BINS];
+    int64_t bin_entries[LPA_MAX_RECORDED_ITERS][LPA_BINS];
+    int64_t bin_changed[LPA_MAX_RECORDED_ITERS][LPA_BINS];
+    int64_t bin_changed_entries[LPA_MAX_RECORDED_ITERS][LPA_BINS];  /* entries of changed vertices */
 } lpa_profile;
 
 typedef struct lpa_graph  *lpa_graph_t;

@@ -41,7 +41,9 @@ LPA_DEVICE_PTRS = 1
 LPA_BORROW = 2
 
 LPA_MAX_RECORDED_ITERS = 64
+LPA_BINS = 5
 _H = LPA_MAX_RECORDED_ITERS
+_B = LPA_BINS
 
 
 class LpaRunInfo(ctypes.Structure):
@@ -69,7 +71,7 @@ class LpaGraphProps(ctypes.Structure):
 
 class LpaConfig(ctypes.Structure):
     _fields_ = [("small_max", ctypes.c_int32), ("warp_max", ctypes.c_int32),
-                ("hub_threads", ctypes.c_int32), ("hub_slots", ctypes.c_int32),
+                ("mid_max", ctypes.c_int32), ("large_max", ctypes.c_int32),
                 ("dense_permille", ctypes.c_int32)]
 
     def as_dict(self):
@@ -78,9 +80,9 @@ class LpaConfig(ctypes.Structure):
 
 class LpaProfile(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32), ("init_ms", ctypes.c_float),
-                ("finish_ms", ctypes.c_float * _H), ("sweep_ms", (ctypes.c_float * 3) * _H),
-                ("bin_vertices", (ctypes.c_int64 * 3) * _H), ("bin_entries", (ctypes.c_int64 * 3) * _H),
-                ("bin_changed", (ctypes.c_int64 * 3) * _H), ("bin_changed_entries", (ctypes.c_int64 * 3) * _H)]
+                ("finish_ms", ctypes.c_float * _H), ("sweep_ms", (ctypes.c_float * _B) * _H),
+                ("bin_vertices", (ctypes.c_int64 * _B) * _H), ("bin_entries", (ctypes.c_int64 * _B) * _H),
+                ("bin_changed", (ctypes.c_int64 * _B) * _H), ("bin_changed_entries", (ctypes.c_int64 * _B) * _H)]
 
     def as_dict(self):
         it = min(self.iterations, _H)

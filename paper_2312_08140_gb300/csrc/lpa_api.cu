@@ -18,6 +18,7 @@
 using namespace lpa;
 
 static_assert(LPA_MAX_RECORDED_ITERS == kMaxHist, "history depth mismatch");
+static_assert(LPA_BINS == kBins, "bin count mismatch");
 
 namespace {
 
@@ -62,8 +63,8 @@ struct Engine {
     bool exact = false;
     int64_t max_degree = 0;
     int64_t device_bytes = 0;
-    lpa_config cfg{4, 128, 256, 4096, 500};
-    int hub_blocks = 0;
+    lpa_config cfg{4, 128, 512, 2048, 500};
+    int block_grid[kBlockBins] = {0, 0, 0};
     int32_t* spill_keys = nullptr;
     void* spill_vals = nullptr;
     cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
@@ -112,10 +113,11 @@ void engine_free(Engine& E) {
     E.spill_vals = nullptr;
 }
 
-// Hub spill tables: needed when a hub's row can hold more distinct labels than
-// half the shared table.  Sized for the maximum degree; the number of hub
-// blocks is capped so the tables stay within a fixed budget.
-lpa_status setup_hub(Engine& E) {
+// Spill tables of the last block bin: needed when a row there can hold more
+// distinct labels than half the shared table.  Sized for the maximum degree;
+// the number of blocks of that bin is capped so the tables stay within a
+// fixed budget.
+lpa_status setup_spill(Engine& E) {
     if (E.spill_keys) cudaFree(E.spill_keys);
     if (E.spill_vals) cudaFree(E.spill_vals);
     E.spill_keys = nullptr;
@@ -123,13 +125,13 @@ lpa_status setup_hub(Engine& E) {
     E.s.spill_keys = nullptr;
     E.s.spill_vals = nullptr;
     E.s.spill_slots = 0;
-    E.hub_blocks = hub_blocks_for(E.sms, E.cfg.hub_threads, E.cfg.hub_slots);
+    for (int b = 0; b < kBlockBins; ++b) E.block_grid[b] = block_grid_for(E.s, b + 2, E.sms);
     const int64_t need = pow2ceil(2 * std::max<int64_t>(E.max_degree, 1));
-    if (E.max_degree > E.cfg.warp_max && need > E.cfg.hub_slots) {
+    if (E.max_degree > E.cfg.large_max && need > kLargeSlots) {
         const int64_t budget = (int64_t)2 << 30;   // 2 GiB of spill tables at most
         const int64_t per_block = need * 8;
-        int64_t blocks = std::min<int64_t>(E.hub_blocks, std::max<int64_t>(1, budget / per_block));
-        E.hub_blocks = (int)blocks;
+        int64_t blocks = std::min<int64_t>(E.block_grid[kBlockBins - 1], std::max<int64_t>(1, budget / per_block));
+        E.block_grid[kBlockBins - 1] = (int)blocks;
         cudaError_t err = cudaMalloc(&E.spill_keys, (size_t)(blocks * need * 4));
         if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(spill keys)");
         err = cudaMalloc(&E.spill_vals, (size_t)(blocks * need * 4));
@@ -146,19 +148,23 @@ lpa_status setup_hub(Engine& E) {
 void apply_config_fields(Engine& E) {
     E.s.small_max = E.cfg.small_max;
     E.s.warp_max = E.cfg.warp_max;
+    E.s.mid_max = E.cfg.mid_max;
+    E.s.large_max = E.cfg.large_max;
     E.s.warp_slots = (int32_t)pow2ceil(2 * (int64_t)E.cfg.warp_max);
-    E.s.hub_slots = E.cfg.hub_slots;
+    E.s.block_slots[0] = (int32_t)pow2ceil(2 * (int64_t)E.cfg.mid_max);
+    E.s.block_slots[1] = (int32_t)pow2ceil(2 * (int64_t)E.cfg.large_max);
+    E.s.block_slots[2] = kLargeSlots;
     E.s.dense_permille = E.cfg.dense_permille;
 }
 
 lpa_status check_config(const lpa_config& c) {
     if (c.small_max < 1 || c.small_max > 8) return fail(LPA_ERR_INVALID_ARG, "small_max must be in [1, 8]");
-    if (c.warp_max <= c.small_max || c.warp_max > 1024)
-        return fail(LPA_ERR_INVALID_ARG, "warp_max must be in (small_max, 1024]");
-    if (c.hub_threads != 128 && c.hub_threads != 256 && c.hub_threads != 512 && c.hub_threads != 1024)
-        return fail(LPA_ERR_INVALID_ARG, "hub_threads must be 128, 256, 512 or 1024");
-    if (c.hub_slots < 1024 || c.hub_slots > 16384 || (c.hub_slots & (c.hub_slots - 1)))
-        return fail(LPA_ERR_INVALID_ARG, "hub_slots must be a power of two in [1024, 16384]");
+    if (c.warp_max <= c.small_max || c.warp_max > 256)
+        return fail(LPA_ERR_INVALID_ARG, "warp_max must be in (small_max, 256]");
+    if (c.mid_max <= c.warp_max || c.mid_max > 2048)
+        return fail(LPA_ERR_INVALID_ARG, "mid_max must be in (warp_max, 2048]");
+    if (c.large_max <= c.mid_max || c.large_max > 4096)
+        return fail(LPA_ERR_INVALID_ARG, "large_max must be in (mid_max, 4096]");
     if (c.dense_permille < 0 || c.dense_permille > 1001)
         return fail(LPA_ERR_INVALID_ARG, "dense_permille must be in [0, 1001]");
     return LPA_OK;
@@ -272,7 +278,7 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     LPA_CUDA(cudaMemsetAsync(E.s.ctrl, 0, sizeof(Ctrl), st));
     LPA_CUDA(cudaMemsetAsync(E.s.hist_changed, 0, (size_t)G * kMaxHist * 8, st));
     apply_config_fields(E);
-    if ((rs = setup_hub(E)) != LPA_OK) return rs;
+    if ((rs = setup_spill(E)) != LPA_OK) return rs;
     LPA_CUDA(build_static_lists(E.s, st));
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_top, cudaStreamNonBlocking));
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_body, cudaStreamNonBlocking));
@@ -280,12 +286,18 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     return LPA_OK;
 }
 
+cudaError_t launch_bin(Engine& E, int mode, int bin, cudaStream_t st) {
+    if (bin == 0) return launch_sweep_small(E.s, mode, st, E.sms);
+    if (bin == 1) return launch_sweep_warp(E.s, mode, st, E.sms);
+    return launch_sweep_block(E.s, mode, bin, E.block_grid[bin - 2], st);
+}
+
 cudaError_t enqueue_pass(Engine& E, int mode, cudaStream_t st) {
-    cudaError_t err = launch_sweep_small(E.s, mode, st, E.sms);
-    if (err != cudaSuccess) return err;
-    err = launch_sweep_warp(E.s, mode, st, E.sms);
-    if (err != cudaSuccess) return err;
-    return launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st);
+    for (int b = 0; b < kBins; ++b) {
+        cudaError_t err = launch_bin(E, mode, b, st);
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
 }
 
 // One sweep (lpaMove of Algorithm 1).  Sync modes: one pass over the frontier,
@@ -434,7 +446,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
     if (!prof) return fail(LPA_ERR_INVALID_ARG, "prof is NULL");
     memset(prof, 0, sizeof(*prof));
     if (E.s.N == 0) return engine_run(E, mode, tol, max_iters, labels_out, st, infos, local_ids);
-    cudaEvent_t ev[6];
+    cudaEvent_t ev[kBins + 2];
     for (auto& e : ev) LPA_CUDA(cudaEventCreate(&e));
     auto cleanup = [&]() {
         for (auto& e : ev) cudaEventDestroy(e);
@@ -462,24 +474,22 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
     LPA_P(cudaMemcpy(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
     int t = 0;
     while (c.any_active) {
-        float sweep_ms[3] = {0.f, 0.f, 0.f}, fin_ms = 0.f;
+        float sweep_ms[kBins] = {0.f}, fin_ms = 0.f;
         const int passes = mode == MODE_ASYNC ? 2 : 1;
         for (int p = 0; p < passes; ++p) {
-            LPA_P(cudaEventRecord(ev[0], st));
-            LPA_P(launch_sweep_small(E.s, mode, st, E.sms));
-            LPA_P(cudaEventRecord(ev[1], st));
-            LPA_P(launch_sweep_warp(E.s, mode, st, E.sms));
-            LPA_P(cudaEventRecord(ev[2], st));
-            LPA_P(launch_sweep_hub(E.s, mode, E.cfg.hub_threads, E.hub_blocks, st));
-            LPA_P(cudaEventRecord(ev[3], st));
+            for (int b = 0; b < kBins; ++b) {
+                LPA_P(cudaEventRecord(ev[b], st));
+                LPA_P(launch_bin(E, mode, b, st));
+            }
+            LPA_P(cudaEventRecord(ev[kBins], st));
             LPA_P(launch_finish(E.s, mode, p + 1 < passes ? 1 : 0, none, 0, st, E.sms));
-            LPA_P(cudaEventRecord(ev[4], st));
-            LPA_P(cudaEventSynchronize(ev[4]));
+            LPA_P(cudaEventRecord(ev[kBins + 1], st));
+            LPA_P(cudaEventSynchronize(ev[kBins + 1]));
             for (int b = 0; b < kBins; ++b) {
                 LPA_P(cudaEventElapsedTime(&ms, ev[b], ev[b + 1]));
                 sweep_ms[b] += ms;
             }
-            LPA_P(cudaEventElapsedTime(&ms, ev[3], ev[4]));
+            LPA_P(cudaEventElapsedTime(&ms, ev[kBins], ev[kBins + 1]));
             fin_ms += ms;
         }
         LPA_P(cudaMemcpy(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
@@ -545,7 +555,7 @@ lpa_status fill_props(const Engine& E, lpa_graph_props* p) {
     p->weighted = E.weighted ? 1 : 0;
     p->exact = E.exact ? 1 : 0;
     p->max_degree = E.max_degree;
-    p->device_bytes = E.device_bytes + (E.spill_keys ? E.hub_blocks * E.s.spill_slots * 8 : 0);
+    p->device_bytes = E.device_bytes + (E.spill_keys ? E.block_grid[kBlockBins - 1] * E.s.spill_slots * 8 : 0);
     return LPA_OK;
 }
 
@@ -624,7 +634,7 @@ static lpa_status set_config(Engine& E, const lpa_config* cfg) {
     destroy_graphs(E);
     E.cfg = *cfg;
     apply_config_fields(E);
-    lpa_status rs2 = setup_hub(E);
+    lpa_status rs2 = setup_spill(E);
     if (rs2 != LPA_OK) return rs2;
     LPA_CUDA(build_static_lists(E.s, 0));
     return LPA_OK;
@@ -667,13 +677,15 @@ lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t m
     LPA_CUDA(cudaMalloc(&out, (size_t)E.s.N * 4));
     std::vector<lpa_config> cands;
     const int smalls[] = {4, 8};
-    const int warps[] = {128, 512, 1024};
-    const int hubs[][2] = {{256, 4096}, {512, 8192}, {1024, 16384}};
+    const int warps[] = {64, 128, 256};
+    const int mids[] = {512, 1024};
+    const int larges[] = {2048, 4096};
     const int denses[] = {300, 600, 1001};
     for (int sm : smalls)
         for (int wm : warps)
-            for (auto& hb : hubs)
-                for (int dp : denses) cands.push_back(lpa_config{sm, wm, hb[0], hb[1], dp});
+            for (int md : mids)
+                for (int lg : larges)
+                    for (int dp : denses) cands.push_back(lpa_config{sm, wm, md, lg, dp});
     cudaEvent_t e0, e1;
     LPA_CUDA(cudaEventCreate(&e0));
     LPA_CUDA(cudaEventCreate(&e1));

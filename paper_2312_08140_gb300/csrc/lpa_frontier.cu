@@ -104,8 +104,8 @@ cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, in
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ int bin_of(int64_t d, int small_max, int warp_max) {
-    return d <= small_max ? 0 : (d <= warp_max ? 1 : 2);
+__device__ __forceinline__ int bin_of(const DevState& s, int64_t d) {
+    return d <= s.small_max ? 0 : d <= s.warp_max ? 1 : d <= s.mid_max ? 2 : d <= s.large_max ? 3 : 4;
 }
 
 // Block-wide ordered append of up to kVertsPerThread vertices per thread into
@@ -225,7 +225,7 @@ __device__ __forceinline__ void static_chunk(const DevState& s, int64_t v0, int3
             const int64_t d = s.off[v + 1] - s.off[v];
             if (d > 0) {
                 deg[q] = d;
-                bin[q] = (int8_t)bin_of(d, s.small_max, s.warp_max);
+                bin[q] = (int8_t)bin_of(s, d);
             }
         }
     }
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
                     const int64_t d = s.off[v0 + q + 1] - s.off[v0 + q];
                     if (d > 0) {
                         deg[q] = d;
-                        bin[q] = (int8_t)bin_of(d, s.small_max, s.warp_max);
+                        bin[q] = (int8_t)bin_of(s, d);
                     }
                 }
             }

@@ -18,7 +18,10 @@
 namespace lpa {
 
 constexpr int kMaxHist = 64;            // per-sweep history depth (LPA_MAX_RECORDED_ITERS)
-constexpr int kBins = 3;                // small / warp / hub
+constexpr int kBins = 5;                // thread / warp / 128-, 256-, 512-thread block per vertex
+constexpr int kBlockBins = 3;           // bins 2..4 use the block kernel
+constexpr int kBlockThreads[kBlockBins] = {128, 256, 512};
+constexpr int kLargeSlots = 8192;       // shared table of the last bin (spills beyond)
 constexpr int32_t kEmptyKey = -1;       // free slot in label tables; labels are >= 0
 
 enum WeightKind : int { W_UNIT = 0, W_U32 = 1, W_F32 = 2 };
@@ -86,13 +89,15 @@ struct DevState {
     int32_t* iters;            // [G]
     int32_t* exit_reason;      // [G]
     long long* hist_changed;   // [G * kMaxHist]
-    int32_t* spill_keys;       // hub spill tables: [hub_blocks * spill_slots]
+    int32_t* spill_keys;       // spill tables of the last bin: [blocks * spill_slots]
     void* spill_vals;
-    int64_t spill_slots;       // slots per hub block (power of two, 0 = no spill table)
+    int64_t spill_slots;       // slots per block (power of two, 0 = no spill table)
     int32_t small_max;         // degree bins (see lpa_config)
     int32_t warp_max;
+    int32_t mid_max;
+    int32_t large_max;
     int32_t warp_slots;        // per-warp table slots = next pow2 >= 2 * warp_max
-    int32_t hub_slots;         // per-block shared table slots
+    int32_t block_slots[kBlockBins];   // per-block shared table slots of bins 2..4
     int32_t dense_permille;    // dense sweep when entries of changed vertices >= this / 1000 of E
 };
 
@@ -118,9 +123,9 @@ cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, i
                               int local_ids, cudaStream_t st);
 cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms);
 cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int sms);
-cudaError_t launch_sweep_hub(const DevState& s, int mode, int hub_threads, int hub_blocks,
-                             cudaStream_t st);
-int hub_blocks_for(int sms, int hub_threads, int hub_slots);
+// Block-per-vertex sweep of bin 2, 3 or 4; `blocks` from block_grid_for.
+cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int blocks, cudaStream_t st);
+int block_grid_for(const DevState& s, int bin, int sms);
 
 // Graph validation (row-wise).  Results accumulate into *res (device).
 struct ValidateResult {

@@ -1,13 +1,15 @@
-// lpa_sweep_hub.cu -- sweep for high-degree vertices (d > warp_max): one
-// thread block per frontier vertex.
+// lpa_sweep_block.cu -- sweep for vertices with degree above warp_max: one
+// thread block per frontier vertex, the block size growing with the degree
+// bin (128 threads up to mid_max, 256 up to large_max, 512 above) so that the
+// shared table (2^ceil(log2(2d)) slots) per warp stays about constant and the
+// SM keeps enough warps in flight.
 //
 // Warps read the row in 32-entry chunks and group equal labels with
 // __match_any_sync as in the warp kernel; group leaders add their sums into a
-// shared-memory open-addressing table of up to hub_slots slots.  When the row
-// could hold more distinct labels than half the shared table (2d > slots),
-// inserts probe at most kSharedProbes slots and then go to a spill table in
-// global memory private to this block (2^ceil(log2(2d)) slots, so it never
-// fills).  Each label lives in exactly one of the two tables, so scanning both
+// shared-memory open-addressing table.  In the last bin, when the row could
+// hold more distinct labels than half the shared table (2d > slots), inserts
+// probe at most kSharedProbes slots and then go to a spill table in global
+// memory private to this block (2^ceil(log2(2d)) slots, so it never fills).  Each label lives in exactly one of the two tables, so scanning both
 // yields every K_{i->c} (Eq. 3).  The block then reduces (sum, smallest label)
 // to the winner (Section 4.1.5), clears what it used, and on change marks the
 // neighbours unprocessed (Section 4.1.4).
@@ -18,10 +20,10 @@ namespace lpa {
 constexpr int kSharedProbes = 16;
 
 template <bool ASYNC, int WK, bool BATCH>
-__global__ void k_sweep_hub(DevState s, int flag_neighbours) {
+__global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int S = s.hub_slots;
+    const int S = s.block_slots[bin - 2];
     int32_t* keys = reinterpret_cast<int32_t*>(smem_raw);
     T* vals = reinterpret_cast<T*>(keys + S);
     __shared__ uint32_t red_key[32];
@@ -37,11 +39,12 @@ __global__ void k_sweep_hub(DevState s, int flag_neighbours) {
         vals[q] = (T)0;
     }
     if (threadIdx.x == 0) spilled = 0;
-    int32_t* gkeys = s.spill_keys ? s.spill_keys + (size_t)blockIdx.x * s.spill_slots : nullptr;
-    T* gvals = s.spill_keys ? static_cast<T*>(s.spill_vals) + (size_t)blockIdx.x * s.spill_slots : nullptr;
+    const bool last_bin = bin == kBins - 1;
+    int32_t* gkeys = (last_bin && s.spill_keys) ? s.spill_keys + (size_t)blockIdx.x * s.spill_slots : nullptr;
+    T* gvals = gkeys ? static_cast<T*>(s.spill_vals) + (size_t)blockIdx.x * s.spill_slots : nullptr;
     __syncthreads();
 
-    const BinView bv = bin_view(s, 2);
+    const BinView bv = bin_view(s, bin);
     const Labels L = labels_of(s);
     const unsigned cnt = bv.cnt;
     unsigned long long my_changed = 0, my_changed_entries = 0;
@@ -165,44 +168,45 @@ __global__ void k_sweep_hub(DevState s, int flag_neighbours) {
         }
         __syncthreads();    // tables clear and `winner` consumed before the next vertex
     }
-    flush_bin_counts(s, 2, my_changed, my_changed_entries);
+    flush_bin_counts(s, bin, my_changed, my_changed_entries);
 }
 
-int hub_blocks_for(int sms, int hub_threads, int hub_slots) {
-    const size_t smem_per_block = (size_t)hub_slots * 8 + 512;
-    int by_smem = (int)((200 * 1024) / smem_per_block);
-    int by_threads = 2048 / hub_threads;
+int block_grid_for(const DevState& s, int bin, int sms) {
+    const int threads = kBlockThreads[bin - 2];
+    const size_t smem = (size_t)s.block_slots[bin - 2] * 8 + 512;
+    int by_smem = (int)((220 * 1024) / smem);
+    int by_threads = 2048 / threads;
     int per_sm = by_smem < by_threads ? by_smem : by_threads;
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
 }
 
 template <bool ASYNC, int WK, bool BATCH>
-static cudaError_t launch_hub_t(const DevState& s, int flag, int threads, int blocks, cudaStream_t st) {
-    const size_t smem = (size_t)s.hub_slots * 8;
-    auto kern = k_sweep_hub<ASYNC, WK, BATCH>;
+static cudaError_t launch_block_t(const DevState& s, int bin, int flag, int blocks, cudaStream_t st) {
+    const size_t smem = (size_t)s.block_slots[bin - 2] * 8;
+    auto kern = k_sweep_block<ASYNC, WK, BATCH>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    kern<<<blocks, threads, smem, st>>>(s, flag);
+    kern<<<blocks, kBlockThreads[bin - 2], smem, st>>>(s, bin, flag);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_hub(const DevState& s, int mode, int hub_threads, int hub_blocks, cudaStream_t st) {
+cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int blocks, cudaStream_t st) {
     const bool async = mode == MODE_ASYNC;
     const int flag = mode != MODE_SYNC_FULL;
     const bool batch = s.G > 1;
-#define LPA_HUB_W(A, B)                                                                   \
-    switch (s.weight_kind) {                                                              \
-        case W_UNIT: return launch_hub_t<A, W_UNIT, B>(s, flag, hub_threads, hub_blocks, st); \
-        case W_U32: return launch_hub_t<A, W_U32, B>(s, flag, hub_threads, hub_blocks, st);   \
-        default: return launch_hub_t<A, W_F32, B>(s, flag, hub_threads, hub_blocks, st);      \
+#define LPA_BLOCK_W(A, B)                                                             \
+    switch (s.weight_kind) {                                                          \
+        case W_UNIT: return launch_block_t<A, W_UNIT, B>(s, bin, flag, blocks, st);   \
+        case W_U32: return launch_block_t<A, W_U32, B>(s, bin, flag, blocks, st);     \
+        default: return launch_block_t<A, W_F32, B>(s, bin, flag, blocks, st);        \
     }
     if (async) {
-        if (batch) { LPA_HUB_W(true, true) } else { LPA_HUB_W(true, false) }
+        if (batch) { LPA_BLOCK_W(true, true) } else { LPA_BLOCK_W(true, false) }
     } else {
-        if (batch) { LPA_HUB_W(false, true) } else { LPA_HUB_W(false, false) }
+        if (batch) { LPA_BLOCK_W(false, true) } else { LPA_BLOCK_W(false, false) }
     }
-#undef LPA_HUB_W
+#undef LPA_BLOCK_W
 }
 
 }  // namespace lpa

@@ -61,4 +61,5 @@ def test_struct_layouts_match_c(lib_path):
     assert ctypes.sizeof(lpa.LpaRunInfo) == 8 + 3 * 8 * H + 8
     assert ctypes.sizeof(lpa.LpaGraphProps) == 8 * 2 + 4 * 4 + 8 * 5
     assert ctypes.sizeof(lpa.LpaConfig) == 20
-    assert ctypes.sizeof(lpa.LpaProfile) == 16 + 4 * H + 12 * H + 4 * 3 * 8 * H
+    B = lpa.LPA_BINS
+    assert ctypes.sizeof(lpa.LpaProfile) == 16 + 4 * H + 4 * B * H + 4 * B * 8 * H

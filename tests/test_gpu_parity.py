@@ -95,13 +95,14 @@ def test_planted_partition_sync(lpa):
     assert it >= 3
 
 
-@pytest.mark.parametrize("cfg", [None, (4, 64, 256, 1024, 0), (8, 1024, 1024, 16384, 1001),
-                                 (1, 33, 128, 1024, 200)])
+@pytest.mark.parametrize("cfg", [None, (4, 64, 512, 1024, 0), (8, 256, 2048, 4096, 1001),
+                                 (1, 33, 100, 200, 200)])
 def test_rmat_bins_and_spill_sync(lpa, cfg):
-    """R-MAT scale 14 has vertices in all three degree bins; hub_slots = 1024 forces
-    the global spill table for every hub with degree > 512."""
-    g = L.rmat(14, 16, seed=3)
-    assert int(np.diff(g.off).max()) > 2048
+    """R-MAT scale 16 has vertices in all five degree bins; rows above 4096
+    entries overflow the 8192-slot shared table of the last bin and use its
+    global spill table."""
+    g = L.rmat(16, 16, seed=3)
+    assert int(np.diff(g.off).max()) > 4096
     assert_sync_parity(lpa, g, cfg=cfg)
 
 
