@@ -111,7 +111,9 @@ typedef struct {
  *   warp_max  < d <= mid_max        one 128-thread block per vertex, shared table
  *   mid_max   < d <= large_max      one 256-thread block per vertex, shared table
  *   d > large_max                   one 512-thread block per vertex, 8192-slot shared
- *                                   table spilling to a global table
+ *                                   table; a row whose distinct labels overflow it
+ *                                   is rescanned by several blocks, each keeping
+ *                                   one hash partition of the labels
  * A sweep is "dense" (every vertex with an entry is scanned, no frontier
  * compaction) when the vertices changed since the previous compaction hold
  * at least dense_permille / 1000 of all entries; the first sweep is always

@@ -65,8 +65,7 @@ struct Engine {
     int64_t device_bytes = 0;
     lpa_config cfg{4, 128, 512, 2048, 500};
     int block_grid[kBlockBins] = {0, 0, 0};
-    int32_t* spill_keys = nullptr;
-    void* spill_vals = nullptr;
+    Overflow* ovf = nullptr;
     cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
     cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
     cudaStream_t cap_top = nullptr, cap_body = nullptr;
@@ -107,41 +106,20 @@ void engine_free(Engine& E) {
     if (E.cap_body) cudaStreamDestroy(E.cap_body);
     for (void* p : E.owned) cudaFree(p);
     E.owned.clear();
-    if (E.spill_keys) cudaFree(E.spill_keys);
-    if (E.spill_vals) cudaFree(E.spill_vals);
-    E.spill_keys = nullptr;
-    E.spill_vals = nullptr;
+    if (E.ovf) cudaFree(E.ovf);
+    E.ovf = nullptr;
 }
 
-// Spill tables of the last block bin: needed when a row there can hold more
-// distinct labels than half the shared table.  Sized for the maximum degree;
-// the number of blocks of that bin is capped so the tables stay within a
-// fixed budget.
-lpa_status setup_spill(Engine& E) {
-    if (E.spill_keys) cudaFree(E.spill_keys);
-    if (E.spill_vals) cudaFree(E.spill_vals);
-    E.spill_keys = nullptr;
-    E.spill_vals = nullptr;
-    E.s.spill_keys = nullptr;
-    E.s.spill_vals = nullptr;
-    E.s.spill_slots = 0;
+// Grid sizes of the block bins, and the overflow list of the last bin (one
+// entry per vertex of that bin at most).
+lpa_status setup_blocks(Engine& E) {
     for (int b = 0; b < kBlockBins; ++b) E.block_grid[b] = block_grid_for(E.s, b + 2, E.sms);
-    const int64_t need = pow2ceil(2 * std::max<int64_t>(E.max_degree, 1));
-    if (E.max_degree > E.cfg.large_max && need > kLargeSlots) {
-        const int64_t budget = (int64_t)2 << 30;   // 2 GiB of spill tables at most
-        const int64_t per_block = need * 8;
-        int64_t blocks = std::min<int64_t>(E.block_grid[kBlockBins - 1], std::max<int64_t>(1, budget / per_block));
-        E.block_grid[kBlockBins - 1] = (int)blocks;
-        cudaError_t err = cudaMalloc(&E.spill_keys, (size_t)(blocks * need * 4));
-        if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(spill keys)");
-        err = cudaMalloc(&E.spill_vals, (size_t)(blocks * need * 4));
-        if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(spill values)");
-        LPA_CUDA(cudaMemset(E.spill_keys, 0xff, (size_t)(blocks * need * 4)));
-        LPA_CUDA(cudaMemset(E.spill_vals, 0, (size_t)(blocks * need * 4)));
-        E.s.spill_keys = E.spill_keys;
-        E.s.spill_vals = E.spill_vals;
-        E.s.spill_slots = need;
-    }
+    if (E.ovf) cudaFree(E.ovf);
+    E.ovf = nullptr;
+    const size_t n = std::max<size_t>(E.s.bin_static[kBins - 1], 1);
+    cudaError_t err = cudaMalloc(&E.ovf, n * sizeof(Overflow));
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(overflow list)");
+    E.s.ovf = E.ovf;
     return LPA_OK;
 }
 
@@ -278,8 +256,8 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     LPA_CUDA(cudaMemsetAsync(E.s.ctrl, 0, sizeof(Ctrl), st));
     LPA_CUDA(cudaMemsetAsync(E.s.hist_changed, 0, (size_t)G * kMaxHist * 8, st));
     apply_config_fields(E);
-    if ((rs = setup_spill(E)) != LPA_OK) return rs;
     LPA_CUDA(build_static_lists(E.s, st));
+    if ((rs = setup_blocks(E)) != LPA_OK) return rs;
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_top, cudaStreamNonBlocking));
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_body, cudaStreamNonBlocking));
     LPA_CUDA(cudaStreamSynchronize(st));
@@ -555,7 +533,7 @@ lpa_status fill_props(const Engine& E, lpa_graph_props* p) {
     p->weighted = E.weighted ? 1 : 0;
     p->exact = E.exact ? 1 : 0;
     p->max_degree = E.max_degree;
-    p->device_bytes = E.device_bytes + (E.spill_keys ? E.block_grid[kBlockBins - 1] * E.s.spill_slots * 8 : 0);
+    p->device_bytes = E.device_bytes + (int64_t)std::max<size_t>(E.s.bin_static[kBins - 1], 1) * sizeof(Overflow);
     return LPA_OK;
 }
 
@@ -634,10 +612,8 @@ static lpa_status set_config(Engine& E, const lpa_config* cfg) {
     destroy_graphs(E);
     E.cfg = *cfg;
     apply_config_fields(E);
-    lpa_status rs2 = setup_spill(E);
-    if (rs2 != LPA_OK) return rs2;
     LPA_CUDA(build_static_lists(E.s, 0));
-    return LPA_OK;
+    return setup_blocks(E);
 }
 
 lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config* cfg) {

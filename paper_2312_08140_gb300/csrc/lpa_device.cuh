@@ -114,9 +114,8 @@ __device__ __forceinline__ bool table_add(int32_t* keys, T* vals, int log_slots,
 }
 
 // Bounded variant: gives up after max_probes occupied slots; returns false if
-// the label is not in the table and could not be placed.  Keys are never
-// removed while a vertex is being scanned, so a label that failed once fails
-// again: every label lives in exactly one of the shared and spill tables.
+// the label is not in the table and could not be placed (the caller then
+// treats the row as overflowing the table).
 template <typename T>
 __device__ __forceinline__ bool table_add_bounded(int32_t* keys, T* vals, int log_slots, int32_t label, T w,
                                                   int max_probes) {

@@ -73,6 +73,7 @@ __global__ void k_init(DevState s) {
         c->dense[0] = 1;
         c->dense[1] = 0;
         c->pass_changed_entries = 0;
+        c->ovf_packed = 0;
         for (int b = 0; b < kBins; ++b) {
             c->bin_cnt[0][b] = s.bin_static[b];
             c->bin_entries[0][b] = s.bin_static_entries[b];
@@ -390,7 +391,7 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         }
         c->total_sweeps += 1;
         c->total_scanned += scn;
-        c->total_sweep_launches += mode == MODE_ASYNC ? 8 : 4;
+        c->total_sweep_launches += mode == MODE_ASYNC ? 2 * (kBins + 2) : kBins + 2;
         for (int b = 0; b < kBins; ++b) {
             c->bin_changed[b] = 0;
             c->bin_changed_entries[b] = 0;
@@ -413,6 +414,7 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
     c->dense[wr] = dense_next;
     c->rd = wr;
     c->pass_changed_entries = 0;
+    c->ovf_packed = 0;
     c->ticket = 0;
     __threadfence();
     if (role == 0 && in_graph) cudaGraphSetConditional(h, any ? 1u : 0u);

@@ -21,7 +21,8 @@ constexpr int kMaxHist = 64;            // per-sweep history depth (LPA_MAX_RECO
 constexpr int kBins = 5;                // thread / warp / 128-, 256-, 512-thread block per vertex
 constexpr int kBlockBins = 3;           // bins 2..4 use the block kernel
 constexpr int kBlockThreads[kBlockBins] = {128, 256, 512};
-constexpr int kLargeSlots = 8192;       // shared table of the last bin (spills beyond)
+constexpr int kLargeSlots = 8192;       // shared table of the last bin (overflowing rows are
+                                        // rescanned split over label partitions)
 constexpr int32_t kEmptyKey = -1;       // free slot in label tables; labels are >= 0
 
 enum WeightKind : int { W_UNIT = 0, W_U32 = 1, W_F32 = 2 };
@@ -59,6 +60,24 @@ struct Ctrl {
     long long total_sweeps;              // cumulative over all runs (never reset)
     long long total_scanned;
     long long total_sweep_launches;      // kernel launches of those sweeps
+    unsigned long long ovf_packed;       // overflow list: (entries << 40) | partition work items
+};
+
+// A last-bin row whose distinct labels overflowed the block's shared table.
+// It is rescanned by `parts` blocks, block p aggregating only the labels whose
+// hash falls in partition p; each block folds its best (sum, label) into
+// `best` and the block that completes the row applies the result.
+struct Overflow {
+    int32_t v;                 // vertex
+    uint32_t slot;             // its slot in the bin's frontier list
+    int64_t st;                // row start
+    int32_t d;                 // row length
+    int32_t own;               // label before the sweep
+    uint32_t item_base;        // first partition work item of this row
+    uint32_t parts;            // number of partitions
+    unsigned long long best;   // max over partitions of (sum key << 32) | (~label)
+    unsigned int done;         // partitions completed
+    unsigned int pad;
 };
 
 // Everything a kernel needs, passed by value.
@@ -89,9 +108,8 @@ struct DevState {
     int32_t* iters;            // [G]
     int32_t* exit_reason;      // [G]
     long long* hist_changed;   // [G * kMaxHist]
-    int32_t* spill_keys;       // spill tables of the last bin: [blocks * spill_slots]
-    void* spill_vals;
-    int64_t spill_slots;       // slots per block (power of two, 0 = no spill table)
+    struct Overflow* ovf;      // [bin_static[4]] last-bin rows whose labels overflowed the shared
+                               // table, rescanned split over label partitions
     int32_t small_max;         // degree bins (see lpa_config)
     int32_t warp_max;
     int32_t mid_max;
@@ -124,6 +142,7 @@ cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, i
 cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms);
 cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int sms);
 // Block-per-vertex sweep of bin 2, 3 or 4; `blocks` from block_grid_for.
+// For bin 4 this also launches the partitioned rescan of overflowed rows.
 cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int blocks, cudaStream_t st);
 int block_grid_for(const DevState& s, int bin, int sms);
 

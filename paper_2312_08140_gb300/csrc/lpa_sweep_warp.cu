@@ -45,7 +45,7 @@ __device__ __forceinline__ typename Acc<WK>::T group_sum(unsigned peers, typenam
 }
 
 template <bool ASYNC, int WK, bool BATCH>
-__global__ void __launch_bounds__(kWarpThreads) k_sweep_warp(DevState s, int flag_neighbours) {
+__global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wslots = s.warp_slots;
