@@ -47,6 +47,16 @@ __device__ __forceinline__ int32_t load_index(const int32_t* idx, int64_t e) {
     return __ldcs(idx + e);   // streamed once per sweep: evict-first
 }
 
+// Row indices that are read again when the vertex changes (neighbour marks).
+__device__ __forceinline__ int32_t load_index_keep(const int32_t* idx, int64_t e) {
+    return __ldg(idx + e);
+}
+
+// Whether this pass writes neighbour marks (Section 4.1.4).
+__device__ __forceinline__ bool marks_on(const DevState& s, int flag_neighbours) {
+    return flag_neighbours && !s.ctrl->skip_marks;
+}
+
 // Sync mode reads labels that no thread writes during the sweep (read-only
 // path); async mode reads labels other SMs update in place, so it bypasses L1.
 // A vertex's own label is written only by the thread that scans it, so it may

@@ -70,6 +70,8 @@ __global__ void k_init(DevState s) {
         c->ticket = 0;
         c->cbuf = 0;
         c->rd = 0;
+        c->skip_marks = 1;          // the first pass changes nearly every label
+        c->last_pass_high = 0;
         c->dense[0] = 1;
         c->dense[1] = 0;
         c->pass_changed_entries = 0;
@@ -411,6 +413,12 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         c->bin_cnt[rd][b] = 0;
         c->bin_entries[rd][b] = 0;
     }
+    // Marks are useless when the next pass is dense anyway.  After two passes
+    // in a row that changed almost every vertex, the next pass skips them and
+    // the one after it is dense.
+    const bool high = (double)vc->pass_changed_entries * 1000.0 >= (double)kHighPermille * (double)s.active_entries;
+    c->skip_marks = (high && vc->last_pass_high) ? 1 : 0;
+    c->last_pass_high = high ? 1 : 0;
     c->dense[wr] = dense_next;
     c->rd = wr;
     c->pass_changed_entries = 0;
@@ -456,7 +464,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
     }
 
     const unsigned long long che = ((volatile Ctrl*)s.ctrl)->pass_changed_entries;
-    const int dense = mode == MODE_SYNC_FULL ||
+    const int dense = mode == MODE_SYNC_FULL || s.ctrl->skip_marks ||
                       (double)che * 1000.0 >= (double)s.dense_permille * (double)s.active_entries;
 
     const int64_t nchunks = (s.N + kVertsPerThread - 1) / kVertsPerThread;

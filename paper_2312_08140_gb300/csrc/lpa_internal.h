@@ -21,6 +21,7 @@ constexpr int kMaxHist = 64;            // per-sweep history depth (LPA_MAX_RECO
 constexpr int kBins = 5;                // thread / warp / 128-, 256-, 512-thread block per vertex
 constexpr int kBlockBins = 3;           // bins 2..4 use the block kernel
 constexpr int kBlockThreads[kBlockBins] = {128, 256, 512};
+constexpr int kHighPermille = 900;      // "almost every vertex changed" (see skip_marks)
 constexpr int kLargeSlots = 8192;       // shared table of the last bin (overflowing rows are
                                         // rescanned split over label partitions)
 constexpr int32_t kEmptyKey = -1;       // free slot in label tables; labels are >= 0
@@ -43,6 +44,9 @@ struct Ctrl {
                                          // every compaction, which writes buffer rd ^ 1)
     int32_t dense[2];                    // buffer holds the static bin lists (every vertex)
     int32_t cbuf;                        // labels of the current sweep are lab[cbuf]
+    int32_t skip_marks;                  // current pass writes no neighbour marks; the next
+                                         // pass is dense (scans every vertex) instead
+    int32_t last_pass_high;              // previous pass changed >= kHighPermille of entries
     unsigned int bin_cnt[2][kBins];      // frontier list lengths per buffer
     unsigned long long bin_entries[2][kBins];   // CSR entries of those vertices
     unsigned long long bin_changed[kBins];      // vertices changed in the current sweep, per bin

@@ -104,6 +104,7 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
 
     const BinView bv = bin_view(s, bin);
     const Labels L = labels_of(s);
+    const bool marks = marks_on(s, flag_neighbours);
     const unsigned cnt = bv.cnt;
     const int log_S = ceil_log2((unsigned)S);
     unsigned long long my_changed = 0, my_changed_entries = 0;
@@ -126,7 +127,7 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
             if (!fits && *(volatile int*)&overflow) break;     // warp-uniform
             const int64_t e = e0 + lane;
             const bool in = e < en;
-            const int32_t j = in ? load_index(s.idx, e) : v;
+            const int32_t j = in ? load_index_keep(s.idx, e) : v;
             const bool ok = in && j != v;
             const int32_t lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
             T w = ok ? load_weight<WK>(s.w, e) : (T)0;
@@ -183,7 +184,7 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
                 my_changed_entries += (unsigned long long)d;
                 if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
             }
-            if (flag_neighbours) mark_neighbours(s, v, st, en);
+            if (marks) mark_neighbours(s, v, st, en);
         }
         __syncthreads();    // `winner` consumed before the next vertex
     }
@@ -227,6 +228,7 @@ __global__ void k_sweep_parts(DevState s, int flag_neighbours) {
     const uint32_t items = (uint32_t)(packed & ((1ull << 40) - 1));
     const BinView bv = bin_view(s, kBins - 1);
     const Labels L = labels_of(s);
+    const bool marks = marks_on(s, flag_neighbours);
     const int log_S = ceil_log2((unsigned)S);
     unsigned long long my_changed = 0, my_changed_entries = 0;
     for (uint32_t item = blockIdx.x; item < items; item += gridDim.x) {
@@ -300,7 +302,7 @@ __global__ void k_sweep_parts(DevState s, int flag_neighbours) {
                     if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
                 }
             }
-            if (changed && flag_neighbours) mark_neighbours(s, v, st, en);
+            if (changed && marks) mark_neighbours(s, v, st, en);
         }
         __syncthreads();
     }

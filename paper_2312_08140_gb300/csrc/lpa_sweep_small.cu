@@ -29,6 +29,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
     using T = typename Acc<WK>::T;
     const BinView bv = bin_view(s, 0);
     const Labels L = labels_of(s);
+    const bool marks = marks_on(s, flag_neighbours);
     const unsigned cnt = bv.cnt;
     const unsigned stride = gridDim.x * blockDim.x;
     constexpr int RUN = ASYNC ? kAsyncRun : 1;
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
         const bool changed = act && any && best != own;
         if (slot) record_label<ASYNC>(L, bv.chg + k, v, own, best, changed);
         if (changed) {
-            if (flag_neighbours) {
+            if (marks) {
 #pragma unroll
                 for (int q = 0; q < MAXD; ++q)
                     if (q < d && nb[q] != v) s.flags[nb[q]] = 1;

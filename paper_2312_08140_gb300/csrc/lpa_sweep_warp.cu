@@ -61,14 +61,19 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
 
     const BinView bv = bin_view(s, 1);
     const Labels L = labels_of(s);
+    const bool marks = marks_on(s, flag_neighbours);
     const unsigned cnt = bv.cnt;
     const unsigned nwarps = gridDim.x * kWarpsPerBlock;
+    // each warp takes batches of B consecutive frontier entries (B <= 32), B
+    // shrinking when the bin is too small to give every warp a full batch
+    unsigned B = (cnt + nwarps - 1) / nwarps;
+    B = B < 1u ? 1u : (B > 32u ? 32u : B);
     unsigned long long my_changed = 0, my_changed_entries = 0;
-    for (unsigned base = (blockIdx.x * kWarpsPerBlock + wib) * 32u; base < cnt; base += nwarps * 32u) {
-        // Metadata of up to 32 consecutive frontier entries, one per lane, loaded
+    for (unsigned base = (blockIdx.x * kWarpsPerBlock + wib) * B; base < cnt; base += nwarps * B) {
+        // Metadata of up to B consecutive frontier entries, one per lane, loaded
         // together so their latencies overlap.
         const unsigned kl = base + lane;
-        const bool okl = kl < cnt;
+        const bool okl = lane < B && kl < cnt;
         const int32_t vl = okl ? bv.list[kl] : 0;
         int64_t stl = 0, enl = 0;
         int32_t ownl = 0;
@@ -81,12 +86,12 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
                 if (s.done[s.gid[vl]]) actl = 0;
             }
         }
-        const unsigned nv = min(32u, cnt - base);
+        const unsigned nv = min(B, cnt - base);
         // indices of the first chunk of the next vertex are fetched one vertex ahead
         int32_t jpre = kEmptyKey;
         {
             const int64_t st0 = __shfl_sync(kFull, stl, 0), en0 = __shfl_sync(kFull, enl, 0);
-            if (__shfl_sync(kFull, actl, 0) && st0 + lane < en0) jpre = load_index(s.idx, st0 + lane);
+            if (__shfl_sync(kFull, actl, 0) && st0 + lane < en0) jpre = load_index_keep(s.idx, st0 + lane);
         }
         for (unsigned i = 0; i < nv; ++i) {
             const int32_t v = __shfl_sync(kFull, vl, i);
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
                 const unsigned i2 = (i + 1) & 31u;
                 const int64_t st2 = __shfl_sync(kFull, stl, i2), en2 = __shfl_sync(kFull, enl, i2);
                 const int a2 = __shfl_sync(kFull, actl, i2) && (i + 1 < nv);
-                jpre = (a2 && st2 + lane < en2) ? load_index(s.idx, st2 + lane) : kEmptyKey;
+                jpre = (a2 && st2 + lane < en2) ? load_index_keep(s.idx, st2 + lane) : kEmptyKey;
             }
             uint32_t key = 0;
             int32_t cand = 0;
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
                 const int log_slots = ceil_log2(2u * (unsigned)d);
                 for (int64_t e0 = st; e0 < en; e0 += 32) {
                     const int64_t e = e0 + lane;
-                    const int32_t jn = (e + 32 < en) ? load_index(s.idx, e + 32) : kEmptyKey;
+                    const int32_t jn = (e + 32 < en) ? load_index_keep(s.idx, e + 32) : kEmptyKey;
                     const bool ok = e < en && j != v;
                     const int32_t lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
                     const T w = ok ? load_weight<WK>(s.w, e) : (T)0;
@@ -160,10 +165,14 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
             const bool changed = act && best >= 0 && best != own;   // warp-uniform
             if (lane == 0) record_label<ASYNC>(L, bv.chg + base + i, v, own, best, changed);
             if (changed) {
-                if (flag_neighbours) {
-                    for (int64_t e = st + lane; e < en; e += 32) {
-                        const int32_t jj = s.idx[e];
-                        if (jj != v) s.flags[jj] = 1;
+                if (marks) {
+                    if (d <= 32) {                   // this row's indices are still in j
+                        if ((int)lane < d && j != v) s.flags[j] = 1;
+                    } else {
+                        for (int64_t e = st + lane; e < en; e += 32) {
+                            const int32_t jj = s.idx[e];
+                            if (jj != v) s.flags[jj] = 1;
+                        }
                     }
                 }
                 if (lane == 0) {
