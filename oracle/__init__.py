@@ -6,7 +6,7 @@ share no code.  The arithmetic lives in ``lpa_oracle.c`` (plain single-threaded
 C, fp64 sums); this module compiles it with gcc and marshals numpy arrays.
 
 Functions and the passages they follow:
-  pick(...)            Eq. 3 (Section 3.3) with the strict smallest-id tie-break
+  pick(...)            Eq. 2 (Section 3.3) with the strict smallest-id tie-break
                        (Section 4.1.5); scanCommunities of Algorithm 1.
   lpa_sync(...)        Jacobi reading of Algorithm 1 (all vertices read the
                        previous sweep's labels); tolerance and cap of Sections

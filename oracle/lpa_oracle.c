@@ -8,7 +8,7 @@
  * (the CUDA library) never calls it and shares no code with it.
  *
  * What it computes, in the paper's order and notation:
- *   - oracle_pick:       the label update rule (Eq. 3, Section 3.3): the
+ *   - oracle_pick:       the label update rule (Eq. 2, Section 3.3): the
  *                        label c maximising K_{i->c}, the summed weight of
  *                        i's neighbours j != i with C_j = c, as the
  *                        scanCommunities step of Algorithm 1 accumulates it
@@ -106,7 +106,7 @@ static int64_t scan_communities(kv_table *H, const int64_t *off, const int32_t *
     return used;
 }
 
-/* The most weighted label in H (Eq. 3); ties go to the smallest label id. */
+/* The most weighted label in H (Eq. 2); ties go to the smallest label id. */
 static int32_t most_weighted_label(const kv_table *H) {
     int32_t best = -1;
     double best_w = 0.0;
@@ -145,7 +145,7 @@ static int converged(int64_t dN, int64_t n, double tau) {
     return (double)dN / (double)n <= tau;
 }
 
-/* One label for vertex i given labels C (Eq. 3 with the strict tie-break). */
+/* One label for vertex i given labels C (Eq. 2 with the strict tie-break). */
 int32_t oracle_pick(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                     const int32_t *C, int64_t i) {
     if (check_csr(n, off, idx) || i < 0 || i >= n || !C) return ORACLE_BAD_ARG;

@@ -5,7 +5,7 @@
 // One engine runs G >= 1 independent graphs packed into one CSR with global
 // vertex ids (a single graph is G = 1).  Per sweep t (lpaMove of Algorithm 1):
 //   sweep kernels  (one per degree bin) read the frontier lists L_t, pick the
-//                  most weighted label per vertex (Eq. 3, smallest-id ties),
+//                  most weighted label per vertex (Eq. 2, smallest-id ties),
 //                  write changes and re-flag neighbours (vertex pruning);
 //   finish kernel  applies the sync-mode changes, compacts flags into L_{t+1}
 //                  and, in its last block, runs the per-graph tolerance test

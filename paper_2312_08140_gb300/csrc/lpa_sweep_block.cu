@@ -7,7 +7,7 @@
 // Warps read the row in 32-entry chunks and group equal labels with
 // __match_any_sync as in the warp kernel; group leaders add their sums into a
 // shared-memory open-addressing table; the block then reduces (sum, smallest
-// label) to the winner (Eq. 3; Section 4.1.5) and, on change, marks the
+// label) to the winner (Eq. 2; Section 4.1.5) and, on change, marks the
 // neighbours unprocessed (Section 4.1.4).
 //
 // Last bin (d > large_max): the table has kLargeSlots slots.  Rows longer than

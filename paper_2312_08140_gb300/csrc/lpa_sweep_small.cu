@@ -1,7 +1,7 @@
 // lpa_sweep_small.cu -- sweep for low-degree vertices (degree <= small_max <= 8):
 // one thread per frontier vertex.  The thread loads its row's neighbour ids,
 // weights and neighbour labels into registers and evaluates the update rule
-// (Eq. 3, Section 3.3) by comparing every pair of entries: the sum for the
+// (Eq. 2, Section 3.3) by comparing every pair of entries: the sum for the
 // label of entry q is the total weight of entries carrying the same label.
 // Self-loops are skipped (scanCommunities, Algorithm 1); ties go to the
 // smallest label id (Section 4.1.5).  When the label changes the thread marks

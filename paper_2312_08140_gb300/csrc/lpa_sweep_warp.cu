@@ -7,7 +7,7 @@
 // combined (a popcount for unit weights, a group reduction for integer
 // weights), so each distinct label of the chunk costs one table update.
 //   d <= 32: the grouped sums are already the per-label totals K_{i->c}
-//            (Eq. 3) and the warp takes the argmax directly.
+//            (Eq. 2) and the warp takes the argmax directly.
 //   d  > 32: group leaders add their sums into a per-warp open-addressing
 //            table in shared memory sized 2^ceil(log2(2d)) slots (so it can
 //            never fill), then the warp scans the table for the argmax and

@@ -1,7 +1,7 @@
 """Pins for the CPU oracle: each check ties it to something other than itself.
 
-- hand-worked runs derived on paper from Algorithm 1 and Eq. 3 (tests/golden),
-- brute-force enumeration of the label space for the update rule (Eq. 3),
+- hand-worked runs derived on paper from Algorithm 1 and Eq. 2 (tests/golden),
+- brute-force enumeration of the label space for the update rule (Eq. 2),
 - invariants any label propagation run has (labels travel along edges only;
   a synchronous fixed point is stable),
 - modularity (Eq. 1) closed forms and the networkx library routine,
@@ -48,9 +48,9 @@ def test_hand_worked(case):
     assert changed.tolist() == case["changed"]
 
 
-# ---------------------------------------------------------------- Eq. 3 --
+# ---------------------------------------------------------------- Eq. 2 --
 def _enumerated_pick(g, C, i):
-    """Eq. 3 by enumerating every candidate label c = 0..n-1 in increasing order:
+    """Eq. 2 by enumerating every candidate label c = 0..n-1 in increasing order:
     K_{i->c} is summed over the row directly; the first c reaching the maximum
     wins.  A vertex with no neighbour besides itself keeps C[i]."""
     n = g.n
@@ -110,7 +110,7 @@ def test_sync_run_is_iterated_sweeps():
 
 def _serial_async_restated(g, tau, cap):
     """Algorithm 1 with one thread, written as a worklist of pending vertices
-    scanned in increasing id order; each pick is the enumerated Eq. 3."""
+    scanned in increasing id order; each pick is the enumerated Eq. 2."""
     n = g.n
     C = np.arange(n, dtype=np.int32)
     pending = set(range(n))
