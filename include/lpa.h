@@ -225,6 +225,23 @@ lpa_status lpa_modularity(lpa_graph_t g, const int32_t *labels, double *q_out, v
 lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters,
                         int32_t trials, void *stream, lpa_config *chosen);
 
+/* Modularity of a labelling, as lpa_modularity, for callers that cannot let
+ * the library allocate device memory: the CSR stays in the caller's device
+ * arrays (same rules as lpa_graph_create; not validated here) and the working
+ * memory is a fixed array inside the library, sized for at most 1,048,576
+ * vertices (larger n returns LPA_ERR_INVALID_ARG).  The paper has no
+ * counterpart to this entry point; it exists for code that runs where
+ * cudaMalloc is not available to it (a host framework's memory pool, a
+ * latency-critical loop, an ongoing stream capture).
+ *   n, nnz, offsets, indices, weights   device CSR (weights NULL = unit)
+ *   labels   device int32[n], each in [0, n)
+ *   q_out    host double; the call synchronises `stream` before returning.
+ * Allocates nothing.  The first call on each device looks up the array's
+ * device address; make it before any stream capture.  Every call uses the
+ * same array: calls that run concurrently on the GPU race. */
+lpa_status lpa_modularity_noalloc(int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *indices,
+                                  const float *weights, const int32_t *labels, double *q_out, void *stream);
+
 /* ---------------------------------------------------------------- batches */
 
 /* G independent graphs packed back to back into one handle, solved together

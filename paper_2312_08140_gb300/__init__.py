@@ -126,6 +126,7 @@ _SIGS = {
     "lpa_run": ([_V, ctypes.c_int, _F, _I32, _V, _V, _P(LpaRunInfo)], ctypes.c_int),
     "lpa_run_profiled": ([_V, ctypes.c_int, _F, _I32, _V, _V, _P(LpaRunInfo), _P(LpaProfile)], ctypes.c_int),
     "lpa_modularity": ([_V, _V, _P(ctypes.c_double), _V], ctypes.c_int),
+    "lpa_modularity_noalloc": ([_I64, _I64, _V, _V, _V, _V, _P(ctypes.c_double), _V], ctypes.c_int),
     "lpa_autotune": ([_V, ctypes.c_int, _F, _I32, _I32, _V, _P(LpaConfig)], ctypes.c_int),
     "lpa_batch_create": ([_I32, _V, _V, _V, _V, _V, _U32, _V, _P(_V)], ctypes.c_int),
     "lpa_batch_destroy": ([_V], ctypes.c_int),
@@ -250,6 +251,15 @@ def lpa_run_profiled(g, mode, tolerance, max_iters, labels_out, stream=None):
 def lpa_modularity(g, labels, stream=None) -> float:
     q = ctypes.c_double()
     _check(load().lpa_modularity(g, _ptr(labels), ctypes.byref(q), _stream(stream)))
+    return q.value
+
+
+def lpa_modularity_noalloc(n, nnz, offsets, indices, weights, labels, stream=None) -> float:
+    """Modularity from caller-owned device CSR and labels; the library allocates
+    nothing for it (for callers that may not allocate device memory)."""
+    q = ctypes.c_double()
+    _check(load().lpa_modularity_noalloc(n, nnz, _ptr(offsets), _ptr(indices), _ptr(weights), _ptr(labels),
+                                         ctypes.byref(q), _stream(stream)))
     return q.value
 
 

@@ -539,6 +539,14 @@ lpa_status fill_props(const Engine& E, lpa_graph_props* p) {
 
 }  // namespace
 
+namespace lpa {
+// Error text for entry points defined in other translation units.
+void set_last_error(lpa_status st, const char* msg) {
+    (void)st;
+    g_last_error = msg;
+}
+}  // namespace lpa
+
 struct lpa_graph {
     Engine e;
 };
