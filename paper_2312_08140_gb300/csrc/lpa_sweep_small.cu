@@ -7,13 +7,21 @@
 // smallest label id (Section 4.1.5).  When the label changes the thread marks
 // all other neighbours unprocessed (vertex pruning, Section 4.1.4).
 //
-// Asynchronous mode: each thread takes a run of kAsyncRun consecutive
-// frontier entries and processes them one after another, so a vertex reads the
-// labels its predecessors in the run have just written -- the GPU counterpart
-// of the paper's threads walking contiguous chunks of vertices (Section 4.1,
-// 4.1.1).  One vertex per thread would make every thread of a sweep read the
-// labels left by the previous sweep, which turns the sweep into a Jacobi
-// update that oscillates on bipartite structure such as lattices.
+// Asynchronous mode (k_sweep_small_async): each thread takes a run of kRun
+// consecutive frontier entries and processes them one after another, so a
+// vertex reads the labels its predecessors in the run have just written --
+// the GPU counterpart of the paper's threads walking contiguous chunks of
+// vertices (Sections 4.1, 4.1.1).  One vertex per thread would make every
+// thread of a sweep read the labels left by the previous sweep, which turns
+// the sweep into a Jacobi update that oscillates on bipartite structure such
+// as lattices.  Walking runs straight from global memory scatters each warp's
+// loads over 32 rows and re-reads the CSR from DRAM many times over, so the
+// block first stages a tile of kRun x 256 rows (frontier id, row length,
+// indices, weights) into shared memory with loads in which the lanes of a
+// warp read consecutive rows, then each thread walks its run out of shared
+// memory (run stride kRun + 1 words: conflict-free banks).  Neighbour labels
+// are still read from global memory at processing time, so updates made
+// during the sweep are seen.
 //
 // Memory per vertex: two offsets, d indices, d weights, d label gathers, one
 // own-label load; on change one label write and d flag bytes.
@@ -22,7 +30,9 @@
 namespace lpa {
 
 constexpr int kSmallThreads = 256;
-constexpr int kAsyncRun = 32;
+constexpr int kRun = 8;                               // async run length
+constexpr int kTile = kRun * kSmallThreads;           // frontier entries staged per block step
+constexpr int kStride = kRun + 1;                     // shared-memory words per run
 
 template <bool ASYNC, int WK, bool BATCH, int MAXD>
 __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int flag_neighbours) {
@@ -32,7 +42,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
     const bool marks = marks_on(s, flag_neighbours);
     const unsigned cnt = bv.cnt;
     const unsigned stride = gridDim.x * blockDim.x;
-    constexpr int RUN = ASYNC ? kAsyncRun : 1;
+    constexpr int RUN = 1;                            // async mode uses k_sweep_small_async
     const unsigned nruns = (cnt + RUN - 1) / RUN;
     unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned rbase = blockIdx.x * blockDim.x; rbase < nruns; rbase += stride)
@@ -97,31 +107,154 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
     flush_bin_counts(s, 0, my_changed, my_changed_entries);
 }
 
+// Staged asynchronous variant (see the file comment).
+template <int WK, int MAXD>
+__host__ __device__ constexpr size_t async_smem_bytes() {
+    return (size_t)kSmallThreads * kStride * (4 + 4 + 4 * MAXD + (WK == W_UNIT ? 0 : 4 * MAXD) + 1);
+}
+
+template <int WK, bool BATCH, int MAXD>
+__global__ void __launch_bounds__(kSmallThreads) k_sweep_small_async(DevState s, int flag_neighbours) {
+    using T = typename Acc<WK>::T;
+    constexpr int SL = kSmallThreads * kStride;              // slots per array
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int32_t* sv = reinterpret_cast<int32_t*>(smem_raw);       // vertex, -1 = inactive slot
+    int32_t* sown = sv + SL;                                   // its label before the sweep
+    int32_t* sidx = sown + SL;                                 // [MAXD][SL] row indices
+    T* sw = reinterpret_cast<T*>(sidx + MAXD * SL);            // [MAXD][SL] weights (not for unit weights)
+    uint8_t* sd = reinterpret_cast<uint8_t*>(sidx + MAXD * SL + (WK == W_UNIT ? 0 : MAXD * SL));
+    const BinView bv = bin_view(s, 0);
+    const Labels L = labels_of(s);
+    const bool marks = marks_on(s, flag_neighbours);
+    const unsigned cnt = bv.cnt;
+    unsigned long long my_changed = 0, my_changed_entries = 0;
+    for (unsigned tile = blockIdx.x * (unsigned)kTile; tile < cnt; tile += gridDim.x * (unsigned)kTile) {
+        // stage: entry i of the tile goes to run i / kRun, position i % kRun
+#pragma unroll 1
+        for (int r = 0; r < kRun; ++r) {
+            const unsigned i = (unsigned)r * kSmallThreads + threadIdx.x;
+            const unsigned pos = (i / kRun) * kStride + (i % kRun);
+            const unsigned k = tile + i;
+            int32_t v = -1;
+            int d = 0;
+            int64_t st = 0;
+            if (k < cnt) {
+                v = bv.list[k];
+                bool act = true;
+                if constexpr (BATCH) act = !s.done[s.gid[v]];
+                if (act) {
+                    st = s.off[v];
+                    d = (int)(s.off[v + 1] - st);
+                } else {
+                    v = -1;
+                }
+            }
+            sv[pos] = v;
+            sd[pos] = (uint8_t)d;
+            sown[pos] = v >= 0 ? __ldcg(L.C + v) : 0;
+#pragma unroll
+            for (int q = 0; q < MAXD; ++q) {
+                const bool ok = q < d;
+                sidx[q * SL + pos] = ok ? load_index(s.idx, st + q) : -1;
+                if constexpr (WK != W_UNIT) sw[q * SL + pos] = ok ? load_weight<WK>(s.w, st + q) : (T)0;
+            }
+        }
+        __syncthreads();
+        // walk this thread's run in order
+        for (int step = 0; step < kRun; ++step) {
+            const unsigned pos = threadIdx.x * kStride + step;
+            const int32_t v = sv[pos];
+            bool changed = false;
+            if (v >= 0) {
+                const int d = sd[pos];
+                int32_t lab[MAXD];
+                T wt[MAXD];
+#pragma unroll
+                for (int q = 0; q < MAXD; ++q) {
+                    const int32_t j = sidx[q * SL + pos];
+                    const bool ok = q < d && j != v;
+                    lab[q] = ok ? load_label<true>(L.C, j) : kEmptyKey;
+                    if constexpr (WK == W_UNIT) wt[q] = ok ? (T)1 : (T)0;
+                    else wt[q] = ok ? sw[q * SL + pos] : (T)0;
+                }
+                bool any = false;
+                T best_w = 0;
+                int32_t best = 0x7fffffff;
+#pragma unroll
+                for (int q = 0; q < MAXD; ++q) {
+                    T sum = 0;
+#pragma unroll
+                    for (int r = 0; r < MAXD; ++r) sum += (lab[r] == lab[q]) ? wt[r] : (T)0;
+                    const bool better = lab[q] != kEmptyKey &&
+                                        (!any || sum > best_w || (sum == best_w && lab[q] < best));
+                    if (better) {
+                        any = true;
+                        best_w = sum;
+                        best = lab[q];
+                    }
+                }
+                const int32_t own = sown[pos];
+                changed = any && best != own;
+                if (changed) {
+                    L.C[v] = best;
+                    if (marks) {
+#pragma unroll
+                        for (int q = 0; q < MAXD; ++q) {
+                            const int32_t j = sidx[q * SL + pos];
+                            if (q < d && j != v) s.flags[j] = 1;
+                        }
+                    }
+                    ++my_changed;
+                    my_changed_entries += (unsigned)d;
+                }
+            }
+            count_graph_changes<BATCH>(s, changed, v);
+        }
+        __syncthreads();    // the tile is consumed before the next one is staged
+    }
+    flush_bin_counts(s, 0, my_changed, my_changed_entries);
+}
+
+template <int WK, bool BATCH, int MAXD>
+static cudaError_t launch_small_async_t(const DevState& s, int flag, int sms, cudaStream_t st) {
+    const size_t smem = async_smem_bytes<WK, MAXD>();
+    auto kern = k_sweep_small_async<WK, BATCH, MAXD>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmallThreads, smem);
+    if (err != cudaSuccess) return err;
+    kern<<<sms * (per_sm > 0 ? per_sm : 1), kSmallThreads, smem, st>>>(s, flag);
+    return cudaGetLastError();
+}
+
+template <int WK, bool BATCH>
+static cudaError_t launch_small_t(const DevState& s, bool async, int flag, int sms, cudaStream_t st) {
+    const bool four = s.small_max <= 4;
+    if (async) {
+        return four ? launch_small_async_t<WK, BATCH, 4>(s, flag, sms, st)
+                    : launch_small_async_t<WK, BATCH, 8>(s, flag, sms, st);
+    }
+    if (four) k_sweep_small<false, WK, BATCH, 4><<<sms * 8, kSmallThreads, 0, st>>>(s, flag);
+    else k_sweep_small<false, WK, BATCH, 8><<<sms * 8, kSmallThreads, 0, st>>>(s, flag);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms) {
     const bool async = mode == MODE_ASYNC;
     const int flag = mode != MODE_SYNC_FULL;
     const bool batch = s.G > 1;
-    const bool four = s.small_max <= 4;
-    dim3 grid(sms * 8), block(kSmallThreads);
-#define LPA_SMALL(A, W, B)                                                          \
-    do {                                                                            \
-        if (four) k_sweep_small<A, W, B, 4><<<grid, block, 0, st>>>(s, flag);       \
-        else k_sweep_small<A, W, B, 8><<<grid, block, 0, st>>>(s, flag);            \
-    } while (0)
-#define LPA_SMALL_W(A, B)                                      \
-    switch (s.weight_kind) {                                   \
-        case W_UNIT: LPA_SMALL(A, W_UNIT, B); break;           \
-        case W_U32: LPA_SMALL(A, W_U32, B); break;             \
-        default: LPA_SMALL(A, W_F32, B); break;                \
+    switch (s.weight_kind) {
+        case W_UNIT:
+            return batch ? launch_small_t<W_UNIT, true>(s, async, flag, sms, st)
+                         : launch_small_t<W_UNIT, false>(s, async, flag, sms, st);
+        case W_U32:
+            return batch ? launch_small_t<W_U32, true>(s, async, flag, sms, st)
+                         : launch_small_t<W_U32, false>(s, async, flag, sms, st);
+        default:
+            return batch ? launch_small_t<W_F32, true>(s, async, flag, sms, st)
+                         : launch_small_t<W_F32, false>(s, async, flag, sms, st);
     }
-    if (async) {
-        if (batch) { LPA_SMALL_W(true, true) } else { LPA_SMALL_W(true, false) }
-    } else {
-        if (batch) { LPA_SMALL_W(false, true) } else { LPA_SMALL_W(false, false) }
-    }
-#undef LPA_SMALL_W
-#undef LPA_SMALL
-    return cudaGetLastError();
 }
 
 }  // namespace lpa
