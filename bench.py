@@ -64,6 +64,28 @@ WORKLOAD_TEXT = {
 }
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the same
+# command (dram__bytes_read.sum + dram__bytes_write.sum over every launch of
+# the kernel in one step of the profiled run path), valid only while the
+# kernel's sources are unchanged (sha1 of the files below).
+TRAFFIC = {
+    "k_sweep_small": {"bytes_per_launch": 612.8e6, "sha1": "f34031815ca228e13e27caeabce4c1853a0f6deb",
+                      "files": ["lpa_sweep_small.cu", "lpa_device.cuh", "lpa_internal.h"]},
+}
+
+
+def measured_traffic(kernel):
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if not t:
+        return None
+    h = hashlib.sha1()
+    for f in t["files"]:
+        with open(os.path.join(ROOT, "paper_2312_08140_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes_per_launch"] if h.hexdigest() == t["sha1"] else None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -338,7 +360,7 @@ def main():
         dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
         d = kernels[dom]
         roofline = {"bound": "hbm", "kernel": dom, "achieved": d["GB_per_s"], "peak": hbm, "unit": "GB/s",
-                    "frac": d["GB_per_s"] / hbm, "peak_kind": hbm_kind, "traffic": None,
+                    "frac": d["GB_per_s"] / hbm, "peak_kind": hbm_kind, "traffic": measured_traffic(dom),
                     "bytes_per_launch": d["bytes_per_launch"],
                     "mean_launch_ms": d["ms_per_step"] / d["launches_per_step"]}
 
