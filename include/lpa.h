@@ -274,6 +274,62 @@ lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, float tolerance, int32_t 
 lpa_status lpa_batch_modularity(lpa_batch_t b, int32_t g, const int32_t *labels, double *q_out,
                                 void *stream);
 
+/* ---------------------------------------------------------------- serving */
+
+/* Continuous batching of independent label propagation requests.  Small
+ * requests share a device-resident arena that a worker thread advances one
+ * sweep per cycle; a request joins at the next cycle after its copy to the
+ * device and leaves when its own test (dN/N <= tolerance or max_iters sweeps,
+ * Algorithm 1) is met.  Each request keeps its own counters, so in the
+ * synchronous mode its labels are the same as a run on its own.  Requests
+ * with at least solo_min_entries entries run on a separate lane (their own
+ * graph and stream, one at a time).  Labels come back as host int32[n] in the
+ * request's own vertex ids. */
+typedef struct {
+    int64_t hbm_budget_bytes;   /* device memory the server may hold: arena + solo-lane graphs */
+    int64_t arena_vertices;     /* vertex capacity of the shared arena (>= 1) */
+    int64_t arena_entries;      /* CSR entry capacity of the shared arena (>= 1) */
+    int32_t max_slots;          /* requests in the arena at once (>= 2) */
+    int32_t mode;               /* lpa_mode; LPA_MODE_SYNC_FULL is run as LPA_MODE_SYNC */
+    float   tolerance;          /* in [0, 1] */
+    int32_t max_iters;          /* in [0, 1 << 20] */
+    int64_t solo_min_entries;   /* requests with at least this many entries use the solo lane; 0 = never */
+} lpa_serve_config;
+
+typedef struct {
+    int64_t cycles;             /* arena cycles run so far */
+    int32_t active;             /* requests in the arena now */
+    int32_t pending;            /* requests copied or queued but not yet running */
+    int64_t arena_bytes;        /* device memory held by the arena */
+    int64_t solo_bytes;         /* device memory reserved by queued or running solo requests */
+} lpa_serve_stats_t;
+
+/* Allocates the arena on the current device and starts the worker threads. */
+lpa_status lpa_serve_create(const lpa_serve_config *cfg, lpa_server_t *out);
+
+/* Queues a request given as host CSR (same rules as lpa_graph_create; checked
+ * here on the host).  Copies the data before returning.  Returns
+ * LPA_ERR_BUSY when it does not fit now (no free slot, vertex or entry range,
+ * or device-memory budget); the caller may retry after results are released.
+ * *ticket identifies the request. */
+lpa_status lpa_serve_submit(lpa_server_t s, int64_t n, int64_t nnz, const int64_t *offsets,
+                            const int32_t *indices, const float *weights, uint64_t *ticket);
+
+/* Non-blocking: writes up to cap finished tickets (each reported once). */
+lpa_status lpa_serve_poll(lpa_server_t s, uint64_t *done, int32_t cap, int32_t *n_done);
+
+/* Copies a finished request's labels (host int32[n], nullable) and run info
+ * (nullable).  LPA_ERR_NOT_READY while it runs, LPA_ERR_NOT_FOUND if unknown. */
+lpa_status lpa_serve_fetch(lpa_server_t s, uint64_t ticket, int32_t *labels_host, lpa_run_info *info);
+
+/* Forgets a finished request's result. */
+lpa_status lpa_serve_release(lpa_server_t s, uint64_t ticket);
+
+lpa_status lpa_serve_stats(lpa_server_t s, lpa_serve_stats_t *out);
+
+/* Stops the workers (requests not finished are dropped) and frees the arena. */
+lpa_status lpa_serve_destroy(lpa_server_t s);
+
 #ifdef __cplusplus
 }
 #endif

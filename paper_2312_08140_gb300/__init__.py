@@ -95,6 +95,21 @@ class LpaProfile(ctypes.Structure):
                 "bin_changed_entries": [list(self.bin_changed_entries[t]) for t in range(it)]}
 
 
+class LpaServeConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("arena_vertices", ctypes.c_int64),
+                ("arena_entries", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("tolerance", ctypes.c_float), ("max_iters", ctypes.c_int32),
+                ("solo_min_entries", ctypes.c_int64)]
+
+
+class LpaServeStats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int64), ("active", ctypes.c_int32), ("pending", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_int64), ("solo_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class LpaError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{_STATUS.get(status, status)}: {message}")
@@ -133,6 +148,13 @@ _SIGS = {
     "lpa_batch_props_get": ([_V, _P(LpaGraphProps)], ctypes.c_int),
     "lpa_batch_run": ([_V, ctypes.c_int, _F, _I32, _V, _V, _P(LpaRunInfo)], ctypes.c_int),
     "lpa_batch_modularity": ([_V, _I32, _V, _P(ctypes.c_double), _V], ctypes.c_int),
+    "lpa_serve_create": ([_P(LpaServeConfig), _P(_V)], ctypes.c_int),
+    "lpa_serve_submit": ([_V, _I64, _I64, _V, _V, _V, _P(ctypes.c_uint64)], ctypes.c_int),
+    "lpa_serve_poll": ([_V, _P(ctypes.c_uint64), _I32, _P(_I32)], ctypes.c_int),
+    "lpa_serve_fetch": ([_V, ctypes.c_uint64, _V, _P(LpaRunInfo)], ctypes.c_int),
+    "lpa_serve_release": ([_V, ctypes.c_uint64], ctypes.c_int),
+    "lpa_serve_stats": ([_V, _P(LpaServeStats)], ctypes.c_int),
+    "lpa_serve_destroy": ([_V], ctypes.c_int),
 }
 
 
@@ -299,6 +321,53 @@ def lpa_batch_modularity(b, g, labels, stream=None) -> float:
     q = ctypes.c_double()
     _check(load().lpa_batch_modularity(b, g, _ptr(labels), ctypes.byref(q), _stream(stream)))
     return q.value
+
+
+def lpa_serve_create(hbm_budget_bytes, arena_vertices, arena_entries, max_slots=64, mode="sync",
+                     tolerance=0.05, max_iters=20, solo_min_entries=0):
+    cfg = LpaServeConfig(hbm_budget_bytes, arena_vertices, arena_entries, max_slots, _mode(mode), tolerance,
+                         max_iters, solo_min_entries)
+    h = _V()
+    _check(load().lpa_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def lpa_serve_submit(s, n, nnz, offsets, indices, weights=None) -> int:
+    """Host arrays in; returns the ticket.  Raises LpaError with status
+    LPA_ERR_BUSY when the request does not fit now."""
+    t = ctypes.c_uint64()
+    _check(load().lpa_serve_submit(s, n, nnz, _ptr(offsets), _ptr(indices), _ptr(weights), ctypes.byref(t)))
+    return t.value
+
+
+def lpa_serve_poll(s, cap=1024):
+    buf = (ctypes.c_uint64 * max(cap, 1))()
+    k = _I32()
+    _check(load().lpa_serve_poll(s, buf, cap, ctypes.byref(k)))
+    return list(buf[:k.value])
+
+
+def lpa_serve_fetch(s, ticket, n):
+    """Returns (labels numpy int32[n], LpaRunInfo)."""
+    import numpy as np
+    lab = np.empty(max(n, 1), dtype=np.int32)
+    ri = LpaRunInfo()
+    _check(load().lpa_serve_fetch(s, ticket, lab.ctypes.data, ctypes.byref(ri)))
+    return lab[:n], ri
+
+
+def lpa_serve_release(s, ticket):
+    _check(load().lpa_serve_release(s, ticket))
+
+
+def lpa_serve_stats(s) -> dict:
+    st = LpaServeStats()
+    _check(load().lpa_serve_stats(s, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def lpa_serve_destroy(s):
+    _check(load().lpa_serve_destroy(s))
 
 
 class Graph:

@@ -233,10 +233,13 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
         E.s.weight_kind = W_F32;
     }
     E.s.off = off_d;
+    E.s.off_end = off_d + 1;
     E.s.idx = idx_d;
     E.s.w = w_d;
     E.s.gid = gid_d;
     E.s.vtx_off = vo_d;
+    E.s.g_begin = vo_d;
+    E.s.g_end = vo_d + 1;
 
     // working state
     const size_t N1 = (size_t)std::max<int64_t>(n, 1);

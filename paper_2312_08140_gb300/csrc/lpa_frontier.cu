@@ -45,7 +45,7 @@ __global__ void k_init(DevState s) {
     Ctrl* c = s.ctrl;
     const int max_iters = c->max_iters;
     for (int64_t g = tid; g < s.G; g += stride) {
-        const int64_t ng = s.vtx_off[g + 1] - s.vtx_off[g];
+        const int64_t ng = s.g_end[g] - s.g_begin[g];
         const bool nothing = ng == 0 || max_iters == 0;
         s.dN[g] = 0;
         s.done[g] = nothing ? 1 : 0;
@@ -70,6 +70,7 @@ __global__ void k_init(DevState s) {
         c->ticket = 0;
         c->cbuf = 0;
         c->rd = 0;
+        c->allow_dense = 1;
         c->skip_marks = 1;          // the first pass changes nearly every label
         c->last_pass_high = 0;
         c->dense[0] = 1;
@@ -225,7 +226,7 @@ __device__ __forceinline__ void static_chunk(const DevState& s, int64_t v0, int3
         bin[q] = -1;
         deg[q] = 0;
         if (v < s.N) {
-            const int64_t d = s.off[v + 1] - s.off[v];
+            const int64_t d = s.off_end[v] - s.off[v];
             if (d > 0) {
                 deg[q] = d;
                 bin[q] = (int8_t)bin_of(s, d);
@@ -333,7 +334,8 @@ cudaError_t build_static_lists(DevState& s, cudaStream_t st) {
 
 // Run by the last block of k_finish once every block is done.  `rd` is the
 // buffer the pass just consumed; `wr` = rd ^ 1 received the next frontier
-// (or is dense).  For role 0 (end of sweep t) it also runs the per-graph
+// (or is dense; role 2 compacts nothing and keeps rd).  For roles 0 and 2
+// (end of sweep t) it also runs the per-graph
 // convergence test of Algorithm 1 and sets the loop condition.
 __device__ void control_step(const DevState& s, int mode, int role, int dense_next, cudaGraphConditionalHandle h,
                              int in_graph) {
@@ -342,7 +344,7 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
     const int t = vc->iter;
     const int rd = vc->rd, wr = rd ^ 1;
     int any = 0;
-    if (role == 0) {
+    if (role != 1) {
         const double tau = vc->tau;
         const int max_iters = vc->max_iters;
         unsigned long long changed_total = 0;
@@ -351,13 +353,14 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
             if (!s.done[g]) {
                 const unsigned long long dn =
                     (s.G == 1) ? changed_total : ((volatile unsigned long long*)s.dN)[g];
-                if (t < kMaxHist) s.hist_changed[g * kMaxHist + t] = (long long)dn;
-                s.iters[g] = t + 1;
-                const int64_t ng = s.vtx_off[g + 1] - s.vtx_off[g];
+                const int it = s.iters[g] + 1;          // sweeps of graph g so far
+                if (it <= kMaxHist) s.hist_changed[g * kMaxHist + it - 1] = (long long)dn;
+                s.iters[g] = it;
+                const int64_t ng = s.g_end[g] - s.g_begin[g];
                 if ((double)dn / (double)ng <= tau) {            // Algorithm 1: dN / N <= tau
                     s.done[g] = 1;
                     s.exit_reason[g] = 0;
-                } else if (t + 1 >= max_iters) {
+                } else if (it >= max_iters) {
                     s.done[g] = 1;
                     s.exit_reason[g] = 1;
                 }
@@ -373,7 +376,7 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         c->sweep_bin_vertices[b] += vc->bin_cnt[rd][b];
         c->sweep_bin_entries[b] += (long long)vc->bin_entries[rd][b];
     }
-    if (role == 0) {
+    if (role != 1) {
         long long act = 0, scn = 0, che = 0;
         for (int b = 0; b < kBins; ++b) {
             act += vc->sweep_bin_vertices[b];
@@ -406,7 +409,7 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         c->any_active = any;
     }
     for (int b = 0; b < kBins; ++b) {
-        if (dense_next) {
+        if (dense_next && role != 2) {
             c->bin_cnt[wr][b] = s.bin_static[b];
             c->bin_entries[wr][b] = s.bin_static_entries[b];
         }
@@ -417,15 +420,17 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
     // in a row that changed almost every vertex, the next pass skips them and
     // the one after it is dense.
     const bool high = (double)vc->pass_changed_entries * 1000.0 >= (double)kHighPermille * (double)s.active_entries;
-    c->skip_marks = (high && vc->last_pass_high) ? 1 : 0;
+    c->skip_marks = (high && vc->last_pass_high && vc->allow_dense) ? 1 : 0;
     c->last_pass_high = high ? 1 : 0;
-    c->dense[wr] = dense_next;
-    c->rd = wr;
+    if (role != 2) {
+        c->dense[wr] = dense_next;
+        c->rd = wr;
+    }
     c->pass_changed_entries = 0;
     c->ovf_packed = 0;
     c->ticket = 0;
     __threadfence();
-    if (role == 0 && in_graph) cudaGraphSetConditional(h, any ? 1u : 0u);
+    if (role != 1 && in_graph) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 // After a pass over buffer rd: (1) at the end of a sparse sync sweep, apply
@@ -442,7 +447,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned gstride = gridDim.x * blockDim.x;
 
-    if (role == 0 && mode != MODE_ASYNC && !s.ctrl->dense[rd]) {
+    if (role != 1 && mode != MODE_ASYNC && !s.ctrl->dense[rd]) {
         const int cb = s.ctrl->cbuf;
         int32_t* C = s.lab[cb];
         const int32_t* Cn = s.lab[cb ^ 1];
@@ -464,11 +469,14 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
     }
 
     const unsigned long long che = ((volatile Ctrl*)s.ctrl)->pass_changed_entries;
-    const int dense = mode == MODE_SYNC_FULL || s.ctrl->skip_marks ||
-                      (double)che * 1000.0 >= (double)s.dense_permille * (double)s.active_entries;
+    const int dense = s.ctrl->allow_dense &&
+                      (mode == MODE_SYNC_FULL || s.ctrl->skip_marks ||
+                       (double)che * 1000.0 >= (double)s.dense_permille * (double)s.active_entries);
 
     const int64_t nchunks = (s.N + kVertsPerThread - 1) / kVertsPerThread;
-    if (dense) {
+    if (role == 2) {
+        // serving cycles leave the marks for the next cycle's compaction
+    } else if (dense) {
         if (mode != MODE_SYNC_FULL) {
             for (int64_t ch = gtid; ch < nchunks; ch += gstride) {
                 const int64_t v0 = ch * kVertsPerThread;
@@ -500,7 +508,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
                 bin[q] = -1;
                 deg[q] = 0;
                 if (f[q]) {
-                    const int64_t d = s.off[v0 + q + 1] - s.off[v0 + q];
+                    const int64_t d = s.off_end[v0 + q] - s.off[v0 + q];
                     if (d > 0) {
                         deg[q] = d;
                         bin[q] = (int8_t)bin_of(s, d);
@@ -540,7 +548,7 @@ __global__ void k_finalize(DevState s) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.N; i += stride) {
         int32_t c = C[i];
-        if (local && s.G > 1) c -= (int32_t)s.vtx_off[s.gid[i]];
+        if (local && s.G > 1) c -= (int32_t)s.g_begin[s.gid[i]];
         out[i] = c;
     }
 }
@@ -677,7 +685,7 @@ __global__ void k_mod_rows(DevState s, int64_t v0, int64_t v1, const int32_t* la
             continue;
         }
         double K = 0.0, sg = 0.0;
-        const int64_t st = s.off[v0 + i], en = s.off[v0 + i + 1];
+        const int64_t st = s.off[v0 + i], en = s.off_end[v0 + i];
         for (int64_t e = st + lane; e < en; e += 32) {
             const double w = weight_f64(s, e);
             K += w;

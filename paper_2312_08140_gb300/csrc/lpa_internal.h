@@ -44,6 +44,7 @@ struct Ctrl {
                                          // every compaction, which writes buffer rd ^ 1)
     int32_t dense[2];                    // buffer holds the static bin lists (every vertex)
     int32_t cbuf;                        // labels of the current sweep are lab[cbuf]
+    int32_t allow_dense;                 // 0: every pass compacts the marks (serving arena)
     int32_t skip_marks;                  // current pass writes no neighbour marks; the next
                                          // pass is dense (scans every vertex) instead
     int32_t last_pass_high;              // previous pass changed >= kHighPermille of entries
@@ -90,11 +91,14 @@ struct DevState {
     int64_t E;                 // CSR entries
     int32_t G;                 // graphs
     int32_t weight_kind;       // WeightKind
-    const int64_t* off;        // [N+1]
+    const int64_t* off;        // [N] row begins (positions in idx)
+    const int64_t* off_end;    // [N] row ends (off + 1 for an ordinary CSR)
     const int32_t* idx;        // [E] global vertex ids
     const void* w;             // [E] uint32 (W_U32), float (W_F32) or null (W_UNIT)
     const int32_t* gid;        // [N] graph of each vertex, null when G == 1
-    const int64_t* vtx_off;    // [G+1]
+    const int64_t* vtx_off;    // [G+1] (batches)
+    const int64_t* g_begin;    // [G] first vertex of graph g (vtx_off for batches)
+    const int64_t* g_end;      // [G] one past its last vertex (vtx_off + 1 for batches)
     int32_t* lab[2];           // [N] label buffers (global ids): current lab[cbuf]; sync sweeps write
                                // the other one (every scanned vertex in dense sweeps, then the
                                // buffers flip; only changed vertices in sparse sweeps, then applied)
@@ -136,8 +140,10 @@ cudaError_t launch_init(const DevState& s, cudaStream_t st, int sms);
 cudaError_t build_static_lists(DevState& s, cudaStream_t st);
 cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st);
 // role 0: end of a sweep (apply, compaction for the next sweep, control);
-// role 1: inside an asynchronous sweep, compaction of the vertices re-marked by
-// the main pass for the catch-up pass.
+// role 1: compaction only (inside an asynchronous sweep, of the vertices the
+// main pass re-marked; or at the start of a serving cycle);
+// role 2: end of a serving cycle (apply, control; the marks stay for the next
+// cycle's compaction, which also picks up newly admitted requests).
 cudaError_t launch_finish(const DevState& s, int mode, int role, cudaGraphConditionalHandle h, int in_graph,
                           cudaStream_t st, int sms);
 cudaError_t launch_finalize(const DevState& s, cudaStream_t st, int sms);

@@ -118,7 +118,7 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
             }
         }
         const int64_t st = s.off[v];
-        const int64_t en = s.off[v + 1];
+        const int64_t en = s.off_end[v];
         const int64_t d = en - st;
         const int log_full = ceil_log2((unsigned)(2 * d));
         const bool fits = log_full <= log_S;

@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
         if (slot) own = ASYNC ? __ldcg(L.C + v) : L.C[v];
         if (act) {
             st = s.off[v];
-            d = (int)(s.off[v + 1] - st);
+            d = (int)(s.off_end[v] - st);
         }
         int32_t nb[MAXD];
         int32_t lab[MAXD];
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small_async(DevState s,
                 if constexpr (BATCH) act = !s.done[s.gid[v]];
                 if (act) {
                     st = s.off[v];
-                    d = (int)(s.off[v + 1] - st);
+                    d = (int)(s.off_end[v] - st);
                 } else {
                     v = -1;
                 }

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
         int actl = okl;
         if (okl) {
             stl = s.off[vl];
-            enl = s.off[vl + 1];
+            enl = s.off_end[vl];
             ownl = ASYNC ? __ldcg(L.C + vl) : L.C[vl];
             if constexpr (BATCH) {
                 if (s.done[s.gid[vl]]) actl = 0;

@@ -1,0 +1,118 @@
+"""Serving loop (lpa_serve_*): requests admitted while others run share one
+device arena; in the synchronous mode each result must equal the oracle's
+(hence a run on its own) label for label, with the same sweep count and
+per-sweep changed counts; admission refuses what does not fit and accepts it
+once space is released; large requests take the solo lane."""
+import time
+
+import numpy as np
+import pytest
+
+import lpa_inputs as L
+import oracle as O
+
+
+def test_serve_config_is_validated_before_any_device_call():
+    import paper_2312_08140_gb300 as lpa
+    from paper_2312_08140_gb300 import _build
+    lpa.load(_build.build())
+    for bad in (dict(arena_vertices=0, arena_entries=10), dict(arena_vertices=10, arena_entries=10, max_slots=1),
+                dict(arena_vertices=10, arena_entries=10, tolerance=2.0),
+                dict(arena_vertices=10, arena_entries=10, mode=9)):
+        args = dict(hbm_budget_bytes=1 << 30, max_slots=4)
+        args.update(bad)
+        with pytest.raises(lpa.LpaError) as e:
+            lpa.lpa_serve_create(**args)
+        assert e.value.status == lpa.LPA_ERR_INVALID_ARG
+
+
+def _drain(lpa, srv, tickets, timeout=120.0):
+    done = set()
+    t0 = time.time()
+    while len(done) < len(tickets):
+        done.update(lpa.lpa_serve_poll(srv))
+        assert time.time() - t0 < timeout, "serving did not finish"
+        time.sleep(0.001)
+    return done
+
+
+@pytest.mark.gpu
+def test_serve_mix_equals_alone_sync():
+    import paper_2312_08140_gb300 as lpa
+    lpa.load()
+    graphs = [L.batched_sbm_graph(g, n_max=8000) for g in range(40)]
+    graphs += [L.road_grid(60, 41, seed=7), L.rmat(12, 16, seed=9), L.from_undirected_pairs(5, []),
+               L.from_undirected_pairs(2, [(0, 1)]), L.Graph(np.zeros(1, np.int64), np.zeros(0, np.int32), None)]
+    srv = lpa.lpa_serve_create(hbm_budget_bytes=4 << 30, arena_vertices=400_000, arena_entries=20_000_000,
+                               max_slots=48, mode="sync")
+    try:
+        tickets = {}
+        for k, g in enumerate(graphs):            # staggered: later requests join running cycles
+            tickets[lpa.lpa_serve_submit(srv, g.n, g.nnz, g.off, g.idx, g.w)] = k
+            if k % 7 == 3:
+                time.sleep(0.002)
+        _drain(lpa, srv, tickets)
+        assert lpa.lpa_serve_stats(srv)["cycles"] > 0
+        for t, k in tickets.items():
+            g = graphs[k]
+            lab, info = lpa.lpa_serve_fetch(srv, t, g.n)
+            ref, it, ch = O.lpa_sync(g.off, g.idx, g.w)
+            assert np.array_equal(lab, ref), k
+            if g.n:
+                assert info.iterations == it and list(info.changed[:it]) == ch.tolist(), k
+            lpa.lpa_serve_release(srv, t)
+    finally:
+        lpa.lpa_serve_destroy(srv)
+
+
+@pytest.mark.gpu
+def test_serve_busy_then_admitted_and_solo_lane():
+    import paper_2312_08140_gb300 as lpa
+    lpa.load()
+    g = L.planted_partition(n=3000, blocks=6, seed=3)
+    big = L.rmat(14, 16, seed=2)
+    srv = lpa.lpa_serve_create(hbm_budget_bytes=2 << 30, arena_vertices=4000, arena_entries=g.nnz + 100,
+                               max_slots=4, mode="sync", solo_min_entries=200_000)
+    try:
+        t1 = lpa.lpa_serve_submit(srv, g.n, g.nnz, g.off, g.idx, g.w)
+        with pytest.raises(lpa.LpaError) as e:      # arena full until t1 leaves
+            lpa.lpa_serve_submit(srv, g.n, g.nnz, g.off, g.idx, g.w)
+        assert e.value.status == lpa.LPA_ERR_BUSY
+        tb = lpa.lpa_serve_submit(srv, big.n, big.nnz, big.off, big.idx, big.w)   # solo lane
+        _drain(lpa, srv, [t1, tb])
+        t2 = lpa.lpa_serve_submit(srv, g.n, g.nnz, g.off, g.idx, g.w)
+        _drain(lpa, srv, [t2])
+        ref, _, _ = O.lpa_sync(g.off, g.idx, g.w)
+        for t in (t1, t2):
+            lab, _ = lpa.lpa_serve_fetch(srv, t, g.n)
+            assert np.array_equal(lab, ref)
+        lab, info = lpa.lpa_serve_fetch(srv, tb, big.n)
+        refb, itb, _ = O.lpa_sync(big.off, big.idx, big.w)
+        assert np.array_equal(lab, refb) and info.iterations == itb
+        with pytest.raises(lpa.LpaError) as e:
+            lpa.lpa_serve_fetch(srv, 987654, 1)
+        assert e.value.status == lpa.LPA_ERR_NOT_FOUND
+    finally:
+        lpa.lpa_serve_destroy(srv)
+
+
+@pytest.mark.gpu
+def test_serve_async_invariants():
+    import paper_2312_08140_gb300 as lpa
+    lpa.load()
+    graphs = [L.batched_sbm_graph(g, n_max=5000) for g in range(50, 70)]
+    srv = lpa.lpa_serve_create(hbm_budget_bytes=4 << 30, arena_vertices=200_000, arena_entries=10_000_000,
+                               max_slots=32, mode="async")
+    try:
+        tickets = {lpa.lpa_serve_submit(srv, g.n, g.nnz, g.off, g.idx, g.w): k for k, g in enumerate(graphs)}
+        _drain(lpa, srv, tickets)
+        for t, k in tickets.items():
+            g = graphs[k]
+            lab, info = lpa.lpa_serve_fetch(srv, t, g.n)
+            assert O.count_labels_outside_component(g.off, g.idx, lab) == 0
+            q = O.modularity(g.off, g.idx, g.w, lab)
+            ref, _, _ = O.lpa_async(g.off, g.idx, g.w)
+            assert q >= O.modularity(g.off, g.idx, g.w, ref) - 0.02
+            assert 1 <= info.iterations <= 20
+    finally:
+        lpa.lpa_serve_destroy(srv)
