@@ -106,6 +106,7 @@ extern "C" lpa_status lpa_modularity_noalloc(int64_t n, int64_t nnz, const int64
     s.G = 1;
     s.weight_kind = weights ? W_F32 : W_UNIT;
     s.off = offsets;
+    s.off_end = offsets + 1;
     s.idx = indices;
     s.w = weights;
 
