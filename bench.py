@@ -192,6 +192,131 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- batched and serving
+def batched_sample(lpa, torch, stream, G, reps=5):
+    """G graphs of the batched planted-partition distribution (seeds 1000+g):
+    one handle and one device loop per run, against one handle and one
+    lpa_run per graph on the same stream."""
+    import numpy as np
+    import lpa_inputs as L
+    graphs = [L.batched_sbm_graph(g) for g in range(G)]
+    vo, eo, off, _, w = L.pack(graphs)
+    idx = np.concatenate([gr.idx for gr in graphs]).astype(np.int32)
+    N = int(vo[-1])
+    b = lpa.lpa_batch_create(G, vo, eo, off, idx, w, lpa.LPA_HOST_PTRS, stream)
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    res = {"graphs": G, "vertices": N, "entries": int(eo[-1])}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for m in MODES:
+        infos = lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=True)
+        edges = sum(gr.nnz * inf.iterations for gr, inf in zip(graphs, infos))
+        for _ in range(2):
+            lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=False)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3 / reps
+        res[m] = {"batched_graphs_per_s": G / sec, "batched_edges_per_s": edges / sec, "batched_ms": sec * 1e3}
+    lpa.lpa_batch_destroy(b)
+    handles = [lpa.lpa_graph_create(gr.n, gr.nnz, gr.off, gr.idx, gr.w, lpa.LPA_HOST_PTRS, stream) for gr in graphs]
+    outs = [torch.empty(max(gr.n, 1), dtype=torch.int32, device="cuda") for gr in graphs]
+    for m in MODES:
+        for h, o in zip(handles, outs):
+            lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            for h, o in zip(handles, outs):
+                lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3 / reps
+        res[m]["one_launch_per_graph_graphs_per_s"] = G / sec
+        res[m]["speedup_vs_one_launch_per_graph"] = res[m]["batched_graphs_per_s"] / (G / sec)
+    for h in handles:
+        lpa.lpa_graph_destroy(h)
+    return res
+
+
+def _percentiles(lat):
+    import numpy as np
+    a = np.asarray(lat) * 1e3
+    return {"p50_ms": float(np.percentile(a, 50)), "p99_ms": float(np.percentile(a, 99)),
+            "mean_ms": float(a.mean())}
+
+
+def serving_sample(lpa, torch, stream, rate, seconds, pool_size, big=None, big_every=0, seed=1):
+    """Poisson arrivals at `rate` req/s for `seconds`, requests drawn from a
+    pool of the batched distribution (and `big` every `big_every` requests):
+    the continuous-batching server against an unbatched FIFO that creates a
+    graph and runs lpa_run for one request at a time."""
+    import numpy as np
+    import lpa_inputs as L
+    rng = np.random.default_rng(seed)
+    pool = [L.batched_sbm_graph(g) for g in range(pool_size)]
+    count = int(rate * seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    picks = rng.integers(0, pool_size, size=count)
+    reqs = [(big if (big is not None and big_every and (k + 1) % big_every == 0) else pool[picks[k]])
+            for k in range(count)]
+    max_n = max(g.n for g in pool)
+    max_e = max(g.nnz for g in pool)
+    srv = lpa.lpa_serve_create(hbm_budget_bytes=48 << 30, arena_vertices=64 * max_n, arena_entries=64 * max_e,
+                               max_slots=256, mode="sync", tolerance=TAU, max_iters=MAX_ITERS,
+                               solo_min_entries=(4 * max_e if big is not None else 0))
+    t0 = time.perf_counter()
+    submit_t, done_t, ticket_of = {}, {}, {}
+    backlog = list(range(count))
+    k_next = 0
+    while len(done_t) < count:
+        now = time.perf_counter() - t0
+        while k_next < count and arrivals[k_next] <= now:
+            k_next += 1
+        while backlog and backlog[0] < k_next:
+            k = backlog[0]
+            g = reqs[k]
+            try:
+                t = lpa.lpa_serve_submit(srv, g.n, g.nnz, g.off, g.idx, g.w)
+            except lpa.LpaError as e:
+                if e.status != lpa.LPA_ERR_BUSY:
+                    raise
+                break
+            ticket_of[t] = k
+            backlog.pop(0)
+        for t in lpa.lpa_serve_poll(srv):
+            done_t[ticket_of[t]] = time.perf_counter() - t0
+            lpa.lpa_serve_release(srv, t)
+        if time.perf_counter() - t0 > seconds * 20 + 60:
+            raise RuntimeError("serving sample did not drain")
+        time.sleep(0.0002)
+    stats = lpa.lpa_serve_stats(srv)
+    lpa.lpa_serve_destroy(srv)
+    lat = [done_t[k] - arrivals[k] for k in range(count)]
+    served = {"requests": count, "offered_req_per_s": rate, "graphs_per_s": count / (max(done_t.values()) - arrivals[0]),
+              "cycles": stats["cycles"], **_percentiles(lat)}
+    # unbatched FIFO: one graph handle and one lpa_run per request, in arrival order
+    out = torch.empty(max(max(g.n for g in reqs), 1), dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    fifo_done = []
+    for k in range(count):
+        now = time.perf_counter() - t0
+        if now < arrivals[k]:
+            time.sleep(arrivals[k] - now)
+        g = reqs[k]
+        h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS, stream)
+        lpa.lpa_run(h, "sync", TAU, MAX_ITERS, out, stream, info=False)
+        lab = out[:g.n].cpu()
+        del lab
+        lpa.lpa_graph_destroy(h)
+        fifo_done.append(time.perf_counter() - t0)
+    flat = [fifo_done[k] - arrivals[k] for k in range(count)]
+    fifo = {"graphs_per_s": count / (fifo_done[-1] - arrivals[0]), **_percentiles(flat)}
+    return {"server": served, "unbatched_fifo": fifo}
+
+
 # ------------------------------------------------------------------- GPU arm
 def kernel_bytes(prof, wbytes, sync, passes):
     """Algorithmic bytes per sweep-kernel launch from the per-bin counts:
@@ -223,6 +348,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip the event-timed roofline pass")
     ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--batched-graphs", type=int, default=128, help="0 skips the batched sample")
+    ap.add_argument("--serving-seconds", type=float, default=0.5, help="0 skips the serving sample")
+    ap.add_argument("--serving-full", action="store_true",
+                    help="serving sample with an R-MAT scale 24 request every 500 requests")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -364,6 +493,17 @@ def main():
                     "bytes_per_launch": d["bytes_per_launch"],
                     "mean_launch_ms": d["ms_per_step"] / d["launches_per_step"]}
 
+    batched = batched_sample(lpa, torch, stream, args.batched_graphs) if args.batched_graphs > 0 else None
+    serving = None
+    if args.serving_seconds > 0:
+        import lpa_inputs as L
+        big = L.rmat(24, 16, seed=3) if args.serving_full else None
+        serving = serving_sample(lpa, torch, stream, rate=2000.0, seconds=args.serving_seconds, pool_size=48,
+                                 big=big, big_every=500 if big is not None else 0)
+        serving["sample"] = ("Poisson arrivals at 2000 req/s, graphs of the batched distribution (pool of 48)" +
+                             ("; an R-MAT scale 24 request every 500" if big is not None else
+                              "; without the R-MAT scale 24 request of the full serving config (--serving-full)"))
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pairs = [(gi, m) for gi in range(len(graphs)) for m in MODES]
@@ -382,7 +522,7 @@ def main():
                 "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
                 "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline, "kernels": kernels,
-                "cpu_baseline": cpu, "per_run": per_run}
+                "cpu_baseline": cpu, "batched": batched, "serving": serving, "per_run": per_run}
         print(json.dumps(line), flush=True)
     for h in handles:
         lpa.lpa_graph_destroy(h)
