@@ -269,6 +269,7 @@ def serving_sample(lpa, torch, stream, rate, seconds, pool_size, big=None, big_e
                                solo_min_entries=(4 * max_e if big is not None else 0))
     t0 = time.perf_counter()
     submit_t, done_t, ticket_of = {}, {}, {}
+    submit_s = 0.0
     backlog = list(range(count))
     k_next = 0
     while len(done_t) < count:
@@ -278,8 +279,10 @@ def serving_sample(lpa, torch, stream, rate, seconds, pool_size, big=None, big_e
         while backlog and backlog[0] < k_next:
             k = backlog[0]
             g = reqs[k]
+            ts = time.perf_counter()
             try:
                 t = lpa.lpa_serve_submit(srv, g.n, g.nnz, g.off, g.idx, g.w)
+                submit_s += time.perf_counter() - ts
             except lpa.LpaError as e:
                 if e.status != lpa.LPA_ERR_BUSY:
                     raise
@@ -295,8 +298,10 @@ def serving_sample(lpa, torch, stream, rate, seconds, pool_size, big=None, big_e
     stats = lpa.lpa_serve_stats(srv)
     lpa.lpa_serve_destroy(srv)
     lat = [done_t[k] - arrivals[k] for k in range(count)]
-    served = {"requests": count, "offered_req_per_s": rate, "graphs_per_s": count / (max(done_t.values()) - arrivals[0]),
-              "cycles": stats["cycles"], **_percentiles(lat)}
+    span = max(done_t.values()) - arrivals[0]
+    served = {"requests": count, "offered_req_per_s": rate, "graphs_per_s": count / span,
+              "cycles": stats["cycles"], "cycles_per_s": stats["cycles"] / span,
+              "submit_ms_mean": 1e3 * submit_s / count, **_percentiles(lat)}
     # unbatched FIFO: one graph handle and one lpa_run per request, in arrival order
     out = torch.empty(max(max(g.n for g in reqs), 1), dtype=torch.int32, device="cuda")
     t0 = time.perf_counter()
