@@ -256,7 +256,14 @@ def serving_sample(lpa, torch, stream, rate, seconds, pool_size, big=None, big_e
     import numpy as np
     import lpa_inputs as L
     rng = np.random.default_rng(seed)
-    pool = [L.batched_sbm_graph(g) for g in range(pool_size)]
+
+    def pinned(g):    # request buffers in page-locked memory, as a server's receive buffers would be
+        pin = lambda a: None if a is None else torch.from_numpy(a).pin_memory().numpy()
+        return L.Graph(pin(g.off), pin(g.idx), pin(g.w), g.meta)
+
+    pool = [pinned(L.batched_sbm_graph(g)) for g in range(pool_size)]
+    if big is not None:
+        big = pinned(big)
     count = int(rate * seconds)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
     picks = rng.integers(0, pool_size, size=count)

@@ -307,8 +307,15 @@ typedef struct {
 /* Allocates the arena on the current device and starts the worker threads. */
 lpa_status lpa_serve_create(const lpa_serve_config *cfg, lpa_server_t *out);
 
-/* Queues a request given as host CSR (same rules as lpa_graph_create; checked
- * here on the host).  Copies the data before returning.  Returns
+/* Queues a request given as host CSR (same rules as lpa_graph_create).  Here
+ * the host checks only offsets[0] == 0 and offsets[n] == nnz; an arena
+ * request's rows, indices and weights are checked on the device while it is
+ * admitted, and a request that fails is never run: its ticket is reported
+ * by lpa_serve_poll like any other and lpa_serve_fetch returns
+ * LPA_ERR_INVALID_GRAPH for it.  Solo-lane requests are checked
+ * in full here.  The data is copied (pageable buffers) or read by DMA and
+ * waited for (page-locked buffers) before returning, so the caller may reuse
+ * its buffers at once.  Returns
  * LPA_ERR_BUSY when it does not fit now (no free slot, vertex or entry range,
  * or device-memory budget); the caller may retry after results are released.
  * *ticket identifies the request. */
@@ -319,7 +326,8 @@ lpa_status lpa_serve_submit(lpa_server_t s, int64_t n, int64_t nnz, const int64_
 lpa_status lpa_serve_poll(lpa_server_t s, uint64_t *done, int32_t cap, int32_t *n_done);
 
 /* Copies a finished request's labels (host int32[n], nullable) and run info
- * (nullable).  LPA_ERR_NOT_READY while it runs, LPA_ERR_NOT_FOUND if unknown. */
+ * (nullable).  LPA_ERR_NOT_READY while it runs, LPA_ERR_NOT_FOUND if unknown,
+ * the request's own error (e.g. LPA_ERR_INVALID_GRAPH) if it failed. */
 lpa_status lpa_serve_fetch(lpa_server_t s, uint64_t ticket, int32_t *labels_host, lpa_run_info *info);
 
 /* Forgets a finished request's result. */

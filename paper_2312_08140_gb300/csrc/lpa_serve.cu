@@ -65,43 +65,74 @@ lpa_status cuda_err(cudaError_t e, const char* where) {
 // New request at vertices [v0, v0+n), entries [e0, e0+nnz): the row offsets
 // were copied as local positions; make them arena positions, make the
 // indices arena vertex ids, set labels to ids and the slot of each vertex.
+// The request's CSR is checked here (rows in order within [0, nnz], indices
+// in [0, n), weights finite and >= 0); any failure sets bad[slot] and the
+// request is never run.  A row found out of order is emptied so that no later
+// read can leave the request's entry range.
 __global__ void k_admit(int64_t* begin, int64_t* end, int32_t* idx, float* w, int32_t* lab0, int32_t* lab1,
-                        int32_t* gid, int64_t v0, int64_t n, int64_t e0, int64_t nnz, int unit, int32_t slot) {
+                        int32_t* gid, int64_t v0, int64_t n, int64_t e0, int64_t nnz, int unit, int32_t slot,
+                        int32_t* bad) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int fail = 0;
     for (int64_t i = t; i < n; i += stride) {
-        begin[v0 + i] += e0;
-        end[v0 + i] += e0;
+        int64_t b = begin[v0 + i], e = end[v0 + i];
+        if (b < 0 || e < b || e > nnz) {
+            fail = 1;
+            b = e = 0;
+        }
+        begin[v0 + i] = b + e0;
+        end[v0 + i] = e + e0;
         lab0[v0 + i] = (int32_t)(v0 + i);
         lab1[v0 + i] = (int32_t)(v0 + i);
         gid[v0 + i] = slot;
     }
     for (int64_t e = t; e < nnz; e += stride) {
-        idx[e0 + e] += (int32_t)v0;
-        if (unit) w[e0 + e] = 1.0f;
+        const int32_t j = idx[e0 + e];
+        if (j < 0 || j >= n) {
+            fail = 1;
+            idx[e0 + e] = (int32_t)v0;
+        } else {
+            idx[e0 + e] = j + (int32_t)v0;
+        }
+        if (unit) {
+            w[e0 + e] = 1.0f;
+        } else {
+            const float x = w[e0 + e];
+            if (!isfinite(x) || x < 0.f) fail = 1;
+        }
     }
+    if (fail) atomicExch(&bad[slot], 1);
 }
 
 // Start of a request's run (Algorithm 1, lpa(): every vertex unprocessed).
+// A request whose admission check failed starts done, with kExitInvalid as
+// its exit reason, and no vertex marked: no sweep touches it.
+constexpr int32_t kExitInvalid = -1;
+
 __global__ void k_activate(const int64_t* begin, const int64_t* end, uint8_t* flags, int64_t v0, int64_t n,
                            int32_t slot, int32_t* done, int32_t* iters, int32_t* exit_reason,
-                           unsigned long long* dN, long long* hist, int64_t* g_begin, int64_t* g_end) {
+                           unsigned long long* dN, long long* hist, int64_t* g_begin, int64_t* g_end,
+                           const int32_t* bad) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    for (int64_t i = t; i < n; i += stride) flags[v0 + i] = end[v0 + i] > begin[v0 + i] ? 1 : 0;
+    const bool ok = bad[slot] == 0;
+    for (int64_t i = t; i < n; i += stride) flags[v0 + i] = ok && end[v0 + i] > begin[v0 + i] ? 1 : 0;
     if (t < kMaxHist) hist[(int64_t)slot * kMaxHist + t] = 0;
     if (t == 0) {
-        done[slot] = 0;
+        done[slot] = ok ? 0 : 1;
         iters[slot] = 0;
-        exit_reason[slot] = 0;
+        exit_reason[slot] = ok ? 0 : kExitInvalid;
         dN[slot] = 0;
         g_begin[slot] = v0;
         g_end[slot] = v0 + n;
     }
 }
 
-__global__ void k_release(int64_t* begin, int64_t* end, int32_t* gid, uint8_t* flags, int64_t v0, int64_t n) {
+__global__ void k_release(int64_t* begin, int64_t* end, int32_t* gid, uint8_t* flags, int64_t v0, int64_t n,
+                          int32_t* bad, int32_t slot) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) bad[slot] = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         begin[v0 + i] = 0;
         end[v0 + i] = 0;
@@ -202,6 +233,7 @@ struct lpa_server {
     int64_t arena_bytes = 0;
     cudaStream_t run_st = nullptr, copy_st = nullptr, solo_st = nullptr;
     int32_t* h_done = nullptr;                // pinned mirror of done[S]
+    int32_t* bad = nullptr;                   // [S] admission check failed
     // host state (guarded by mu)
     std::mutex mu;
     std::condition_variable cv;
@@ -289,7 +321,8 @@ void retire_arena(lpa_server* S, Request* r) {
     if (e == cudaSuccess && r->n) {
         k_release<<<grid_for(r->n, S->sms), 256, 0, st>>>(const_cast<int64_t*>(S->s.off),
                                                          const_cast<int64_t*>(S->s.off_end),
-                                                         const_cast<int32_t*>(S->s.gid), S->s.flags, r->v0, r->n);
+                                                         const_cast<int32_t*>(S->s.gid), S->s.flags, r->v0, r->n,
+                                                         S->bad, r->slot);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -297,6 +330,12 @@ void retire_arena(lpa_server* S, Request* r) {
         res.state = 3;
         res.status = LPA_ERR_CUDA;
         res.error = cudaGetErrorString(e);
+    } else if (ex == kExitInvalid) {
+        res = Result{};
+        res.state = 3;
+        res.status = LPA_ERR_INVALID_GRAPH;
+        res.error = "request CSR failed validation: row offsets out of order or beyond nnz, an index outside "
+                    "[0, n), or a weight negative or not finite";
     } else {
         for (auto& x : res.labels) x -= (int32_t)r->v0;
         res.info.iterations = it;
@@ -331,8 +370,7 @@ void worker_main(lpa_server* S) {
                     ++it;
                 }
             }
-            for (Request* r : to_activate) S->active[r->slot] = r;
-            if (S->active.empty()) {
+            if (S->active.empty() && to_activate.empty()) {
                 if (!S->pending.empty()) {           // copies still in flight
                     lock.unlock();
                     std::this_thread::sleep_for(std::chrono::microseconds(50));
@@ -347,10 +385,12 @@ void worker_main(lpa_server* S) {
             {
                 std::lock_guard<std::mutex> lock(S->mu);
                 S->results[r->ticket].state = 1;
+                S->active[r->slot] = r;
             }
             k_activate<<<grid_for(std::max<int64_t>(r->n, kMaxHist), S->sms), 256, 0, S->run_st>>>(
                 S->s.off, S->s.off_end, S->s.flags, r->v0, r->n, r->slot, S->s.done, S->s.iters, S->s.exit_reason,
-                S->s.dN, S->s.hist_changed, const_cast<int64_t*>(S->s.g_begin), const_cast<int64_t*>(S->s.g_end));
+                S->s.dN, S->s.hist_changed, const_cast<int64_t*>(S->s.g_begin), const_cast<int64_t*>(S->s.g_end),
+                S->bad);
             if (e == cudaSuccess) e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = run_cycle(S);
@@ -414,6 +454,15 @@ void solo_main(lpa_server* S) {
     }
 }
 
+bool host_pinned(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 lpa_status check_host_csr(int64_t n, int64_t nnz, const int64_t* off, const int32_t* idx, const float* w) {
     if (off[0] != 0 || off[n] != nnz) return err(LPA_ERR_INVALID_GRAPH, "offsets must start at 0 and end at nnz");
     for (int64_t i = 0; i < n; ++i)
@@ -464,14 +513,15 @@ lpa_status lpa_serve_create(const lpa_serve_config* cfg, lpa_server_t* out) {
         (rs = dalloc_t(S, &s.flist, V * kBins)) || (rs = dalloc_t(S, &s.chg, V * kBins)) ||
         (rs = dalloc_t(S, &s.ctrl, 1)) || (rs = dalloc_t(S, &s.dN, G)) || (rs = dalloc_t(S, &s.done, G)) ||
         (rs = dalloc_t(S, &s.iters, G)) || (rs = dalloc_t(S, &s.exit_reason, G)) ||
-        (rs = dalloc_t(S, &s.hist_changed, G * kMaxHist)) || (rs = dalloc_t(S, &s.ovf, E / 2048 + 1)))
+        (rs = dalloc_t(S, &s.hist_changed, G * kMaxHist)) || (rs = dalloc_t(S, &s.ovf, E / 2048 + 1)) ||
+        (rs = dalloc_t(S, &S->bad, G)))
         return bail(rs);
     if (S->arena_bytes > cfg->hbm_budget_bytes)
         return bail(err(LPA_ERR_INVALID_ARG, "arena sizes exceed hbm_budget_bytes"));
     auto zero = [&](void* p, size_t b) { return cudaMemset(p, 0, b) == cudaSuccess; };
     bool ok = zero(begin, V * 8) && zero(end, V * 8) && zero(s.flags, V + 16) && zero(s.ctrl, sizeof(Ctrl)) &&
               zero(s.dN, G * 8) && zero(s.iters, G * 4) && zero(s.exit_reason, G * 4) &&
-              cudaMemset(gid, 0xff, V * 4) == cudaSuccess && zero(gb, G * 8) && zero(ge, G * 8);
+              cudaMemset(gid, 0xff, V * 4) == cudaSuccess && zero(gb, G * 8) && zero(ge, G * 8) && zero(S->bad, G * 4);
     std::vector<int32_t> ones(G, 1);
     ok = ok && cudaMemcpy(s.done, ones.data(), G * 4, cudaMemcpyHostToDevice) == cudaSuccess;
     if (!ok) return bail(err(LPA_ERR_CUDA, "arena initialisation failed"));
@@ -524,8 +574,12 @@ lpa_status lpa_serve_submit(lpa_server_t S, int64_t n, int64_t nnz, const int64_
     if (!S || !ticket) return err(LPA_ERR_INVALID_ARG, "NULL argument");
     if (n < 0 || n > 0x7fffffffLL || nnz < 0) return err(LPA_ERR_INVALID_ARG, "n or nnz out of range");
     if (!offsets || (nnz > 0 && !indices)) return err(LPA_ERR_INVALID_ARG, "offsets or indices is NULL");
-    lpa_status rs = check_host_csr(n, nnz, offsets, indices, weights);
-    if (rs != LPA_OK) return rs;
+    const bool solo = S->cfg.solo_min_entries > 0 && nnz >= S->cfg.solo_min_entries;
+    if (offsets[0] != 0 || offsets[n] != nnz) return err(LPA_ERR_INVALID_GRAPH, "offsets must start at 0 and end at nnz");
+    if (n == 0 || solo) {
+        lpa_status rs = check_host_csr(n, nnz, offsets, indices, weights);
+        if (rs != LPA_OK) return rs;
+    }
     {
         std::lock_guard<std::mutex> lock(S->mu);
         if (!S->fatal.empty()) return err(LPA_ERR_CUDA, S->fatal);
@@ -534,7 +588,6 @@ lpa_status lpa_serve_submit(lpa_server_t S, int64_t n, int64_t nnz, const int64_
     r->n = n;
     r->nnz = nnz;
     r->weighted = weights != nullptr;
-    const bool solo = S->cfg.solo_min_entries > 0 && nnz >= S->cfg.solo_min_entries;
     if (n == 0 || solo) {
         std::lock_guard<std::mutex> lock(S->mu);
         if (solo) {
@@ -597,11 +650,15 @@ lpa_status lpa_serve_submit(lpa_server_t S, int64_t n, int64_t nnz, const int64_
         k_admit<<<grid_for(std::max(n, nnz), S->sms), 256, 0, st>>>(
             const_cast<int64_t*>(s.off), const_cast<int64_t*>(s.off_end), const_cast<int32_t*>(s.idx),
             const_cast<float*>(static_cast<const float*>(s.w)), s.lab[0], s.lab[1], const_cast<int32_t*>(s.gid), r->v0,
-            n, r->e0, nnz, weights ? 0 : 1, r->slot);
+            n, r->e0, nnz, weights ? 0 : 1, r->slot, S->bad);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(r->ready, st);
+    // Page-locked inputs are read by DMA after this call is enqueued: wait for
+    // the copies so the caller may reuse its buffers on return.  (Pageable
+    // inputs were staged by the copies themselves before they returned.)
+    if (e == cudaSuccess && host_pinned(offsets)) e = cudaEventSynchronize(r->ready);
     std::lock_guard<std::mutex> lock(S->mu);
     if (e != cudaSuccess) {
         S->vfree.release(r->v0, n);

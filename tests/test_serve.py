@@ -116,3 +116,71 @@ def test_serve_async_invariants():
             assert 1 <= info.iterations <= 20
     finally:
         lpa.lpa_serve_destroy(srv)
+
+
+@pytest.mark.gpu
+def test_serve_rejects_malformed_requests_on_device_and_runs_the_rest():
+    """Arena requests are checked while they are admitted (row order and range,
+    index range, finite non-negative weights); a malformed one is reported as
+    LPA_ERR_INVALID_GRAPH at fetch and never disturbs the requests around it.
+    Page-locked inputs take the direct-copy path and must give the same labels."""
+    import torch
+    import paper_2312_08140_gb300 as lpa
+    lpa.load()
+    good = [L.batched_sbm_graph(g, n_max=4000) for g in range(80, 92)]
+    base = L.planted_partition(n=600, blocks=3, seed=11)
+    w = np.ones(base.nnz, np.float32)
+    bad = []
+    idx = base.idx.copy(); idx[base.nnz // 2] = base.n                     # index == n
+    bad.append((base.off, idx, None))
+    idx = base.idx.copy(); idx[7] = -3                                     # negative index
+    bad.append((base.off, idx, None))
+    off = base.off.copy(); off[5] = off[6] + 1                             # rows out of order
+    bad.append((off, base.idx, None))
+    wn = w.copy(); wn[3] = -1.0                                            # negative weight
+    bad.append((base.off, base.idx, wn))
+    wn = w.copy(); wn[base.nnz - 1] = np.nan                               # weight not finite
+    bad.append((base.off, base.idx, wn))
+    srv = lpa.lpa_serve_create(hbm_budget_bytes=4 << 30, arena_vertices=200_000, arena_entries=10_000_000,
+                               max_slots=32, mode="sync")
+    try:
+        kinds = {}
+        for k in range(max(len(good), len(bad))):
+            if k < len(good):
+                g = good[k]
+                if k % 2:                                                  # page-locked copies of the inputs
+                    off_p = torch.from_numpy(g.off).pin_memory().numpy()
+                    idx_p = torch.from_numpy(g.idx).pin_memory().numpy()
+                    w_p = None if g.w is None else torch.from_numpy(g.w).pin_memory().numpy()
+                    t = lpa.lpa_serve_submit(srv, g.n, g.nnz, off_p, idx_p, w_p)
+                else:
+                    t = lpa.lpa_serve_submit(srv, g.n, g.nnz, g.off, g.idx, g.w)
+                kinds[t] = ("good", k)
+            if k < len(bad):
+                o, i, ww = bad[k]
+                kinds[lpa.lpa_serve_submit(srv, base.n, base.nnz, o, i, ww)] = ("bad", k)
+        _drain(lpa, srv, kinds)
+        for t, (kind, k) in kinds.items():
+            if kind == "bad":
+                with pytest.raises(lpa.LpaError) as e:
+                    lpa.lpa_serve_fetch(srv, t, base.n)
+                assert e.value.status == lpa.LPA_ERR_INVALID_GRAPH, k
+            else:
+                g = good[k]
+                lab, info = lpa.lpa_serve_fetch(srv, t, g.n)
+                ref, it, ch = O.lpa_sync(g.off, g.idx, g.w)
+                assert np.array_equal(lab, ref), k
+                assert info.iterations == it and list(info.changed[:it]) == ch.tolist(), k
+            lpa.lpa_serve_release(srv, t)
+        # a slot and range freed by a rejected request are reusable
+        t = lpa.lpa_serve_submit(srv, base.n, base.nnz, base.off, base.idx, None)
+        _drain(lpa, srv, [t])
+        lab, _ = lpa.lpa_serve_fetch(srv, t, base.n)
+        assert np.array_equal(lab, O.lpa_sync(base.off, base.idx, None)[0])
+        # the O(1) host checks still refuse at submit
+        off = base.off.copy(); off[-1] += 1
+        with pytest.raises(lpa.LpaError) as e:
+            lpa.lpa_serve_submit(srv, base.n, base.nnz, off, base.idx, None)
+        assert e.value.status == lpa.LPA_ERR_INVALID_GRAPH
+    finally:
+        lpa.lpa_serve_destroy(srv)
