@@ -52,6 +52,8 @@ def workload(name):
         return [("rmat22", lambda: L.rmat(22, 16, seed=1)), ("grid4096", lambda: L.road_grid(4096, 4096, seed=1))]
     if name == "rmat21+grid2048":
         return [("rmat21", lambda: L.rmat(21, 16, seed=1)), ("grid2048", lambda: L.road_grid(2048, 2048, seed=1))]
+    if name == "planted1e4+grid64":
+        return [("planted1e4", lambda: L.planted_partition(seed=1)), ("grid64", lambda: L.road_grid(64, 64, seed=1))]
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -61,6 +63,8 @@ WORKLOAD_TEXT = {
                        "shortcuts, integer weights 1..8); sync and async-with-pruning; tau=0.05, cap 20",
     "rmat21+grid2048": "R-MAT scale 21 + 2048x2048 road-like grid (smaller profiling case of the same "
                        "generators, still larger than L2); sync and async-with-pruning; tau=0.05, cap 20",
+    "planted1e4+grid64": "planted partition 10 x 1000 + 64x64 road-like grid (a seconds-long check of the "
+                         "launch path, smaller than L2: not a performance workload); tau=0.05, cap 20",
 }
 
 
@@ -330,6 +334,19 @@ def serving_sample(lpa, torch, stream, rate, seconds, pool_size, big=None, big_e
 
 
 # ------------------------------------------------------------------- GPU arm
+def reduce_over_ranks(dist, device, slowest, counts):
+    """Replicas: the job's time is the slowest rank's and its work the sum of
+    every rank's counters.  Returns (max over ranks, [sums])."""
+    if dist is None:
+        return float(slowest), [float(c) for c in counts]
+    import torch
+    t = torch.tensor([float(slowest)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(c) for c in counts], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(x) for x in u.tolist()]
+
+
 def kernel_bytes(prof, wbytes, sync, passes):
     """Algorithmic bytes per sweep-kernel launch from the per-bin counts:
     per scanned vertex 16 B offsets + 4 B own label + 4 B frontier id; per
@@ -424,13 +441,7 @@ def main():
     edges = sum(g.nnz * s for g, s in zip(graphs, sweeps))
     touched = sum(a["scanned_total"] - b["scanned_total"] for a, b in zip(after, before))
     launches = sum(a["launches_total"] - b["launches_total"] for a, b in zip(after, before))
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        u = torch.tensor([edges, touched, launches], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        edges, touched, launches = (float(x) for x in u.tolist())
+    ms, (edges, touched, launches) = reduce_over_ranks(dist, "cuda", ms, [edges, touched, launches])
     value = edges / (ms / 1e3)
 
     # per-run detail (one run each, with info) for the record
@@ -471,13 +482,7 @@ def main():
     e2e_edges = sum(e2e_step() for _ in range(args.e2e_steps))
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-        u = torch.tensor([e2e_edges], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        e2e_edges = float(u.item())
+    e2e_s, (e2e_edges,) = reduce_over_ranks(dist, "cuda", e2e_s, [e2e_edges])
 
     # roofline: event-timed profiled runs, same kernels and launch shapes
     roofline, kernels = None, None
