@@ -173,11 +173,20 @@ const char *lpa_last_error(void);
  *   flags     LPA_HOST_PTRS | LPA_DEVICE_PTRS, optionally | LPA_BORROW
  * Validates the CSR on the device (returns LPA_ERR_INVALID_GRAPH on failure)
  * and synchronises `stream` before returning.  Device memory: the CSR copy
- * (unless borrowed) plus about 17 bytes per vertex of working state. */
+ * (unless borrowed) plus about 17 bytes per vertex of working state, taken
+ * from the library's per-device memory pool. */
 lpa_status lpa_graph_create(int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *indices,
                             const float *weights, uint32_t flags, void *stream, lpa_graph_t *out);
 
+/* Waits for all work on the graph's device (as cudaFree does), then returns
+ * the graph's memory to the library's pool, which keeps it for the next
+ * graph or batch created on that device. */
 lpa_status lpa_graph_destroy(lpa_graph_t g);
+
+/* Gives the pool's cached (freed, not in use) device memory back to the
+ * driver on every device; memory of live graphs and batches is unaffected.
+ * No counterpart in the paper: a memory-management call of this library. */
+lpa_status lpa_release_cached_memory(void);
 
 /* Properties of a handle (host struct).  Waits for all work on the device
  * (cudaDeviceSynchronize) so that the cumulative counters are current. */

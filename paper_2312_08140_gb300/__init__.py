@@ -135,6 +135,7 @@ _SIGS = {
     "lpa_last_error": ([], ctypes.c_char_p),
     "lpa_graph_create": ([_I64, _I64, _V, _V, _V, _U32, _V, _P(_V)], ctypes.c_int),
     "lpa_graph_destroy": ([_V], ctypes.c_int),
+    "lpa_release_cached_memory": ([], ctypes.c_int),
     "lpa_graph_props_get": ([_V, _P(LpaGraphProps)], ctypes.c_int),
     "lpa_graph_get_config": ([_V, _P(LpaConfig)], ctypes.c_int),
     "lpa_graph_set_config": ([_V, _P(LpaConfig)], ctypes.c_int),
@@ -233,6 +234,10 @@ def lpa_graph_create(n, nnz, offsets, indices, weights=None, flags=LPA_HOST_PTRS
 
 def lpa_graph_destroy(g):
     _check(load().lpa_graph_destroy(g))
+
+
+def lpa_release_cached_memory():
+    _check(load().lpa_release_cached_memory())
 
 
 def lpa_graph_props_get(g) -> dict:

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -52,11 +53,81 @@ int64_t pow2ceil(int64_t x) {
     return p;
 }
 
+// ------------------------------------------------------------ memory pool --
+// Device memory of graphs and batches comes from one stream-ordered pool per
+// device that keeps freed pages mapped (no release threshold): creating a
+// graph after another was destroyed reuses those pages instead of mapping new
+// ones and destroying one does not unmap.  lpa_release_cached_memory() hands
+// the cached pages back to the driver.  Allocations and frees are issued on
+// the pool's own stream and waited for, so memory is usable from any stream
+// on return and a free never races a later allocation.
+constexpr int kMaxPoolDevices = 64;
+struct DevicePool {
+    cudaMemPool_t pool = nullptr;
+    cudaStream_t st = nullptr;
+};
+std::mutex g_pool_mu;
+DevicePool g_pools[kMaxPoolDevices];
+
+cudaError_t pool_of(int dev, DevicePool** out) {
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    DevicePool& P = g_pools[dev];
+    if (!P.pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        cudaStream_t st = nullptr;
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        P.pool = pool;
+        P.st = st;
+    }
+    *out = &P;
+    return cudaSuccess;
+}
+
+cudaError_t pool_alloc(int dev, void** p, size_t bytes) {
+    DevicePool* P = nullptr;
+    cudaError_t e = pool_of(dev, &P);
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(p, bytes, P->pool, P->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->st);
+    return e;
+}
+
+// Frees a list of pool allocations once all work on the device is done (the
+// same guarantee cudaFree gives).
+void pool_free_all(int dev, std::vector<void*>& ptrs) {
+    if (ptrs.empty()) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != dev) cudaSetDevice(dev);
+    DevicePool* P = nullptr;
+    if (pool_of(dev, &P) == cudaSuccess) {
+        cudaDeviceSynchronize();
+        for (void* q : ptrs) cudaFreeAsync(q, P->st);
+        cudaStreamSynchronize(P->st);
+    }
+    ptrs.clear();
+    if (cur != dev) cudaSetDevice(cur);
+}
+
 struct Engine {
     int device = 0;
     int sms = 1;
     DevState s{};
-    std::vector<void*> owned;        // device allocations freed at destroy
+    std::vector<void*> owned;        // pool allocations freed at destroy
+    unsigned* static_counts = nullptr;             // static-list scratch
+    unsigned long long* static_ents = nullptr;
     int32_t* idx_owned = nullptr;
     bool borrowed = false;
     bool weighted = false;
@@ -79,8 +150,12 @@ struct Engine {
 
 lpa_status dalloc(Engine& E, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
-    cudaError_t err = cudaMalloc(p, bytes);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc");
+    cudaError_t err = pool_alloc(E.device, p, bytes);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        return err == cudaErrorMemoryAllocation ? fail(LPA_ERR_OUT_OF_MEMORY, "device memory: %zu bytes", bytes)
+                                                : cuda_fail(err, "cudaMallocFromPoolAsync");
+    }
     E.owned.push_back(*p);
     E.device_bytes += (int64_t)bytes;
     return LPA_OK;
@@ -104,21 +179,25 @@ void engine_free(Engine& E) {
     destroy_graphs(E);
     if (E.cap_top) cudaStreamDestroy(E.cap_top);
     if (E.cap_body) cudaStreamDestroy(E.cap_body);
-    for (void* p : E.owned) cudaFree(p);
-    E.owned.clear();
-    if (E.ovf) cudaFree(E.ovf);
+    if (E.ovf) E.owned.push_back(E.ovf);
     E.ovf = nullptr;
+    pool_free_all(E.device, E.owned);
 }
 
 // Grid sizes of the block bins, and the overflow list of the last bin (one
 // entry per vertex of that bin at most).
 lpa_status setup_blocks(Engine& E) {
     for (int b = 0; b < kBlockBins; ++b) E.block_grid[b] = block_grid_for(E.s, b + 2, E.sms);
-    if (E.ovf) cudaFree(E.ovf);
+    if (E.ovf) {
+        std::vector<void*> old{E.ovf};
+        pool_free_all(E.device, old);
+    }
     E.ovf = nullptr;
     const size_t n = std::max<size_t>(E.s.bin_static[kBins - 1], 1);
-    cudaError_t err = cudaMalloc(&E.ovf, n * sizeof(Overflow));
-    if (err != cudaSuccess) return cuda_fail(err, "cudaMalloc(overflow list)");
+    void* p = nullptr;
+    cudaError_t err = pool_alloc(E.device, &p, n * sizeof(Overflow));
+    if (err != cudaSuccess) return cuda_fail(err, "overflow list");
+    E.ovf = static_cast<Overflow*>(p);
     E.s.ovf = E.ovf;
     return LPA_OK;
 }
@@ -214,22 +293,22 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     LPA_CUDA(cudaMemcpyAsync(&vr, vr_d, sizeof(vr), cudaMemcpyDeviceToHost, st));
     LPA_CUDA(cudaStreamSynchronize(st));
     if (n == 0 && nnz != 0) return fail(LPA_ERR_INVALID_GRAPH, "n == 0 but nnz != 0");
-    if (vr.bad_offsets) return fail(LPA_ERR_INVALID_GRAPH, "%u rows have invalid offsets", vr.bad_offsets);
-    if (vr.bad_index) return fail(LPA_ERR_INVALID_GRAPH, "%u indices out of range", vr.bad_index);
-    if (vr.bad_weight) return fail(LPA_ERR_INVALID_GRAPH, "%u weights negative or not finite", vr.bad_weight);
+    if (vr.c[0]) return fail(LPA_ERR_INVALID_GRAPH, "%u rows have invalid offsets", vr.c[0]);
+    if (vr.c[1]) return fail(LPA_ERR_INVALID_GRAPH, "%u indices out of range", vr.c[1]);
+    if (vr.c[2]) return fail(LPA_ERR_INVALID_GRAPH, "%u weights negative or not finite", vr.c[2]);
     E.max_degree = (int64_t)vr.max_degree;
 
     // weight representation: integer sums when every sum is an exact integer
     if (!weights) {
-        E.exact = vr.huge_row == 0;
+        E.exact = vr.c[5] == 0;
         E.s.weight_kind = E.exact ? W_UNIT : W_F32;
         if (!E.exact) return fail(LPA_ERR_INVALID_GRAPH, "a vertex has degree >= 2^31");
-    } else if (!borrow && vr.non_integer == 0 && vr.huge_row == 0) {
+    } else if (!borrow && vr.c[3] == 0 && vr.c[5] == 0) {
         LPA_CUDA(launch_weights_to_u32(w_d, nnz, st, E.sms));
         E.exact = true;
         E.s.weight_kind = W_U32;
     } else {
-        E.exact = vr.non_integer == 0 && vr.heavy_row == 0;
+        E.exact = vr.c[3] == 0 && vr.c[4] == 0;
         E.s.weight_kind = W_F32;
     }
     E.s.off = off_d;
@@ -259,7 +338,10 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     LPA_CUDA(cudaMemsetAsync(E.s.ctrl, 0, sizeof(Ctrl), st));
     LPA_CUDA(cudaMemsetAsync(E.s.hist_changed, 0, (size_t)G * kMaxHist * 8, st));
     apply_config_fields(E);
-    LPA_CUDA(build_static_lists(E.s, st));
+    const size_t sblk = (size_t)std::max<int64_t>(static_scratch_blocks(n), 1) * kBins;
+    if ((rs = dalloc_t(E, &E.static_counts, sblk)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.static_ents, sblk)) != LPA_OK) return rs;
+    LPA_CUDA(build_static_lists(E.s, st, E.static_counts, E.static_ents));
     if ((rs = setup_blocks(E)) != LPA_OK) return rs;
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_top, cudaStreamNonBlocking));
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_body, cudaStreamNonBlocking));
@@ -623,7 +705,7 @@ static lpa_status set_config(Engine& E, const lpa_config* cfg) {
     destroy_graphs(E);
     E.cfg = *cfg;
     apply_config_fields(E);
-    LPA_CUDA(build_static_lists(E.s, 0));
+    LPA_CUDA(build_static_lists(E.s, 0, E.static_counts, E.static_ents));
     return setup_blocks(E);
 }
 
@@ -712,6 +794,17 @@ lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t m
 }
 
 // ------------------------------------------------------------------ batches
+lpa_status lpa_release_cached_memory(void) {
+    g_last_error.clear();
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    for (int d = 0; d < kMaxPoolDevices; ++d) {
+        if (!g_pools[d].pool) continue;
+        cudaError_t e = cudaMemPoolTrimTo(g_pools[d].pool, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemPoolTrimTo");
+    }
+    return LPA_OK;
+}
+
 lpa_status lpa_batch_create(int32_t G, const int64_t* graph_vtx_off, const int64_t* graph_edge_off,
                             const int64_t* offsets, const int32_t* indices, const float* weights, uint32_t flags,
                             void* stream, lpa_batch_t* out) {

@@ -278,8 +278,10 @@ __global__ void __launch_bounds__(kFrontThreads) k_static_scatter(DevState s, co
     block_append<false>(s.bin_base, s.slist, cursor, ent, vid, bin, deg);
 }
 
-cudaError_t build_static_lists(DevState& s, cudaStream_t st) {
-    const int64_t nblk = (s.N + kStaticChunk - 1) / kStaticChunk;
+int64_t static_scratch_blocks(int64_t N) { return (N + kStaticChunk - 1) / kStaticChunk; }
+
+cudaError_t build_static_lists(DevState& s, cudaStream_t st, unsigned* counts, unsigned long long* ents) {
+    const int64_t nblk = static_scratch_blocks(s.N);
     for (int b = 0; b < kBins; ++b) {
         s.bin_base[b] = 0;
         s.bin_static[b] = 0;
@@ -287,19 +289,10 @@ cudaError_t build_static_lists(DevState& s, cudaStream_t st) {
     }
     s.active_entries = 0;
     if (nblk == 0) return cudaSuccess;
-    unsigned* counts = nullptr;
-    unsigned long long* ents = nullptr;
-    cudaError_t err = cudaMalloc(&counts, (size_t)nblk * kBins * sizeof(unsigned));
-    if (err != cudaSuccess) return err;
-    err = cudaMalloc(&ents, (size_t)nblk * kBins * sizeof(unsigned long long));
-    if (err != cudaSuccess) {
-        cudaFree(counts);
-        return err;
-    }
     std::vector<unsigned> hc((size_t)nblk * kBins);
     std::vector<unsigned long long> he((size_t)nblk * kBins);
     k_static_count<<<(unsigned)nblk, kFrontThreads, 0, st>>>(s, counts, ents);
-    err = cudaGetLastError();
+    cudaError_t err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaMemcpyAsync(hc.data(), counts, hc.size() * 4, cudaMemcpyDeviceToHost, st);
     if (err == cudaSuccess) err = cudaMemcpyAsync(he.data(), ents, he.size() * 8, cudaMemcpyDeviceToHost, st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
@@ -327,8 +320,6 @@ cudaError_t build_static_lists(DevState& s, cudaStream_t st) {
         err = cudaGetLastError();
     }
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
-    cudaFree(counts);
-    cudaFree(ents);
     return err;
 }
 
@@ -559,70 +550,173 @@ cudaError_t launch_finalize(const DevState& s, cudaStream_t st, int sms) {
 }
 
 // ------------------------------------------------------------ validation --
-// One warp per row.  For a batch (G > 1) indices are graph-local on input and
-// are rewritten to global ids in idx_rw (the library's own copy).
-__global__ void k_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N, int64_t E,
-                           const int64_t* vtx_off, const int64_t* edge_off, const int32_t* gid, int32_t G,
-                           int rewrite, int32_t* idx_rw, ValidateResult* res) {
+// Two flat passes, each with per-thread counters, one shared-memory reduction
+// per block and one global atomic per field per block.
+//   entries: index range (graph-local for a batch, then rewritten to global
+//            ids in idx_rw, the library's own copy), weights finite and
+//            >= 0, integer-valued or not, and the largest weight;
+//   rows:    offsets (in order, within [0, E], the first at 0, the last at E,
+//            batch boundaries at edge_off), degree, and the weighted-degree
+//            thresholds 2^24 (fp32 sums may round) and 2^31 (32-bit integer
+//            sums may overflow).  A row's exact weighted sum is taken (by the
+//            whole warp) only when degree x largest weight reaches 2^24.
+constexpr int kValThreads = 256;
+
+struct ValAcc {
+    unsigned int c[6];          // bad_offsets, bad_index, bad_weight, non_integer, heavy_row, huge_row
+    unsigned long long max_degree;
+    unsigned int max_weight_bits;
+};
+
+__device__ __forceinline__ void val_flush(ValAcc& a, ValidateResult* res) {
+    __shared__ unsigned int sc[6];
+    __shared__ unsigned long long smax;
+    __shared__ unsigned int swmax;
+    if (threadIdx.x < 6) sc[threadIdx.x] = 0;
+    if (threadIdx.x == 0) {
+        smax = 0;
+        swmax = 0;
+    }
+    __syncthreads();
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const unsigned v = __reduce_add_sync(kFull, a.c[k]);
+        if (lane == 0 && v) atomicAdd(&sc[k], v);
+    }
+    unsigned long long m = a.max_degree;
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_xor_sync(kFull, m, o);
+        m = x > m ? x : m;
+    }
+    const unsigned wm = __reduce_max_sync(kFull, a.max_weight_bits);
+    if (lane == 0) {
+        if (m) atomicMax(&smax, m);
+        if (wm) atomicMax(&swmax, wm);
+    }
+    __syncthreads();
+    if (threadIdx.x < 6 && sc[threadIdx.x]) atomicAdd(&res->c[threadIdx.x], sc[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        if (smax) atomicMax(&res->max_degree, smax);
+        if (swmax) atomicMax(&res->max_weight_bits, swmax);
+    }
+}
+
+// Entries: block b owns the contiguous chunk [b*chunk, (b+1)*chunk).
+__global__ void __launch_bounds__(kValThreads) k_validate_entries(const int32_t* idx, const float* w, int64_t N,
+                                                                  int64_t E, const int64_t* vtx_off,
+                                                                  const int64_t* edge_off, int32_t G, int rewrite,
+                                                                  int32_t* idx_rw, int64_t chunk,
+                                                                  ValidateResult* res) {
+    ValAcc a{};
+    const int64_t beg = (int64_t)blockIdx.x * chunk;
+    const int64_t end = beg + chunk < E ? beg + chunk : E;
+    int64_t ge_lo = 0, ge_hi = E, lo = 0, n_local = N;      // entry range, first vertex, size of the graph
+    if (rewrite) ge_hi = -1;
+    for (int64_t e = beg + threadIdx.x; e < end; e += kValThreads) {
+        const int32_t j = idx[e];
+        if (rewrite) {
+            if (e < ge_lo || e >= ge_hi) {                      // graph g with edge_off[g] <= e < edge_off[g+1]
+                int32_t l = 0, h = G;
+                while (h - l > 1) {
+                    const int32_t mid = (l + h) >> 1;
+                    if (edge_off[mid] <= e) l = mid;
+                    else h = mid;
+                }
+                ge_lo = edge_off[l];
+                ge_hi = edge_off[l + 1];
+                lo = vtx_off[l];
+                n_local = vtx_off[l + 1] - lo;
+            }
+            if (j < 0 || j >= n_local) ++a.c[1];
+            else idx_rw[e] = (int32_t)(j + lo);
+        } else if (j < 0 || j >= N) {
+            ++a.c[1];
+        }
+        if (w) {
+            const float x = w[e];
+            if (!isfinite(x) || x < 0.f) {
+                ++a.c[2];
+            } else {
+                if (x != truncf(x)) ++a.c[3];
+                const unsigned bits = __float_as_uint(x);     // x >= 0: bit order is value order
+                a.max_weight_bits = bits > a.max_weight_bits ? bits : a.max_weight_bits;
+            }
+        }
+    }
+    val_flush(a, res);
+}
+
+// Rows: lane l of a warp takes row base + l; all lanes run the same trips.
+__global__ void __launch_bounds__(kValThreads) k_validate_rows(const int64_t* off, const float* w, int64_t N,
+                                                               int64_t E, const int64_t* vtx_off,
+                                                               const int64_t* edge_off, const int32_t* gid,
+                                                               int32_t G, ValidateResult* res) {
+    ValAcc a{};
     const unsigned lane = lane_id();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp; v < N; v += nwarps) {
-        const int64_t st = off[v], en = off[v + 1];
-        const int32_t g = G > 1 ? gid[v] : 0;
-        const int64_t lo = G > 1 ? vtx_off[g] : 0;
-        const int64_t hi = G > 1 ? vtx_off[g + 1] : N;
-        bool bad = st < 0 || en < st || en > E || (v == 0 && st != 0) || (v == N - 1 && en != E);
-        if (G > 1 && v == lo && st != edge_off[g]) bad = true;
-        if (G > 1 && v == hi - 1 && en != edge_off[g + 1]) bad = true;
-        if (bad) {
-            if (lane == 0) atomicAdd(&res->bad_offsets, 1u);
-            continue;
-        }
-        const int64_t n_local = hi - lo;
-        unsigned bad_i = 0, bad_w = 0, non_int = 0;
-        double rowsum = 0.0;
-        for (int64_t e = st + lane; e < en; e += 32) {
-            int64_t j = idx[e];
-            if (rewrite) {
-                if (j < 0 || j >= n_local) ++bad_i;
-                else idx_rw[e] = (int32_t)(j + lo);
-            } else if (j < 0 || j >= N) {
-                ++bad_i;
+    const double wmax = w ? (double)__uint_as_float(res->max_weight_bits) : 1.0;   // entries pass ran first
+    for (int64_t base = warp * 32; base < N; base += nwarps * 32) {
+        const int64_t v = base + lane;
+        int64_t st = 0, en = 0;
+        bool need_sum = false;
+        if (v < N) {
+            st = off[v];
+            en = off[v + 1];
+            bool bad = st < 0 || en < st || en > E || (v == 0 && st != 0) || (v == N - 1 && en != E);
+            if (G > 1) {
+                const int32_t g = gid[v];
+                if (v == vtx_off[g] && st != edge_off[g]) bad = true;
+                if (v == vtx_off[g + 1] - 1 && en != edge_off[g + 1]) bad = true;
             }
-            if (w) {
-                const float x = w[e];
-                if (!isfinite(x) || x < 0.f) ++bad_w;
-                else {
-                    if (x != truncf(x)) ++non_int;
-                    rowsum += (double)x;
+            if (bad) {
+                ++a.c[0];
+            } else {
+                const int64_t d = en - st;
+                a.max_degree = (unsigned long long)d > a.max_degree ? (unsigned long long)d : a.max_degree;
+                if (!w) {
+                    if (d >= 16777216) ++a.c[4];
+                    if (d >= 2147483648LL) ++a.c[5];
+                } else {
+                    need_sum = (double)d * wmax >= 16777216.0;
                 }
             }
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            bad_i += __shfl_xor_sync(kFull, bad_i, o);
-            bad_w += __shfl_xor_sync(kFull, bad_w, o);
-            non_int += __shfl_xor_sync(kFull, non_int, o);
-            rowsum += __shfl_xor_sync(kFull, rowsum, o);
-        }
-        if (lane == 0) {
-            if (bad_i) atomicAdd(&res->bad_index, bad_i);
-            if (bad_w) atomicAdd(&res->bad_weight, bad_w);
-            if (non_int) atomicAdd(&res->non_integer, non_int);
-            const double deg_w = w ? rowsum : (double)(en - st);
-            if (deg_w >= 16777216.0) atomicAdd(&res->heavy_row, 1u);
-            if (deg_w >= 2147483648.0) atomicAdd(&res->huge_row, 1u);
-            atomicMax(&res->max_degree, (unsigned long long)(en - st));
+        unsigned m = __ballot_sync(kFull, need_sum);
+        while (m) {                                             // exact weighted degree, whole warp
+            const int l = __ffs(m) - 1;
+            m &= m - 1;
+            const int64_t rs = __shfl_sync(kFull, st, l), re = __shfl_sync(kFull, en, l);
+            double sum = 0.0;
+            for (int64_t e = rs + lane; e < re; e += 32) sum += (double)w[e];
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+            if (lane == 0) {
+                if (sum >= 16777216.0) ++a.c[4];
+                if (sum >= 2147483648.0) ++a.c[5];
+            }
         }
     }
+    val_flush(a, res);
 }
 
 cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N, int64_t E,
                             const int64_t* vtx_off, const int64_t* edge_off, const int32_t* gid, int32_t G,
                             int rewrite_local_ids, int32_t* idx_rw, ValidateResult* res, cudaStream_t st,
                             int sms) {
-    k_validate<<<sms * 8, 256, 0, st>>>(off, idx, w, N, E, vtx_off, edge_off, gid, G, rewrite_local_ids,
-                                        idx_rw, res);
+    if (E > 0) {
+        const int64_t max_blocks = (int64_t)sms * 8;
+        int64_t chunk = (E + max_blocks - 1) / max_blocks;
+        chunk = std::max<int64_t>((chunk + kValThreads - 1) / kValThreads * kValThreads, kValThreads * 4);
+        const int blocks = (int)((E + chunk - 1) / chunk);
+        k_validate_entries<<<blocks, kValThreads, 0, st>>>(idx, w, N, E, vtx_off, edge_off, G, rewrite_local_ids,
+                                                           idx_rw, chunk, res);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t warps = (N + 31) / 32;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)sms * 8));
+    k_validate_rows<<<blocks, kValThreads, 0, st>>>(off, w, N, E, vtx_off, edge_off, gid, G, res);
     return cudaGetLastError();
 }
 

@@ -137,7 +137,10 @@ struct LaunchShape {
 cudaError_t launch_init(const DevState& s, cudaStream_t st, int sms);
 // Static bin lists (slist, bin_base, bin_static*, active_entries) from the
 // degrees and the bin limits in s.  Synchronises `st`.
-cudaError_t build_static_lists(DevState& s, cudaStream_t st);
+// Static per-bin vertex lists (used by dense sweeps).  counts/ents: device
+// scratch of kBins * static_scratch_blocks(N) elements each.
+int64_t static_scratch_blocks(int64_t N);
+cudaError_t build_static_lists(DevState& s, cudaStream_t st, unsigned* counts, unsigned long long* ents);
 cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st);
 // role 0: end of a sweep (apply, compaction for the next sweep, control);
 // role 1: compaction only (inside an asynchronous sweep, of the vertices the
@@ -158,13 +161,14 @@ int block_grid_for(const DevState& s, int bin, int sms);
 
 // Graph validation (row-wise).  Results accumulate into *res (device).
 struct ValidateResult {
-    unsigned int bad_offsets;
-    unsigned int bad_index;
-    unsigned int bad_weight;
-    unsigned int non_integer;
-    unsigned int heavy_row;            // weighted degree >= 2^24 (fp32 sums may round)
-    unsigned int huge_row;             // weighted degree >= 2^31 (32-bit integer sums may overflow)
+    // c[0] rows with invalid offsets, c[1] indices out of range, c[2] weights
+    // negative or not finite, c[3] weights not integer-valued, c[4] rows of
+    // weighted degree >= 2^24 (fp32 sums may round), c[5] rows of weighted
+    // degree >= 2^31 (32-bit integer sums may overflow)
+    unsigned int c[6];
     unsigned long long max_degree;
+    unsigned int max_weight_bits;      // bits of the largest valid weight (>= 0, so ordered as unsigned)
+    unsigned int pad;
 };
 cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N,
                             int64_t E, const int64_t* vtx_off, const int64_t* edge_off,

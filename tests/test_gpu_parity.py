@@ -185,6 +185,51 @@ def test_non_integer_weights_flagged_inexact(lpa):
     lpa.lpa_graph_destroy(h)
 
 
+def test_weighted_degree_thresholds_and_max_degree(lpa):
+    """Creation records the largest degree and whether every per-label sum is
+    exact: integer weights whose row sums reach 2^31 are not (32-bit sums could
+    overflow), and borrowed integer weights (kept as fp32) are not once a row
+    sum reaches 2^24.  A row whose degree x largest weight reaches 2^24 but
+    whose sum does not stays exact."""
+    import torch
+    # star 0 - {1, 2}, plus an edge 3 - 4
+    off = np.array([0, 2, 3, 4, 5, 6], np.int64)
+    idx = np.array([1, 2, 0, 0, 4, 3], np.int32)
+    cases = [
+        (np.array([1.5e9, 1.5e9, 1.5e9, 1.5e9, 1, 1], np.float32), 0, 0),     # row 0 sums to 3e9 >= 2^31
+        (np.array([1.5e9, 1, 1.5e9, 1, 1, 1], np.float32), 0, 1),             # largest row sum 1.5e9 + 1
+        (np.array([2 ** 23, 2 ** 23, 2 ** 23, 2 ** 23, 1, 1], np.float32), True, 0),   # 2^24
+        (np.array([2 ** 23, 2 ** 23 - 1, 2 ** 23, 2 ** 23 - 1, 1, 1], np.float32), True, 1),
+    ]
+    for w, borrow, exact in cases:
+        if borrow:
+            t_off, t_idx, t_w = (torch.from_numpy(a).cuda() for a in (off, idx, w))
+            h = lpa.lpa_graph_create(5, 6, t_off, t_idx, t_w, lpa.LPA_DEVICE_PTRS | lpa.LPA_BORROW)
+        else:
+            h = lpa.lpa_graph_create(5, 6, off, idx, w)
+        p = lpa.lpa_graph_props_get(h)
+        lpa.lpa_graph_destroy(h)
+        assert p["exact"] == exact, (w, borrow)
+        assert p["max_degree"] == 2
+    g = L.rmat(14, 16, seed=5)
+    h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w)
+    assert lpa.lpa_graph_props_get(h)["max_degree"] == int(np.diff(g.off).max())
+    lpa.lpa_graph_destroy(h)
+
+
+def test_pool_reuse_and_release(lpa):
+    """Graph memory comes from the library's pool: graphs created after others
+    were destroyed (reusing their pages), and after the cache was released,
+    still give the oracle's labels."""
+    graphs = [L.planted_partition(n=3000, blocks=6, seed=21), L.road_grid(70, 50, seed=2),
+              L.planted_partition(n=3000, blocks=6, seed=21)]
+    for k, g in enumerate(graphs):
+        assert_sync_parity(lpa, g)
+        if k == 1:
+            lpa.lpa_release_cached_memory()
+    lpa.lpa_release_cached_memory()
+
+
 def check_async(lpa, g, tau=0.05, iters=20, cfg=None, q_slack=0.02):
     """Async run held to: labels in range and inside the vertex's component;
     GPU modularity equal to the fp64 oracle's on the same labels (1e-6 rel);
