@@ -112,42 +112,68 @@ __device__ __forceinline__ int bin_of(const DevState& s, int64_t d) {
     return d <= s.small_max ? 0 : d <= s.warp_max ? 1 : d <= s.mid_max ? 2 : d <= s.large_max ? 3 : 4;
 }
 
-// Block-wide ordered append of up to kVertsPerThread vertices per thread into
-// the three bin regions of `list`; `cursor[b]` is the running length of bin b
-// (device counter when `atomic`, otherwise a block-private running offset kept
-// by the caller in shared memory).  Entries keep ascending thread order.  All
-// threads of the block must call.
+// A thread's chunk of kVertsPerThread consecutive vertices v0 + q, each
+// either left out or given a degree bin: the bins packed 4 bits per vertex
+// (0 = left out, else bin + 1) and the entries (degree sum) per bin.  Kept this
+// compact so the compaction kernels stay at a few dozen registers.
+struct Chunk {
+    int64_t v0;
+    uint64_t code;
+    unsigned long long ent[kBins];
+};
+
+__device__ __forceinline__ void chunk_reset(Chunk& c, int64_t v0) {
+    c.v0 = v0;
+    c.code = 0;
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) c.ent[b] = 0;
+}
+
+__device__ __forceinline__ void chunk_add(Chunk& c, int q, int bin, int64_t d) {
+    c.code |= (uint64_t)(bin + 1) << (4 * q);
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) c.ent[b] += bin == b ? (unsigned long long)d : 0ull;
+}
+
+// Number of 4-bit fields of `code` equal to `val` (exact: no borrow between fields).
+__device__ __forceinline__ unsigned nibbles_equal(uint64_t code, unsigned val) {
+    const uint64_t x = code ^ (0x1111111111111111ull * val);
+    const uint64_t lo = 0x7777777777777777ull;
+    return (unsigned)__popcll(~(((x & lo) + lo) | x | lo));
+}
+
+// Bin of vertex v0 + q of the chunk, or -1.
+__device__ __forceinline__ int chunk_bin(const Chunk& c, int q) { return (int)((c.code >> (4 * q)) & 0xf) - 1; }
+
+// Block-wide ordered append of every thread's chunk into the kBins bin
+// regions of `list`; `cursor[b]` is the running length of bin b (device
+// counter when ATOMIC, otherwise a running offset owned by the caller).
+// Entries keep ascending thread order.  The block's ids are grouped by bin in
+// shared memory first, so each bin's run is written with coalesced stores.
+// All threads of the block must call.
 template <bool ATOMIC>
 __device__ __forceinline__ void block_append(const int64_t (&base)[kBins], int32_t* list, unsigned* cursor,
-                                             unsigned long long* entries, const int32_t (&vid)[kVertsPerThread],
-                                             const int8_t (&bin)[kVertsPerThread],
-                                             const int64_t (&deg)[kVertsPerThread]) {
+                                             unsigned long long* entries, const Chunk& c) {
     __shared__ unsigned wcnt[kBins][32];
     __shared__ unsigned long long went[kBins][32];
-    __shared__ unsigned bbase[kBins];
+    __shared__ unsigned bbase[kBins], brun[kBins], boff[kBins];
+    __shared__ int32_t stage[kFrontThreads * kVertsPerThread];   // the block's ids, grouped by bin
     const unsigned lane = lane_id();
     const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    unsigned cnt[kBins], excl[kBins];
+    unsigned excl[kBins];
 #pragma unroll
     for (int b = 0; b < kBins; ++b) {
-        unsigned c = 0;
-        unsigned long long ent = 0;
-#pragma unroll
-        for (int q = 0; q < kVertsPerThread; ++q)
-            if (bin[q] == b) {
-                ++c;
-                ent += (unsigned long long)deg[q];
-            }
-        unsigned incl = c;
+        const unsigned cnt = nibbles_equal(c.code, (unsigned)b + 1u);
+        unsigned incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned y = __shfl_up_sync(kFull, incl, o);
             if ((int)lane >= o) incl += y;
         }
+        unsigned long long ent = c.ent[b];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) ent += __shfl_xor_sync(kFull, ent, o);
-        cnt[b] = c;
-        excl[b] = incl - c;
+        excl[b] = incl - cnt;
         if (lane == 31) {
             wcnt[b][w] = incl;
             went[b][w] = ent;
@@ -164,6 +190,7 @@ __device__ __forceinline__ void block_append(const int64_t (&base)[kBins], int32
             run += x;
             ent += went[b][q];
         }
+        brun[b] = run;
         if (ATOMIC) {
             bbase[b] = run ? atomicAdd(&cursor[b], run) : 0u;
             if (run) atomicAdd(&entries[b], ent);
@@ -174,41 +201,62 @@ __device__ __forceinline__ void block_append(const int64_t (&base)[kBins], int32
         }
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned o = 0;
+#pragma unroll
+        for (int b = 0; b < kBins; ++b) {
+            boff[b] = o;
+            o += brun[b];
+        }
+    }
+    __syncthreads();
+    if (c.code) {
+        unsigned pos[kBins];
+#pragma unroll
+        for (int b = 0; b < kBins; ++b) pos[b] = boff[b] + wcnt[b][w] + excl[b];
+#pragma unroll
+        for (int q = 0; q < kVertsPerThread; ++q) {
+            const int b = chunk_bin(c, q);
+#pragma unroll
+            for (int k = 0; k < kBins; ++k)
+                if (b == k) stage[pos[k]++] = (int32_t)(c.v0 + q);
+        }
+    }
+    __syncthreads();
+    // coalesced copy of each bin's run to its place in the list
 #pragma unroll
     for (int b = 0; b < kBins; ++b) {
-        unsigned pos = bbase[b] + wcnt[b][w] + excl[b];
-        if (cnt[b] == 0) continue;
-        int32_t* out = list + base[b];
-#pragma unroll
-        for (int q = 0; q < kVertsPerThread; ++q)
-            if (bin[q] == b) out[pos++] = vid[q];
+        int32_t* out = list + base[b] + bbase[b];
+        const int32_t* in = stage + boff[b];
+        for (unsigned i = threadIdx.x; i < brun[b]; i += blockDim.x) out[i] = in[i];
     }
     __syncthreads();
 }
 
-// Loads the flags of vertices [v0, v0 + kVertsPerThread) (zeros past N) and
-// clears them when `clear`.  Returns true if any is set.
-__device__ __forceinline__ bool load_flags(uint8_t* flags, int64_t N, int64_t v0, bool clear,
-                                           uint8_t (&f)[kVertsPerThread]) {
-    bool anyf = false;
+// Loads the flags of vertices [v0, v0 + kVertsPerThread) (zeros past N), one
+// byte per vertex in `raw`, and clears them when `clear`.  Returns true if any
+// is set.
+__device__ __forceinline__ bool load_flags(uint8_t* flags, int64_t N, int64_t v0, bool clear, uint4& raw) {
     if (v0 + kVertsPerThread <= N) {
-        uint4 raw = *reinterpret_cast<const uint4*>(flags + v0);
-        const uint8_t* pb = reinterpret_cast<const uint8_t*>(&raw);
-#pragma unroll
-        for (int q = 0; q < kVertsPerThread; ++q) f[q] = pb[q];
-        anyf = (raw.x | raw.y | raw.z | raw.w) != 0;
+        raw = *reinterpret_cast<const uint4*>(flags + v0);
+        const bool anyf = (raw.x | raw.y | raw.z | raw.w) != 0;
         if (anyf && clear) *reinterpret_cast<uint4*>(flags + v0) = make_uint4(0, 0, 0, 0);
-    } else {
-#pragma unroll
-        for (int q = 0; q < kVertsPerThread; ++q) {
-            f[q] = (v0 + q < N) ? flags[v0 + q] : 0;
-            anyf |= f[q] != 0;
-        }
-        if (anyf && clear)
-            for (int q = 0; q < kVertsPerThread; ++q)
-                if (v0 + q < N) flags[v0 + q] = 0;
+        return anyf;
     }
+    uint32_t wd[4] = {0, 0, 0, 0};
+    for (int q = 0; q < kVertsPerThread; ++q)
+        if (v0 + q < N) wd[q >> 2] |= (uint32_t)flags[v0 + q] << (8 * (q & 3));
+    raw = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    const bool anyf = (raw.x | raw.y | raw.z | raw.w) != 0;
+    if (anyf && clear)
+        for (int q = 0; q < kVertsPerThread; ++q)
+            if (v0 + q < N) flags[v0 + q] = 0;
     return anyf;
+}
+
+__device__ __forceinline__ bool flag_at(const uint4& raw, int q) {
+    const uint32_t wd = q < 4 ? raw.x : q < 8 ? raw.y : q < 12 ? raw.z : raw.w;
+    return ((wd >> (8 * (q & 3))) & 0xffu) != 0;
 }
 
 // ------------------------------------------------------------ static lists --
@@ -217,20 +265,14 @@ __device__ __forceinline__ bool load_flags(uint8_t* flags, int64_t N, int64_t v0
 // per-block bases computed on the host.
 constexpr int kStaticChunk = kFrontThreads * kVertsPerThread;
 
-__device__ __forceinline__ void static_chunk(const DevState& s, int64_t v0, int32_t (&vid)[kVertsPerThread],
-                                             int8_t (&bin)[kVertsPerThread], int64_t (&deg)[kVertsPerThread]) {
+__device__ __forceinline__ void static_chunk(const DevState& s, int64_t v0, Chunk& c) {
+    chunk_reset(c, v0);
 #pragma unroll
     for (int q = 0; q < kVertsPerThread; ++q) {
         const int64_t v = v0 + q;
-        vid[q] = (int32_t)v;
-        bin[q] = -1;
-        deg[q] = 0;
         if (v < s.N) {
             const int64_t d = s.off_end[v] - s.off[v];
-            if (d > 0) {
-                deg[q] = d;
-                bin[q] = (int8_t)bin_of(s, d);
-            }
+            if (d > 0) chunk_add(c, q, bin_of(s, d), d);
         }
     }
 }
@@ -238,36 +280,38 @@ __device__ __forceinline__ void static_chunk(const DevState& s, int64_t v0, int3
 __global__ void __launch_bounds__(kFrontThreads) k_static_count(DevState s, unsigned* counts,
                                                                  unsigned long long* ents) {
     const int64_t v0 = (int64_t)blockIdx.x * kStaticChunk + (int64_t)threadIdx.x * kVertsPerThread;
-    int32_t vid[kVertsPerThread];
-    int8_t bin[kVertsPerThread];
-    int64_t deg[kVertsPerThread];
-    static_chunk(s, v0, vid, bin, deg);
-    __shared__ unsigned c[kBins];
-    __shared__ unsigned long long e[kBins];
+    Chunk c;
+    static_chunk(s, v0, c);
+    __shared__ unsigned sc[kBins];
+    __shared__ unsigned long long se[kBins];
     if (threadIdx.x < kBins) {
-        c[threadIdx.x] = 0;
-        e[threadIdx.x] = 0;
+        sc[threadIdx.x] = 0;
+        se[threadIdx.x] = 0;
     }
     __syncthreads();
+    // one shared atomic per warp and bin
+    const unsigned lane = lane_id();
 #pragma unroll
-    for (int q = 0; q < kVertsPerThread; ++q)
-        if (bin[q] >= 0) {
-            atomicAdd(&c[bin[q]], 1u);
-            atomicAdd(&e[bin[q]], (unsigned long long)deg[q]);
+    for (int b = 0; b < kBins; ++b) {
+        const unsigned cw = __reduce_add_sync(kFull, nibbles_equal(c.code, (unsigned)b + 1u));
+        unsigned long long ew = c.ent[b];
+        for (int o = 16; o > 0; o >>= 1) ew += __shfl_xor_sync(kFull, ew, o);
+        if (lane == 0 && cw) {
+            atomicAdd(&sc[b], cw);
+            atomicAdd(&se[b], ew);
         }
+    }
     __syncthreads();
     if (threadIdx.x < kBins) {
-        counts[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = c[threadIdx.x];
-        ents[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = e[threadIdx.x];
+        counts[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = sc[threadIdx.x];
+        ents[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = se[threadIdx.x];
     }
 }
 
 __global__ void __launch_bounds__(kFrontThreads) k_static_scatter(DevState s, const unsigned* block_base) {
     const int64_t v0 = (int64_t)blockIdx.x * kStaticChunk + (int64_t)threadIdx.x * kVertsPerThread;
-    int32_t vid[kVertsPerThread];
-    int8_t bin[kVertsPerThread];
-    int64_t deg[kVertsPerThread];
-    static_chunk(s, v0, vid, bin, deg);
+    Chunk c;
+    static_chunk(s, v0, c);
     __shared__ unsigned cursor[kBins];
     __shared__ unsigned long long ent[kBins];
     if (threadIdx.x < kBins) {
@@ -275,7 +319,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_static_scatter(DevState s, co
         ent[threadIdx.x] = 0;
     }
     __syncthreads();
-    block_append<false>(s.bin_base, s.slist, cursor, ent, vid, bin, deg);
+    block_append<false>(s.bin_base, s.slist, cursor, ent, c);
 }
 
 int64_t static_scratch_blocks(int64_t N) { return (N + kStaticChunk - 1) / kStaticChunk; }
@@ -482,33 +526,22 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
         for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nchunks; base += gstride) {
             const int64_t ch = base + threadIdx.x;
             const int64_t v0 = ch * kVertsPerThread;
-            uint8_t f[kVertsPerThread];
+            uint4 raw = make_uint4(0, 0, 0, 0);
             bool anyf = false;
-            if (ch < nchunks) {
-                anyf = load_flags(s.flags, s.N, v0, true, f);
-            } else {
+            if (ch < nchunks) anyf = load_flags(s.flags, s.N, v0, true, raw);
+            Chunk c;
+            chunk_reset(c, v0);
+            if (anyf) {
 #pragma unroll
-                for (int q = 0; q < kVertsPerThread; ++q) f[q] = 0;
-            }
-            int32_t vid[kVertsPerThread];
-            int8_t bin[kVertsPerThread];
-            int64_t deg[kVertsPerThread];
-#pragma unroll
-            for (int q = 0; q < kVertsPerThread; ++q) {
-                vid[q] = (int32_t)(v0 + q);
-                bin[q] = -1;
-                deg[q] = 0;
-                if (f[q]) {
-                    const int64_t d = s.off_end[v0 + q] - s.off[v0 + q];
-                    if (d > 0) {
-                        deg[q] = d;
-                        bin[q] = (int8_t)bin_of(s, d);
+                for (int q = 0; q < kVertsPerThread; ++q) {
+                    if (flag_at(raw, q)) {
+                        const int64_t d = s.off_end[v0 + q] - s.off[v0 + q];
+                        if (d > 0) chunk_add(c, q, bin_of(s, d), d);
                     }
                 }
             }
             if (__syncthreads_or(anyf))
-                block_append<true>(s.bin_base, s.flist, s.ctrl->bin_cnt[wr], s.ctrl->bin_entries[wr], vid, bin,
-                                   deg);
+                block_append<true>(s.bin_base, s.flist, s.ctrl->bin_cnt[wr], s.ctrl->bin_entries[wr], c);
         }
     }
 

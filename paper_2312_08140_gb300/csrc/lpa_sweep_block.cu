@@ -24,6 +24,7 @@
 namespace lpa {
 
 constexpr int kSharedProbes = 16;
+constexpr int kUnroll = 4;          // chunks of 32 entries in flight per warp
 
 // Block-wide argmax of one (key, label) candidate per thread; returns the
 // winner (or -1) to every thread.  Uses red_key/red_lab (32 entries) and
@@ -80,7 +81,10 @@ __device__ __forceinline__ void mark_neighbours(const DevState& s, int32_t v, in
     }
 }
 
-template <bool ASYNC, int WK, bool BATCH>
+// U: chunks in flight per warp (4 for the last bin, whose rows span many
+// chunks per warp; 1 for the middle bins, where the SM's 64 warps already
+// overlap the few chunks of each row).
+template <bool ASYNC, int WK, bool BATCH, int U>
 __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -123,29 +127,47 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
         const int log_full = ceil_log2((unsigned)(2 * d));
         const bool fits = log_full <= log_S;
         const int log_s = fits ? log_full : log_S;
-        for (int64_t e0 = st + (int64_t)wib * 32; e0 < en; e0 += (int64_t)nw * 32) {
+        // Each warp takes U chunks per step (chunk c = wib + (u + U*it)*nw):
+        // their index loads, then their label gathers and weights, are issued
+        // together so the latencies overlap; then the chunks are aggregated.
+        const int64_t step = (int64_t)nw * 32;
+        for (int64_t e0 = st + (int64_t)wib * 32; e0 < en; e0 += step * U) {
             if (!fits && *(volatile int*)&overflow) break;     // warp-uniform
-            const int64_t e = e0 + lane;
-            const bool in = e < en;
-            const int32_t j = in ? load_index_keep(s.idx, e) : v;
-            const bool ok = in && j != v;
-            const int32_t lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
-            T w = ok ? load_weight<WK>(s.w, e) : (T)0;
-            bool lead = ok;
-            if constexpr (WK != W_F32) {
-                const unsigned peers = __match_any_sync(kFull, lab);
-                if constexpr (WK == W_UNIT) {
-                    w = (T)__popc(peers);
-                } else {
-                    w = __reduce_add_sync(peers, w);
-                }
-                lead = ok && lane == (unsigned)(__ffs(peers) - 1);
+            int32_t jj[U], lab[U];
+            T ww[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t e = e0 + u * step + lane;
+                jj[u] = e < en ? load_index_keep(s.idx, e) : v;
             }
-            if (lead) {
-                if (fits) {
-                    if (!table_add<T>(keys, vals, log_s, lab, w)) atomicExch(&s.ctrl->error, 3);
-                } else if (!table_add_bounded<T>(keys, vals, log_s, lab, w, kSharedProbes)) {
-                    overflow = 1;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t e = e0 + u * step + lane;
+                const bool ok = jj[u] != v;                      // also false past the row end
+                lab[u] = ok ? load_label<ASYNC>(L.C, jj[u]) : kEmptyKey;
+                ww[u] = ok ? load_weight<WK>(s.w, e) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (e0 + u * step >= en) break;                 // warp-uniform
+                const bool ok = jj[u] != v;
+                T w = ww[u];
+                bool lead = ok;
+                if constexpr (WK != W_F32) {
+                    const unsigned peers = __match_any_sync(kFull, lab[u]);
+                    if constexpr (WK == W_UNIT) {
+                        w = (T)__popc(peers);
+                    } else {
+                        w = __reduce_add_sync(peers, w);
+                    }
+                    lead = ok && lane == (unsigned)(__ffs(peers) - 1);
+                }
+                if (lead) {
+                    if (fits) {
+                        if (!table_add<T>(keys, vals, log_s, lab[u], w)) atomicExch(&s.ctrl->error, 3);
+                    } else if (!table_add_bounded<T>(keys, vals, log_s, lab[u], w, kSharedProbes)) {
+                        overflow = 1;
+                    }
                 }
             }
         }
@@ -243,26 +265,41 @@ __global__ void k_sweep_parts(DevState s, int flag_neighbours) {
         const int32_t v = o.v;
         const int64_t st = o.st, en = o.st + o.d;
         const uint32_t parts = o.parts, p = item - o.item_base;
-        for (int64_t e0 = st + (int64_t)wib * 32; e0 < en; e0 += (int64_t)nw * 32) {
-            const int64_t e = e0 + lane;
-            const bool in = e < en;
-            const int32_t j = in ? load_index(s.idx, e) : v;
-            bool ok = in && j != v;
-            int32_t lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
-            ok = ok && part_of(lab, parts) == p;
-            if (!ok) lab = kEmptyKey;
-            T w = ok ? load_weight<WK>(s.w, e) : (T)0;
-            bool lead = ok;
-            if constexpr (WK != W_F32) {
-                const unsigned peers = __match_any_sync(kFull, lab);
-                if constexpr (WK == W_UNIT) {
-                    w = (T)__popc(peers);
-                } else {
-                    w = __reduce_add_sync(peers, w);
-                }
-                lead = ok && lane == (unsigned)(__ffs(peers) - 1);
+        const int64_t step = (int64_t)nw * 32;
+        for (int64_t e0 = st + (int64_t)wib * 32; e0 < en; e0 += step * kUnroll) {
+            int32_t jj[kUnroll], lab[kUnroll];
+            T ww[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int64_t e = e0 + u * step + lane;
+                jj[u] = e < en ? load_index(s.idx, e) : v;
             }
-            if (lead && !table_add<T>(keys, vals, log_S, lab, w)) atomicExch(&s.ctrl->error, 4);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int64_t e = e0 + u * step + lane;
+                bool ok = jj[u] != v;
+                int32_t l = ok ? load_label<ASYNC>(L.C, jj[u]) : kEmptyKey;
+                ok = ok && part_of(l, parts) == p;
+                lab[u] = ok ? l : kEmptyKey;
+                ww[u] = ok ? load_weight<WK>(s.w, e) : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                if (e0 + u * step >= en) break;                 // warp-uniform
+                const bool ok = lab[u] != kEmptyKey;
+                T w = ww[u];
+                bool lead = ok;
+                if constexpr (WK != W_F32) {
+                    const unsigned peers = __match_any_sync(kFull, lab[u]);
+                    if constexpr (WK == W_UNIT) {
+                        w = (T)__popc(peers);
+                    } else {
+                        w = __reduce_add_sync(peers, w);
+                    }
+                    lead = ok && lane == (unsigned)(__ffs(peers) - 1);
+                }
+                if (lead && !table_add<T>(keys, vals, log_S, lab[u], w)) atomicExch(&s.ctrl->error, 4);
+            }
         }
         __syncthreads();
         uint32_t key;
@@ -322,7 +359,7 @@ int block_grid_for(const DevState& s, int bin, int sms) {
 template <bool ASYNC, int WK, bool BATCH>
 static cudaError_t launch_block_t(const DevState& s, int bin, int flag, int blocks, cudaStream_t st) {
     const size_t smem = (size_t)s.block_slots[bin - 2] * 8;
-    auto kern = k_sweep_block<ASYNC, WK, BATCH>;
+    auto kern = bin == kBins - 1 ? k_sweep_block<ASYNC, WK, BATCH, kUnroll> : k_sweep_block<ASYNC, WK, BATCH, 1>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     kern<<<blocks, kBlockThreads[bin - 2], smem, st>>>(s, bin, flag);

@@ -21,6 +21,7 @@ namespace lpa {
 
 constexpr int kWarpThreads = 256;
 constexpr int kWarpsPerBlock = kWarpThreads / 32;
+constexpr int kWarpUnroll = 3;      // chunks of 32 entries in flight per warp beyond the first
 
 // Combined weight of the lanes in `peers` (all hold the same label).
 template <int WK>
@@ -45,7 +46,7 @@ __device__ __forceinline__ typename Acc<WK>::T group_sum(unsigned peers, typenam
 }
 
 template <bool ASYNC, int WK, bool BATCH>
-__global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int flag_neighbours) {
+__global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wslots = s.warp_slots;
@@ -87,12 +88,27 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
             }
         }
         const unsigned nv = min(B, cnt - base);
-        // indices of the first chunk of the next vertex are fetched one vertex ahead
-        int32_t jpre = kEmptyKey;
-        {
-            const int64_t st0 = __shfl_sync(kFull, stl, 0), en0 = __shfl_sync(kFull, enl, 0);
-            if (__shfl_sync(kFull, actl, 0) && st0 + lane < en0) jpre = load_index_keep(s.idx, st0 + lane);
-        }
+        // Two-stage pipeline over the batch: while vertex i is aggregated, the
+        // first-chunk labels and weights of vertex i+1 and the first-chunk
+        // indices of vertex i+2 are in flight.
+        auto first_index = [&](unsigned i) -> int32_t {
+            const unsigned q = i & 31u;
+            const int64_t sq = __shfl_sync(kFull, stl, q), eq = __shfl_sync(kFull, enl, q);
+            const int aq = __shfl_sync(kFull, actl, q) && (i < nv);
+            return (aq && sq + lane < eq) ? load_index_keep(s.idx, sq + lane) : kEmptyKey;
+        };
+        auto first_label = [&](unsigned i, int32_t j, int32_t& lab, T& w) {
+            const unsigned q = i & 31u;
+            const int32_t vq = __shfl_sync(kFull, vl, q);
+            const int64_t sq = __shfl_sync(kFull, stl, q);
+            const bool ok = j != kEmptyKey && j != vq;
+            lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
+            w = ok ? load_weight<WK>(s.w, sq + lane) : (T)0;
+        };
+        int32_t j_cur = first_index(0), j_nxt = first_index(1);
+        int32_t lab_cur;
+        T w_cur;
+        first_label(0, j_cur, lab_cur, w_cur);
         for (unsigned i = 0; i < nv; ++i) {
             const int32_t v = __shfl_sync(kFull, vl, i);
             const int64_t st = __shfl_sync(kFull, stl, i);
@@ -100,33 +116,25 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
             const int32_t own = __shfl_sync(kFull, ownl, i);
             const int act = __shfl_sync(kFull, actl, i);
             const int d = (int)(en - st);
-            int32_t j = jpre;
-            {
-                const unsigned i2 = (i + 1) & 31u;
-                const int64_t st2 = __shfl_sync(kFull, stl, i2), en2 = __shfl_sync(kFull, enl, i2);
-                const int a2 = __shfl_sync(kFull, actl, i2) && (i + 1 < nv);
-                jpre = (a2 && st2 + lane < en2) ? load_index_keep(s.idx, st2 + lane) : kEmptyKey;
-            }
+            const int32_t j = j_cur;
+            const int32_t j_nn = first_index(i + 2);
+            int32_t lab_nxt;
+            T w_nxt;
+            first_label(i + 1, j_nxt, lab_nxt, w_nxt);
             uint32_t key = 0;
             int32_t cand = 0;
             if (act && d <= 32) {
-                const bool ok = (int)lane < d && j != v;
-                const int32_t lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
-                const T w = ok ? load_weight<WK>(s.w, st + lane) : (T)0;
-                const unsigned peers = __match_any_sync(kFull, lab);
-                const T sum = group_sum<WK>(peers, w, lab, ok);
+                const bool ok = lab_cur != kEmptyKey;
+                const unsigned peers = __match_any_sync(kFull, lab_cur);
+                const T sum = group_sum<WK>(peers, w_cur, lab_cur, ok);
                 if (ok && lane == (unsigned)(__ffs(peers) - 1)) {
                     key = sum_key(sum);
-                    cand = lab;
+                    cand = lab_cur;
                 }
             } else if (act) {
                 const int log_slots = ceil_log2(2u * (unsigned)d);
-                for (int64_t e0 = st; e0 < en; e0 += 32) {
-                    const int64_t e = e0 + lane;
-                    const int32_t jn = (e + 32 < en) ? load_index_keep(s.idx, e + 32) : kEmptyKey;
-                    const bool ok = e < en && j != v;
-                    const int32_t lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
-                    const T w = ok ? load_weight<WK>(s.w, e) : (T)0;
+                auto add_chunk = [&](int32_t lab, T w) {
+                    const bool ok = lab != kEmptyKey;
                     if constexpr (WK == W_F32) {
                         if (ok && !table_add<T>(keys, vals, log_slots, lab, w)) atomicExch(&s.ctrl->error, 2);
                     } else {
@@ -135,7 +143,27 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
                         if (ok && lane == (unsigned)(__ffs(peers) - 1) && !table_add<T>(keys, vals, log_slots, lab, sum))
                             atomicExch(&s.ctrl->error, 2);
                     }
-                    j = jn;
+                };
+                add_chunk(lab_cur, w_cur);                 // first chunk, prefetched
+                for (int64_t e0 = st + 32; e0 < en; e0 += 32 * kWarpUnroll) {
+                    int32_t jj[kWarpUnroll], ll[kWarpUnroll];
+                    T wq[kWarpUnroll];
+#pragma unroll
+                    for (int u = 0; u < kWarpUnroll; ++u) {
+                        const int64_t e = e0 + 32 * u + lane;
+                        jj[u] = e < en ? load_index_keep(s.idx, e) : v;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kWarpUnroll; ++u) {
+                        const bool ok = jj[u] != v;
+                        ll[u] = ok ? load_label<ASYNC>(L.C, jj[u]) : kEmptyKey;
+                        wq[u] = ok ? load_weight<WK>(s.w, e0 + 32 * u + lane) : (T)0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kWarpUnroll; ++u) {
+                        if (e0 + 32 * u >= en) break;      // warp-uniform
+                        add_chunk(ll[u], wq[u]);
+                    }
                 }
                 __syncwarp();
                 bool any = false;
@@ -161,6 +189,10 @@ __global__ void __launch_bounds__(kWarpThreads, 6) k_sweep_warp(DevState s, int 
                     cand = best;
                 }
             }
+            j_cur = j_nxt;
+            j_nxt = j_nn;
+            lab_cur = lab_nxt;
+            w_cur = w_nxt;
             const int32_t best = warp_argmax(key, cand);
             const bool changed = act && best >= 0 && best != own;   // warp-uniform
             if (lane == 0) record_label<ASYNC>(L, bv.chg + base + i, v, own, best, changed);
