@@ -355,8 +355,12 @@ cudaError_t launch_bin(Engine& E, int mode, int bin, cudaStream_t st) {
     return launch_sweep_block(E.s, mode, bin, E.block_grid[bin - 2], st);
 }
 
+// A sweep's frontier is a subset of the static bin lists (same thresholds,
+// vertices with no entries never join), so a bin that is statically empty is
+// not launched at all.
 cudaError_t enqueue_pass(Engine& E, int mode, cudaStream_t st) {
     for (int b = 0; b < kBins; ++b) {
+        if (E.s.bin_static[b] == 0) continue;
         cudaError_t err = launch_bin(E, mode, b, st);
         if (err != cudaSuccess) return err;
     }
@@ -542,7 +546,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
         for (int p = 0; p < passes; ++p) {
             for (int b = 0; b < kBins; ++b) {
                 LPA_P(cudaEventRecord(ev[b], st));
-                LPA_P(launch_bin(E, mode, b, st));
+                if (E.s.bin_static[b]) LPA_P(launch_bin(E, mode, b, st));
             }
             LPA_P(cudaEventRecord(ev[kBins], st));
             LPA_P(launch_finish(E.s, mode, p + 1 < passes ? 1 : 0, none, 0, st, E.sms));

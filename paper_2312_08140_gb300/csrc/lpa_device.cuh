@@ -52,6 +52,17 @@ __device__ __forceinline__ int32_t load_index_keep(const int32_t* idx, int64_t e
     return __ldg(idx + e);
 }
 
+// Marks vertex j unprocessed (Section 4.1.4), for the rows of the warp and
+// block kernels: their neighbours are marked by many rows each (hubs by
+// thousands), so the flag is read first and the store issued only while it is
+// still 0.  A flag only goes 0 -> 1 during a pass (the next compaction clears
+// it), so a stale 0 costs one redundant store, never a lost mark.  The
+// low-degree kernels store unconditionally: there the load would sit on each
+// thread's sequential path and save few stores.
+__device__ __forceinline__ void mark_unprocessed(uint8_t* flags, int32_t j) {
+    if (__ldcg(flags + j) == 0) flags[j] = 1;
+}
+
 // Whether this pass writes neighbour marks (Section 4.1.4).
 __device__ __forceinline__ bool marks_on(const DevState& s, int flag_neighbours) {
     return flag_neighbours && !s.ctrl->skip_marks;

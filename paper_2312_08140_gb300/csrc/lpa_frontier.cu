@@ -431,7 +431,11 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         }
         c->total_sweeps += 1;
         c->total_scanned += scn;
-        c->total_sweep_launches += mode == MODE_ASYNC ? 2 * (kBins + 2) : kBins + 2;
+        // per pass: one launch per statically non-empty bin (the last bin adds
+        // the partitioned rescan), then the finish kernel
+        int per_pass = 1;
+        for (int b = 0; b < kBins; ++b) per_pass += s.bin_static[b] ? (b == kBins - 1 ? 2 : 1) : 0;
+        c->total_sweep_launches += mode == MODE_ASYNC ? 2 * per_pass : per_pass;
         for (int b = 0; b < kBins; ++b) {
             c->bin_changed[b] = 0;
             c->bin_changed_entries[b] = 0;

@@ -14,11 +14,12 @@
 // kLargeSlots / 2 may carry more distinct labels than it holds; their inserts
 // probe a bounded number of slots and, if one fails, the block stops and
 // appends the row to an overflow list.  A second kernel (k_sweep_parts) then
-// rescans each overflowed row with `parts` blocks: block p aggregates only the
-// labels whose hash lands in partition p (about d / parts distinct labels, a
-// quarter of the table), folds its winner into a 64-bit atomicMax of
-// (sum << 32 | ~label) -- larger sum first, then smaller label -- and the block
-// that completes the row applies the result.  No block waits on another.
+// rescans each overflowed row with parts = ceil(2d / kLargeSlots) blocks:
+// block p aggregates only the labels whose hash lands in partition p (about
+// d / parts distinct labels at most, half of the table, so an insert always
+// finds a slot), folds its winner into a 64-bit atomicMax of
+// (sum << 32 | ~label) -- larger sum first, then smaller label -- and the
+// block that completes the row applies the result.  No block waits on another.
 #include "lpa_device.cuh"
 
 namespace lpa {
@@ -77,7 +78,7 @@ __device__ __forceinline__ void scan_table(int32_t* keys, T* vals, int slots, ui
 __device__ __forceinline__ void mark_neighbours(const DevState& s, int32_t v, int64_t st, int64_t en) {
     for (int64_t e = st + threadIdx.x; e < en; e += blockDim.x) {
         const int32_t j = s.idx[e];
-        if (j != v) s.flags[j] = 1;
+        if (j != v) mark_unprocessed(s.flags, j);
     }
 }
 
@@ -180,7 +181,7 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
         if (ovf) {
             // hand the row to the partitioned rescan
             if (threadIdx.x == 0) {
-                const uint32_t parts = (uint32_t)((4 * d + S - 1) / S);
+                const uint32_t parts = (uint32_t)((2 * d + S - 1) / S);
                 const unsigned long long old =
                     atomicAdd(&s.ctrl->ovf_packed, (1ull << 40) | (unsigned long long)parts);
                 Overflow& o = s.ovf[old >> 40];

@@ -22,6 +22,7 @@ namespace lpa {
 constexpr int kWarpThreads = 256;
 constexpr int kWarpsPerBlock = kWarpThreads / 32;
 constexpr int kWarpUnroll = 3;      // chunks of 32 entries in flight per warp beyond the first
+constexpr unsigned kAsyncMinBatch = 8;
 
 // Combined weight of the lanes in `peers` (all hold the same label).
 template <int WK>
@@ -66,8 +67,12 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
     const unsigned cnt = bv.cnt;
     const unsigned nwarps = gridDim.x * kWarpsPerBlock;
     // each warp takes batches of B consecutive frontier entries (B <= 32), B
-    // shrinking when the bin is too small to give every warp a full batch
+    // shrinking when the bin is too small to give every warp a full batch.  In
+    // the asynchronous mode a warp keeps at least kAsyncMinBatch consecutive
+    // vertices, visited in order, so that a small graph is not scanned all at
+    // once (which would make the pass synchronous).
     unsigned B = (cnt + nwarps - 1) / nwarps;
+    if (ASYNC && B < kAsyncMinBatch) B = kAsyncMinBatch;
     B = B < 1u ? 1u : (B > 32u ? 32u : B);
     unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned base = (blockIdx.x * kWarpsPerBlock + wib) * B; base < cnt; base += nwarps * B) {
@@ -196,14 +201,19 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
             const int32_t best = warp_argmax(key, cand);
             const bool changed = act && best >= 0 && best != own;   // warp-uniform
             if (lane == 0) record_label<ASYNC>(L, bv.chg + base + i, v, own, best, changed);
+            if constexpr (ASYNC) {
+                // the next vertex's first-chunk labels were read before this
+                // update: lanes holding v as neighbour take its new label
+                if (changed && j_cur == v) lab_cur = best;
+            }
             if (changed) {
                 if (marks) {
                     if (d <= 32) {                   // this row's indices are still in j
-                        if ((int)lane < d && j != v) s.flags[j] = 1;
+                        if ((int)lane < d && j != v) mark_unprocessed(s.flags, j);
                     } else {
                         for (int64_t e = st + lane; e < en; e += 32) {
                             const int32_t jj = s.idx[e];
-                            if (jj != v) s.flags[jj] = 1;
+                            if (jj != v) mark_unprocessed(s.flags, jj);
                         }
                     }
                 }
