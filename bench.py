@@ -490,7 +490,7 @@ def main():
     if not args.no_profile:
         agg = {}
         for g, h, o in zip(graphs, handles, outs):
-            wbytes = 0 if g.w is None else 4
+            wbytes = lpa.lpa_graph_props_get(h)["weight_bytes"]     # as the sweeps read them
             for m in MODES:
                 _, prof = lpa.lpa_run_profiled(h, m, TAU, MAX_ITERS, o, stream)
                 for b, d in kernel_bytes(prof.as_dict(), wbytes, m == "sync", 1 if m == "sync" else 2).items():

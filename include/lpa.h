@@ -97,7 +97,8 @@ typedef struct {
                               integers (or unit) and every weighted degree is < 2^31 (the
                               library's own copy, summed in 32-bit integers) or < 2^24
                               (borrowed weights, summed in fp32) */
-    int32_t reserved;
+    int32_t weight_bytes;  /* bytes per entry of the weights the sweeps read: 0 (unit), 1 (integer
+                              weights <= 255 in the library's copy), 4 (other) */
     int64_t max_degree;
     int64_t device_bytes;  /* device memory the handle holds */
     int64_t sweeps_total;  /* sweeps run on this handle since creation (all runs) */

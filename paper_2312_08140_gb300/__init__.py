@@ -60,13 +60,13 @@ class LpaRunInfo(ctypes.Structure):
 
 class LpaGraphProps(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("num_graphs", ctypes.c_int32),
-                ("weighted", ctypes.c_int32), ("exact", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("weighted", ctypes.c_int32), ("exact", ctypes.c_int32), ("weight_bytes", ctypes.c_int32),
                 ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("sweeps_total", ctypes.c_int64), ("scanned_total", ctypes.c_int64),
                 ("launches_total", ctypes.c_int64)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class LpaConfig(ctypes.Structure):

@@ -304,9 +304,28 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
         E.s.weight_kind = E.exact ? W_UNIT : W_F32;
         if (!E.exact) return fail(LPA_ERR_INVALID_GRAPH, "a vertex has degree >= 2^31");
     } else if (!borrow && vr.c[3] == 0 && vr.c[5] == 0) {
-        LPA_CUDA(launch_weights_to_u32(w_d, nnz, st, E.sms));
+        float wmax = 0.f;
+        memcpy(&wmax, &vr.max_weight_bits, sizeof(wmax));
         E.exact = true;
-        E.s.weight_kind = W_U32;
+        if (wmax <= 255.f && nnz > 0) {
+            // one byte per entry: the float copy is converted, then freed
+            unsigned char* w8 = nullptr;
+            if ((rs = dalloc_t(E, &w8, (size_t)std::max<int64_t>(nnz, 1))) != LPA_OK) return rs;
+            LPA_CUDA(launch_weights_to_u8(w_d, w8, nnz, st, E.sms));
+            LPA_CUDA(cudaStreamSynchronize(st));
+            auto it = std::find(E.owned.begin(), E.owned.end(), static_cast<void*>(w_d));
+            if (it != E.owned.end()) {
+                E.owned.erase(it);
+                std::vector<void*> old{static_cast<void*>(w_d)};
+                pool_free_all(E.device, old);
+                E.device_bytes -= nnz * (int64_t)sizeof(float);
+            }
+            w_d = reinterpret_cast<float*>(w8);
+            E.s.weight_kind = W_U8;
+        } else {
+            LPA_CUDA(launch_weights_to_u32(w_d, nnz, st, E.sms));
+            E.s.weight_kind = W_U32;
+        }
     } else {
         E.exact = vr.c[3] == 0 && vr.c[4] == 0;
         E.s.weight_kind = W_F32;
@@ -620,6 +639,7 @@ lpa_status fill_props(const Engine& E, lpa_graph_props* p) {
     p->nnz = E.s.E;
     p->num_graphs = E.s.G;
     p->weighted = E.weighted ? 1 : 0;
+    p->weight_bytes = E.s.weight_kind == W_UNIT ? 0 : E.s.weight_kind == W_U8 ? 1 : 4;
     p->exact = E.exact ? 1 : 0;
     p->max_degree = E.max_degree;
     p->device_bytes = E.device_bytes + (int64_t)std::max<size_t>(E.s.bin_static[kBins - 1], 1) * sizeof(Overflow);

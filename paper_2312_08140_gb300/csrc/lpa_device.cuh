@@ -38,6 +38,8 @@ __device__ __forceinline__ typename Acc<WK>::T load_weight(const void* w, int64_
         return 1u;
     } else if constexpr (WK == W_U32) {
         return __ldcs(static_cast<const uint32_t*>(w) + e);
+    } else if constexpr (WK == W_U8) {
+        return (uint32_t)__ldcs(static_cast<const unsigned char*>(w) + e);
     } else {
         return __ldcs(static_cast<const float*>(w) + e);
     }

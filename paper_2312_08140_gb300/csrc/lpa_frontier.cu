@@ -787,10 +787,22 @@ cudaError_t launch_weights_to_u32(float* w, int64_t E, cudaStream_t st, int sms)
     return cudaGetLastError();
 }
 
+__global__ void k_weights_to_u8(const float* w, unsigned char* out, int64_t E) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += stride)
+        out[e] = (unsigned char)w[e];
+}
+
+cudaError_t launch_weights_to_u8(const float* w, unsigned char* out, int64_t E, cudaStream_t st, int sms) {
+    k_weights_to_u8<<<sms * 8, 256, 0, st>>>(w, out, E);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ modularity --
 __device__ __forceinline__ double weight_f64(const DevState& s, int64_t e) {
     if (s.weight_kind == W_UNIT) return 1.0;
     if (s.weight_kind == W_U32) return (double)static_cast<const uint32_t*>(s.w)[e];
+    if (s.weight_kind == W_U8) return (double)static_cast<const unsigned char*>(s.w)[e];
     return (double)static_cast<const float*>(s.w)[e];
 }
 

@@ -26,7 +26,9 @@ constexpr int kLargeSlots = 8192;       // shared table of the last bin (overflo
                                         // rescanned split over label partitions)
 constexpr int32_t kEmptyKey = -1;       // free slot in label tables; labels are >= 0
 
-enum WeightKind : int { W_UNIT = 0, W_U32 = 1, W_F32 = 2 };
+// Weight storage: none (unit weights), integer weights as uint32 or, when all
+// are at most 255, as uint8 (sums are uint32 in both), or float.
+enum WeightKind : int { W_UNIT = 0, W_U32 = 1, W_F32 = 2, W_U8 = 3 };
 enum Mode : int { MODE_SYNC = 0, MODE_ASYNC = 1, MODE_SYNC_FULL = 2 };
 
 // Control block, one per engine, in device memory.
@@ -94,7 +96,7 @@ struct DevState {
     const int64_t* off;        // [N] row begins (positions in idx)
     const int64_t* off_end;    // [N] row ends (off + 1 for an ordinary CSR)
     const int32_t* idx;        // [E] global vertex ids
-    const void* w;             // [E] uint32 (W_U32), float (W_F32) or null (W_UNIT)
+    const void* w;             // [E] uint8 (W_U8), uint32 (W_U32), float (W_F32) or null (W_UNIT)
     const int32_t* gid;        // [N] graph of each vertex, null when G == 1
     const int64_t* vtx_off;    // [G+1] (batches)
     const int64_t* g_begin;    // [G] first vertex of graph g (vtx_off for batches)
@@ -177,6 +179,7 @@ cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float*
 cudaError_t launch_fill_gid(const int64_t* vtx_off, int32_t G, int64_t N, int32_t* gid,
                             cudaStream_t st, int sms);
 cudaError_t launch_weights_to_u32(float* w, int64_t E, cudaStream_t st, int sms);
+cudaError_t launch_weights_to_u8(const float* w, unsigned char* out, int64_t E, cudaStream_t st, int sms);
 
 // Modularity (Eq. 1), fp64.  Vertex range [v0, v1), labels local to v0.
 struct ModAccum {

@@ -382,6 +382,7 @@ cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int blocks,
     switch (s.weight_kind) {                                                          \
         case W_UNIT: return launch_block_t<A, W_UNIT, B>(s, bin, flag, blocks, st);   \
         case W_U32: return launch_block_t<A, W_U32, B>(s, bin, flag, blocks, st);     \
+        case W_U8: return launch_block_t<A, W_U8, B>(s, bin, flag, blocks, st);       \
         default: return launch_block_t<A, W_F32, B>(s, bin, flag, blocks, st);        \
     }
     if (async) {

@@ -251,6 +251,9 @@ cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int
         case W_U32:
             return batch ? launch_small_t<W_U32, true>(s, async, flag, sms, st)
                          : launch_small_t<W_U32, false>(s, async, flag, sms, st);
+        case W_U8:
+            return batch ? launch_small_t<W_U8, true>(s, async, flag, sms, st)
+                         : launch_small_t<W_U8, false>(s, async, flag, sms, st);
         default:
             return batch ? launch_small_t<W_F32, true>(s, async, flag, sms, st)
                          : launch_small_t<W_F32, false>(s, async, flag, sms, st);

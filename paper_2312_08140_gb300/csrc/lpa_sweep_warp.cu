@@ -30,7 +30,7 @@ __device__ __forceinline__ typename Acc<WK>::T group_sum(unsigned peers, typenam
                                                          int32_t lab, bool ok) {
     if constexpr (WK == W_UNIT) {
         return (typename Acc<WK>::T)__popc(peers);
-    } else if constexpr (WK == W_U32) {
+    } else if constexpr (WK == W_U32 || WK == W_U8) {
         return __reduce_add_sync(peers, w);
     } else {
         // fp32: every lane of a group adds the group's weights in lane order,
@@ -250,6 +250,7 @@ cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int 
     switch (s.weight_kind) {                                                 \
         case W_UNIT: return launch_warp_t<A, W_UNIT, B>(s, flag, st, sms);   \
         case W_U32: return launch_warp_t<A, W_U32, B>(s, flag, st, sms);     \
+        case W_U8: return launch_warp_t<A, W_U8, B>(s, flag, st, sms);       \
         default: return launch_warp_t<A, W_F32, B>(s, flag, st, sms);        \
     }
     if (async) {

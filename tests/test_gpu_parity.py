@@ -181,8 +181,28 @@ def test_non_integer_weights_flagged_inexact(lpa):
     lpa.lpa_graph_destroy(h)
     h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w)
     p = lpa.lpa_graph_props_get(h)
-    assert p["exact"] == 1 and p["weighted"] == 1
+    assert p["exact"] == 1 and p["weighted"] == 1 and p["weight_bytes"] == 1    # integers <= 255: one byte
     lpa.lpa_graph_destroy(h)
+
+
+def test_integer_weight_widths(lpa):
+    """Integer weights are stored in one byte when all are <= 255 and in four
+    otherwise; both give the oracle's labels exactly, as do non-integer ones."""
+    base = L.road_grid(90, 70, seed=9)
+    rng = np.random.default_rng(4)
+    # symmetric weights: the same value on (i, j) and (j, i)
+    src = np.repeat(np.arange(base.n), np.diff(base.off))
+    key = np.minimum(src, base.idx).astype(np.int64) * base.n + np.maximum(src, base.idx)
+    for wmax, width in ((255, 1), (256, 4), (100000, 4)):
+        vals = rng.integers(1, wmax + 1, size=key.size)
+        _, inv = np.unique(key, return_inverse=True)
+        w = vals[inv].astype(np.float32)
+        w[inv == inv[np.argmax(vals[inv])]] = wmax             # the largest weight occurs
+        g = L.Graph(base.off, base.idx, w, {})
+        h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w)
+        assert lpa.lpa_graph_props_get(h)["weight_bytes"] == width
+        lpa.lpa_graph_destroy(h)
+        assert_sync_parity(lpa, g)
 
 
 def test_weighted_degree_thresholds_and_max_degree(lpa):
