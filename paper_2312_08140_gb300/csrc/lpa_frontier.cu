@@ -332,6 +332,7 @@ cudaError_t build_static_lists(DevState& s, cudaStream_t st, unsigned* counts, u
         s.bin_static_entries[b] = 0;
     }
     s.active_entries = 0;
+    s.small_iota = 0;
     if (nblk == 0) return cudaSuccess;
     std::vector<unsigned> hc((size_t)nblk * kBins);
     std::vector<unsigned long long> he((size_t)nblk * kBins);
@@ -357,6 +358,7 @@ cudaError_t build_static_lists(DevState& s, cudaStream_t st, unsigned* counts, u
             s.active_entries += (int64_t)e;
             base += run;
         }
+        s.small_iota = (int64_t)s.bin_static[0] * 4 >= s.N * 3 ? 1 : 0;
         err = cudaMemcpyAsync(counts, hc.data(), hc.size() * 4, cudaMemcpyHostToDevice, st);
     }
     if (err == cudaSuccess) {

@@ -93,6 +93,7 @@ struct DevState {
     int64_t E;                 // CSR entries
     int32_t G;                 // graphs
     int32_t weight_kind;       // WeightKind
+    int32_t small_iota;        // dense sync passes of bin 0 walk vertex ids 0..N-1 (bin 0 holds >= 3/4 of them)
     const int64_t* off;        // [N] row begins (positions in idx)
     const int64_t* off_end;    // [N] row ends (off + 1 for an ordinary CSR)
     const int32_t* idx;        // [E] global vertex ids

@@ -40,7 +40,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
     const BinView bv = bin_view(s, 0);
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
-    const unsigned cnt = bv.cnt;
+    // A dense pass over a bin holding most vertices walks the vertex ids
+    // themselves (coalesced offsets, one dependent load less than the list)
+    // and keeps those of this bin.
+    const bool iota = !ASYNC && L.dense && s.small_iota;
+    const unsigned cnt = iota ? (unsigned)s.N : bv.cnt;
     const unsigned stride = gridDim.x * blockDim.x;
     constexpr int RUN = 1;                            // async mode uses k_sweep_small_async
     const unsigned nruns = (cnt + RUN - 1) / RUN;
@@ -49,17 +53,25 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
     for (int step = 0; step < RUN; ++step) {
         const unsigned run = rbase + threadIdx.x;
         const unsigned k = run * RUN + step;
-        const bool slot = run < nruns && k < cnt;
+        bool slot = run < nruns && k < cnt;
+        const int32_t v = slot ? (iota ? (int32_t)k : bv.list[k]) : 0;
+        int64_t st = 0;
+        int d = 0;
+        if (iota && slot) {
+            st = s.off[v];
+            const int64_t dd = s.off_end[v] - st;
+            slot = dd >= 1 && dd <= s.small_max;
+            d = slot ? (int)dd : 0;
+        }
         bool act = slot;
-        const int32_t v = slot ? bv.list[k] : 0;
         if constexpr (BATCH) {
             if (act && s.done[s.gid[v]]) act = false;
         }
-        int64_t st = 0;
-        int d = 0;
         int32_t own = 0;
         if (slot) own = ASYNC ? __ldcg(L.C + v) : L.C[v];
-        if (act) {
+        if (!act) {
+            d = 0;
+        } else if (!iota) {
             st = s.off[v];
             d = (int)(s.off_end[v] - st);
         }

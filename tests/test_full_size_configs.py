@@ -1,0 +1,138 @@
+"""The two largest workloads at their full sizes, inputs drawn on the device
+(lpa_inputs.device):
+
+  * R-MAT scale 27, edge factor 14 (~3.7e9 entries, int64 offsets), the
+    asynchronous mode: labels in range, isolated vertices keep their ids,
+    GPU modularity (Eq. 1) equal to the oracle's on the same labels, run info
+    consistent with the tolerance test (Algorithm 1); and, in the synchronous
+    mode, sampled vertices of sweep k+1 recomputed by the oracle from the
+    labels of sweep k (Eq. 2 with the strict tie-break).
+  * 4,096 planted-partition graphs in one batch (~1e8 vertices): sampled
+    graphs bit-exact against the synchronous oracle (labels, sweep count,
+    per-sweep changed counts), and the asynchronous batch held to the
+    component invariant and the modularity bound on the sampled graphs.
+
+The component invariant needs a union-find over every entry, minutes on the
+host at 3.7e9 entries; it is checked on the full R-MAT 22 workload and on
+every smaller case instead.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TAU, ITERS = 0.05, 20
+
+
+@pytest.fixture(scope="module")
+def lpa():
+    import paper_2312_08140_gb300 as m
+    m.load()
+    return m
+
+
+def star_pick(off_h, idx_h, C, v):
+    """Eq. 2 for vertex v given labels C, by the oracle, on a star holding only
+    v's row: vertex 0 is v, vertex 1 + e carries the label of entry e (a
+    self-loop entry points back to 0 and is skipped); labels are replaced by
+    their ranks, which keeps the smallest-label tie-break."""
+    s, e = int(off_h[v]), int(off_h[v + 1])
+    nb = idx_h[s:e].astype(np.int64)
+    labs = np.concatenate([[C[v]], C[nb]]).astype(np.int64)
+    uniq = np.unique(labs)
+    rank = np.searchsorted(uniq, labs).astype(np.int32)
+    d = e - s
+    n_small = max(1 + d, int(uniq.size))
+    star_off = np.zeros(n_small + 1, dtype=np.int64)
+    star_off[1:] = d
+    tgt = np.where(nb == v, 0, 1 + np.arange(d)).astype(np.int32)
+    C_small = np.zeros(n_small, dtype=np.int32)
+    C_small[0] = rank[0]
+    C_small[1:1 + d] = rank[1:]
+    got = O.pick(star_off, tgt, None, C_small, 0)
+    return int(uniq[got])
+
+
+def test_rmat27_full_size(lpa):
+    import torch
+    from lpa_inputs.device import rmat_device
+    g = rmat_device(27, 14, seed=1)
+    torch.cuda.empty_cache()
+    n, nnz = g.n, g.nnz
+    assert nnz > 2 ** 31                                          # int64 offsets are exercised
+    h = lpa.lpa_graph_create(n, nnz, g.off, g.idx, None, lpa.LPA_DEVICE_PTRS | lpa.LPA_BORROW)
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    try:
+        deg = g.off[1:] - g.off[:-1]
+        # asynchronous mode (the workload's mode)
+        info = lpa.lpa_run(h, "async", TAU, ITERS, out)
+        assert 1 <= info.iterations <= ITERS
+        ch = list(info.changed[:info.iterations])
+        if info.exit_reason == 0:
+            assert ch[-1] / n <= TAU and all(c / n > TAU for c in ch[:-1])
+        else:
+            assert info.iterations == ITERS
+        assert bool(((out >= 0) & (out < n)).all())
+        ar = torch.arange(n, device="cuda", dtype=torch.int32)
+        assert bool((out[deg == 0] == ar[deg == 0]).all())      # isolated vertices keep their ids
+        q_gpu = lpa.lpa_modularity(h, out)
+        off_h, idx_h = g.off.cpu().numpy(), g.idx.cpu().numpy()
+        lab = out.cpu().numpy()
+        q_ref = O.modularity(off_h, idx_h, None, lab)
+        assert abs(q_gpu - q_ref) <= 1e-6 * max(1.0, abs(q_ref)), (q_gpu, q_ref)
+        # synchronous mode: sweep k+1 from sweep k on sampled vertices (tolerance 0: no early stop)
+        rng = np.random.default_rng(27)
+        nz = np.flatnonzero(np.diff(off_h) > 0)
+        sample = np.concatenate([rng.choice(nz, 1500, replace=False),
+                                 np.argsort(np.diff(off_h))[-20:]])          # and the largest hubs
+        prev = np.arange(n, dtype=np.int32)
+        for k in (1, 2, 3):
+            lpa.lpa_run(h, "sync", 0.0, k, out, info=False)
+            cur = out.cpu().numpy()
+            for v in sample:
+                assert cur[v] == star_pick(off_h, idx_h, prev, int(v)), (k, int(v))
+            prev = cur
+    finally:
+        lpa.lpa_graph_destroy(h)
+        del g
+        torch.cuda.empty_cache()
+
+
+def test_batch4096_full_size(lpa):
+    import torch
+    from lpa_inputs.device import batched_planted_partition_device, graph_slice_to_host
+    G = 4096
+    vo, eo, off, idx, w, params = batched_planted_partition_device(G)
+    torch.cuda.empty_cache()
+    N = int(vo[-1])
+    b = lpa.lpa_batch_create(G, vo, eo, off, idx, w, lpa.LPA_DEVICE_PTRS)
+    props = lpa.lpa_batch_props_get(b)
+    assert props["num_graphs"] == G and props["n"] == N and props["weight_bytes"] == 1
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    ns = np.diff(vo)
+    rng = np.random.default_rng(4096)
+    picks = sorted(set([int(np.argmin(ns)), int(np.argmax(ns))] + rng.choice(G, 6, replace=False).tolist()))
+    try:
+        infos = lpa.lpa_batch_run(b, G, "sync", TAU, ITERS, out)
+        got = out.cpu().numpy()
+        for k in picks:
+            o, i, ww = graph_slice_to_host(vo, eo, off, idx, w, k)
+            ref, it, ch = O.lpa_sync(o, i, ww, TAU, ITERS)
+            assert np.array_equal(got[vo[k]:vo[k + 1]], ref), k
+            assert infos[k].iterations == it and list(infos[k].changed[:it]) == ch.tolist(), k
+        lpa.lpa_batch_run(b, G, "async", TAU, ITERS, out, info=False)
+        got = out.cpu().numpy()
+        for k in picks:
+            o, i, ww = graph_slice_to_host(vo, eo, off, idx, w, k)
+            lab = got[vo[k]:vo[k + 1]]
+            assert O.count_labels_outside_component(o, i, lab) == 0, k
+            q = O.modularity(o, i, ww, lab)
+            q_serial = O.modularity(o, i, ww, O.lpa_async(o, i, ww, TAU, ITERS)[0])
+            assert q >= q_serial - 0.02, (k, q, q_serial)
+            assert abs(lpa.lpa_batch_modularity(b, k, out[vo[k]:vo[k + 1]]) - q) <= 1e-6
+    finally:
+        lpa.lpa_batch_destroy(b)
+        del off, idx, w
+        torch.cuda.empty_cache()
