@@ -52,10 +52,29 @@ def workload(name):
         return [("rmat22", lambda: L.rmat(22, 16, seed=1)), ("grid4096", lambda: L.road_grid(4096, 4096, seed=1))]
     if name == "rmat21+grid2048":
         return [("rmat21", lambda: L.rmat(21, 16, seed=1)), ("grid2048", lambda: L.road_grid(2048, 2048, seed=1))]
+    if name == "rmat27":
+        return [("rmat27", _rmat27_host)]
     if name == "planted1e4+grid64":
         return [("planted1e4", lambda: L.planted_partition(seed=1)), ("grid64", lambda: L.road_grid(64, 64, seed=1))]
     raise SystemExit(f"unknown workload {name}")
 
+
+def _rmat27_host():
+    """R-MAT scale 27, edge factor 14, drawn on the device (lpa_inputs.device) and
+    copied to host arrays, so the run path starts from host CSR like the others."""
+    import torch
+    import lpa_inputs as L
+    from lpa_inputs.device import rmat_device
+    g = rmat_device(27, 14, seed=1)
+    host = L.Graph(g.off.cpu().numpy(), g.idx.cpu().numpy(), None,
+                   {"kind": "rmat", "scale": 27, "edge_factor": 14, "generator": "device"})
+    del g
+    torch.cuda.empty_cache()
+    return host
+
+
+# modes each workload runs (every other workload: both)
+WORKLOAD_MODES = {"rmat27": ("async",)}
 
 WORKLOAD_TEXT = {
     "rmat22+grid4096": "R-MAT scale 22 edge factor 16 (a,b,c,d=.57,.19,.19,.05; symmetrised, deduplicated, "
@@ -63,6 +82,9 @@ WORKLOAD_TEXT = {
                        "shortcuts, integer weights 1..8); sync and async-with-pruning; tau=0.05, cap 20",
     "rmat21+grid2048": "R-MAT scale 21 + 2048x2048 road-like grid (smaller profiling case of the same "
                        "generators, still larger than L2); sync and async-with-pruning; tau=0.05, cap 20",
+    "rmat27": "R-MAT scale 27 edge factor 14 (a,b,c,d=.57,.19,.19,.05; symmetrised, deduplicated, no "
+              "self-loops; unit weights; ~3.7e9 entries, int64 offsets; drawn on the device with torch); "
+              "asynchronous mode with pruning; tau=0.05, cap 20",
     "planted1e4+grid64": "planted partition 10 x 1000 + 64x64 road-like grid (a seconds-long check of the "
                          "launch path, smaller than L2: not a performance workload); tau=0.05, cap 20",
 }
@@ -174,7 +196,8 @@ def run_reference(args, rank, world):
     O.build()
     wl = workload(args.workload)
     graphs = [make() for _, make in wl]
-    pairs = [(gi, m) for gi in range(len(graphs)) for m in MODES]
+    modes = WORKLOAD_MODES.get(args.workload, MODES)
+    pairs = [(gi, m) for gi in range(len(graphs)) for m in modes]
     for s in range(args.warmup):
         oracle_sample(graphs, [pairs[s % len(pairs)]])
     edges, secs = 0, 0.0
@@ -242,6 +265,58 @@ def batched_sample(lpa, torch, stream, G, reps=5):
         res[m]["speedup_vs_one_launch_per_graph"] = res[m]["batched_graphs_per_s"] / (G / sec)
     for h in handles:
         lpa.lpa_graph_destroy(h)
+    return res
+
+
+def batched_sample_full(lpa, torch, stream, G=4096, reps=3):
+    """The full batched workload: 4,096 planted-partition graphs drawn on the
+    device (lpa_inputs.device), one handle and one device loop per run, against
+    one handle and one lpa_run per graph (handles made from device slices)."""
+    import numpy as np
+    from lpa_inputs.device import batched_planted_partition_device
+    vo, eo, off, idx, w, _ = batched_planted_partition_device(G)
+    torch.cuda.empty_cache()
+    N = int(vo[-1])
+    b = lpa.lpa_batch_create(G, vo, eo, off, idx, w, lpa.LPA_DEVICE_PTRS, stream)
+    out = torch.empty(N, dtype=torch.int32, device="cuda")
+    nnz = np.diff(eo)
+    res = {"graphs": G, "vertices": N, "entries": int(eo[-1]), "inputs": "drawn on the device"}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for m in MODES:
+        infos = lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=True)
+        edges = int(sum(int(nnz[k]) * infos[k].iterations for k in range(G)))
+        lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=False)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3 / reps
+        res[m] = {"batched_graphs_per_s": G / sec, "batched_edges_per_s": edges / sec, "batched_ms": sec * 1e3}
+    lpa.lpa_batch_destroy(b)
+    handles, outs = [], []
+    for k in range(G):
+        v0, v1, e0, e1 = int(vo[k]), int(vo[k + 1]), int(eo[k]), int(eo[k + 1])
+        o = (off[v0:v1 + 1] - e0).contiguous()
+        handles.append(lpa.lpa_graph_create(v1 - v0, e1 - e0, o, idx[e0:e1], w[e0:e1], lpa.LPA_DEVICE_PTRS, stream))
+        outs.append(torch.empty(max(v1 - v0, 1), dtype=torch.int32, device="cuda"))
+    del off, idx, w
+    for m in MODES:
+        for h, o in zip(handles, outs):
+            lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for h, o in zip(handles, outs):
+            lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) / 1e3
+        res[m]["one_launch_per_graph_graphs_per_s"] = G / sec
+        res[m]["speedup_vs_one_launch_per_graph"] = res[m]["batched_graphs_per_s"] / (G / sec)
+    for h in handles:
+        lpa.lpa_graph_destroy(h)
+    torch.cuda.empty_cache()
     return res
 
 
@@ -379,6 +454,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--batched-graphs", type=int, default=128, help="0 skips the batched sample")
     ap.add_argument("--serving-seconds", type=float, default=0.5, help="0 skips the serving sample")
+    ap.add_argument("--batched-full", action="store_true",
+                    help="batched sample on the full workload: 4,096 graphs drawn on the device")
     ap.add_argument("--serving-full", action="store_true",
                     help="serving sample with an R-MAT scale 24 request every 500 requests")
     args = ap.parse_args()
@@ -407,13 +484,14 @@ def main():
 
     wl = workload(args.workload)
     graphs = [make() for _, make in wl]
+    modes = WORKLOAD_MODES.get(args.workload, MODES)
     stream = torch.cuda.current_stream()
     handles = [lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS, stream) for g in graphs]
     outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
 
     def step():
         for h, g, o in zip(handles, graphs, outs):
-            for m in MODES:
+            for m in modes:
                 lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
 
     for _ in range(args.warmup):
@@ -447,7 +525,7 @@ def main():
     # per-run detail (one run each, with info) for the record
     per_run = []
     for (name, _), h, g, o in zip(wl, handles, graphs, outs):
-        for m in MODES:
+        for m in modes:
             ri = lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=True)
             per_run.append({"graph": name, "mode": m, "n": g.n, "nnz": g.nnz, "iterations": ri.iterations,
                             "exit_reason": ri.exit_reason, "scanned": ri.edges_touched})
@@ -461,13 +539,13 @@ def main():
         t_lab = torch.empty(g.n, dtype=torch.int32).pin_memory()
         pinned.append((t_off, t_idx, t_w, t_lab))
     h2d = sum(g.off.nbytes + g.idx.nbytes + (g.w.nbytes if g.w is not None else 0) for g in graphs)
-    d2h = sum(4 * g.n * len(MODES) for g in graphs)
+    d2h = sum(4 * g.n * len(modes) for g in graphs)
 
     def e2e_step():
         e = 0
         for g, (t_off, t_idx, t_w, t_lab), o in zip(graphs, pinned, outs):
             h = lpa.lpa_graph_create(g.n, g.nnz, t_off, t_idx, t_w, lpa.LPA_HOST_PTRS, stream)
-            for m in MODES:
+            for m in modes:
                 lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
                 t_lab.copy_(o, non_blocking=True)
             e += g.nnz * lpa.lpa_graph_props_get(h)["sweeps_total"]   # waits for the device
@@ -491,7 +569,7 @@ def main():
         agg = {}
         for g, h, o in zip(graphs, handles, outs):
             wbytes = lpa.lpa_graph_props_get(h)["weight_bytes"]     # as the sweeps read them
-            for m in MODES:
+            for m in modes:
                 _, prof = lpa.lpa_run_profiled(h, m, TAU, MAX_ITERS, o, stream)
                 for b, d in kernel_bytes(prof.as_dict(), wbytes, m == "sync", 1 if m == "sync" else 2).items():
                     a = agg.setdefault(b, {"bytes": 0.0, "ms": 0.0, "launches": 0})
@@ -510,7 +588,10 @@ def main():
                     "bytes_per_launch": d["bytes_per_launch"],
                     "mean_launch_ms": d["ms_per_step"] / d["launches_per_step"]}
 
-    batched = batched_sample(lpa, torch, stream, args.batched_graphs) if args.batched_graphs > 0 else None
+    if args.batched_full:
+        batched = batched_sample_full(lpa, torch, stream)
+    else:
+        batched = batched_sample(lpa, torch, stream, args.batched_graphs) if args.batched_graphs > 0 else None
     serving = None
     if args.serving_seconds > 0:
         import lpa_inputs as L
@@ -522,8 +603,8 @@ def main():
                               "; without the R-MAT scale 24 request of the full serving config (--serving-full)"))
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        pairs = [(gi, m) for gi in range(len(graphs)) for m in MODES]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and sum(g.nnz for g in graphs) <= 400_000_000:
+        pairs = [(gi, m) for gi in range(len(graphs)) for m in modes]
         e, s = oracle_sample(graphs, pairs + pairs)
         cpu = {"value": e / s, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "CPU oracle, one sweep of each (graph, mode) pair of the workload, twice "

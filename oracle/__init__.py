@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
 
 
 def _bind(lib):
-    for name in ("oracle_lpa_sync", "oracle_lpa_async", "oracle_sync_sweep",
+    for name in ("oracle_lpa_sync", "oracle_lpa_async", "oracle_lpa_async_order", "oracle_sync_sweep",
                  "oracle_count_labels_outside_component", "oracle_count_not_local_max"):
         getattr(lib, name).restype = _i64
     lib.oracle_pick.restype = ctypes.c_int32
@@ -131,9 +131,15 @@ def lpa_sync(off, idx, w=None, tau=0.05, max_iters=20, _lib_override=None):
     return _run((_lib_override or _load()).oracle_lpa_sync, off, idx, w, tau, max_iters)
 
 
-def lpa_async(off, idx, w=None, tau=0.05, max_iters=20, _lib_override=None):
-    """Algorithm 1, one thread, ascending order; returns (labels, iterations, changed)."""
-    return _run((_lib_override or _load()).oracle_lpa_async, off, idx, w, tau, max_iters)
+def lpa_async(off, idx, w=None, tau=0.05, max_iters=20, order=None, _lib_override=None):
+    """Algorithm 1, one thread; the vertex loop visits `order` (a permutation of
+    0..n-1; default ascending) in every sweep.  Returns (labels, iterations, changed)."""
+    lib = _lib_override or _load()
+    if order is None:
+        return _run(lib.oracle_lpa_async, off, idx, w, tau, max_iters)
+    order = np.ascontiguousarray(order, dtype=np.int64)
+    fn = lambda n, o, i, ww, t, m, C, h: lib.oracle_lpa_async_order(n, o, i, ww, t, m, _p(order), C, h)
+    return _run(fn, off, idx, w, tau, max_iters)
 
 
 def modularity(off, idx, w, C, _lib_override=None) -> float:

@@ -22,7 +22,8 @@
  *                        satisfies dN/N <= tau, or after max_iters sweeps
  *                        (Section 4.1.2, 4.1.3).
  *   - oracle_lpa_async:  Algorithm 1 run by one thread in ascending vertex
- *                        order: labels updated in place, a vertex is marked
+ *                        order (oracle_lpa_async_order: in a given order of
+ *                        the vertex loop): labels updated in place, a vertex is marked
  *                        processed when visited and, when its label changes,
  *                        all of its neighbours other than itself are marked
  *                        unprocessed (vertex pruning, Section 4.1.4).
@@ -201,10 +202,23 @@ int64_t oracle_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const
 }
 
 /* Algorithm 1 (lpa / lpaMove / scanCommunities) run by a single thread that
- * visits vertices in ascending order.  Returns the number of sweeps. */
-int64_t oracle_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
-                         double tau, int64_t max_iters, int32_t *C_out, int64_t *changed_hist) {
+ * visits the vertices in the order given by `order` (a permutation of
+ * 0..n-1; NULL: ascending) in every sweep.  Algorithm 1 leaves the order of
+ * its vertex loop open; any order is one of its executions.  Returns the
+ * number of sweeps. */
+int64_t oracle_lpa_async_order(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                               double tau, int64_t max_iters, const int64_t *order, int32_t *C_out,
+                               int64_t *changed_hist) {
     if (check_csr(n, off, idx) || !C_out || max_iters < 0 || !(tau >= 0.0)) return ORACLE_BAD_ARG;
+    if (order) {                                                     /* must be a permutation */
+        uint8_t *hit = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+        if (!hit) return ORACLE_NO_MEM;
+        for (int64_t k = 0; k < n; ++k) {
+            if (order[k] < 0 || order[k] >= n || hit[order[k]]) { free(hit); return ORACLE_BAD_ARG; }
+            hit[order[k]] = 1;
+        }
+        free(hit);
+    }
     for (int64_t i = 0; i < n; ++i) C_out[i] = (int32_t)i;          /* C <- [0 .. |V|) */
     if (n == 0) return 0;
     uint8_t *unprocessed = (uint8_t *)malloc((size_t)n);
@@ -215,7 +229,8 @@ int64_t oracle_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, cons
     int64_t it = 0;
     while (it < max_iters) {
         int64_t dN = 0;                                              /* lpaMove */
-        for (int64_t i = 0; i < n; ++i) {
+        for (int64_t k = 0; k < n; ++k) {
+            const int64_t i = order ? order[k] : k;
             if (!unprocessed[i]) continue;
             unprocessed[i] = 0;                                      /* prune */
             int32_t c = pick(&H, off, idx, w, C_out, i);
@@ -232,6 +247,12 @@ int64_t oracle_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, cons
     kv_free(&H);
     free(unprocessed);
     return it;
+}
+
+/* Algorithm 1 by one thread in ascending vertex order. */
+int64_t oracle_lpa_async(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                         double tau, int64_t max_iters, int32_t *C_out, int64_t *changed_hist) {
+    return oracle_lpa_async_order(n, off, idx, w, tau, max_iters, NULL, C_out, changed_hist);
 }
 
 /* Modularity, Eq. 1 in community form: Q = sum_c [sigma_c/2m - (Sigma_c/2m)^2]

@@ -128,6 +128,8 @@ struct Engine {
     std::vector<void*> owned;        // pool allocations freed at destroy
     unsigned* static_counts = nullptr;             // static-list scratch
     unsigned long long* static_ents = nullptr;
+    unsigned long long* cap_scratch = nullptr;     // [3] overflow capacity sums
+    std::vector<void*> ovf_scratch;                // sliced overflow path: pairs, counts, offsets
     int32_t* idx_owned = nullptr;
     bool borrowed = false;
     bool weighted = false;
@@ -181,24 +183,49 @@ void engine_free(Engine& E) {
     if (E.cap_body) cudaStreamDestroy(E.cap_body);
     if (E.ovf) E.owned.push_back(E.ovf);
     E.ovf = nullptr;
+    for (void* p : E.ovf_scratch) E.owned.push_back(p);
+    E.ovf_scratch.clear();
     pool_free_all(E.device, E.owned);
 }
 
 // Grid sizes of the block bins, and the overflow list of the last bin (one
 // entry per vertex of that bin at most).
-lpa_status setup_blocks(Engine& E) {
+lpa_status setup_blocks(Engine& E, cudaStream_t st) {
     for (int b = 0; b < kBlockBins; ++b) E.block_grid[b] = block_grid_for(E.s, b + 2, E.sms);
-    if (E.ovf) {
-        std::vector<void*> old{E.ovf};
-        pool_free_all(E.device, old);
-    }
+    std::vector<void*> old;
+    if (E.ovf) old.push_back(E.ovf);
+    for (void* p : E.ovf_scratch) old.push_back(p);
+    pool_free_all(E.device, old);
     E.ovf = nullptr;
+    E.ovf_scratch.clear();
     const size_t n = std::max<size_t>(E.s.bin_static[kBins - 1], 1);
     void* p = nullptr;
     cudaError_t err = pool_alloc(E.device, &p, n * sizeof(Overflow));
     if (err != cudaSuccess) return cuda_fail(err, "overflow list");
     E.ovf = static_cast<Overflow*>(p);
     E.s.ovf = E.ovf;
+    // sliced overflow path: scratch for every last-bin row that can overflow
+    int64_t pairs = 0, counts = 0, rows = 0;
+    err = ovf_capacity(E.s, st, E.sms, &pairs, &counts, &rows, E.cap_scratch);
+    if (err != cudaSuccess) return cuda_fail(err, "overflow capacity");
+    void* q[3] = {nullptr, nullptr, nullptr};
+    const size_t bytes[3] = {(size_t)std::max<int64_t>(pairs, 1) * sizeof(uint2),
+                             (size_t)std::max<int64_t>(counts, 1) * sizeof(uint32_t),
+                             (size_t)std::max<int64_t>(counts, 1) * sizeof(uint32_t)};
+    for (int k = 0; k < 3; ++k) {
+        if ((err = pool_alloc(E.device, &q[k], bytes[k])) != cudaSuccess) {
+            for (int j = 0; j < k; ++j) E.ovf_scratch.push_back(q[j]);
+            cudaGetLastError();
+            return fail(LPA_ERR_OUT_OF_MEMORY, "overflow scratch: %zu bytes", bytes[k]);
+        }
+        E.ovf_scratch.push_back(q[k]);
+    }
+    E.s.ovf_pairs = static_cast<uint2*>(q[0]);
+    E.s.ovf_cnt = static_cast<uint32_t*>(q[1]);
+    E.s.ovf_off = static_cast<uint32_t*>(q[2]);
+    E.s.ovf_pairs_cap = pairs;
+    E.s.ovf_cnt_cap = counts;
+    E.s.ovf_possible = rows > 0 ? 1 : 0;
     return LPA_OK;
 }
 
@@ -360,8 +387,9 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     const size_t sblk = (size_t)std::max<int64_t>(static_scratch_blocks(n), 1) * kBins;
     if ((rs = dalloc_t(E, &E.static_counts, sblk)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.static_ents, sblk)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.cap_scratch, 3)) != LPA_OK) return rs;
     LPA_CUDA(build_static_lists(E.s, st, E.static_counts, E.static_ents));
-    if ((rs = setup_blocks(E)) != LPA_OK) return rs;
+    if ((rs = setup_blocks(E, st)) != LPA_OK) return rs;
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_top, cudaStreamNonBlocking));
     LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_body, cudaStreamNonBlocking));
     LPA_CUDA(cudaStreamSynchronize(st));
@@ -730,7 +758,7 @@ static lpa_status set_config(Engine& E, const lpa_config* cfg) {
     E.cfg = *cfg;
     apply_config_fields(E);
     LPA_CUDA(build_static_lists(E.s, 0, E.static_counts, E.static_ents));
-    return setup_blocks(E);
+    return setup_blocks(E, 0);
 }
 
 lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config* cfg) {

@@ -76,7 +76,7 @@ __global__ void k_init(DevState s) {
         c->dense[0] = 1;
         c->dense[1] = 0;
         c->pass_changed_entries = 0;
-        c->ovf_packed = 0;
+        c->ovf_count = 0;
         for (int b = 0; b < kBins; ++b) {
             c->bin_cnt[0][b] = s.bin_static[b];
             c->bin_entries[0][b] = s.bin_static_entries[b];
@@ -436,7 +436,8 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         // per pass: one launch per statically non-empty bin (the last bin adds
         // the partitioned rescan), then the finish kernel
         int per_pass = 1;
-        for (int b = 0; b < kBins; ++b) per_pass += s.bin_static[b] ? (b == kBins - 1 ? 2 : 1) : 0;
+        for (int b = 0; b < kBins; ++b) per_pass += s.bin_static[b] ? 1 : 0;
+        if (s.bin_static[kBins - 1] && s.ovf_possible) per_pass += 4;   // plan, slices, partitions, rescan
         c->total_sweep_launches += mode == MODE_ASYNC ? 2 * per_pass : per_pass;
         for (int b = 0; b < kBins; ++b) {
             c->bin_changed[b] = 0;
@@ -468,7 +469,7 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         c->rd = wr;
     }
     c->pass_changed_entries = 0;
-    c->ovf_packed = 0;
+    c->ovf_count = 0;
     c->ticket = 0;
     __threadfence();
     if (role != 1 && in_graph) cudaGraphSetConditional(h, any ? 1u : 0u);

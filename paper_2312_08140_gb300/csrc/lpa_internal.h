@@ -22,6 +22,10 @@ constexpr int kBins = 5;                // thread / warp / 128-, 256-, 512-threa
 constexpr int kBlockBins = 3;           // bins 2..4 use the block kernel
 constexpr int kBlockThreads[kBlockBins] = {128, 256, 512};
 constexpr int kHighPermille = 900;      // "almost every vertex changed" (see skip_marks)
+constexpr int kSliceLen = 4096;         // entries per slice of an overflowing row
+constexpr int kMaxParts = 4096;         // partitions a row may use on the sliced path
+constexpr int kMaxSlices = 4096;        // slices a row may use on the sliced path (with the above: d <= 2^24)
+constexpr int kSliceMinParts = 9;       // rows with fewer partitions are rescanned (at most 8 reads per entry)
 constexpr int kLargeSlots = 8192;       // shared table of the last bin (overflowing rows are
                                         // rescanned split over label partitions)
 constexpr int32_t kEmptyKey = -1;       // free slot in label tables; labels are >= 0
@@ -67,21 +71,36 @@ struct Ctrl {
     long long total_sweeps;              // cumulative over all runs (never reset)
     long long total_scanned;
     long long total_sweep_launches;      // kernel launches of those sweeps
-    unsigned long long ovf_packed;       // overflow list: (entries << 40) | partition work items
+    unsigned long long ovf_count;        // overflow rows appended in this pass
+    unsigned int ovf_slice_items;        // work items of the overflow kernels (set by k_ovf_plan)
+    unsigned int ovf_part_items;
+    unsigned int ovf_rescan_items;
+    unsigned int ovf_pad;
 };
 
 // A last-bin row whose distinct labels overflowed the block's shared table.
 // It is rescanned by `parts` blocks, block p aggregating only the labels whose
 // hash falls in partition p; each block folds its best (sum, label) into
 // `best` and the block that completes the row applies the result.
+// A last-bin row whose labels overflowed the shared table in this pass.
+// Sliced path (kSliceMinParts <= parts <= kMaxParts, scratch available): blocks over
+// kSliceLen-entry slices group the row's labels by hash partition into
+// scratch, then a block per partition aggregates its share.  Rescan path
+// (otherwise): a block per partition rescans the whole row.
 struct Overflow {
     int32_t v;                 // vertex
     uint32_t slot;             // its slot in the bin's frontier list
     int64_t st;                // row start
     int32_t d;                 // row length
     int32_t own;               // label before the sweep
-    uint32_t item_base;        // first partition work item of this row
-    uint32_t parts;            // number of partitions
+    uint32_t parts;            // P = ceil(2d / kLargeSlots) label partitions
+    uint32_t slices;           // Q = ceil(d / kSliceLen) on the sliced path, else 0
+    int64_t pair_base;         // sliced: first (label, sum) pair of its scratch (d reserved)
+    int64_t cnt_base;          // sliced: first of its Q x P (slice, partition) counts and offsets
+    uint32_t slice_base;       // sliced: first slice work item
+    uint32_t part_base;        // sliced: first partition work item
+    uint32_t rescan_base;      // rescan: first partition work item
+    uint32_t rescan_parts;     // rescan: P, else 0
     unsigned long long best;   // max over partitions of (sum key << 32) | (~label)
     unsigned int done;         // partitions completed
     unsigned int pad;
@@ -119,8 +138,13 @@ struct DevState {
     int32_t* iters;            // [G]
     int32_t* exit_reason;      // [G]
     long long* hist_changed;   // [G * kMaxHist]
-    struct Overflow* ovf;      // [bin_static[4]] last-bin rows whose labels overflowed the shared
-                               // table, rescanned split over label partitions
+    struct Overflow* ovf;      // [bin_static[4]] last-bin rows whose labels overflowed the shared table
+    uint2* ovf_pairs;          // sliced path: (label, sum bits) pairs grouped by partition per slice
+    uint32_t* ovf_cnt;         // sliced path: pairs per (slice, partition)
+    uint32_t* ovf_off;         // sliced path: their offsets within the slice
+    int64_t ovf_pairs_cap;     // capacity of ovf_pairs (0: every overflow row takes the rescan path)
+    int64_t ovf_cnt_cap;       // capacity of ovf_cnt / ovf_off
+    int32_t ovf_possible;      // some last-bin row is longer than kLargeSlots / 2 (else no row overflows)
     int32_t small_max;         // degree bins (see lpa_config)
     int32_t warp_max;
     int32_t mid_max;
@@ -144,6 +168,11 @@ cudaError_t launch_init(const DevState& s, cudaStream_t st, int sms);
 // scratch of kBins * static_scratch_blocks(N) elements each.
 int64_t static_scratch_blocks(int64_t N);
 cudaError_t build_static_lists(DevState& s, cudaStream_t st, unsigned* counts, unsigned long long* ents);
+// Scratch of the sliced overflow path for the current static lists: pairs and
+// (slice, partition) counts it may need, and the number of last-bin rows that
+// can overflow at all.  scratch3: device unsigned long long[3].  Synchronises st.
+cudaError_t ovf_capacity(const DevState& s, cudaStream_t st, int sms, int64_t* pairs, int64_t* counts,
+                         int64_t* rows, unsigned long long* scratch3);
 cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st);
 // role 0: end of a sweep (apply, compaction for the next sweep, control);
 // role 1: compaction only (inside an asynchronous sweep, of the vertices the

@@ -545,6 +545,13 @@ lpa_status lpa_serve_create(const lpa_serve_config* cfg, lpa_server_t* out) {
     s.block_slots[0] = 1024;
     s.block_slots[1] = 4096;
     s.block_slots[2] = kLargeSlots;
+    // overflowing rows take the rescan path (no sliced scratch in the arena)
+    s.ovf_pairs = nullptr;
+    s.ovf_cnt = nullptr;
+    s.ovf_off = nullptr;
+    s.ovf_pairs_cap = 0;
+    s.ovf_cnt_cap = 0;
+    s.ovf_possible = 1;
     s.dense_permille = 1001;
     for (int b = 0; b < kBins; ++b) {
         s.bin_base[b] = (int64_t)b * S->V;

@@ -4,12 +4,15 @@ Synchronous modes (LPA_MODE_SYNC, LPA_MODE_SYNC_FULL) must reproduce the
 oracle's labels, sweep count and per-sweep changed counts exactly: every graph
 here has integer weights, so every per-label sum is exact in any order.  The
 asynchronous mode is order-dependent (Section 4.1), so it is held to
-invariants: labels stay inside the vertex's connected component, at most
-tau*N vertices are off their local argmax when the tolerance ended the run, and
-modularity not lower than the serial oracle's by more than 0.02.
+invariants: labels stay inside the vertex's connected component, the GPU's
+modularity of its labels equals the oracle's, and that modularity is not below
+the floor of tests/async_bounds.py (serial runs of Algorithm 1 in several
+vertex orders); vertices off their local argmax are reported.
 """
 import json
 import os
+
+from async_bounds import async_floor
 
 import numpy as np
 import pytest
@@ -246,6 +249,24 @@ def test_async_small_sbm_graphs(lpa):
         check_async(lpa, L.batched_sbm_graph(gi, n_max=5000))
 
 
+def hub_graph(leaves, seed=0):
+    """A hub joined to `leaves` vertices that are paired into triangles with it
+    (every leaf pair also linked), so the hub's row holds `leaves` distinct
+    labels in the first sweep: more than the last bin's shared table holds."""
+    pairs = [(0, k) for k in range(1, leaves + 1)]
+    pairs += [(k, k + 1) for k in range(1, leaves, 2)]
+    return L.from_undirected_pairs(leaves + 1, pairs)
+
+
+def test_hub_rows_that_overflow_the_shared_table(lpa):
+    """Rows with more distinct labels than the 8192-slot table take the
+    overflow path (slices grouped by label partition, then one block per
+    partition); labels, sweep counts and changed counts stay exact."""
+    for leaves in (5000, 9000, 40000):
+        assert_sync_parity(lpa, hub_graph(leaves))
+    check_async(lpa, hub_graph(40000))
+
+
 def test_pool_reuse_and_release(lpa):
     """Graph memory comes from the library's pool: graphs created after others
     were destroyed (reusing their pages), and after the cache was released,
@@ -259,12 +280,13 @@ def test_pool_reuse_and_release(lpa):
     lpa.lpa_release_cached_memory()
 
 
-def check_async(lpa, g, tau=0.05, iters=20, cfg=None, q_slack=0.02):
+def check_async(lpa, g, tau=0.05, iters=20, cfg=None):
     """Async run held to: labels in range and inside the vertex's component;
     GPU modularity equal to the fp64 oracle's on the same labels (1e-6 rel);
-    modularity not lower than the serial oracle run's by more than q_slack
-    (the paper reports parallel runs reaching higher modularity than serial
-    ones, Section 4.1); vertices off their local argmax reported."""
+    modularity at least async_floor(g): the lowest of serial runs of
+    Algorithm 1 in several vertex orders less 0.01, or, above 300K vertices,
+    the ascending serial run less 0.02; vertices off their local argmax
+    reported."""
     import torch
     got, info, h = run_gpu(lpa, g, "async", tau, iters, cfg)
     try:
@@ -275,13 +297,12 @@ def check_async(lpa, g, tau=0.05, iters=20, cfg=None, q_slack=0.02):
         lpa.lpa_graph_destroy(h)
     q_ref_gpu_labels = O.modularity(g.off, g.idx, g.w, got)
     assert abs(q_gpu - q_ref_gpu_labels) <= 1e-6 * max(1.0, abs(q_ref_gpu_labels))
-    ref, it_ref, _ = O.lpa_async(g.off, g.idx, g.w, tau, iters)
-    q_ser = O.modularity(g.off, g.idx, g.w, ref)
+    floor = async_floor(g, tau, iters)
     off_max = O.count_not_local_max(g.off, g.idx, g.w, got)
-    print(f"async n={g.n}: Q_gpu={q_gpu:.4f} Q_serial={q_ser:.4f} sweeps={info['iterations']} "
+    print(f"async n={g.n}: Q_gpu={q_gpu:.4f} floor={floor:.4f} sweeps={info['iterations']} "
           f"exit={info['exit_reason']} off_local_max={off_max} ({off_max / max(g.n, 1):.4f} of N)")
-    assert q_gpu >= q_ser - q_slack, (q_gpu, q_ser)
-    return info, q_gpu, q_ser, off_max
+    assert q_gpu >= floor, (q_gpu, floor)
+    return info, q_gpu, floor, off_max
 
 
 def test_async_invariants_small(lpa):

@@ -36,8 +36,11 @@ def _case_graph(case):
 
 def _run_case(case, mod=O):
     g = _case_graph(case)
+    kw = dict(tau=case.get("tau", 0.05), max_iters=case.get("max_iters", 20))
+    if "order" in case:
+        kw["order"] = case["order"]
     fn = mod.lpa_sync if case["mode"] == "sync" else mod.lpa_async
-    return fn(g.off, g.idx, g.w, tau=case.get("tau", 0.05), max_iters=case.get("max_iters", 20))
+    return fn(g.off, g.idx, g.w, **kw)
 
 
 @pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: c["name"])
@@ -108,17 +111,18 @@ def test_sync_run_is_iterated_sweeps():
             assert Co.tolist() == C.tolist() and it == len(hist) and ho.tolist() == hist
 
 
-def _serial_async_restated(g, tau, cap):
+def _serial_async_restated(g, tau, cap, order=None):
     """Algorithm 1 with one thread, written as a worklist of pending vertices
-    scanned in increasing id order; each pick is the enumerated Eq. 2."""
+    scanned in increasing id order (or in `order`); each pick is the
+    enumerated Eq. 2."""
     n = g.n
     C = np.arange(n, dtype=np.int32)
     pending = set(range(n))
     hist = []
+    seq = list(range(n)) if order is None else [int(x) for x in order]
     for _ in range(cap):
         dN = 0
-        i = 0
-        while i < n:
+        for i in seq:
             if i in pending:
                 pending.discard(i)
                 c = _enumerated_pick(g, C, i)
@@ -128,7 +132,6 @@ def _serial_async_restated(g, tau, cap):
                     for e in range(int(g.off[i]), int(g.off[i + 1])):
                         if int(g.idx[e]) != i:
                             pending.add(int(g.idx[e]))
-            i += 1
         hist.append(dN)
         if dN / n <= tau:
             break
@@ -274,6 +277,7 @@ MUTANTS = {
     "sync_reads_in_place": ("C_out[i] = pick(&H, off, idx, w, prev, i);", "C_out[i] = pick(&H, off, idx, w, C_out, i);"),
     "async_no_remark": ("if ((int64_t)idx[e] != i) unprocessed[idx[e]] = 1;", "(void)0;"),
     "async_counts_visits": ("if (c == C_out[i]) continue;", "if (c == C_out[i]) { ++dN; continue; }"),
+    "async_order_ignored": ("const int64_t i = order ? order[k] : k;", "const int64_t i = k;"),
     "isolated_takes_zero": ("int32_t c = used ? most_weighted_label(H) : C[i];", "int32_t c = used ? most_weighted_label(H) : 0;"),
     "modularity_null_term_dropped": ("q = sigma / two_m - null_term;", "q = sigma / two_m;"),
     "modularity_sigma_by_other_end": ("Sigma[C[i]] += K_i;", "Sigma[C[idx[off[i]]]] += K_i;"),
@@ -325,3 +329,31 @@ def test_planted_mistake_is_caught(name, tmp_path):
     so = tmp_path / f"lib_{name}.so"
     subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(path)])
     assert not _pins_pass(O.load_variant(str(so)))
+
+
+def test_async_order_ascending_equals_default_and_rejects_non_permutations():
+    """The ordered serial run with the identity order is the ascending run;
+    an order that is not a permutation of 0..n-1 is refused."""
+    for g, _ in _random_cases(40, seed0=70000):
+        if g.n == 0:
+            continue
+        a = O.lpa_async(g.off, g.idx, g.w)
+        b = O.lpa_async(g.off, g.idx, g.w, order=np.arange(g.n))
+        assert a[0].tolist() == b[0].tolist() and a[1] == b[1] and a[2].tolist() == b[2].tolist()
+    g = L.from_undirected_pairs(3, [(0, 1), (1, 2)])
+    for bad in ([0, 0, 1], [0, 1, 3], [2, 1, -1]):
+        with pytest.raises(Exception):
+            O.lpa_async(g.off, g.idx, None, order=bad)
+
+
+def test_async_order_matches_restatement_in_that_order():
+    """A second restatement of Algorithm 1 in Python, visiting a random order,
+    agrees with the ordered oracle on random small graphs."""
+    rng = np.random.default_rng(5)
+    for g, _ in _random_cases(40, seed0=80000):
+        if g.n == 0:
+            continue
+        order = rng.permutation(g.n)
+        C, it, hist = _serial_async_restated(g, 0.05, 20, order=order)
+        Co, ito, ho = O.lpa_async(g.off, g.idx, g.w, order=order)
+        assert Co.tolist() == C.tolist() and ito == it and ho.tolist() == hist
