@@ -322,10 +322,12 @@ lpa_status lpa_serve_create(const lpa_serve_config *cfg, lpa_server_t *out);
  * request's rows, indices and weights are checked on the device while it is
  * admitted, and a request that fails is never run: its ticket is reported
  * by lpa_serve_poll like any other and lpa_serve_fetch returns
- * LPA_ERR_INVALID_GRAPH for it.  Solo-lane requests are checked
- * in full here.  The data is copied (pageable buffers) or read by DMA and
- * waited for (page-locked buffers) before returning, so the caller may reuse
- * its buffers at once.  Returns
+ * LPA_ERR_INVALID_GRAPH for it.  A solo-lane request is uploaded to device
+ * memory here and validated by lpa_graph_create on the solo lane, a failure
+ * likewise reported at fetch; the solo lane's streams have the lowest
+ * priority, so the arena's cycles run first.  The data is copied (pageable
+ * buffers) or read by DMA and waited for (page-locked buffers) before
+ * returning, so the caller may reuse its buffers at once.  Returns
  * LPA_ERR_BUSY when it does not fit now (no free slot, vertex or entry range,
  * or device-memory budget); the caller may retry after results are released.
  * *ticket identifies the request. */

@@ -212,10 +212,10 @@ struct Request {
     int32_t slot = -1;
     int64_t v0 = 0, e0 = 0;
     cudaEvent_t ready = nullptr;
-    // solo lane: host copies of the CSR
-    std::vector<int64_t> off;
-    std::vector<int32_t> idx;
-    std::vector<float> w;
+    // solo lane: the CSR uploaded at submit (stream-ordered allocations)
+    int64_t* d_off = nullptr;
+    int32_t* d_idx = nullptr;
+    float* d_w = nullptr;
     bool weighted = false;
     int64_t est_bytes = 0;
 };
@@ -231,7 +231,7 @@ struct lpa_server {
     DevState s{};
     std::vector<void*> owned;
     int64_t arena_bytes = 0;
-    cudaStream_t run_st = nullptr, copy_st = nullptr, solo_st = nullptr;
+    cudaStream_t run_st = nullptr, copy_st = nullptr, solo_st = nullptr, solo_copy_st = nullptr;
     int32_t* h_done = nullptr;                // pinned mirror of done[S]
     int32_t* bad = nullptr;                   // [S] admission check failed
     // host state (guarded by mu)
@@ -274,6 +274,7 @@ void free_server(lpa_server* S) {
     if (S->run_st) cudaStreamDestroy(S->run_st);
     if (S->copy_st) cudaStreamDestroy(S->copy_st);
     if (S->solo_st) cudaStreamDestroy(S->solo_st);
+    if (S->solo_copy_st) cudaStreamDestroy(S->solo_copy_st);
 }
 
 int grid_for(int64_t n, int sms) {
@@ -411,6 +412,15 @@ void worker_main(lpa_server* S) {
     }
 }
 
+void free_solo_upload(lpa_server* S, Request* r) {
+    if (r->d_off) cudaFreeAsync(r->d_off, S->solo_st);
+    if (r->d_idx) cudaFreeAsync(r->d_idx, S->solo_st);
+    if (r->d_w) cudaFreeAsync(r->d_w, S->solo_st);
+    r->d_off = nullptr;
+    r->d_idx = nullptr;
+    r->d_w = nullptr;
+}
+
 void solo_main(lpa_server* S) {
     cudaSetDevice(S->device);
     for (;;) {
@@ -426,15 +436,22 @@ void solo_main(lpa_server* S) {
         }
         Result res;
         lpa_graph_t g = nullptr;
-        lpa_status st = lpa_graph_create(r->n, r->nnz, r->off.data(), r->idx.data(), r->weighted ? r->w.data() : nullptr,
-                                         LPA_HOST_PTRS, S->solo_st, &g);
+        // borrowed device CSR: validated on the device by lpa_graph_create
+        lpa_status st = lpa_graph_create(r->n, r->nnz, r->d_off, r->d_idx, r->weighted ? r->d_w : nullptr,
+                                         LPA_DEVICE_PTRS | LPA_BORROW, S->solo_st, &g);
         int32_t* lab = nullptr;
-        if (st == LPA_OK && cudaMalloc(&lab, (size_t)std::max<int64_t>(r->n, 1) * 4) != cudaSuccess) st = LPA_ERR_OUT_OF_MEMORY;
+        if (st == LPA_OK &&
+            cudaMallocAsync(&lab, (size_t)std::max<int64_t>(r->n, 1) * 4, S->solo_st) != cudaSuccess) {
+            cudaGetLastError();
+            st = LPA_ERR_OUT_OF_MEMORY;
+        }
         const lpa_mode mode = S->cfg.mode == LPA_MODE_ASYNC ? LPA_MODE_ASYNC : LPA_MODE_SYNC;
         if (st == LPA_OK) st = lpa_run(g, mode, S->cfg.tolerance, S->cfg.max_iters, lab, S->solo_st, &res.info);
         if (st == LPA_OK) {
             res.labels.resize((size_t)r->n);
-            if (r->n && cudaMemcpy(res.labels.data(), lab, (size_t)r->n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+            if (r->n && (cudaMemcpyAsync(res.labels.data(), lab, (size_t)r->n * 4, cudaMemcpyDeviceToHost,
+                                         S->solo_st) != cudaSuccess ||
+                         cudaStreamSynchronize(S->solo_st) != cudaSuccess))
                 st = LPA_ERR_CUDA;
         }
         if (st != LPA_OK) {
@@ -444,8 +461,10 @@ void solo_main(lpa_server* S) {
         } else {
             res.state = 2;
         }
-        if (lab) cudaFree(lab);
         if (g) lpa_graph_destroy(g);
+        if (lab) cudaFreeAsync(lab, S->solo_st);
+        free_solo_upload(S, r);
+        cudaStreamSynchronize(S->solo_st);
         std::lock_guard<std::mutex> lock(S->mu);
         S->solo_bytes -= r->est_bytes;
         S->results[r->ticket] = std::move(res);
@@ -461,18 +480,6 @@ bool host_pinned(const void* p) {
         return false;
     }
     return a.type == cudaMemoryTypeHost;
-}
-
-lpa_status check_host_csr(int64_t n, int64_t nnz, const int64_t* off, const int32_t* idx, const float* w) {
-    if (off[0] != 0 || off[n] != nnz) return err(LPA_ERR_INVALID_GRAPH, "offsets must start at 0 and end at nnz");
-    for (int64_t i = 0; i < n; ++i)
-        if (off[i + 1] < off[i]) return err(LPA_ERR_INVALID_GRAPH, "offsets decrease");
-    for (int64_t e = 0; e < nnz; ++e)
-        if (idx[e] < 0 || idx[e] >= n) return err(LPA_ERR_INVALID_GRAPH, "index out of range");
-    if (w)
-        for (int64_t e = 0; e < nnz; ++e)
-            if (!(w[e] >= 0.f) || w[e] == INFINITY) return err(LPA_ERR_INVALID_GRAPH, "weight negative or not finite");
-    return LPA_OK;
 }
 
 }  // namespace
@@ -563,9 +570,14 @@ lpa_status lpa_serve_create(const lpa_serve_config* cfg, lpa_server_t* out) {
                           cfg->mode == LPA_MODE_ASYNC ? MODE_ASYNC : MODE_SYNC);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(err(LPA_ERR_CUDA, "control initialisation failed"));
     if (cudaMallocHost(&S->h_done, G * 4) != cudaSuccess) return bail(err(LPA_ERR_OUT_OF_MEMORY, "pinned buffer"));
-    if (cudaStreamCreateWithFlags(&S->run_st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->copy_st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&S->solo_st, cudaStreamNonBlocking) != cudaSuccess)
+    // arena streams first, the solo lane's at the lowest priority: a large
+    // request runs in the gaps left by the arena's cycles
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (cudaStreamCreateWithPriority(&S->run_st, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&S->copy_st, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&S->solo_st, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&S->solo_copy_st, cudaStreamNonBlocking, prio_low) != cudaSuccess)
         return bail(err(LPA_ERR_CUDA, "stream creation failed"));
     S->vfree = RangeAlloc(S->V);
     S->efree = RangeAlloc(S->E);
@@ -583,10 +595,7 @@ lpa_status lpa_serve_submit(lpa_server_t S, int64_t n, int64_t nnz, const int64_
     if (!offsets || (nnz > 0 && !indices)) return err(LPA_ERR_INVALID_ARG, "offsets or indices is NULL");
     const bool solo = S->cfg.solo_min_entries > 0 && nnz >= S->cfg.solo_min_entries;
     if (offsets[0] != 0 || offsets[n] != nnz) return err(LPA_ERR_INVALID_GRAPH, "offsets must start at 0 and end at nnz");
-    if (n == 0 || solo) {
-        lpa_status rs = check_host_csr(n, nnz, offsets, indices, weights);
-        if (rs != LPA_OK) return rs;
-    }
+
     {
         std::lock_guard<std::mutex> lock(S->mu);
         if (!S->fatal.empty()) return err(LPA_ERR_CUDA, S->fatal);
@@ -616,10 +625,30 @@ lpa_status lpa_serve_submit(lpa_server_t S, int64_t n, int64_t nnz, const int64_
             delete r;
             return LPA_OK;
         }
-        r->off.assign(offsets, offsets + n + 1);
-        r->idx.assign(indices, indices + nnz);
-        if (weights) r->w.assign(weights, weights + nnz);
         S->results[r->ticket] = Result();
+    }
+    if (solo) {
+        // upload on the solo copy stream and wait, so the caller may reuse its buffers
+        cudaStream_t st = S->solo_copy_st;
+        cudaError_t e = cudaMallocAsync(&r->d_off, (size_t)(n + 1) * 8, st);
+        if (e == cudaSuccess && nnz) e = cudaMallocAsync(&r->d_idx, (size_t)nnz * 4, st);
+        if (e == cudaSuccess && nnz && weights) e = cudaMallocAsync(&r->d_w, (size_t)nnz * 4, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r->d_off, offsets, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(r->d_idx, indices, (size_t)nnz * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && nnz && weights)
+            e = cudaMemcpyAsync(r->d_w, weights, (size_t)nnz * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        std::lock_guard<std::mutex> lock(S->mu);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            if (r->d_off) cudaFreeAsync(r->d_off, st);
+            if (r->d_idx) cudaFreeAsync(r->d_idx, st);
+            if (r->d_w) cudaFreeAsync(r->d_w, st);
+            S->solo_bytes -= r->est_bytes;
+            S->results.erase(r->ticket);
+            delete r;
+            return err(e == cudaErrorMemoryAllocation ? LPA_ERR_OUT_OF_MEMORY : LPA_ERR_CUDA, "solo upload failed");
+        }
         S->solo_q.push_back(r);
         S->cv.notify_all();
         return LPA_OK;
@@ -747,7 +776,11 @@ lpa_status lpa_serve_destroy(lpa_server_t S) {
         if (kv.second->ready) cudaEventDestroy(kv.second->ready);
         delete kv.second;
     }
-    for (Request* r : S->solo_q) delete r;
+    for (Request* r : S->solo_q) {
+        free_solo_upload(S, r);
+        delete r;
+    }
+    if (S->solo_st) cudaStreamSynchronize(S->solo_st);
     free_server(S);
     delete S;
     return LPA_OK;

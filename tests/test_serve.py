@@ -96,6 +96,14 @@ def test_serve_busy_then_admitted_and_solo_lane():
         with pytest.raises(lpa.LpaError) as e:
             lpa.lpa_serve_fetch(srv, 987654, 1)
         assert e.value.status == lpa.LPA_ERR_NOT_FOUND
+        # a malformed solo-lane request is validated on the device and fails at fetch
+        bad_idx = big.idx.copy()
+        bad_idx[big.nnz // 3] = big.n
+        tbad = lpa.lpa_serve_submit(srv, big.n, big.nnz, big.off, bad_idx, big.w)
+        _drain(lpa, srv, [tbad])
+        with pytest.raises(lpa.LpaError) as e:
+            lpa.lpa_serve_fetch(srv, tbad, big.n)
+        assert e.value.status == lpa.LPA_ERR_INVALID_GRAPH
     finally:
         lpa.lpa_serve_destroy(srv)
 
