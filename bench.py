@@ -95,7 +95,7 @@ WORKLOAD_TEXT = {
 # the kernel in one step of the profiled run path), valid only while the
 # kernel's sources are unchanged (sha1 of the files below).
 TRAFFIC = {
-    "k_sweep_small": {"bytes_per_launch": 612.8e6, "sha1": "f34031815ca228e13e27caeabce4c1853a0f6deb",
+    "k_sweep_small": {"bytes_per_launch": 432.5e6, "sha1": "e270bbc9668336baadeea0353dfaaf4567437527",
                       "files": ["lpa_sweep_small.cu", "lpa_device.cuh", "lpa_internal.h"]},
 }
 
