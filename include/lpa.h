@@ -66,6 +66,19 @@ typedef enum {
     LPA_MODE_SYNC_FULL = 2
 } lpa_mode;
 
+/* OR into the mode of lpa_run / lpa_run_profiled / lpa_batch_run / lpa_autotune
+ * for the non-strict tie-break of Section 4.1.5 (one of the most weighted
+ * labels "at random, using a simple modulo operator on the label id"), read
+ * as: vertex i (id within its graph) in its graph's sweep t draws
+ * r = SplitMix64((t << 32) | i) mod n and takes, among the most weighted
+ * labels, the first one at or after r in cyclic label order (the label c
+ * minimising (c - r) mod n, c within the graph).  Deterministic, so the
+ * synchronous modes stay exact; since a non-strict pick depends on the sweep,
+ * pruning no longer leaves the result unchanged, and LPA_MODE_SYNC |
+ * LPA_NONSTRICT runs as LPA_MODE_SYNC_FULL (every vertex every sweep).
+ * Not accepted by lpa_serve_*. */
+#define LPA_NONSTRICT 0x100
+
 /* lpa_graph_create / lpa_batch_create flags */
 #define LPA_HOST_PTRS   0u  /* offsets/indices/weights are host memory; the library copies them */
 #define LPA_DEVICE_PTRS 1u  /* they are device memory; the library copies them (unless LPA_BORROW) */

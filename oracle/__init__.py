@@ -50,10 +50,12 @@ def build(force: bool = False) -> str:
 
 
 def _bind(lib):
-    for name in ("oracle_lpa_sync", "oracle_lpa_async", "oracle_lpa_async_order", "oracle_sync_sweep",
+    for name in ("oracle_lpa_sync", "oracle_lpa_async", "oracle_lpa_async_order", "oracle_lpa_sync_nonstrict",
+                 "oracle_lpa_async_nonstrict", "oracle_sync_sweep",
                  "oracle_count_labels_outside_component", "oracle_count_not_local_max"):
         getattr(lib, name).restype = _i64
     lib.oracle_pick.restype = ctypes.c_int32
+    lib.oracle_pick_nonstrict.restype = ctypes.c_int32
     lib.oracle_modularity.restype = ctypes.c_int
     return lib
 
@@ -101,10 +103,15 @@ def _check(ret, what):
     return ret
 
 
-def pick(off, idx, w, C, i, _lib_override=None) -> int:
+def pick(off, idx, w, C, i, sweep=None, _lib_override=None) -> int:
+    """Eq. 2 for vertex i given labels C; sweep=t (>= 1) selects the non-strict
+    tie-break of sweep t, None the strict one."""
     n, off, idx, w = _csr(off, idx, w)
     C = np.ascontiguousarray(C, dtype=np.int32)
-    return _check((_lib_override or _load()).oracle_pick(_i64(n), _p(off), _p(idx), _p(w), _p(C), _i64(i)), "pick")
+    lib = _lib_override or _load()
+    if sweep is None:
+        return _check(lib.oracle_pick(_i64(n), _p(off), _p(idx), _p(w), _p(C), _i64(i)), "pick")
+    return _check(lib.oracle_pick_nonstrict(_i64(n), _p(off), _p(idx), _p(w), _p(C), _i64(i), _i64(sweep)), "pick")
 
 
 def sync_sweep(off, idx, w, C_in, _lib_override=None):
@@ -126,19 +133,23 @@ def _run(fn, off, idx, w, tau, max_iters):
     return C, int(it), hist[:it].copy()
 
 
-def lpa_sync(off, idx, w=None, tau=0.05, max_iters=20, _lib_override=None):
-    """Synchronous LPA; returns (labels, iterations, changed-per-sweep)."""
-    return _run((_lib_override or _load()).oracle_lpa_sync, off, idx, w, tau, max_iters)
-
-
-def lpa_async(off, idx, w=None, tau=0.05, max_iters=20, order=None, _lib_override=None):
-    """Algorithm 1, one thread; the vertex loop visits `order` (a permutation of
-    0..n-1; default ascending) in every sweep.  Returns (labels, iterations, changed)."""
+def lpa_sync(off, idx, w=None, tau=0.05, max_iters=20, nonstrict=False, _lib_override=None):
+    """Synchronous LPA (strict or non-strict tie-break); returns (labels,
+    iterations, changed-per-sweep)."""
     lib = _lib_override or _load()
-    if order is None:
+    return _run(lib.oracle_lpa_sync_nonstrict if nonstrict else lib.oracle_lpa_sync, off, idx, w, tau, max_iters)
+
+
+def lpa_async(off, idx, w=None, tau=0.05, max_iters=20, order=None, nonstrict=False, _lib_override=None):
+    """Algorithm 1, one thread; the vertex loop visits `order` (a permutation of
+    0..n-1; default ascending) in every sweep; strict or non-strict tie-break.
+    Returns (labels, iterations, changed)."""
+    lib = _lib_override or _load()
+    if order is None and not nonstrict:
         return _run(lib.oracle_lpa_async, off, idx, w, tau, max_iters)
-    order = np.ascontiguousarray(order, dtype=np.int64)
-    fn = lambda n, o, i, ww, t, m, C, h: lib.oracle_lpa_async_order(n, o, i, ww, t, m, _p(order), C, h)
+    order = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+    f = lib.oracle_lpa_async_nonstrict if nonstrict else lib.oracle_lpa_async_order
+    fn = lambda n, o, i, ww, t, m, C, h: f(n, o, i, ww, t, m, _p(order), C, h)
     return _run(fn, off, idx, w, tau, max_iters)
 
 

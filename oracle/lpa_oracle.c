@@ -27,6 +27,11 @@
  *                        processed when visited and, when its label changes,
  *                        all of its neighbours other than itself are marked
  *                        unprocessed (vertex pruning, Section 4.1.4).
+ *   - *_nonstrict:       the same with the non-strict tie-break (Section
+ *                        4.1.5, "a modulo on the label id"), read as: in
+ *                        sweep t, vertex i draws r = SplitMix64((t << 32) | i)
+ *                        mod n and takes the most weighted label c minimising
+ *                        (c - r) mod n.
  *   - oracle_modularity: Eq. 1 (Section 3.2) in its community form, all sums
  *                        in fp64.
  *   - checkers used by the tests on any output (labels inside the vertex's
@@ -122,12 +127,60 @@ static int32_t most_weighted_label(const kv_table *H) {
     return best;
 }
 
-static int32_t pick(kv_table *H, const int64_t *off, const int32_t *idx, const float *w,
-                    const int32_t *C, int64_t i) {
+/* SplitMix64 (Steele, Lea & Flood, OOPSLA 2014; the generator's output
+ * function applied to state x): the counter-based draw of the non-strict
+ * tie-break. */
+static uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Non-strict LPA (Section 4.1.5) picks one of the most weighted labels at
+ * random with a modulo on the label id.  Read here as: for vertex i in sweep t
+ * (1-based), draw r = SplitMix64((t << 32) | i) mod n and take, among the
+ * most weighted labels, the first one at or after r in cyclic label order,
+ * i.e. the one minimising (c - r) mod n. */
+static int32_t most_weighted_label_rotated(const kv_table *H, int64_t n, uint64_t r) {
+    int32_t best = -1;
+    double best_w = 0.0;
+    int64_t best_key = 0;
+    for (int64_t k = 0; k < H->nkeys; ++k) {
+        int32_t c = H->keys[k];
+        double v = H->val[c];
+        int64_t key = ((int64_t)c - (int64_t)r) % n;
+        if (key < 0) key += n;
+        if (best < 0 || v > best_w || (v == best_w && key < best_key)) {
+            best = c;
+            best_w = v;
+            best_key = key;
+        }
+    }
+    return best;
+}
+
+/* Pick for vertex i; sweep t >= 1 selects the non-strict tie-break, t == 0
+ * the strict one. */
+static int32_t pick_t(kv_table *H, int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                      const int32_t *C, int64_t i, int64_t t) {
     int64_t used = scan_communities(H, off, idx, w, C, i);
-    int32_t c = used ? most_weighted_label(H) : C[i];
+    int32_t c = C[i];
+    if (used) {
+        if (t > 0) {
+            const uint64_t r = splitmix64(((uint64_t)t << 32) | (uint64_t)i) % (uint64_t)n;
+            c = most_weighted_label_rotated(H, n, r);
+        } else {
+            c = most_weighted_label(H);
+        }
+    }
     kv_clear(H);
     return c;
+}
+
+static int32_t pick(kv_table *H, const int64_t *off, const int32_t *idx, const float *w,
+                    const int32_t *C, int64_t i) {
+    return pick_t(H, 0, off, idx, w, C, i, 0);
 }
 
 static int check_csr(int64_t n, const int64_t *off, const int32_t *idx) {
@@ -175,8 +228,9 @@ int64_t oracle_sync_sweep(int64_t n, const int64_t *off, const int32_t *idx, con
 
 /* Synchronous LPA.  C_out: int32[n]; changed_hist (nullable): int64[max_iters]
  * receives dN of each sweep.  Returns the number of sweeps performed. */
-int64_t oracle_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
-                        double tau, int64_t max_iters, int32_t *C_out, int64_t *changed_hist) {
+static int64_t lpa_sync_impl(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                             double tau, int64_t max_iters, int nonstrict, int32_t *C_out,
+                             int64_t *changed_hist) {
     if (check_csr(n, off, idx) || !C_out || max_iters < 0 || !(tau >= 0.0)) return ORACLE_BAD_ARG;
     for (int64_t i = 0; i < n; ++i) C_out[i] = (int32_t)i;          /* C <- [0 .. |V|) */
     if (n == 0) return 0;
@@ -189,7 +243,7 @@ int64_t oracle_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const
         memcpy(prev, C_out, (size_t)n * sizeof(int32_t));
         int64_t dN = 0;
         for (int64_t i = 0; i < n; ++i) {
-            C_out[i] = pick(&H, off, idx, w, prev, i);
+            C_out[i] = pick_t(&H, n, off, idx, w, prev, i, nonstrict ? it + 1 : 0);
             dN += (C_out[i] != prev[i]);
         }
         if (changed_hist) changed_hist[it] = dN;
@@ -201,14 +255,26 @@ int64_t oracle_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const
     return it;
 }
 
+/* Synchronous LPA, strict tie-break. */
+int64_t oracle_lpa_sync(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                        double tau, int64_t max_iters, int32_t *C_out, int64_t *changed_hist) {
+    return lpa_sync_impl(n, off, idx, w, tau, max_iters, 0, C_out, changed_hist);
+}
+
+/* Synchronous LPA with the non-strict tie-break (sweeps t = 1, 2, ...). */
+int64_t oracle_lpa_sync_nonstrict(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                                  double tau, int64_t max_iters, int32_t *C_out, int64_t *changed_hist) {
+    return lpa_sync_impl(n, off, idx, w, tau, max_iters, 1, C_out, changed_hist);
+}
+
 /* Algorithm 1 (lpa / lpaMove / scanCommunities) run by a single thread that
  * visits the vertices in the order given by `order` (a permutation of
  * 0..n-1; NULL: ascending) in every sweep.  Algorithm 1 leaves the order of
- * its vertex loop open; any order is one of its executions.  Returns the
- * number of sweeps. */
-int64_t oracle_lpa_async_order(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
-                               double tau, int64_t max_iters, const int64_t *order, int32_t *C_out,
-                               int64_t *changed_hist) {
+ * its vertex loop open; any order is one of its executions.  nonstrict: the
+ * non-strict tie-break of sweep it + 1.  Returns the number of sweeps. */
+static int64_t lpa_async_impl(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                              double tau, int64_t max_iters, const int64_t *order, int nonstrict,
+                              int32_t *C_out, int64_t *changed_hist) {
     if (check_csr(n, off, idx) || !C_out || max_iters < 0 || !(tau >= 0.0)) return ORACLE_BAD_ARG;
     if (order) {                                                     /* must be a permutation */
         uint8_t *hit = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
@@ -233,7 +299,7 @@ int64_t oracle_lpa_async_order(int64_t n, const int64_t *off, const int32_t *idx
             const int64_t i = order ? order[k] : k;
             if (!unprocessed[i]) continue;
             unprocessed[i] = 0;                                      /* prune */
-            int32_t c = pick(&H, off, idx, w, C_out, i);
+            int32_t c = pick_t(&H, n, off, idx, w, C_out, i, nonstrict ? it + 1 : 0);
             if (c == C_out[i]) continue;
             C_out[i] = c;
             ++dN;
@@ -247,6 +313,32 @@ int64_t oracle_lpa_async_order(int64_t n, const int64_t *off, const int32_t *idx
     kv_free(&H);
     free(unprocessed);
     return it;
+}
+
+/* Eq. 2 for vertex i with the non-strict tie-break of sweep t (t >= 1). */
+int32_t oracle_pick_nonstrict(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                              const int32_t *C, int64_t i, int64_t t) {
+    if (check_csr(n, off, idx) || i < 0 || i >= n || !C || t < 1) return ORACLE_BAD_ARG;
+    kv_table H;
+    if (kv_init(&H, n)) return ORACLE_NO_MEM;
+    int32_t c = pick_t(&H, n, off, idx, w, C, i, t);
+    kv_free(&H);
+    return c;
+}
+
+/* Algorithm 1 by one thread in the given vertex order, strict tie-break. */
+int64_t oracle_lpa_async_order(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                               double tau, int64_t max_iters, const int64_t *order, int32_t *C_out,
+                               int64_t *changed_hist) {
+    return lpa_async_impl(n, off, idx, w, tau, max_iters, order, 0, C_out, changed_hist);
+}
+
+/* Algorithm 1 by one thread in the given vertex order (NULL: ascending) with
+ * the non-strict tie-break. */
+int64_t oracle_lpa_async_nonstrict(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
+                                   double tau, int64_t max_iters, const int64_t *order, int32_t *C_out,
+                                   int64_t *changed_hist) {
+    return lpa_async_impl(n, off, idx, w, tau, max_iters, order, 1, C_out, changed_hist);
 }
 
 /* Algorithm 1 by one thread in ascending vertex order. */

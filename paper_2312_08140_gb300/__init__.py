@@ -39,6 +39,7 @@ MODES = {"sync": LPA_MODE_SYNC, "async": LPA_MODE_ASYNC, "sync_full": LPA_MODE_S
 LPA_HOST_PTRS = 0
 LPA_DEVICE_PTRS = 1
 LPA_BORROW = 2
+LPA_NONSTRICT = 0x100
 
 LPA_MAX_RECORDED_ITERS = 64
 LPA_BINS = 5
@@ -257,7 +258,14 @@ def lpa_graph_set_config(g, cfg: LpaConfig):
 
 
 def _mode(m):
-    return MODES[m] if isinstance(m, str) else int(m)
+    """"sync", "async", "sync_full", each optionally with a "+nonstrict" suffix
+    (LPA_NONSTRICT), or an int."""
+    if isinstance(m, str):
+        base, _, flag = m.partition("+")
+        if flag not in ("", "nonstrict"):
+            raise ValueError(f"unknown mode {m!r}")
+        return MODES[base] | (LPA_NONSTRICT if flag else 0)
+    return int(m)
 
 
 def lpa_run(g, mode, tolerance, max_iters, labels_out, stream=None, info=True):

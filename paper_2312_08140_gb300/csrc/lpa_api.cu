@@ -139,8 +139,8 @@ struct Engine {
     lpa_config cfg{4, 128, 512, 2048, 500};
     int block_grid[kBlockBins] = {0, 0, 0};
     Overflow* ovf = nullptr;
-    cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
-    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    cudaGraph_t graph[6] = {};         // per mode, strict (0..2) and non-strict (3..5)
+    cudaGraphExec_t exec[6] = {};
     cudaStream_t cap_top = nullptr, cap_body = nullptr;
     // modularity scratch
     double* Sigma = nullptr;
@@ -169,7 +169,7 @@ lpa_status dalloc_t(Engine& E, T** p, size_t count) {
 }
 
 void destroy_graphs(Engine& E) {
-    for (int m = 0; m < 3; ++m) {
+    for (int m = 0; m < 6; ++m) {
         if (E.exec[m]) cudaGraphExecDestroy(E.exec[m]);
         if (E.graph[m]) cudaGraphDestroy(E.graph[m]);
         E.exec[m] = nullptr;
@@ -420,21 +420,26 @@ cudaError_t enqueue_pass(Engine& E, int mode, cudaStream_t st) {
 // them within the same sweep -- the parallel counterpart of the serial loop,
 // where a vertex re-marked by an earlier vertex is scanned again later in the
 // same sweep -- then the finish kernel.
+// `mode` may carry kModeNonstrict, which only the sweep kernels take.
 cudaError_t enqueue_sweep(Engine& E, int mode, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) {
+    const int base = mode & ~kModeNonstrict;
     cudaError_t err = enqueue_pass(E, mode, st);
     if (err != cudaSuccess) return err;
-    if (mode == MODE_ASYNC) {
-        err = launch_finish(E.s, mode, 1, h, in_graph, st, E.sms);
+    if (base == MODE_ASYNC) {
+        err = launch_finish(E.s, base, 1, h, in_graph, st, E.sms);
         if (err != cudaSuccess) return err;
         err = enqueue_pass(E, mode, st);
         if (err != cudaSuccess) return err;
     }
-    return launch_finish(E.s, mode, 0, h, in_graph, st, E.sms);
+    return launch_finish(E.s, base, 0, h, in_graph, st, E.sms);
 }
+
+int graph_index(int mode) { return (mode & ~kModeNonstrict) + ((mode & kModeNonstrict) ? 3 : 0); }
 
 // Graph for one mode:  init -> init_cond -> WHILE { sweep } -> finalize
 lpa_status build_graph(Engine& E, int mode) {
-    if (E.exec[mode]) return LPA_OK;
+    const int gi = graph_index(mode);
+    if (E.exec[gi]) return LPA_OK;
     cudaGraph_t top = nullptr;
     LPA_CUDA(cudaGraphCreate(&top, 0));
     cudaGraphConditionalHandle h;
@@ -491,9 +496,20 @@ lpa_status build_graph(Engine& E, int mode) {
     cudaGraphExec_t ex = nullptr;
     err = cudaGraphInstantiate(&ex, top, 0);
     if (err != cudaSuccess) return bail(err, "instantiate");
-    E.graph[mode] = top;
-    E.exec[mode] = ex;
+    E.graph[gi] = top;
+    E.exec[gi] = ex;
     return LPA_OK;
+}
+
+// The mode argument of the run calls: an lpa_mode, optionally | LPA_NONSTRICT.
+// Pruning is exact in the synchronous mode only for the strict tie-break (a
+// pick depends on the neighbours' labels alone); a non-strict pick also
+// depends on the sweep, so the synchronous mode then scans every vertex in
+// every sweep.
+void split_mode(int& mode, int& nonstrict) {
+    nonstrict = (mode & (int)LPA_NONSTRICT) ? 1 : 0;
+    mode &= ~(int)LPA_NONSTRICT;
+    if (nonstrict && mode == MODE_SYNC) mode = MODE_SYNC_FULL;
 }
 
 lpa_status check_run_args(const Engine& E, int mode, float tol, int32_t max_iters, const int32_t* labels_out) {
@@ -535,6 +551,8 @@ lpa_status collect_info(Engine& E, cudaStream_t st, lpa_run_info* infos, int32_t
 
 lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t* labels_out, cudaStream_t st,
                       lpa_run_info* infos, int local_ids) {
+    int ns = 0;
+    split_mode(mode, ns);
     lpa_status rs = check_run_args(E, mode, tol, max_iters, labels_out);
     if (rs != LPA_OK) return rs;
     if (E.s.N == 0) {
@@ -544,9 +562,10 @@ lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t
         }
         return LPA_OK;
     }
-    if ((rs = build_graph(E, mode)) != LPA_OK) return rs;
-    LPA_CUDA(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, labels_out, local_ids, st));
-    LPA_CUDA(cudaGraphLaunch(E.exec[mode], st));
+    const int lm = mode | (ns ? kModeNonstrict : 0);
+    if ((rs = build_graph(E, lm)) != LPA_OK) return rs;
+    LPA_CUDA(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, ns, labels_out, local_ids, st));
+    LPA_CUDA(cudaGraphLaunch(E.exec[graph_index(lm)], st));
     ++E.runs_total;
     if (infos) return collect_info(E, st, infos, E.s.G);
     return LPA_OK;
@@ -555,11 +574,14 @@ lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t
 // Host-driven run with an event pair around every launch.
 lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters, int32_t* labels_out,
                                cudaStream_t st, lpa_run_info* infos, lpa_profile* prof, int local_ids) {
+    const int mode_arg = mode;
+    int ns = 0;
+    split_mode(mode, ns);
     lpa_status rs = check_run_args(E, mode, tol, max_iters, labels_out);
     if (rs != LPA_OK) return rs;
     if (!prof) return fail(LPA_ERR_INVALID_ARG, "prof is NULL");
     memset(prof, 0, sizeof(*prof));
-    if (E.s.N == 0) return engine_run(E, mode, tol, max_iters, labels_out, st, infos, local_ids);
+    if (E.s.N == 0) return engine_run(E, mode_arg, tol, max_iters, labels_out, st, infos, local_ids);
     cudaEvent_t ev[kBins + 2];
     for (auto& e : ev) LPA_CUDA(cudaEventCreate(&e));
     auto cleanup = [&]() {
@@ -576,7 +598,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
             return cuda_fail(err, #call);    \
         }                                    \
     } while (0)
-    LPA_P(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, labels_out, local_ids, st));
+    LPA_P(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, ns, labels_out, local_ids, st));
     LPA_P(cudaEventRecord(ev[0], st));
     LPA_P(launch_init(E.s, st, E.sms));
     LPA_P(launch_init_cond(E.s, none, 0, st));
@@ -593,7 +615,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
         for (int p = 0; p < passes; ++p) {
             for (int b = 0; b < kBins; ++b) {
                 LPA_P(cudaEventRecord(ev[b], st));
-                if (E.s.bin_static[b]) LPA_P(launch_bin(E, mode, b, st));
+                if (E.s.bin_static[b]) LPA_P(launch_bin(E, mode | (ns ? kModeNonstrict : 0), b, st));
             }
             LPA_P(cudaEventRecord(ev[kBins], st));
             LPA_P(launch_finish(E.s, mode, p + 1 < passes ? 1 : 0, none, 0, st, E.sms));

@@ -92,13 +92,70 @@ __device__ __forceinline__ uint32_t sum_key(T s) {
     }
 }
 
-// Warp-wide argmax over (key, label): returns the winning label, or -1 when no
-// lane holds a candidate (key == 0).  All 32 lanes must call.
-__device__ __forceinline__ int32_t warp_argmax(uint32_t key, int32_t label) {
-    uint32_t m = __reduce_max_sync(kFull, key);
-    if (m == 0) return -1;
-    uint32_t cand = (key == m) ? (uint32_t)label : 0xffffffffu;
-    return (int32_t)__reduce_min_sync(kFull, cand);
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the generator's output
+// function applied to state x, the counter-based draw of the non-strict
+// tie-break.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Tie-break among the most weighted labels of one vertex (Section 4.1.5).
+// Strict: the smallest label id.  Non-strict ("a modulo on the label id"):
+// for vertex i (graph-local id) in its graph's sweep t, r = SplitMix64((t <<
+// 32) | i) mod n, and the label c minimising (c_local - r) mod n wins.  key()
+// maps a label to the value minimised (a bijection on the graph's labels, so
+// it identifies the label); label() undoes it.
+struct TieRule {
+    uint32_t r;
+    uint32_t n;
+    int32_t v0;
+    bool rot;
+    __device__ __forceinline__ uint32_t key(int32_t c) const {
+        if (!rot) return (uint32_t)c;
+        const uint32_t k = (uint32_t)(c - v0);
+        return k >= r ? k - r : k + (n - r);
+    }
+    __device__ __forceinline__ int32_t label(uint32_t k) const {
+        if (!rot) return (int32_t)k;
+        uint32_t x = k + r;
+        if (x >= n) x -= n;
+        return v0 + (int32_t)x;
+    }
+};
+
+// Rule for vertex v; ns and sweep (the single graph's 1-based sweep) are read
+// from the control block once per kernel.  In a batch each graph counts its
+// own sweeps.
+__device__ __forceinline__ TieRule tie_rule(const DevState& s, bool ns, uint32_t sweep, int32_t v) {
+    TieRule t;
+    t.r = 0;
+    t.n = 0;
+    t.v0 = 0;
+    t.rot = ns;
+    if (!ns) return t;
+    int64_t v0 = 0, n = s.N;
+    if (s.G > 1) {
+        const int32_t g = s.gid[v];
+        v0 = s.g_begin[g];
+        n = s.g_end[g] - v0;
+        sweep = (uint32_t)s.iters[g] + 1u;
+    }
+    t.v0 = (int32_t)v0;
+    t.n = (uint32_t)n;
+    t.r = (uint32_t)(splitmix64(((uint64_t)sweep << 32) | (uint64_t)(v - v0)) % (uint64_t)n);
+    return t;
+}
+
+// Warp-wide argmax over (sum key, tie key): the largest sum key, then the
+// smallest tie key.  Returns the winning tie key, or 0xffffffff when no lane
+// holds a candidate (sum key == 0).  All 32 lanes must call.
+__device__ __forceinline__ uint32_t warp_argmax_tie(uint32_t key, uint32_t tie) {
+    const uint32_t m = __reduce_max_sync(kFull, key);
+    if (m == 0) return 0xffffffffu;
+    return __reduce_min_sync(kFull, key == m ? tie : 0xffffffffu);
 }
 
 __device__ __forceinline__ int ceil_log2(uint32_t x) {  // x >= 1

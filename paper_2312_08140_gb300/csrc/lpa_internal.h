@@ -34,6 +34,9 @@ constexpr int32_t kEmptyKey = -1;       // free slot in label tables; labels are
 // are at most 255, as uint8 (sums are uint32 in both), or float.
 enum WeightKind : int { W_UNIT = 0, W_U32 = 1, W_F32 = 2, W_U8 = 3 };
 enum Mode : int { MODE_SYNC = 0, MODE_ASYNC = 1, MODE_SYNC_FULL = 2 };
+// OR'd into the mode passed to the sweep launchers: instantiate the
+// non-strict tie-break (compile-time, so the strict kernels are unchanged).
+constexpr int kModeNonstrict = 8;
 
 // Control block, one per engine, in device memory.
 struct Ctrl {
@@ -71,6 +74,8 @@ struct Ctrl {
     long long total_sweeps;              // cumulative over all runs (never reset)
     long long total_scanned;
     long long total_sweep_launches;      // kernel launches of those sweeps
+    int32_t nonstrict;                   // non-strict tie-break for this run (Section 4.1.5)
+    int32_t nonstrict_pad;
     unsigned long long ovf_count;        // overflow rows appended in this pass
     unsigned int ovf_slice_items;        // work items of the overflow kernels (set by k_ovf_plan)
     unsigned int ovf_part_items;
@@ -182,8 +187,8 @@ cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, in
 cudaError_t launch_finish(const DevState& s, int mode, int role, cudaGraphConditionalHandle h, int in_graph,
                           cudaStream_t st, int sms);
 cudaError_t launch_finalize(const DevState& s, cudaStream_t st, int sms);
-cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int32_t* labels_out,
-                              int local_ids, cudaStream_t st);
+cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int nonstrict,
+                              int32_t* labels_out, int local_ids, cudaStream_t st);
 cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms);
 cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int sms);
 // Block-per-vertex sweep of bin 2, 3 or 4; `blocks` from block_grid_for.

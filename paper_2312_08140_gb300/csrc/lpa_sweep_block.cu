@@ -13,12 +13,14 @@
 // Last bin (d > large_max): the table has kLargeSlots slots.  Rows longer than
 // kLargeSlots / 2 may carry more distinct labels than it holds; their inserts
 // probe a bounded number of slots and, if one fails, the block stops and
-// appends the row to an overflow list.  A second kernel (k_sweep_parts) then
-// rescans each overflowed row with parts = ceil(2d / kLargeSlots) blocks:
-// block p aggregates only the labels whose hash lands in partition p (about
-// d / parts distinct labels at most, half of the table, so an insert always
-// finds a slot), folds its winner into a 64-bit atomicMax of
-// (sum << 32 | ~label) -- larger sum first, then smaller label -- and the
+// appends the row to an overflow list.  The row's labels are then split over
+// parts = ceil(2d / kLargeSlots) hash partitions (about d / parts distinct
+// labels each at most, half of the table, so an insert always finds a slot):
+// rows of up to 8 partitions are rescanned by one block per partition
+// (k_sweep_parts); longer rows are read once in slices grouped by partition
+// (k_ovf_slices) and aggregated by one block per partition (k_ovf_parts).
+// Each partition's winner is folded into a 64-bit atomicMax of
+// (sum << 32 | ~tie key) -- larger sum first, then the tie-break -- and the
 // block that completes the row applies the result.  No block waits on another.
 #include "lpa_device.cuh"
 
@@ -28,52 +30,55 @@ constexpr int kSharedProbes = 16;
 constexpr int kUnroll = 4;          // chunks of 32 entries in flight per warp
 constexpr int kSliceThreads = 512;  // blocks of the sliced overflow path
 
-// Block-wide argmax of one (key, label) candidate per thread; returns the
-// winner (or -1) to every thread.  Uses red_key/red_lab (32 entries) and
-// `winner` in shared memory.
-__device__ __forceinline__ int32_t block_argmax(uint32_t key, int32_t label, uint32_t* red_key, int32_t* red_lab,
-                                                int32_t* winner) {
+// Block-wide argmax of one (sum key, tie key) candidate per thread: the
+// largest sum key, then the smallest tie key.  Returns the winning tie key
+// (0xffffffff when no thread holds a candidate) to every thread.  Uses
+// red_key/red_tie (32 entries) and `winner` in shared memory.
+__device__ __forceinline__ uint32_t block_argmax(uint32_t key, uint32_t tie, uint32_t* red_key, uint32_t* red_tie,
+                                                 uint32_t* winner) {
     const unsigned lane = lane_id();
     const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const uint32_t m = __reduce_max_sync(kFull, key);
-    const uint32_t c = __reduce_min_sync(kFull, (m != 0 && key == m) ? (uint32_t)label : 0xffffffffu);
+    const uint32_t c = __reduce_min_sync(kFull, (m != 0 && key == m) ? tie : 0xffffffffu);
     if (lane == 0) {
         red_key[wib] = m;
-        red_lab[wib] = (int32_t)c;
+        red_tie[wib] = c;
     }
     __syncthreads();
     if (wib == 0) {
         const uint32_t kk = (int)lane < nw ? red_key[lane] : 0u;
-        const int32_t ll = (int)lane < nw ? red_lab[lane] : 0;
-        const int32_t w = warp_argmax(kk, ll);
+        const uint32_t tt = (int)lane < nw ? red_tie[lane] : 0xffffffffu;
+        const uint32_t w = warp_argmax_tie(kk, tt);
         if (lane == 0) *winner = w;
     }
     __syncthreads();
     return *winner;
 }
 
-// Scans table slots [0, slots) for this thread's best candidate and clears
-// the slots it visits.
+// Scans table slots [0, slots) for this thread's best candidate under the
+// row's tie rule (sum key, tie key) and clears the slots it visits.
 template <typename T>
-__device__ __forceinline__ void scan_table(int32_t* keys, T* vals, int slots, uint32_t& key, int32_t& cand) {
+__device__ __forceinline__ void scan_table(int32_t* keys, T* vals, int slots, const TieRule& tr, uint32_t& key,
+                                           uint32_t& tie) {
     bool any = false;
     T best_w = 0;
-    int32_t best = 0x7fffffff;
+    uint32_t best_k = 0xffffffffu;
     for (int q = threadIdx.x; q < slots; q += blockDim.x) {
         const int32_t kq = keys[q];
         if (kq != kEmptyKey) {
             const T vq = vals[q];
-            if (!any || vq > best_w || (vq == best_w && kq < best)) {
+            const uint32_t tq = tr.key(kq);
+            if (!any || vq > best_w || (vq == best_w && tq < best_k)) {
                 any = true;
                 best_w = vq;
-                best = kq;
+                best_k = tq;
             }
             keys[q] = kEmptyKey;
             vals[q] = (T)0;
         }
     }
     key = any ? sum_key(best_w) : 0u;
-    cand = best;
+    tie = best_k;
 }
 
 __device__ __forceinline__ void mark_neighbours(const DevState& s, int32_t v, int64_t st, int64_t en) {
@@ -86,7 +91,7 @@ __device__ __forceinline__ void mark_neighbours(const DevState& s, int32_t v, in
 // U: chunks in flight per warp (4 for the last bin, whose rows span many
 // chunks per warp; 1 for the middle bins, where the SM's 64 warps already
 // overlap the few chunks of each row).
-template <bool ASYNC, int WK, bool BATCH, int U>
+template <bool ASYNC, int WK, bool BATCH, int U, bool NS>
 __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -94,9 +99,9 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
     int32_t* keys = reinterpret_cast<int32_t*>(smem_raw);
     T* vals = reinterpret_cast<T*>(keys + S);
     __shared__ uint32_t red_key[32];
-    __shared__ int32_t red_lab[32];
+    __shared__ uint32_t red_tie[32];
     __shared__ int overflow;
-    __shared__ int32_t winner;
+    __shared__ uint32_t winner;
 
     const unsigned lane = lane_id();
     const int wib = threadIdx.x >> 5;
@@ -111,6 +116,7 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
     const BinView bv = bin_view(s, bin);
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
+    const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
     const unsigned cnt = bv.cnt;
     const int log_S = ceil_log2((unsigned)S);
     unsigned long long my_changed = 0, my_changed_entries = 0;
@@ -174,11 +180,12 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
             }
         }
         __syncthreads();
-        uint32_t key;
-        int32_t cand;
-        scan_table<T>(keys, vals, 1 << log_s, key, cand);     // also clears the table
+        const TieRule tr = tie_rule(s, NS, sweep, v);
+        uint32_t key, tie;
+        scan_table<T>(keys, vals, 1 << log_s, tr, key, tie);     // also clears the table
         const int ovf = overflow;
-        const int32_t best_lab = block_argmax(key, cand, red_key, red_lab, &winner);
+        const uint32_t best_tie = block_argmax(key, tie, red_key, red_tie, &winner);
+        const int32_t best_lab = best_tie == 0xffffffffu ? -1 : tr.label(best_tie);
         if (ovf) {
             // hand the row to the partitioned rescan
             if (threadIdx.x == 0) {
@@ -448,22 +455,23 @@ __global__ void __launch_bounds__(kSliceThreads, 2) k_ovf_slices(DevState s) {
     }
 }
 
-// Folds a partition's winner (held by the threads whose candidate it is) into
-// the row's 64-bit atomicMax of (sum key << 32 | ~label): larger sum first,
-// then smaller label (Eq. 2; Section 4.1.5).  The block completing the row's
+// Folds a partition's winner (held by the thread whose candidate it is) into
+// the row's 64-bit atomicMax of (sum key << 32 | ~tie key): larger sum first,
+// then smaller tie key -- the smallest label when strict (Eq. 2; Section
+// 4.1.5); the row's tie rule maps the key back to its label.  The block completing the row's
 // last partition applies the result and marks the neighbours.  All threads
 // of the block must call.
 template <bool ASYNC, bool BATCH>
 __device__ __forceinline__ void fold_partition(const DevState& s, const Labels& L, const BinView& bv, Overflow& o,
-                                               bool marks, uint32_t key, int32_t cand, int32_t part_best,
-                                               unsigned long long& my_changed,
+                                               const TieRule& tr, bool marks, uint32_t key, uint32_t tie,
+                                               uint32_t part_best, unsigned long long& my_changed,
                                                unsigned long long& my_changed_entries) {
     __shared__ int resolver;
     __shared__ unsigned long long best_packed;
     if (threadIdx.x == 0) resolver = 0;
     __syncthreads();
-    if (part_best >= 0 && key != 0 && cand == part_best) {
-        const unsigned long long pk = ((unsigned long long)key << 32) | (unsigned long long)(~(uint32_t)part_best);
+    if (part_best != 0xffffffffu && key != 0 && tie == part_best) {
+        const unsigned long long pk = ((unsigned long long)key << 32) | (unsigned long long)(~part_best);
         atomicMax(&o.best, pk);
     }
     __syncthreads();
@@ -479,7 +487,7 @@ __device__ __forceinline__ void fold_partition(const DevState& s, const Labels& 
     __syncthreads();
     if (resolver) {
         const unsigned long long bp = best_packed;
-        const int32_t best_lab = (bp >> 32) ? (int32_t)(~(uint32_t)(bp & 0xffffffffull)) : -1;
+        const int32_t best_lab = (bp >> 32) ? tr.label(~(uint32_t)(bp & 0xffffffffull)) : -1;
         const int32_t own = o.own;
         const int32_t v = o.v;
         const bool changed = best_lab >= 0 && best_lab != own;
@@ -498,7 +506,7 @@ __device__ __forceinline__ void fold_partition(const DevState& s, const Labels& 
 
 // Sliced path, step 2: a block per (row, partition p) reads partition p's run
 // of every slice, aggregates it in the shared table and folds its winner.
-template <bool ASYNC, int WK, bool BATCH>
+template <bool ASYNC, int WK, bool BATCH, bool NS>
 __global__ void __launch_bounds__(kSliceThreads, 2) k_ovf_parts(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -508,8 +516,8 @@ __global__ void __launch_bounds__(kSliceThreads, 2) k_ovf_parts(DevState s, int 
     uint32_t* qpre = reinterpret_cast<uint32_t*>(vals + S);      // [kMaxSlices + 1]
     uint32_t* qstart = qpre + kMaxSlices + 1;                    // [kMaxSlices]
     __shared__ uint32_t red_key[32];
-    __shared__ int32_t red_lab[32];
-    __shared__ int32_t winner;
+    __shared__ uint32_t red_tie[32];
+    __shared__ uint32_t winner;
     for (int q = threadIdx.x; q < S; q += blockDim.x) {
         keys[q] = kEmptyKey;
         vals[q] = (T)0;
@@ -520,6 +528,7 @@ __global__ void __launch_bounds__(kSliceThreads, 2) k_ovf_parts(DevState s, int 
     const BinView bv = bin_view(s, kBins - 1);
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
+    const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
     const int log_S = ceil_log2((unsigned)S);
     const unsigned lane = lane_id();
     const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -569,11 +578,11 @@ __global__ void __launch_bounds__(kSliceThreads, 2) k_ovf_parts(DevState s, int 
             if (lead && !table_add<T>(keys, vals, log_S, lab, w)) atomicExch(&s.ctrl->error, 4);
         }
         __syncthreads();
-        uint32_t key;
-        int32_t cand;
-        scan_table<T>(keys, vals, S, key, cand);
-        const int32_t part_best = block_argmax(key, cand, red_key, red_lab, &winner);
-        fold_partition<ASYNC, BATCH>(s, L, bv, o, marks, key, cand, part_best, my_changed, my_changed_entries);
+        const TieRule tr = tie_rule(s, NS, sweep, o.v);
+        uint32_t key, tie;
+        scan_table<T>(keys, vals, S, tr, key, tie);
+        const uint32_t part_best = block_argmax(key, tie, red_key, red_tie, &winner);
+        fold_partition<ASYNC, BATCH>(s, L, bv, o, tr, marks, key, tie, part_best, my_changed, my_changed_entries);
     }
     flush_bin_counts(s, kBins - 1, my_changed, my_changed_entries);
 }
@@ -581,7 +590,7 @@ __global__ void __launch_bounds__(kSliceThreads, 2) k_ovf_parts(DevState s, int 
 // Rescan path (rows of fewer than kSliceMinParts or more than kMaxParts
 // partitions, or beyond the scratch): a block per (row, partition p) scans the
 // whole row keeping only the labels whose hash lands in partition p.
-template <bool ASYNC, int WK, bool BATCH>
+template <bool ASYNC, int WK, bool BATCH, bool NS>
 __global__ void k_sweep_parts(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -589,8 +598,8 @@ __global__ void k_sweep_parts(DevState s, int flag_neighbours) {
     int32_t* keys = reinterpret_cast<int32_t*>(smem_raw);
     T* vals = reinterpret_cast<T*>(keys + S);
     __shared__ uint32_t red_key[32];
-    __shared__ int32_t red_lab[32];
-    __shared__ int32_t winner;
+    __shared__ uint32_t red_tie[32];
+    __shared__ uint32_t winner;
 
     const unsigned lane = lane_id();
     const int wib = threadIdx.x >> 5;
@@ -606,6 +615,7 @@ __global__ void k_sweep_parts(DevState s, int flag_neighbours) {
     const BinView bv = bin_view(s, kBins - 1);
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
+    const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
     const int log_S = ceil_log2((unsigned)S);
     unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned item = blockIdx.x; item < items; item += gridDim.x) {
@@ -650,11 +660,11 @@ __global__ void k_sweep_parts(DevState s, int flag_neighbours) {
             }
         }
         __syncthreads();
-        uint32_t key;
-        int32_t cand;
-        scan_table<T>(keys, vals, S, key, cand);
-        const int32_t part_best = block_argmax(key, cand, red_key, red_lab, &winner);
-        fold_partition<ASYNC, BATCH>(s, L, bv, o, marks, key, cand, part_best, my_changed, my_changed_entries);
+        const TieRule tr = tie_rule(s, NS, sweep, o.v);
+        uint32_t key, tie;
+        scan_table<T>(keys, vals, S, tr, key, tie);
+        const uint32_t part_best = block_argmax(key, tie, red_key, red_tie, &winner);
+        fold_partition<ASYNC, BATCH>(s, L, bv, o, tr, marks, key, tie, part_best, my_changed, my_changed_entries);
     }
     flush_bin_counts(s, kBins - 1, my_changed, my_changed_entries);
 }
@@ -718,10 +728,10 @@ int block_grid_for(const DevState& s, int bin, int sms) {
     return sms * per_sm;
 }
 
-template <bool ASYNC, int WK, bool BATCH>
+template <bool ASYNC, int WK, bool BATCH, bool NS>
 static cudaError_t launch_block_t(const DevState& s, int bin, int flag, int blocks, cudaStream_t st) {
     const size_t smem = (size_t)s.block_slots[bin - 2] * 8;
-    auto kern = bin == kBins - 1 ? k_sweep_block<ASYNC, WK, BATCH, kUnroll> : k_sweep_block<ASYNC, WK, BATCH, 1>;
+    auto kern = bin == kBins - 1 ? k_sweep_block<ASYNC, WK, BATCH, kUnroll, NS> : k_sweep_block<ASYNC, WK, BATCH, 1, NS>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     kern<<<blocks, kBlockThreads[bin - 2], smem, st>>>(s, bin, flag);
@@ -736,36 +746,46 @@ static cudaError_t launch_block_t(const DevState& s, int bin, int flag, int bloc
         return err;
     k1<<<blocks, kSliceThreads, tsmem, st>>>(s);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    auto k3 = k_ovf_parts<ASYNC, WK, BATCH>;
+    auto k3 = k_ovf_parts<ASYNC, WK, BATCH, NS>;
     const size_t psmem = tsmem + (size_t)(2 * kMaxSlices + 1) * sizeof(uint32_t);
     if ((err = cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem)) != cudaSuccess)
         return err;
     k3<<<blocks, kSliceThreads, psmem, st>>>(s, flag);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    auto pk = k_sweep_parts<ASYNC, WK, BATCH>;
+    auto pk = k_sweep_parts<ASYNC, WK, BATCH, NS>;
     if ((err = cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem)) != cudaSuccess)
         return err;
     pk<<<blocks, kBlockThreads[kBlockBins - 1], tsmem, st>>>(s, flag);
     return cudaGetLastError();
 }
 
+template <bool ASYNC, bool BATCH, bool NS>
+static cudaError_t launch_block_w(const DevState& s, int bin, int flag, int blocks, cudaStream_t st) {
+    switch (s.weight_kind) {
+        case W_UNIT: return launch_block_t<ASYNC, W_UNIT, BATCH, NS>(s, bin, flag, blocks, st);
+        case W_U32: return launch_block_t<ASYNC, W_U32, BATCH, NS>(s, bin, flag, blocks, st);
+        case W_U8: return launch_block_t<ASYNC, W_U8, BATCH, NS>(s, bin, flag, blocks, st);
+        default: return launch_block_t<ASYNC, W_F32, BATCH, NS>(s, bin, flag, blocks, st);
+    }
+}
+
+template <bool NS>
+static cudaError_t launch_block_ns(const DevState& s, bool async, int bin, int flag, int blocks, cudaStream_t st) {
+    const bool batch = s.G > 1;
+    if (async)
+        return batch ? launch_block_w<true, true, NS>(s, bin, flag, blocks, st)
+                     : launch_block_w<true, false, NS>(s, bin, flag, blocks, st);
+    return batch ? launch_block_w<false, true, NS>(s, bin, flag, blocks, st)
+                 : launch_block_w<false, false, NS>(s, bin, flag, blocks, st);
+}
+
 cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int blocks, cudaStream_t st) {
+    const bool ns = (mode & kModeNonstrict) != 0;
+    mode &= ~kModeNonstrict;
     const bool async = mode == MODE_ASYNC;
     const int flag = mode != MODE_SYNC_FULL;
-    const bool batch = s.G > 1;
-#define LPA_BLOCK_W(A, B)                                                             \
-    switch (s.weight_kind) {                                                          \
-        case W_UNIT: return launch_block_t<A, W_UNIT, B>(s, bin, flag, blocks, st);   \
-        case W_U32: return launch_block_t<A, W_U32, B>(s, bin, flag, blocks, st);     \
-        case W_U8: return launch_block_t<A, W_U8, B>(s, bin, flag, blocks, st);       \
-        default: return launch_block_t<A, W_F32, B>(s, bin, flag, blocks, st);        \
-    }
-    if (async) {
-        if (batch) { LPA_BLOCK_W(true, true) } else { LPA_BLOCK_W(true, false) }
-    } else {
-        if (batch) { LPA_BLOCK_W(false, true) } else { LPA_BLOCK_W(false, false) }
-    }
-#undef LPA_BLOCK_W
+    return ns ? launch_block_ns<true>(s, async, bin, flag, blocks, st)
+              : launch_block_ns<false>(s, async, bin, flag, blocks, st);
 }
 
 }  // namespace lpa

@@ -34,16 +34,17 @@ constexpr int kRun = 8;                               // async run length
 constexpr int kTile = kRun * kSmallThreads;           // frontier entries staged per block step
 constexpr int kStride = kRun + 1;                     // shared-memory words per run
 
-template <bool ASYNC, int WK, bool BATCH, int MAXD>
+template <bool NS, int WK, bool BATCH, int MAXD>
 __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     const BinView bv = bin_view(s, 0);
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
+    const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
     // A dense pass over a bin holding most vertices walks the vertex ids
     // themselves (coalesced offsets, one dependent load less than the list)
     // and keeps those of this bin.
-    const bool iota = !ASYNC && L.dense && s.small_iota;
+    const bool iota = L.dense && s.small_iota;
     const unsigned cnt = iota ? (unsigned)s.N : bv.cnt;
     const unsigned stride = gridDim.x * blockDim.x;
     constexpr int RUN = 1;                            // async mode uses k_sweep_small_async
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
             if (act && s.done[s.gid[v]]) act = false;
         }
         int32_t own = 0;
-        if (slot) own = ASYNC ? __ldcg(L.C + v) : L.C[v];
+        if (slot) own = L.C[v];
         if (!act) {
             d = 0;
         } else if (!iota) {
@@ -84,27 +85,29 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
             const int32_t j = ok ? load_index(s.idx, st + q) : v;
             nb[q] = j;
             ok = ok && (j != v);
-            lab[q] = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
+            lab[q] = ok ? load_label<false>(L.C, j) : kEmptyKey;
             wt[q] = ok ? load_weight<WK>(s.w, st + q) : (T)0;
         }
+        const TieRule tr = tie_rule(s, NS && act, sweep, v);
         bool any = false;
         T best_w = 0;
-        int32_t best = 0x7fffffff;
+        uint32_t best_k = 0xffffffffu;
 #pragma unroll
         for (int q = 0; q < MAXD; ++q) {
             T sum = 0;
 #pragma unroll
             for (int r = 0; r < MAXD; ++r) sum += (lab[r] == lab[q]) ? wt[r] : (T)0;
-            const bool better = lab[q] != kEmptyKey &&
-                                (!any || sum > best_w || (sum == best_w && lab[q] < best));
+            const uint32_t kq = lab[q] != kEmptyKey ? tr.key(lab[q]) : 0xffffffffu;
+            const bool better = lab[q] != kEmptyKey && (!any || sum > best_w || (sum == best_w && kq < best_k));
             if (better) {
                 any = true;
                 best_w = sum;
-                best = lab[q];
+                best_k = kq;
             }
         }
+        const int32_t best = tr.label(best_k);
         const bool changed = act && any && best != own;
-        if (slot) record_label<ASYNC>(L, bv.chg + k, v, own, best, changed);
+        if (slot) record_label<false>(L, bv.chg + k, v, own, best, changed);
         if (changed) {
             if (marks) {
 #pragma unroll
@@ -125,7 +128,7 @@ __host__ __device__ constexpr size_t async_smem_bytes() {
     return (size_t)kSmallThreads * kStride * (4 + 4 + 4 * MAXD + (WK == W_UNIT ? 0 : 4 * MAXD) + 1);
 }
 
-template <int WK, bool BATCH, int MAXD>
+template <int WK, bool BATCH, int MAXD, bool NS>
 __global__ void __launch_bounds__(kSmallThreads) k_sweep_small_async(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     constexpr int SL = kSmallThreads * kStride;              // slots per array
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small_async(DevState s,
     const BinView bv = bin_view(s, 0);
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
+    const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
     const unsigned cnt = bv.cnt;
     unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned tile = blockIdx.x * (unsigned)kTile; tile < cnt; tile += gridDim.x * (unsigned)kTile) {
@@ -189,22 +193,25 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small_async(DevState s,
                     if constexpr (WK == W_UNIT) wt[q] = ok ? (T)1 : (T)0;
                     else wt[q] = ok ? sw[q * SL + pos] : (T)0;
                 }
+                const TieRule tr = tie_rule(s, NS, sweep, v);
                 bool any = false;
                 T best_w = 0;
-                int32_t best = 0x7fffffff;
+                uint32_t best_k = 0xffffffffu;
 #pragma unroll
                 for (int q = 0; q < MAXD; ++q) {
                     T sum = 0;
 #pragma unroll
                     for (int r = 0; r < MAXD; ++r) sum += (lab[r] == lab[q]) ? wt[r] : (T)0;
-                    const bool better = lab[q] != kEmptyKey &&
-                                        (!any || sum > best_w || (sum == best_w && lab[q] < best));
+                    const uint32_t kq = lab[q] != kEmptyKey ? tr.key(lab[q]) : 0xffffffffu;
+                    const bool better =
+                        lab[q] != kEmptyKey && (!any || sum > best_w || (sum == best_w && kq < best_k));
                     if (better) {
                         any = true;
                         best_w = sum;
-                        best = lab[q];
+                        best_k = kq;
                     }
                 }
+                const int32_t best = tr.label(best_k);
                 const int32_t own = sown[pos];
                 changed = any && best != own;
                 if (changed) {
@@ -227,10 +234,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small_async(DevState s,
     flush_bin_counts(s, 0, my_changed, my_changed_entries);
 }
 
-template <int WK, bool BATCH, int MAXD>
+template <int WK, bool BATCH, int MAXD, bool NS>
 static cudaError_t launch_small_async_t(const DevState& s, int flag, int sms, cudaStream_t st) {
     const size_t smem = async_smem_bytes<WK, MAXD>();
-    auto kern = k_sweep_small_async<WK, BATCH, MAXD>;
+    auto kern = k_sweep_small_async<WK, BATCH, MAXD, NS>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
@@ -240,36 +247,40 @@ static cudaError_t launch_small_async_t(const DevState& s, int flag, int sms, cu
     return cudaGetLastError();
 }
 
-template <int WK, bool BATCH>
+template <int WK, bool BATCH, bool NS>
 static cudaError_t launch_small_t(const DevState& s, bool async, int flag, int sms, cudaStream_t st) {
     const bool four = s.small_max <= 4;
     if (async) {
-        return four ? launch_small_async_t<WK, BATCH, 4>(s, flag, sms, st)
-                    : launch_small_async_t<WK, BATCH, 8>(s, flag, sms, st);
+        return four ? launch_small_async_t<WK, BATCH, 4, NS>(s, flag, sms, st)
+                    : launch_small_async_t<WK, BATCH, 8, NS>(s, flag, sms, st);
     }
-    if (four) k_sweep_small<false, WK, BATCH, 4><<<sms * 8, kSmallThreads, 0, st>>>(s, flag);
-    else k_sweep_small<false, WK, BATCH, 8><<<sms * 8, kSmallThreads, 0, st>>>(s, flag);
+    if (four) k_sweep_small<NS, WK, BATCH, 4><<<sms * 8, kSmallThreads, 0, st>>>(s, flag);
+    else k_sweep_small<NS, WK, BATCH, 8><<<sms * 8, kSmallThreads, 0, st>>>(s, flag);
     return cudaGetLastError();
 }
 
+template <int WK, bool NS>
+static cudaError_t launch_small_w(const DevState& s, bool async, int flag, int sms, cudaStream_t st) {
+    return s.G > 1 ? launch_small_t<WK, true, NS>(s, async, flag, sms, st)
+                   : launch_small_t<WK, false, NS>(s, async, flag, sms, st);
+}
+
+template <bool NS>
+static cudaError_t launch_small_ns(const DevState& s, bool async, int flag, int sms, cudaStream_t st) {
+    switch (s.weight_kind) {
+        case W_UNIT: return launch_small_w<W_UNIT, NS>(s, async, flag, sms, st);
+        case W_U32: return launch_small_w<W_U32, NS>(s, async, flag, sms, st);
+        case W_U8: return launch_small_w<W_U8, NS>(s, async, flag, sms, st);
+        default: return launch_small_w<W_F32, NS>(s, async, flag, sms, st);
+    }
+}
+
 cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms) {
+    const bool ns = (mode & kModeNonstrict) != 0;
+    mode &= ~kModeNonstrict;
     const bool async = mode == MODE_ASYNC;
     const int flag = mode != MODE_SYNC_FULL;
-    const bool batch = s.G > 1;
-    switch (s.weight_kind) {
-        case W_UNIT:
-            return batch ? launch_small_t<W_UNIT, true>(s, async, flag, sms, st)
-                         : launch_small_t<W_UNIT, false>(s, async, flag, sms, st);
-        case W_U32:
-            return batch ? launch_small_t<W_U32, true>(s, async, flag, sms, st)
-                         : launch_small_t<W_U32, false>(s, async, flag, sms, st);
-        case W_U8:
-            return batch ? launch_small_t<W_U8, true>(s, async, flag, sms, st)
-                         : launch_small_t<W_U8, false>(s, async, flag, sms, st);
-        default:
-            return batch ? launch_small_t<W_F32, true>(s, async, flag, sms, st)
-                         : launch_small_t<W_F32, false>(s, async, flag, sms, st);
-    }
+    return ns ? launch_small_ns<true>(s, async, flag, sms, st) : launch_small_ns<false>(s, async, flag, sms, st);
 }
 
 }  // namespace lpa

@@ -46,7 +46,7 @@ __device__ __forceinline__ typename Acc<WK>::T group_sum(unsigned peers, typenam
     }
 }
 
-template <bool ASYNC, int WK, bool BATCH>
+template <bool ASYNC, int WK, bool BATCH, bool NS>
 __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
     const BinView bv = bin_view(s, 1);
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
+    const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
     const unsigned cnt = bv.cnt;
     const unsigned nwarps = gridDim.x * kWarpsPerBlock;
     // each warp takes batches of B consecutive frontier entries (B <= 32), B
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
             const int32_t own = __shfl_sync(kFull, ownl, i);
             const int act = __shfl_sync(kFull, actl, i);
             const int d = (int)(en - st);
+            const TieRule tr = tie_rule(s, NS && act, sweep, v);
             const int32_t j = j_cur;
             const int32_t j_nn = first_index(i + 2);
             int32_t lab_nxt;
@@ -173,16 +175,17 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                 __syncwarp();
                 bool any = false;
                 T best_w = 0;
-                int32_t best = 0x7fffffff;
+                uint32_t best_k = 0xffffffffu;
                 const int slots = 1 << log_slots;
                 for (int q = lane; q < slots; q += 32) {
                     const int32_t kq = keys[q];
                     if (kq != kEmptyKey) {
                         const T vq = vals[q];
-                        if (!any || vq > best_w || (vq == best_w && kq < best)) {
+                        const uint32_t tq = tr.key(kq);
+                        if (!any || vq > best_w || (vq == best_w && tq < best_k)) {
                             any = true;
                             best_w = vq;
-                            best = kq;
+                            best_k = tq;
                         }
                         keys[q] = kEmptyKey;
                         vals[q] = (T)0;
@@ -191,14 +194,15 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                 __syncwarp();
                 if (any) {
                     key = sum_key(best_w);
-                    cand = best;
+                    cand = tr.label(best_k);
                 }
             }
             j_cur = j_nxt;
             j_nxt = j_nn;
             lab_cur = lab_nxt;
             w_cur = w_nxt;
-            const int32_t best = warp_argmax(key, cand);
+            const uint32_t best_key = warp_argmax_tie(key, key ? tr.key(cand) : 0xffffffffu);
+            const int32_t best = best_key == 0xffffffffu ? -1 : tr.label(best_key);
             const bool changed = act && best >= 0 && best != own;   // warp-uniform
             if (lane == 0) record_label<ASYNC>(L, bv.chg + base + i, v, own, best, changed);
             if constexpr (ASYNC) {
@@ -228,10 +232,10 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
     flush_bin_counts(s, 1, my_changed, my_changed_entries);
 }
 
-template <bool ASYNC, int WK, bool BATCH>
+template <bool ASYNC, int WK, bool BATCH, bool NS>
 static cudaError_t launch_warp_t(const DevState& s, int flag, cudaStream_t st, int sms) {
     const size_t smem = (size_t)kWarpsPerBlock * s.warp_slots * 8;
-    auto kern = k_sweep_warp<ASYNC, WK, BATCH>;
+    auto kern = k_sweep_warp<ASYNC, WK, BATCH, NS>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
@@ -242,23 +246,29 @@ static cudaError_t launch_warp_t(const DevState& s, int flag, cudaStream_t st, i
     return cudaGetLastError();
 }
 
+template <bool ASYNC, bool BATCH, bool NS>
+static cudaError_t launch_warp_w(const DevState& s, int flag, cudaStream_t st, int sms) {
+    switch (s.weight_kind) {
+        case W_UNIT: return launch_warp_t<ASYNC, W_UNIT, BATCH, NS>(s, flag, st, sms);
+        case W_U32: return launch_warp_t<ASYNC, W_U32, BATCH, NS>(s, flag, st, sms);
+        case W_U8: return launch_warp_t<ASYNC, W_U8, BATCH, NS>(s, flag, st, sms);
+        default: return launch_warp_t<ASYNC, W_F32, BATCH, NS>(s, flag, st, sms);
+    }
+}
+
+template <bool NS>
+static cudaError_t launch_warp_ns(const DevState& s, bool async, int flag, cudaStream_t st, int sms) {
+    const bool batch = s.G > 1;
+    if (async) return batch ? launch_warp_w<true, true, NS>(s, flag, st, sms) : launch_warp_w<true, false, NS>(s, flag, st, sms);
+    return batch ? launch_warp_w<false, true, NS>(s, flag, st, sms) : launch_warp_w<false, false, NS>(s, flag, st, sms);
+}
+
 cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int sms) {
+    const bool ns = (mode & kModeNonstrict) != 0;
+    mode &= ~kModeNonstrict;
     const bool async = mode == MODE_ASYNC;
     const int flag = mode != MODE_SYNC_FULL;
-    const bool batch = s.G > 1;
-#define LPA_WARP_W(A, B)                                                     \
-    switch (s.weight_kind) {                                                 \
-        case W_UNIT: return launch_warp_t<A, W_UNIT, B>(s, flag, st, sms);   \
-        case W_U32: return launch_warp_t<A, W_U32, B>(s, flag, st, sms);     \
-        case W_U8: return launch_warp_t<A, W_U8, B>(s, flag, st, sms);       \
-        default: return launch_warp_t<A, W_F32, B>(s, flag, st, sms);        \
-    }
-    if (async) {
-        if (batch) { LPA_WARP_W(true, true) } else { LPA_WARP_W(true, false) }
-    } else {
-        if (batch) { LPA_WARP_W(false, true) } else { LPA_WARP_W(false, false) }
-    }
-#undef LPA_WARP_W
+    return ns ? launch_warp_ns<true>(s, async, flag, st, sms) : launch_warp_ns<false>(s, async, flag, st, sms);
 }
 
 }  // namespace lpa

@@ -267,6 +267,43 @@ def test_hub_rows_that_overflow_the_shared_table(lpa):
     check_async(lpa, hub_graph(40000))
 
 
+def test_nonstrict_sync_matches_oracle(lpa):
+    """The non-strict tie-break (LPA_NONSTRICT, Section 4.1.5) is deterministic,
+    so the synchronous runs must match the oracle's non-strict runs exactly,
+    through every degree bin, batched graphs included."""
+    import torch
+    graphs = [L.planted_partition(n=3000, blocks=6, seed=8), L.road_grid(80, 61, seed=3),
+              L.rmat(14, 16, seed=4), hub_graph(9000)]
+    for g in graphs:
+        ref, it, ch = O.lpa_sync(g.off, g.idx, g.w, nonstrict=True)
+        for mode in ("sync+nonstrict", "sync_full+nonstrict"):
+            got, info, h = run_gpu(lpa, g, mode, 0.05, 20, None)
+            lpa.lpa_graph_destroy(h)
+            assert info["iterations"] == it and info["changed"] == ch.tolist()[:64], mode
+            assert np.array_equal(got, ref), (mode, int((got != ref).sum()))
+    batch = [L.batched_sbm_graph(gi, n_max=4000) for gi in range(8)]
+    vo, eo, off, idx, w = _batch_inputs(batch)
+    b = lpa.lpa_batch_create(len(batch), vo, eo, off, idx, w)
+    out = torch.empty(int(vo[-1]), dtype=torch.int32, device="cuda")
+    try:
+        infos = lpa.lpa_batch_run(b, len(batch), "sync+nonstrict", 0.05, 20, out)
+        got = out.cpu().numpy()
+        for k, gr in enumerate(batch):
+            ref, it, ch = O.lpa_sync(gr.off, gr.idx, gr.w, nonstrict=True)
+            assert np.array_equal(got[vo[k]:vo[k + 1]], ref), k
+            assert infos[k].iterations == it, k
+    finally:
+        lpa.lpa_batch_destroy(b)
+
+
+def test_nonstrict_async_invariants(lpa):
+    for g in (L.planted_partition(n=3000, blocks=6, seed=9), L.road_grid(120, 90, seed=5)):
+        got, info, h = run_gpu(lpa, g, "async+nonstrict", 0.05, 20, None)
+        lpa.lpa_graph_destroy(h)
+        assert O.count_labels_outside_component(g.off, g.idx, got) == 0
+        assert 1 <= info["iterations"] <= 20
+
+
 def test_pool_reuse_and_release(lpa):
     """Graph memory comes from the library's pool: graphs created after others
     were destroyed (reusing their pages), and after the cache was released,

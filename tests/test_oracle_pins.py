@@ -52,6 +52,18 @@ def test_hand_worked(case):
 
 
 # ---------------------------------------------------------------- Eq. 2 --
+def _label_sums(g, C, i):
+    """{c: K_{i->c}} over i's entries other than self-loops (Eq. 2's sums)."""
+    sums = {}
+    for e in range(int(g.off[i]), int(g.off[i + 1])):
+        j = int(g.idx[e])
+        if j == i:
+            continue
+        c = int(C[j])
+        sums[c] = sums.get(c, 0.0) + (1.0 if g.w is None else float(g.w[e]))
+    return sums
+
+
 def _enumerated_pick(g, C, i):
     """Eq. 2 by enumerating every candidate label c = 0..n-1 in increasing order:
     K_{i->c} is summed over the row directly; the first c reaching the maximum
@@ -274,15 +286,64 @@ MUTANTS = {
     "tie_to_largest": ("(v == best_w && c < best)", "(v == best_w && c > best)"),
     "strict_tolerance": ("return (double)dN / (double)n <= tau;", "return (double)dN / (double)n < tau;"),
     "unit_weights_ignored": ("return w ? (double)w[e] : 1.0;", "return 1.0;"),
-    "sync_reads_in_place": ("C_out[i] = pick(&H, off, idx, w, prev, i);", "C_out[i] = pick(&H, off, idx, w, C_out, i);"),
+    "sync_reads_in_place": ("C_out[i] = pick_t(&H, n, off, idx, w, prev, i, nonstrict ? it + 1 : 0);",
+                            "C_out[i] = pick_t(&H, n, off, idx, w, C_out, i, nonstrict ? it + 1 : 0);"),
+    "nonstrict_is_strict": ("c = most_weighted_label_rotated(H, n, r);", "c = most_weighted_label(H);"),
+    "nonstrict_rotation_reversed": ("int64_t key = ((int64_t)c - (int64_t)r) % n;", "int64_t key = ((int64_t)r - (int64_t)c) % n;"),
     "async_no_remark": ("if ((int64_t)idx[e] != i) unprocessed[idx[e]] = 1;", "(void)0;"),
     "async_counts_visits": ("if (c == C_out[i]) continue;", "if (c == C_out[i]) { ++dN; continue; }"),
     "async_order_ignored": ("const int64_t i = order ? order[k] : k;", "const int64_t i = k;"),
-    "isolated_takes_zero": ("int32_t c = used ? most_weighted_label(H) : C[i];", "int32_t c = used ? most_weighted_label(H) : 0;"),
+    "isolated_takes_zero": ("int32_t c = C[i];\n    if (used) {", "int32_t c = 0;\n    if (used) {"),
     "modularity_null_term_dropped": ("q = sigma / two_m - null_term;", "q = sigma / two_m;"),
     "modularity_sigma_by_other_end": ("Sigma[C[i]] += K_i;", "Sigma[C[idx[off[i]]]] += K_i;"),
     "cap_off_by_one": ("while (it < max_iters) {\n        memcpy", "while (it <= max_iters) {\n        memcpy"),
 }
+
+
+def _tied_star(n=1000, labels=(5, 300, 301)):
+    """Vertex 0 of an n-vertex graph joined to len(labels) vertices carrying
+    the given distinct labels (unit weights): every label of vertex 0's row
+    is tied at weight 1."""
+    g = L.from_undirected_pairs(n, [(0, k + 1) for k in range(len(labels))])
+    C = np.arange(n, dtype=np.int32)
+    for k, lab in enumerate(labels):
+        C[k + 1] = lab
+    return g, C
+
+
+def _nonstrict_frequencies(mod, sweeps=4000):
+    g, C = _tied_star()
+    picks = [mod.pick(g.off, g.idx, None, C, 0, sweep=t) for t in range(1, sweeps + 1)]
+    return {lab: picks.count(lab) / sweeps for lab in (5, 300, 301)}, set(picks)
+
+
+def _nonstrict_pins_pass(mod):
+    """Non-strict tie-break (Section 4.1.5, read as a rotation of the label
+    space by a per-(vertex, sweep) draw): the pick is always a most weighted
+    label, equals the strict pick when the maximum is unique, and over many
+    sweeps each tied label wins in proportion to the gap before it in cyclic
+    label order (label 5 of {5, 300, 301} out of 1000: 704/1000; 300:
+    295/1000; 301: 1/1000)."""
+    freq, seen = _nonstrict_frequencies(mod)
+    if not seen <= {5, 300, 301}:
+        return False
+    for lab, p in ((5, 0.704), (300, 0.295)):
+        sd = (p * (1 - p) / 4000) ** 0.5
+        if abs(freq[lab] - p) > 4 * sd:
+            return False
+    rng = np.random.default_rng(91)
+    for g, C in _random_cases(60, seed0=90000):
+        for i in range(g.n):
+            sums = _label_sums(g, C, i)
+            if not sums:
+                continue
+            m = max(sums.values())
+            tied = [c for c, v in sums.items() if v == m]
+            t = int(rng.integers(1, 30))
+            c = mod.pick(g.off, g.idx, g.w, C, i, sweep=t)
+            if c not in tied or (len(tied) == 1 and c != tied[0]):
+                return False
+    return True
 
 
 def _pins_pass(mod):
@@ -302,6 +363,8 @@ def _pins_pass(mod):
             Co, ito, ho = mod.lpa_async(g.off, g.idx, g.w)
             if Co.tolist() != C.tolist() or ito != it:
                 return False
+        if not _nonstrict_pins_pass(mod):
+            return False
         pairs = [(u, v) for u in range(5) for v in range(u + 1, 5)]
         pairs += [(u + 5, v + 5) for u, v in pairs] + [(4, 5)]
         g = L.from_undirected_pairs(10, pairs)
@@ -357,3 +420,9 @@ def test_async_order_matches_restatement_in_that_order():
         C, it, hist = _serial_async_restated(g, 0.05, 20, order=order)
         Co, ito, ho = O.lpa_async(g.off, g.idx, g.w, order=order)
         assert Co.tolist() == C.tolist() and ito == it and ho.tolist() == hist
+
+
+def test_nonstrict_tie_break_pins():
+    assert _nonstrict_pins_pass(O)
+    freq, _ = _nonstrict_frequencies(O)
+    print("non-strict tie frequencies", freq)
