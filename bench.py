@@ -454,6 +454,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--batched-graphs", type=int, default=128, help="0 skips the batched sample")
     ap.add_argument("--serving-seconds", type=float, default=0.5, help="0 skips the serving sample")
+    ap.add_argument("--tie", default="strict", choices=["strict", "nonstrict"],
+                    help="tie-break among the most weighted labels (Section 4.1.5)")
     ap.add_argument("--batched-full", action="store_true",
                     help="batched sample on the full workload: 4,096 graphs drawn on the device")
     ap.add_argument("--serving-full", action="store_true",
@@ -485,6 +487,8 @@ def main():
     wl = workload(args.workload)
     graphs = [make() for _, make in wl]
     modes = WORKLOAD_MODES.get(args.workload, MODES)
+    if args.tie == "nonstrict":
+        modes = tuple(m + "+nonstrict" for m in modes)
     stream = torch.cuda.current_stream()
     handles = [lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS, stream) for g in graphs]
     outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
@@ -571,7 +575,8 @@ def main():
             wbytes = lpa.lpa_graph_props_get(h)["weight_bytes"]     # as the sweeps read them
             for m in modes:
                 _, prof = lpa.lpa_run_profiled(h, m, TAU, MAX_ITERS, o, stream)
-                for b, d in kernel_bytes(prof.as_dict(), wbytes, m == "sync", 1 if m == "sync" else 2).items():
+                sync = not m.startswith("async")
+                for b, d in kernel_bytes(prof.as_dict(), wbytes, sync, 1 if sync else 2).items():
                     a = agg.setdefault(b, {"bytes": 0.0, "ms": 0.0, "launches": 0})
                     for k in a:
                         a[k] += d[k]
@@ -614,7 +619,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD_TEXT[args.workload], "inputs_larger_than_l2": True,
+                "config": {"workload": WORKLOAD_TEXT[args.workload], "tie_break": args.tie, "inputs_larger_than_l2": True,
                            "parallelism": f"replicas x{world}", "tau": TAU, "max_iters": MAX_ITERS},
                 "touched_edges_per_s": touched / (ms / 1e3),
                 "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
