@@ -68,7 +68,7 @@ typedef enum {
 
 /* OR into the mode of lpa_run / lpa_run_profiled / lpa_batch_run / lpa_autotune
  * for the non-strict tie-break of Section 4.1.5 (one of the most weighted
- * labels "at random, using a simple modulo operator on the label id"), read
+ * labels chosen pseudo-randomly through a modulo of the label id), read
  * as: vertex i (id within its graph) in its graph's sweep t draws
  * r = SplitMix64((t << 32) | i) mod n and takes, among the most weighted
  * labels, the first one at or after r in cyclic label order (the label c

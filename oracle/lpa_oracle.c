@@ -28,7 +28,8 @@
  *                        all of its neighbours other than itself are marked
  *                        unprocessed (vertex pruning, Section 4.1.4).
  *   - *_nonstrict:       the same with the non-strict tie-break (Section
- *                        4.1.5, "a modulo on the label id"), read as: in
+ *                        4.1.5: a pseudo-random choice among the tied
+ *                        labels through a modulo of the label id), read as: in
  *                        sweep t, vertex i draws r = SplitMix64((t << 32) | i)
  *                        mod n and takes the most weighted label c minimising
  *                        (c - r) mod n.

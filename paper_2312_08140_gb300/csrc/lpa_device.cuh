@@ -103,7 +103,8 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 }
 
 // Tie-break among the most weighted labels of one vertex (Section 4.1.5).
-// Strict: the smallest label id.  Non-strict ("a modulo on the label id"):
+// Strict: the smallest label id.  Non-strict (a pseudo-random choice through a
+// modulo of the label id, read as a rotation of the label space):
 // for vertex i (graph-local id) in its graph's sweep t, r = SplitMix64((t <<
 // 32) | i) mod n, and the label c minimising (c_local - r) mod n wins.  key()
 // maps a label to the value minimised (a bijection on the graph's labels, so
