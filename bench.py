@@ -20,6 +20,7 @@ Also reported:
                launch time, from CUDA events around every launch of the
                profiled run path, against the measured HBM copy bandwidth;
   cpu_baseline the single-threaded CPU oracle on a bounded sample;
+  cpu_parallel the paper's own multi-core CPU design on the host cores;
   clocks       nvidia-smi samples taken during the timed region.
 
 --impl reference times the CPU oracle (the reference arm of this method) on
@@ -187,6 +188,26 @@ def oracle_sample(graphs, pairs):
         secs += time.perf_counter() - t0
         edges += g.nnz * it
     return edges, secs
+
+
+def cpu_parallel_sample(graphs, modes):
+    """The paper's own multi-core CPU design (cpu_parallel: OpenMP dynamic
+    chunks, per-thread collision-free tables, 8-bit flags) on the host cores:
+    one full run of each (graph, mode) pair of the workload."""
+    import cpu_parallel as CP
+    edges, secs = 0, 0.0
+    for g in graphs:
+        for m in modes:
+            if "+" in m:
+                continue                                   # the CPU design has the strict tie-break only
+            t0 = time.perf_counter()
+            _, it, _ = CP.run(g.off, g.idx, g.w, m, TAU, MAX_ITERS)
+            secs += time.perf_counter() - t0
+            edges += g.nnz * it
+    if secs == 0.0:
+        return None
+    return {"value": edges / secs, "unit": UNIT, "cores": CP.threads(), "kind": "paper design, OpenMP",
+            "sample": f"one full run of each (graph, mode) pair of the workload ({secs:.1f} s)"}
 
 
 def run_reference(args, rank, world):
@@ -615,6 +636,10 @@ def main():
                "sample": "CPU oracle, one sweep of each (graph, mode) pair of the workload, twice "
                          f"({s:.1f} s of single-thread CPU work)"}
 
+    cpu_par = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and sum(g.nnz for g in graphs) <= 400_000_000:
+        cpu_par = cpu_parallel_sample(graphs, modes)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -625,7 +650,8 @@ def main():
                 "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
                 "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline, "kernels": kernels,
-                "cpu_baseline": cpu, "batched": batched, "serving": serving, "per_run": per_run}
+                "cpu_baseline": cpu, "cpu_parallel": cpu_par, "batched": batched, "serving": serving,
+                "per_run": per_run}
         print(json.dumps(line), flush=True)
     for h in handles:
         lpa.lpa_graph_destroy(h)

@@ -1,0 +1,31 @@
+"""The multi-core CPU baseline (cpu_parallel, the paper's OpenMP design):
+its synchronous runs must equal the oracle's exactly (pruning and thread
+interleaving cannot change a Jacobi sweep with the strict tie-break), and its
+asynchronous runs must meet the invariants and modularity floor the GPU's do."""
+import numpy as np
+
+import cpu_parallel as CP
+import lpa_inputs as L
+import oracle as O
+from async_bounds import async_floor
+
+
+def _graphs():
+    return [L.planted_partition(n=3000, blocks=6, seed=4), L.road_grid(70, 55, seed=2), L.rmat(12, 16, seed=3),
+            L.batched_sbm_graph(66, n_max=5000), L.from_undirected_pairs(3, [(0, 1), (1, 2)])]
+
+
+def test_sync_equals_oracle():
+    for g in _graphs():
+        ref, it, ch = O.lpa_sync(g.off, g.idx, g.w)
+        for t in (1, 4):
+            got, it2, ch2 = CP.run(g.off, g.idx, g.w, "sync", n_threads=t)
+            assert np.array_equal(got, ref) and it2 == it and ch2.tolist() == ch.tolist(), (g.n, t)
+
+
+def test_async_invariants():
+    for g in _graphs():
+        got, it, _ = CP.run(g.off, g.idx, g.w, "async", n_threads=4)
+        assert 1 <= it <= 20
+        assert O.count_labels_outside_component(g.off, g.idx, got) == 0
+        assert O.modularity(g.off, g.idx, g.w, got) >= async_floor(g), g.n
