@@ -96,7 +96,7 @@ WORKLOAD_TEXT = {
 # the kernel in one step of the profiled run path), valid only while the
 # kernel's sources are unchanged (sha1 of the files below).
 TRAFFIC = {
-    "k_sweep_small": {"bytes_per_launch": 432.5e6, "sha1": "e270bbc9668336baadeea0353dfaaf4567437527",
+    "k_sweep_small": {"bytes_per_launch": 432.3e6, "sha1": "857c806f19679b220edb4affeb7c9551b5cae68c",
                       "files": ["lpa_sweep_small.cu", "lpa_device.cuh", "lpa_internal.h"]},
 }
 
@@ -188,6 +188,31 @@ def oracle_sample(graphs, pairs):
         secs += time.perf_counter() - t0
         edges += g.nnz * it
     return edges, secs
+
+
+def param_sweep(lpa, torch, stream, names, graphs, handles, outs, mode="async", reps=3):
+    """Tolerance and iteration-cap sweep per graph class (the paper's ablations
+    of Sections 4.1.2-4.1.3): for tau in {0.1, 0.05, 0.01, 1e-5} and cap in
+    {10, 20, 50}, sweeps run, device time per run, edges/s, time per stored
+    entry and the modularity (Eq. 1) of the labels."""
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for name, g, h, o in zip(names, graphs, handles, outs):
+        for tau in (0.1, 0.05, 0.01, 1e-5):
+            for cap in (10, 20, 50):
+                info = lpa.lpa_run(h, mode, tau, cap, o, stream, info=True)
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                for _ in range(reps):
+                    lpa.lpa_run(h, mode, tau, cap, o, stream, info=False)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                ms = ev0.elapsed_time(ev1) / reps
+                q = lpa.lpa_modularity(h, o)
+                rows.append({"graph": name, "mode": mode, "tau": tau, "cap": cap, "iterations": info.iterations,
+                             "ms": ms, "edges_per_s": g.nnz * info.iterations / (ms / 1e3),
+                             "ns_per_entry": ms * 1e6 / g.nnz, "modularity": q})
+    return rows
 
 
 def cpu_parallel_sample(graphs, modes):
@@ -477,6 +502,8 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=0.5, help="0 skips the serving sample")
     ap.add_argument("--tie", default="strict", choices=["strict", "nonstrict"],
                     help="tie-break among the most weighted labels (Section 4.1.5)")
+    ap.add_argument("--param-sweep", action="store_true",
+                    help="also sweep tau in {0.1, 0.05, 0.01, 1e-5} x cap in {10, 20, 50} per graph (async)")
     ap.add_argument("--batched-full", action="store_true",
                     help="batched sample on the full workload: 4,096 graphs drawn on the device")
     ap.add_argument("--serving-full", action="store_true",
@@ -636,6 +663,10 @@ def main():
                "sample": "CPU oracle, one sweep of each (graph, mode) pair of the workload, twice "
                          f"({s:.1f} s of single-thread CPU work)"}
 
+    sweep_rows = None
+    if args.param_sweep:
+        sweep_rows = param_sweep(lpa, torch, stream, [n for n, _ in wl], graphs, handles, outs)
+
     cpu_par = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and sum(g.nnz for g in graphs) <= 400_000_000:
         cpu_par = cpu_parallel_sample(graphs, modes)
@@ -651,7 +682,7 @@ def main():
                         "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
                 "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline, "kernels": kernels,
                 "cpu_baseline": cpu, "cpu_parallel": cpu_par, "batched": batched, "serving": serving,
-                "per_run": per_run}
+                "param_sweep": sweep_rows, "per_run": per_run}
         print(json.dumps(line), flush=True)
     for h in handles:
         lpa.lpa_graph_destroy(h)
