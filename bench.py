@@ -96,7 +96,7 @@ WORKLOAD_TEXT = {
 # the kernel in one step of the profiled run path), valid only while the
 # kernel's sources are unchanged (sha1 of the files below).
 TRAFFIC = {
-    "k_sweep_small": {"bytes_per_launch": 432.3e6, "sha1": "857c806f19679b220edb4affeb7c9551b5cae68c",
+    "k_sweep_small": {"bytes_per_launch": 431.6e6, "sha1": "71bd362e22ce18a43891b8e478bc7b9b3c5de834",
                       "files": ["lpa_sweep_small.cu", "lpa_device.cuh", "lpa_internal.h"]},
 }
 
@@ -468,20 +468,22 @@ def reduce_over_ranks(dist, device, slowest, counts):
     return float(t.item()), [float(x) for x in u.tolist()]
 
 
-def kernel_bytes(prof, wbytes, sync, passes):
+def kernel_bytes(prof, wbytes, sync, passes, rows_distinct=False):
     """Algorithmic bytes per sweep-kernel launch from the per-bin counts:
     per scanned vertex 16 B offsets + 4 B own label + 4 B frontier id; per
-    scanned entry 4 B index + wbytes weight + 4 B gathered label; per changed
-    vertex 4 B label write (+4 B changed-list entry in sync mode) and 1 B flag
-    per entry of its row."""
+    scanned entry 4 B index + wbytes weight + 4 B gathered label (none in the
+    first synchronous sweep of a graph whose rows repeat no neighbour: its
+    labels are still the vertex ids); per changed vertex 4 B label write (+4 B
+    changed-list entry in sync mode) and 1 B flag per entry of its row."""
     out = {b: {"bytes": 0.0, "ms": 0.0, "launches": 0} for b in BIN_KERNELS}
     for t in range(min(prof["iterations"], 64)):
+        gather = 0 if (sync and rows_distinct and t == 0) else 4
         for bi, b in enumerate(BIN_KERNELS):
             v = prof["bin_vertices"][t][bi]
             e = prof["bin_entries"][t][bi]
             c = prof["bin_changed"][t][bi]
             ce = prof["bin_changed_entries"][t][bi]
-            by = v * 24 + e * (8 + wbytes) + c * (8 if sync else 4) + ce
+            by = v * 24 + e * (4 + wbytes + gather) + c * (8 if sync else 4) + ce
             out[b]["bytes"] += by
             out[b]["ms"] += prof["sweep_ms"][t][bi]
             out[b]["launches"] += passes
@@ -620,11 +622,13 @@ def main():
     if not args.no_profile:
         agg = {}
         for g, h, o in zip(graphs, handles, outs):
-            wbytes = lpa.lpa_graph_props_get(h)["weight_bytes"]     # as the sweeps read them
+            props = lpa.lpa_graph_props_get(h)
+            wbytes = props["weight_bytes"]                           # as the sweeps read them
             for m in modes:
                 _, prof = lpa.lpa_run_profiled(h, m, TAU, MAX_ITERS, o, stream)
                 sync = not m.startswith("async")
-                for b, d in kernel_bytes(prof.as_dict(), wbytes, sync, 1 if sync else 2).items():
+                for b, d in kernel_bytes(prof.as_dict(), wbytes, sync, 1 if sync else 2,
+                                         props["rows_distinct"]).items():
                     a = agg.setdefault(b, {"bytes": 0.0, "ms": 0.0, "launches": 0})
                     for k in a:
                         a[k] += d[k]

@@ -117,6 +117,11 @@ typedef struct {
     int64_t sweeps_total;  /* sweeps run on this handle since creation (all runs) */
     int64_t scanned_total; /* CSR entries scanned by those sweeps */
     int64_t launches_total;/* kernel launches of the lpa_run calls on this handle */
+    int32_t rows_distinct; /* 1: a single graph whose every row lists its neighbours in strictly
+                              increasing order (so none twice); the first LPA_MODE_SYNC sweep then
+                              reads no labels (each still equals its vertex id) and takes the
+                              heaviest entry of each row.  0 for batches and other graphs. */
+    int32_t reserved;
 } lpa_graph_props;
 
 /* Launch parameters of the sweep.  Vertices are binned by degree d:

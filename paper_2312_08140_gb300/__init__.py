@@ -64,7 +64,7 @@ class LpaGraphProps(ctypes.Structure):
                 ("weighted", ctypes.c_int32), ("exact", ctypes.c_int32), ("weight_bytes", ctypes.c_int32),
                 ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("sweeps_total", ctypes.c_int64), ("scanned_total", ctypes.c_int64),
-                ("launches_total", ctypes.c_int64)]
+                ("launches_total", ctypes.c_int64), ("rows_distinct", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -324,6 +324,10 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     if (vr.c[1]) return fail(LPA_ERR_INVALID_GRAPH, "%u indices out of range", vr.c[1]);
     if (vr.c[2]) return fail(LPA_ERR_INVALID_GRAPH, "%u weights negative or not finite", vr.c[2]);
     E.max_degree = (int64_t)vr.max_degree;
+    // rows without a repeated neighbour (each strictly increasing): the first
+    // synchronous sweep, where every label is still the vertex's own id, is a
+    // max-weight reduction over each row
+    E.s.rows_distinct = (G == 1 && vr.desc_all == vr.desc_row_starts) ? 1 : 0;
 
     // weight representation: integer sums when every sum is an exact integer
     if (!weights) {
@@ -692,6 +696,7 @@ lpa_status fill_props(const Engine& E, lpa_graph_props* p) {
     p->weight_bytes = E.s.weight_kind == W_UNIT ? 0 : E.s.weight_kind == W_U8 ? 1 : 4;
     p->exact = E.exact ? 1 : 0;
     p->max_degree = E.max_degree;
+    p->rows_distinct = E.s.rows_distinct;
     p->device_bytes = E.device_bytes + (int64_t)std::max<size_t>(E.s.bin_static[kBins - 1], 1) * sizeof(Overflow);
     return LPA_OK;
 }

@@ -65,6 +65,33 @@ __device__ __forceinline__ void mark_unprocessed(uint8_t* flags, int32_t j) {
     if (__ldcg(flags + j) == 0) flags[j] = 1;
 }
 
+// First synchronous sweep of a single graph whose rows repeat no neighbour:
+// every label is still its vertex's id, so neighbour j carries label j and the
+// sum K_{i->c} of Eq. 2 for each label is one entry's weight.  The kernels
+// then skip the label gathers (and the wider ones the hash table).
+template <bool ASYNC, bool BATCH>
+__device__ __forceinline__ bool identity_sweep(const DevState& s) {
+    if constexpr (ASYNC || BATCH) {
+        return false;
+    } else {
+        return s.rows_distinct && s.ctrl->iter == 0;
+    }
+}
+
+// One candidate packed for a 64-bit max: sum key above, complemented tie key
+// below, so the larger sum wins and then the smaller tie key.  0 = none.
+__device__ __forceinline__ unsigned long long pack_candidate(uint32_t key, uint32_t tie) {
+    return ((unsigned long long)key << 32) | (unsigned long long)(~tie);
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(kFull, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
 // Whether this pass writes neighbour marks (Section 4.1.4).
 __device__ __forceinline__ bool marks_on(const DevState& s, int flag_neighbours) {
     return flag_neighbours && !s.ctrl->skip_marks;

@@ -605,11 +605,12 @@ constexpr int kValThreads = 256;
 
 struct ValAcc {
     unsigned int c[6];          // bad_offsets, bad_index, bad_weight, non_integer, heavy_row, huge_row
+    unsigned long long desc;    // non-increasing adjacent entry pairs (entries pass) / at row starts (rows pass)
     unsigned long long max_degree;
     unsigned int max_weight_bits;
 };
 
-__device__ __forceinline__ void val_flush(ValAcc& a, ValidateResult* res) {
+__device__ __forceinline__ void val_flush(ValAcc& a, ValidateResult* res, unsigned long long* desc_out) {
     __shared__ unsigned int sc[6];
     __shared__ unsigned long long smax;
     __shared__ unsigned int swmax;
@@ -631,9 +632,12 @@ __device__ __forceinline__ void val_flush(ValAcc& a, ValidateResult* res) {
         m = x > m ? x : m;
     }
     const unsigned wm = __reduce_max_sync(kFull, a.max_weight_bits);
+    unsigned long long dsc = a.desc;
+    for (int o = 16; o > 0; o >>= 1) dsc += __shfl_xor_sync(kFull, dsc, o);
     if (lane == 0) {
         if (m) atomicMax(&smax, m);
         if (wm) atomicMax(&swmax, wm);
+        if (dsc) atomicAdd(desc_out, dsc);
     }
     __syncthreads();
     if (threadIdx.x < 6 && sc[threadIdx.x]) atomicAdd(&res->c[threadIdx.x], sc[threadIdx.x]);
@@ -671,8 +675,9 @@ __global__ void __launch_bounds__(kValThreads) k_validate_entries(const int32_t*
             }
             if (j < 0 || j >= n_local) ++a.c[1];
             else idx_rw[e] = (int32_t)(j + lo);
-        } else if (j < 0 || j >= N) {
-            ++a.c[1];
+        } else {
+            if (j < 0 || j >= N) ++a.c[1];
+            if (e > 0 && j <= idx[e - 1]) ++a.desc;           // no writes here: a single graph
         }
         if (w) {
             const float x = w[e];
@@ -685,12 +690,12 @@ __global__ void __launch_bounds__(kValThreads) k_validate_entries(const int32_t*
             }
         }
     }
-    val_flush(a, res);
+    val_flush(a, res, &res->desc_all);
 }
 
 // Rows: lane l of a warp takes row base + l; all lanes run the same trips.
-__global__ void __launch_bounds__(kValThreads) k_validate_rows(const int64_t* off, const float* w, int64_t N,
-                                                               int64_t E, const int64_t* vtx_off,
+__global__ void __launch_bounds__(kValThreads) k_validate_rows(const int64_t* off, const int32_t* idx, const float* w,
+                                                               int64_t N, int64_t E, const int64_t* vtx_off,
                                                                const int64_t* edge_off, const int32_t* gid,
                                                                int32_t G, ValidateResult* res) {
     ValAcc a{};
@@ -716,6 +721,7 @@ __global__ void __launch_bounds__(kValThreads) k_validate_rows(const int64_t* of
             } else {
                 const int64_t d = en - st;
                 a.max_degree = (unsigned long long)d > a.max_degree ? (unsigned long long)d : a.max_degree;
+                if (G == 1 && d > 0 && st > 0 && idx[st] <= idx[st - 1]) ++a.desc;
                 if (!w) {
                     if (d >= 16777216) ++a.c[4];
                     if (d >= 2147483648LL) ++a.c[5];
@@ -738,7 +744,7 @@ __global__ void __launch_bounds__(kValThreads) k_validate_rows(const int64_t* of
             }
         }
     }
-    val_flush(a, res);
+    val_flush(a, res, &res->desc_row_starts);
 }
 
 cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N, int64_t E,
@@ -757,7 +763,7 @@ cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float*
     }
     const int64_t warps = (N + 31) / 32;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)sms * 8));
-    k_validate_rows<<<blocks, kValThreads, 0, st>>>(off, w, N, E, vtx_off, edge_off, gid, G, res);
+    k_validate_rows<<<blocks, kValThreads, 0, st>>>(off, idx, w, N, E, vtx_off, edge_off, gid, G, res);
     return cudaGetLastError();
 }
 

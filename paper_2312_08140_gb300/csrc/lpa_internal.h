@@ -118,6 +118,7 @@ struct DevState {
     int32_t G;                 // graphs
     int32_t weight_kind;       // WeightKind
     int32_t small_iota;        // dense sync passes of bin 0 walk vertex ids 0..N-1 (bin 0 holds >= 3/4 of them)
+    int32_t rows_distinct;     // no row repeats a neighbour: the first synchronous sweep is a max-weight reduction
     const int64_t* off;        // [N] row begins (positions in idx)
     const int64_t* off_end;    // [N] row ends (off + 1 for an ordinary CSR)
     const int32_t* idx;        // [E] global vertex ids
@@ -206,6 +207,10 @@ struct ValidateResult {
     unsigned long long max_degree;
     unsigned int max_weight_bits;      // bits of the largest valid weight (>= 0, so ordered as unsigned)
     unsigned int pad;
+    // single graphs: adjacent entry pairs that do not increase, over all
+    // entries and over row starts only; equal <=> every row strictly increases
+    unsigned long long desc_all;
+    unsigned long long desc_row_starts;
 };
 cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N,
                             int64_t E, const int64_t* vtx_off, const int64_t* edge_off,

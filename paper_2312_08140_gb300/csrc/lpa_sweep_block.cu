@@ -102,6 +102,8 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
     __shared__ uint32_t red_tie[32];
     __shared__ int overflow;
     __shared__ uint32_t winner;
+    __shared__ unsigned long long red_bp[32];
+    __shared__ unsigned long long win_bp;
 
     const unsigned lane = lane_id();
     const int wib = threadIdx.x >> 5;
@@ -117,6 +119,7 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
     const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
+    const bool ident = identity_sweep<ASYNC, BATCH>(s);
     const unsigned cnt = bv.cnt;
     const int log_S = ceil_log2((unsigned)S);
     unsigned long long my_changed = 0, my_changed_entries = 0;
@@ -132,76 +135,100 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
         const int64_t st = s.off[v];
         const int64_t en = s.off_end[v];
         const int64_t d = en - st;
-        const int log_full = ceil_log2((unsigned)(2 * d));
-        const bool fits = log_full <= log_S;
-        const int log_s = fits ? log_full : log_S;
-        // Each warp takes U chunks per step (chunk c = wib + (u + U*it)*nw):
-        // their index loads, then their label gathers and weights, are issued
-        // together so the latencies overlap; then the chunks are aggregated.
-        const int64_t step = (int64_t)nw * 32;
-        for (int64_t e0 = st + (int64_t)wib * 32; e0 < en; e0 += step * U) {
-            if (!fits && *(volatile int*)&overflow) break;     // warp-uniform
-            int32_t jj[U], lab[U];
-            T ww[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t e = e0 + u * step + lane;
-                jj[u] = e < en ? load_index_keep(s.idx, e) : v;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int64_t e = e0 + u * step + lane;
-                const bool ok = jj[u] != v;                      // also false past the row end
-                lab[u] = ok ? load_label<ASYNC>(L.C, jj[u]) : kEmptyKey;
-                ww[u] = ok ? load_weight<WK>(s.w, e) : (T)0;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (e0 + u * step >= en) break;                 // warp-uniform
-                const bool ok = jj[u] != v;
-                T w = ww[u];
-                bool lead = ok;
-                if constexpr (WK != W_F32) {
-                    const unsigned peers = __match_any_sync(kFull, lab[u]);
-                    if constexpr (WK == W_UNIT) {
-                        w = (T)__popc(peers);
-                    } else {
-                        w = __reduce_add_sync(peers, w);
-                    }
-                    lead = ok && lane == (unsigned)(__ffs(peers) - 1);
-                }
-                if (lead) {
-                    if (fits) {
-                        if (!table_add<T>(keys, vals, log_s, lab[u], w)) atomicExch(&s.ctrl->error, 3);
-                    } else if (!table_add_bounded<T>(keys, vals, log_s, lab[u], w, kSharedProbes)) {
-                        overflow = 1;
-                    }
-                }
-            }
-        }
-        __syncthreads();
         const TieRule tr = tie_rule(s, NS, sweep, v);
-        uint32_t key, tie;
-        scan_table<T>(keys, vals, 1 << log_s, tr, key, tie);     // also clears the table
-        const int ovf = overflow;
-        const uint32_t best_tie = block_argmax(key, tie, red_key, red_tie, &winner);
-        const int32_t best_lab = best_tie == 0xffffffffu ? -1 : tr.label(best_tie);
-        if (ovf) {
-            // hand the row to the partitioned rescan
-            if (threadIdx.x == 0) {
-                Overflow& o = s.ovf[atomicAdd(&s.ctrl->ovf_count, 1ull)];
-                o.v = v;
-                o.slot = k;
-                o.st = st;
-                o.d = (int32_t)d;
-                o.own = own;
-                o.parts = (uint32_t)((2 * d + S - 1) / S);
-                o.best = 0ull;
-                o.done = 0u;
-                overflow = 0;
+        int32_t best_lab;
+        if (ident) {
+            // labels are the neighbour ids and occur once: a max over the row
+            unsigned long long bp = 0ull;
+#pragma unroll 4
+            for (int64_t e = st + threadIdx.x; e < en; e += blockDim.x) {
+                const int32_t j = load_index_keep(s.idx, e);
+                if (j != v) {
+                    const unsigned long long c = pack_candidate(sum_key(load_weight<WK>(s.w, e)), tr.key(j));
+                    bp = c > bp ? c : bp;
+                }
+            }
+            bp = warp_max_u64(bp);
+            if (lane == 0) red_bp[wib] = bp;
+            __syncthreads();
+            if (wib == 0) {
+                bp = warp_max_u64((int)lane < nw ? red_bp[lane] : 0ull);
+                if (lane == 0) win_bp = bp;
             }
             __syncthreads();
-            continue;
+            bp = win_bp;
+            best_lab = bp == 0ull ? -1 : tr.label(~(uint32_t)bp);
+        } else {
+            const int log_full = ceil_log2((unsigned)(2 * d));
+            const bool fits = log_full <= log_S;
+            const int log_s = fits ? log_full : log_S;
+            // Each warp takes U chunks per step (chunk c = wib + (u + U*it)*nw):
+            // their index loads, then their label gathers and weights, are issued
+            // together so the latencies overlap; then the chunks are aggregated.
+            const int64_t step = (int64_t)nw * 32;
+            for (int64_t e0 = st + (int64_t)wib * 32; e0 < en; e0 += step * U) {
+                if (!fits && *(volatile int*)&overflow) break;     // warp-uniform
+                int32_t jj[U], lab[U];
+                T ww[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t e = e0 + u * step + lane;
+                    jj[u] = e < en ? load_index_keep(s.idx, e) : v;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t e = e0 + u * step + lane;
+                    const bool ok = jj[u] != v;                      // also false past the row end
+                    lab[u] = ok ? load_label<ASYNC>(L.C, jj[u]) : kEmptyKey;
+                    ww[u] = ok ? load_weight<WK>(s.w, e) : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (e0 + u * step >= en) break;                 // warp-uniform
+                    const bool ok = jj[u] != v;
+                    T w = ww[u];
+                    bool lead = ok;
+                    if constexpr (WK != W_F32) {
+                        const unsigned peers = __match_any_sync(kFull, lab[u]);
+                        if constexpr (WK == W_UNIT) {
+                            w = (T)__popc(peers);
+                        } else {
+                            w = __reduce_add_sync(peers, w);
+                        }
+                        lead = ok && lane == (unsigned)(__ffs(peers) - 1);
+                    }
+                    if (lead) {
+                        if (fits) {
+                            if (!table_add<T>(keys, vals, log_s, lab[u], w)) atomicExch(&s.ctrl->error, 3);
+                        } else if (!table_add_bounded<T>(keys, vals, log_s, lab[u], w, kSharedProbes)) {
+                            overflow = 1;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            uint32_t key, tie;
+            scan_table<T>(keys, vals, 1 << log_s, tr, key, tie);     // also clears the table
+            const int ovf = overflow;
+            const uint32_t best_tie = block_argmax(key, tie, red_key, red_tie, &winner);
+            best_lab = best_tie == 0xffffffffu ? -1 : tr.label(best_tie);
+            if (ovf) {
+                // hand the row to the partitioned rescan
+                if (threadIdx.x == 0) {
+                    Overflow& o = s.ovf[atomicAdd(&s.ctrl->ovf_count, 1ull)];
+                    o.v = v;
+                    o.slot = k;
+                    o.st = st;
+                    o.d = (int32_t)d;
+                    o.own = own;
+                    o.parts = (uint32_t)((2 * d + S - 1) / S);
+                    o.best = 0ull;
+                    o.done = 0u;
+                    overflow = 0;
+                }
+                __syncthreads();
+                continue;
+            }
         }
         const bool changed = best_lab >= 0 && best_lab != own;   // block-uniform
         if (threadIdx.x == 0) record_label<ASYNC>(L, bv.chg + k, v, own, best_lab, changed);
@@ -213,7 +240,7 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
             }
             if (marks) mark_neighbours(s, v, st, en);
         }
-        __syncthreads();    // `winner` consumed before the next vertex
+        __syncthreads();    // `winner` / `win_bp` consumed before the next vertex
     }
     flush_bin_counts(s, bin, my_changed, my_changed_entries);
 }

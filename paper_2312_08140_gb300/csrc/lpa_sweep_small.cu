@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
     // themselves (coalesced offsets, one dependent load less than the list)
     // and keeps those of this bin.
     const bool iota = L.dense && s.small_iota;
+    const bool ident = identity_sweep<false, BATCH>(s);
     const unsigned cnt = iota ? (unsigned)s.N : bv.cnt;
     const unsigned stride = gridDim.x * blockDim.x;
     constexpr int RUN = 1;                            // async mode uses k_sweep_small_async
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
             const int32_t j = ok ? load_index(s.idx, st + q) : v;
             nb[q] = j;
             ok = ok && (j != v);
-            lab[q] = ok ? load_label<false>(L.C, j) : kEmptyKey;
+            lab[q] = ok ? (ident ? j : load_label<false>(L.C, j)) : kEmptyKey;
             wt[q] = ok ? load_weight<WK>(s.w, st + q) : (T)0;
         }
         const TieRule tr = tie_rule(s, NS && act, sweep, v);

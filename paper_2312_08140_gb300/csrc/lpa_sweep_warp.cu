@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
     const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
+    const bool ident = identity_sweep<ASYNC, BATCH>(s);
     const unsigned cnt = bv.cnt;
     const unsigned nwarps = gridDim.x * kWarpsPerBlock;
     // each warp takes batches of B consecutive frontier entries (B <= 32), B
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
             const int32_t vq = __shfl_sync(kFull, vl, q);
             const int64_t sq = __shfl_sync(kFull, stl, q);
             const bool ok = j != kEmptyKey && j != vq;
-            lab = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
+            lab = ok ? (ident ? j : load_label<ASYNC>(L.C, j)) : kEmptyKey;
             w = ok ? load_weight<WK>(s.w, sq + lane) : (T)0;
         };
         int32_t j_cur = first_index(0), j_nxt = first_index(1);
@@ -137,6 +138,22 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                 if (ok && lane == (unsigned)(__ffs(peers) - 1)) {
                     key = sum_key(sum);
                     cand = lab_cur;
+                }
+            } else if (act && ident) {
+                // labels are the neighbour ids and occur once: a max over the row
+                unsigned long long bp = lab_cur != kEmptyKey ? pack_candidate(sum_key(w_cur), tr.key(lab_cur)) : 0ull;
+#pragma unroll 4
+                for (int64_t e = st + 32 + lane; e < en; e += 32) {
+                    const int32_t jj = load_index_keep(s.idx, e);
+                    if (jj != v) {
+                        const unsigned long long c = pack_candidate(sum_key(load_weight<WK>(s.w, e)), tr.key(jj));
+                        bp = c > bp ? c : bp;
+                    }
+                }
+                bp = warp_max_u64(bp);
+                if (lane == 0 && bp != 0ull) {
+                    key = (uint32_t)(bp >> 32);
+                    cand = tr.label(~(uint32_t)bp);
                 }
             } else if (act) {
                 const int log_slots = ceil_log2(2u * (unsigned)d);

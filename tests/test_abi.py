@@ -59,7 +59,7 @@ def test_struct_layouts_match_c(lib_path):
     import paper_2312_08140_gb300 as lpa
     H = lpa.LPA_MAX_RECORDED_ITERS
     assert ctypes.sizeof(lpa.LpaRunInfo) == 8 + 3 * 8 * H + 8
-    assert ctypes.sizeof(lpa.LpaGraphProps) == 8 * 2 + 4 * 4 + 8 * 5
+    assert ctypes.sizeof(lpa.LpaGraphProps) == 8 * 2 + 4 * 4 + 8 * 5 + 4 * 2
     assert ctypes.sizeof(lpa.LpaConfig) == 20
     B = lpa.LPA_BINS
     assert ctypes.sizeof(lpa.LpaProfile) == 16 + 4 * H + 4 * B * H + 4 * B * 8 * H

@@ -114,6 +114,64 @@ def test_rmat_raw_duplicates_selfloops_sync(lpa):
     assert_sync_parity(lpa, g)
 
 
+def _props_rows_distinct(lpa, g):
+    h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w)
+    try:
+        return lpa.lpa_graph_props_get(h)["rows_distinct"]
+    finally:
+        lpa.lpa_graph_destroy(h)
+
+
+def test_first_sweep_of_repeat_free_rows(lpa):
+    """A single graph whose rows list each neighbour once, in increasing order,
+    runs its first synchronous sweep without label reads or hash tables (every
+    label still equals its vertex id, so each label's sum is one entry's
+    weight).  The detection must hold exactly: rows out of order, or with a
+    neighbour listed twice (adjacent, so the only descent is an equal pair),
+    keep the general path.  Every variant matches the oracle in all degree
+    bins, strict and non-strict."""
+    g = L.rmat(14, 16, seed=6, drop_self=False, wmax=8)         # sorted rows, self-loops kept
+    assert int(np.diff(g.off).max()) > 2048                     # reaches the last bin
+    assert _props_rows_distinct(lpa, g) == 1
+
+    # one row (the longest) reversed: distinct but not increasing
+    v = int(np.argmax(np.diff(g.off)))
+    idx_r, w_r = g.idx.copy(), g.w.copy()
+    s0, e0 = int(g.off[v]), int(g.off[v + 1])
+    idx_r[s0:e0] = idx_r[s0:e0][::-1]
+    w_r[s0:e0] = w_r[s0:e0][::-1]
+    g_rev = L.Graph(g.off, idx_r, w_r, {})
+    assert _props_rows_distinct(lpa, g_rev) == 0
+
+    # every row of degree >= 2 lists its lightest neighbour twice, side by side
+    rows_i, rows_w = [], []
+    deg = np.diff(g.off)
+    for u in range(g.n):
+        a, b = int(g.off[u]), int(g.off[u + 1])
+        ri, rw = g.idx[a:b], g.w[a:b]
+        if b - a >= 2:
+            k = int(np.argmin(rw))
+            ri = np.insert(ri, k, ri[k])
+            rw = np.insert(rw, k, rw[k])
+        rows_i.append(ri)
+        rows_w.append(rw)
+    off_d = np.zeros(g.n + 1, dtype=np.int64)
+    np.cumsum(deg + (deg >= 2), out=off_d[1:])
+    g_dup = L.Graph(off_d, np.concatenate(rows_i).astype(np.int32), np.concatenate(rows_w).astype(np.float32), {})
+    assert _props_rows_distinct(lpa, g_dup) == 0
+
+    for gr in (g, g_rev, g_dup):
+        assert_sync_parity(lpa, gr)
+        ref, it, ch = O.lpa_sync(gr.off, gr.idx, gr.w, nonstrict=True)
+        got, info, h = run_gpu(lpa, gr, "sync+nonstrict")
+        lpa.lpa_graph_destroy(h)
+        assert info["iterations"] == it and np.array_equal(got, ref)
+    # the duplicated entries change the first sweep's picks somewhere, so the
+    # two graphs are told apart by the oracle too
+    assert not np.array_equal(O.sync_sweep(g.off, g.idx, g.w, np.arange(g.n, dtype=np.int32))[0],
+                              O.sync_sweep(g_dup.off, g_dup.idx, g_dup.w, np.arange(g.n, dtype=np.int32))[0])
+
+
 def test_weighted_grid_sync(lpa):
     g = L.road_grid(200, 173, seed=2)       # ragged: n is not a multiple of any tile
     assert_sync_parity(lpa, g, iters=7)
