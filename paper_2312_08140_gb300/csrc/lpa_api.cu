@@ -375,6 +375,7 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     if ((rs = dalloc_t(E, &E.s.lab[0], N1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.lab[1], N1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.flags, N1 + 16)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.fr_bits, N1 / 16 + 1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.slist, N1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.flist, N1)) != LPA_OK) return rs;
     if ((rs = dalloc_t(E, &E.s.chg, N1)) != LPA_OK) return rs;
@@ -420,22 +421,23 @@ cudaError_t enqueue_pass(Engine& E, int mode, cudaStream_t st) {
 
 // One sweep (lpaMove of Algorithm 1).  Sync modes: one pass over the frontier,
 // then the finish kernel (apply, compaction, control).  Async mode: a main
-// pass, a compaction of the vertices it re-marked, and a catch-up pass over
-// them within the same sweep -- the parallel counterpart of the serial loop,
-// where a vertex re-marked by an earlier vertex is scanned again later in the
-// same sweep -- then the finish kernel.
+// pass over the frontier, a compaction of the vertices it marked that were
+// not in the frontier, and a catch-up pass over them within the same sweep --
+// the parallel counterpart of the serial loop, which reaches a vertex marked
+// by an earlier vertex later in the same sweep, while a vertex it has already
+// scanned keeps its mark for the next sweep -- then the finish kernel.
 // `mode` may carry kModeNonstrict, which only the sweep kernels take.
 cudaError_t enqueue_sweep(Engine& E, int mode, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st) {
     const int base = mode & ~kModeNonstrict;
     cudaError_t err = enqueue_pass(E, mode, st);
     if (err != cudaSuccess) return err;
     if (base == MODE_ASYNC) {
-        err = launch_finish(E.s, base, 1, h, in_graph, st, E.sms);
+        err = launch_finish(E.s, base, kRoleCatchUp, h, in_graph, st, E.sms);
         if (err != cudaSuccess) return err;
         err = enqueue_pass(E, mode, st);
         if (err != cudaSuccess) return err;
     }
-    return launch_finish(E.s, base, 0, h, in_graph, st, E.sms);
+    return launch_finish(E.s, base, kRoleEndSweep, h, in_graph, st, E.sms);
 }
 
 int graph_index(int mode) { return (mode & ~kModeNonstrict) + ((mode & kModeNonstrict) ? 3 : 0); }
@@ -622,7 +624,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
                 if (E.s.bin_static[b]) LPA_P(launch_bin(E, mode | (ns ? kModeNonstrict : 0), b, st));
             }
             LPA_P(cudaEventRecord(ev[kBins], st));
-            LPA_P(launch_finish(E.s, mode, p + 1 < passes ? 1 : 0, none, 0, st, E.sms));
+            LPA_P(launch_finish(E.s, mode, p + 1 < passes ? kRoleCatchUp : kRoleEndSweep, none, 0, st, E.sms));
             LPA_P(cudaEventRecord(ev[kBins + 1], st));
             LPA_P(cudaEventSynchronize(ev[kBins + 1]));
             for (int b = 0; b < kBins; ++b) {

@@ -260,6 +260,29 @@ __device__ __forceinline__ bool flag_at(const uint4& raw, int q) {
     return ((wd >> (8 * (q & 3))) & 0xffu) != 0;
 }
 
+// Bit q set <=> flag byte q of the chunk is non-zero.
+__device__ __forceinline__ uint32_t flag_mask(const uint4& raw) {
+    const uint32_t wd[4] = {raw.x, raw.y, raw.z, raw.w};
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < kVertsPerThread; ++q) m |= (((wd[q >> 2] >> (8 * (q & 3))) & 0xffu) != 0 ? 1u : 0u) << q;
+    return m;
+}
+
+// Clears the flag bytes of the chunk at v0 selected by `mask` (bit q = byte q).
+__device__ __forceinline__ void clear_flags(uint8_t* flags, int64_t N, int64_t v0, uint4 raw, uint32_t mask) {
+    if (v0 + kVertsPerThread <= N) {
+        uint32_t wd[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+        for (int q = 0; q < kVertsPerThread; ++q)
+            if ((mask >> q) & 1u) wd[q >> 2] &= ~(0xffu << (8 * (q & 3)));
+        *reinterpret_cast<uint4*>(flags + v0) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    } else {
+        for (int q = 0; q < kVertsPerThread && v0 + q < N; ++q)
+            if ((mask >> q) & 1u) flags[v0 + q] = 0;
+    }
+}
+
 // ------------------------------------------------------------ static lists --
 // Every vertex with at least one entry, grouped by degree bin, ascending.
 // Two passes over blocks of 4096 vertices: count, then ordered scatter from
@@ -372,8 +395,8 @@ cudaError_t build_static_lists(DevState& s, cudaStream_t st, unsigned* counts, u
 
 // Run by the last block of k_finish once every block is done.  `rd` is the
 // buffer the pass just consumed; `wr` = rd ^ 1 received the next frontier
-// (or is dense; role 2 compacts nothing and keeps rd).  For roles 0 and 2
-// (end of sweep t) it also runs the per-graph
+// (or is dense; kRoleControl compacts nothing and keeps rd).  At the end of
+// sweep t (kRoleEndSweep, kRoleControl) it also runs the per-graph
 // convergence test of Algorithm 1 and sets the loop condition.
 __device__ void control_step(const DevState& s, int mode, int role, int dense_next, cudaGraphConditionalHandle h,
                              int in_graph) {
@@ -382,7 +405,9 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
     const int t = vc->iter;
     const int rd = vc->rd, wr = rd ^ 1;
     int any = 0;
-    if (role != 1) {
+    const bool ends_sweep = role == kRoleEndSweep || role == kRoleControl;
+    const bool compacted = role != kRoleControl;
+    if (ends_sweep) {
         const double tau = vc->tau;
         const int max_iters = vc->max_iters;
         unsigned long long changed_total = 0;
@@ -414,7 +439,7 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         c->sweep_bin_vertices[b] += vc->bin_cnt[rd][b];
         c->sweep_bin_entries[b] += (long long)vc->bin_entries[rd][b];
     }
-    if (role != 1) {
+    if (ends_sweep) {
         long long act = 0, scn = 0, che = 0;
         for (int b = 0; b < kBins; ++b) {
             act += vc->sweep_bin_vertices[b];
@@ -452,28 +477,32 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         c->any_active = any;
     }
     for (int b = 0; b < kBins; ++b) {
-        if (dense_next && role != 2) {
+        if (dense_next && compacted) {
             c->bin_cnt[wr][b] = s.bin_static[b];
             c->bin_entries[wr][b] = s.bin_static_entries[b];
         }
         c->bin_cnt[rd][b] = 0;
         c->bin_entries[rd][b] = 0;
     }
-    // Marks are useless when the next pass is dense anyway.  After two passes
-    // in a row that changed almost every vertex, the next pass skips them and
-    // the one after it is dense.
-    const bool high = (double)vc->pass_changed_entries * 1000.0 >= (double)kHighPermille * (double)s.active_entries;
-    c->skip_marks = (high && vc->last_pass_high && vc->allow_dense) ? 1 : 0;
-    c->last_pass_high = high ? 1 : 0;
-    if (role != 2) {
+    if (ends_sweep) {
+        // Marks are useless when the next pass is dense anyway.  After two
+        // sweeps in a row that changed almost every vertex, the next sweep
+        // skips them and the one after it is dense.  An asynchronous sweep's
+        // two passes count as one (its catch-up pass marks like its main pass).
+        const bool high =
+            (double)vc->pass_changed_entries * 1000.0 >= (double)kHighPermille * (double)s.active_entries;
+        c->skip_marks = (high && vc->last_pass_high && vc->allow_dense) ? 1 : 0;
+        c->last_pass_high = high ? 1 : 0;
+        c->pass_changed_entries = 0;
+    }
+    if (compacted) {
         c->dense[wr] = dense_next;
         c->rd = wr;
     }
-    c->pass_changed_entries = 0;
     c->ovf_count = 0;
     c->ticket = 0;
     __threadfence();
-    if (role != 1 && in_graph) cudaGraphSetConditional(h, any ? 1u : 0u);
+    if (ends_sweep && in_graph) cudaGraphSetConditional(h, any ? 1u : 0u);
 }
 
 // After a pass over buffer rd: (1) at the end of a sparse sync sweep, apply
@@ -482,15 +511,17 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
 // instead); (2) the next pass is dense (static lists, every vertex) when the
 // vertices changed since the last compaction hold at least dense_permille of
 // all entries -- then the flags are only cleared -- else the flags are
-// compacted into the per-bin frontier lists of buffer rd ^ 1; (3) the last
-// block runs the control step.
+// compacted into the per-bin frontier lists of buffer rd ^ 1 (the catch-up
+// compaction of an asynchronous sweep takes only marked vertices outside the
+// sweep's main frontier and is never dense); (3) the last block runs the
+// control step.
 __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, int role,
                                                            cudaGraphConditionalHandle h, int in_graph) {
     const int rd = s.ctrl->rd, wr = rd ^ 1;
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned gstride = gridDim.x * blockDim.x;
 
-    if (role != 1 && mode != MODE_ASYNC && !s.ctrl->dense[rd]) {
+    if ((role == kRoleEndSweep || role == kRoleControl) && mode != MODE_ASYNC && !s.ctrl->dense[rd]) {
         const int cb = s.ctrl->cbuf;
         int32_t* C = s.lab[cb];
         const int32_t* Cn = s.lab[cb ^ 1];
@@ -511,14 +542,18 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
         }
     }
 
+    const bool catch_up = role == kRoleCatchUp;
     const unsigned long long che = ((volatile Ctrl*)s.ctrl)->pass_changed_entries;
-    const int dense = s.ctrl->allow_dense &&
+    const int dense = !catch_up && s.ctrl->allow_dense &&
                       (mode == MODE_SYNC_FULL || s.ctrl->skip_marks ||
                        (double)che * 1000.0 >= (double)s.dense_permille * (double)s.active_entries);
 
     const int64_t nchunks = (s.N + kVertsPerThread - 1) / kVertsPerThread;
-    if (role == 2) {
+    if (role == kRoleControl) {
         // serving cycles leave the marks for the next cycle's compaction
+    } else if (catch_up && (s.ctrl->dense[rd] || s.ctrl->skip_marks)) {
+        // the main pass scanned every vertex (or recorded no marks): nothing
+        // is left to reach in this sweep; the marks wait for the next one
     } else if (dense) {
         if (mode != MODE_SYNC_FULL) {
             for (int64_t ch = gtid; ch < nchunks; ch += gstride) {
@@ -531,24 +566,33 @@ __global__ void __launch_bounds__(kFrontThreads) k_finish(DevState s, int mode, 
             }
         }
     } else {
+        // the compaction that starts an asynchronous sweep records its frontier
+        const bool record = mode == MODE_ASYNC && !catch_up;
         for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nchunks; base += gstride) {
             const int64_t ch = base + threadIdx.x;
             const int64_t v0 = ch * kVertsPerThread;
             uint4 raw = make_uint4(0, 0, 0, 0);
-            bool anyf = false;
-            if (ch < nchunks) anyf = load_flags(s.flags, s.N, v0, true, raw);
+            uint32_t pick = 0;
+            if (ch < nchunks && load_flags(s.flags, s.N, v0, !catch_up, raw)) {
+                pick = flag_mask(raw);
+                if (catch_up) {
+                    pick &= ~(uint32_t)s.fr_bits[ch];       // scanned this sweep: keep the mark
+                    if (pick) clear_flags(s.flags, s.N, v0, raw, pick);
+                }
+            }
             Chunk c;
             chunk_reset(c, v0);
-            if (anyf) {
+            if (pick) {
 #pragma unroll
                 for (int q = 0; q < kVertsPerThread; ++q) {
-                    if (flag_at(raw, q)) {
+                    if ((pick >> q) & 1u) {
                         const int64_t d = s.off_end[v0 + q] - s.off[v0 + q];
                         if (d > 0) chunk_add(c, q, bin_of(s, d), d);
                     }
                 }
             }
-            if (__syncthreads_or(anyf))
+            if (record && ch < nchunks) s.fr_bits[ch] = (uint16_t)pick;
+            if (__syncthreads_or(pick != 0))
                 block_append<true>(s.bin_base, s.flist, s.ctrl->bin_cnt[wr], s.ctrl->bin_entries[wr], c);
         }
     }

@@ -131,6 +131,8 @@ struct DevState {
                                // the other one (every scanned vertex in dense sweeps, then the
                                // buffers flip; only changed vertices in sparse sweeps, then applied)
     uint8_t* flags;            // [N] 1 = unprocessed (Algorithm 1)
+    uint16_t* fr_bits;         // [N/16 + 1] async: bit q of word c = vertex 16c + q is in this sweep's
+                               // main frontier (written by the sparse compaction that starts a sweep)
     int32_t* slist;            // [N] static lists: vertices with an entry, by bin, ascending
     int32_t* flist;            // [N] frontier lists of the sparse sweeps, same bin regions
     int32_t* chg;              // [N] sync mode, aligned with list slots: vertex if changed, else -1
@@ -180,11 +182,18 @@ cudaError_t build_static_lists(DevState& s, cudaStream_t st, unsigned* counts, u
 cudaError_t ovf_capacity(const DevState& s, cudaStream_t st, int sms, int64_t* pairs, int64_t* counts,
                          int64_t* rows, unsigned long long* scratch3);
 cudaError_t launch_init_cond(const DevState& s, cudaGraphConditionalHandle h, int in_graph, cudaStream_t st);
-// role 0: end of a sweep (apply, compaction for the next sweep, control);
-// role 1: compaction only (inside an asynchronous sweep, of the vertices the
-// main pass re-marked; or at the start of a serving cycle);
-// role 2: end of a serving cycle (apply, control; the marks stay for the next
-// cycle's compaction, which also picks up newly admitted requests).
+// Roles of the finish kernel.  A sweep scans each vertex at most once
+// (Algorithm 1): the compaction that starts a sweep takes every marked vertex
+// and records them in fr_bits; the asynchronous catch-up compaction takes only
+// the vertices marked since then that are not in that frontier (the ones the
+// serial loop would still reach later in the same sweep); the others keep
+// their mark for the next sweep.
+enum FinishRole {
+    kRoleEndSweep = 0,    // apply, compaction that starts the next sweep, control
+    kRoleCatchUp = 1,     // async: compaction of the catch-up set only
+    kRoleControl = 2,     // end of a serving cycle: apply, control; marks stay for the next cycle
+    kRoleStartSweep = 3,  // start of a serving cycle: compaction (also of newly admitted requests)
+};
 cudaError_t launch_finish(const DevState& s, int mode, int role, cudaGraphConditionalHandle h, int in_graph,
                           cudaStream_t st, int sms);
 cudaError_t launch_finalize(const DevState& s, cudaStream_t st, int sms);

@@ -292,13 +292,14 @@ cudaError_t run_cycle(lpa_server* S) {
     const int passes = mode == MODE_ASYNC ? 2 : 1;
     cudaError_t e = cudaSuccess;
     for (int p = 0; p < passes && e == cudaSuccess; ++p) {
-        e = launch_finish(s, mode, 1, none, 0, st, S->sms);                         // compaction
+        // compaction: the cycle's frontier, then (async) the catch-up set
+        e = launch_finish(s, mode, p == 0 ? kRoleStartSweep : kRoleCatchUp, none, 0, st, S->sms);
         if (e == cudaSuccess) e = launch_sweep_small(s, mode, st, S->sms);
         if (e == cudaSuccess) e = launch_sweep_warp(s, mode, st, S->sms);
         for (int b = 2; b < kBins && e == cudaSuccess; ++b)
             e = launch_sweep_block(s, mode, b, block_grid_for(s, b, S->sms), st);
     }
-    if (e == cudaSuccess) e = launch_finish(s, mode, 2, none, 0, st, S->sms);       // apply + control
+    if (e == cudaSuccess) e = launch_finish(s, mode, kRoleControl, none, 0, st, S->sms);   // apply + control
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->h_done, s.done, (size_t)S->S * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
@@ -516,7 +517,8 @@ lpa_status lpa_serve_create(const lpa_serve_config* cfg, lpa_server_t* out) {
     if ((rs = dalloc_t(S, &begin, V)) || (rs = dalloc_t(S, &end, V)) || (rs = dalloc_t(S, &idx, E)) ||
         (rs = dalloc_t(S, &w, E)) || (rs = dalloc_t(S, &gid, V)) || (rs = dalloc_t(S, &gb, G)) ||
         (rs = dalloc_t(S, &ge, G)) || (rs = dalloc_t(S, &s.lab[0], V)) || (rs = dalloc_t(S, &s.lab[1], V)) ||
-        (rs = dalloc_t(S, &s.flags, V + 16)) || (rs = dalloc_t(S, &s.slist, 1)) ||
+        (rs = dalloc_t(S, &s.flags, V + 16)) || (rs = dalloc_t(S, &s.fr_bits, V / 16 + 1)) ||
+        (rs = dalloc_t(S, &s.slist, 1)) ||
         (rs = dalloc_t(S, &s.flist, V * kBins)) || (rs = dalloc_t(S, &s.chg, V * kBins)) ||
         (rs = dalloc_t(S, &s.ctrl, 1)) || (rs = dalloc_t(S, &s.dN, G)) || (rs = dalloc_t(S, &s.done, G)) ||
         (rs = dalloc_t(S, &s.iters, G)) || (rs = dalloc_t(S, &s.exit_reason, G)) ||

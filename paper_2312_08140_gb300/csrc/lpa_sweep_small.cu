@@ -5,7 +5,10 @@
 // label of entry q is the total weight of entries carrying the same label.
 // Self-loops are skipped (scanCommunities, Algorithm 1); ties go to the
 // smallest label id (Section 4.1.5).  When the label changes the thread marks
-// all other neighbours unprocessed (vertex pruning, Section 4.1.4).
+// all other neighbours unprocessed (vertex pruning, Section 4.1.4).  One
+// resident wave of threads walks the frontier, each thread as a three-stage
+// software pipeline (offsets and own label -> row -> neighbour labels) over
+// its slots, so the loads of three consecutive slots overlap.
 //
 // Asynchronous mode (k_sweep_small_async): each thread takes a run of kRun
 // consecutive frontier entries and processes them one after another, so a
@@ -34,6 +37,54 @@ constexpr int kRun = 8;                               // async run length
 constexpr int kTile = kRun * kSmallThreads;           // frontier entries staged per block step
 constexpr int kStride = kRun + 1;                     // shared-memory words per run
 
+// Eq. 2 over the at most MAXD entries of one row held in registers: the sum
+// of each entry's label (empty entries hold kEmptyKey and weight 0), then the
+// largest sum, then the smallest tie key among the entries that hold it.
+// Integer sums are exact in any order, so each pair of entries is compared
+// once and adds both ways; fp32 sums keep ascending entry order.  Returns the
+// winning label, or -1 when the row has no candidate.
+template <int WK, int MAXD>
+__device__ __forceinline__ int32_t small_argmax(const int32_t (&lab)[MAXD], const typename Acc<WK>::T (&wt)[MAXD],
+                                                const TieRule& tr) {
+    using T = typename Acc<WK>::T;
+    uint32_t sk[MAXD];
+    if constexpr (WK == W_F32) {
+#pragma unroll
+        for (int q = 0; q < MAXD; ++q) {
+            T sum = 0;
+#pragma unroll
+            for (int r = 0; r < MAXD; ++r) sum += (lab[r] == lab[q]) ? wt[r] : (T)0;
+            sk[q] = lab[q] != kEmptyKey ? sum_key(sum) : 0u;
+        }
+    } else {
+        T sum[MAXD];
+#pragma unroll
+        for (int q = 0; q < MAXD; ++q) sum[q] = wt[q];
+#pragma unroll
+        for (int q = 0; q < MAXD; ++q) {
+#pragma unroll
+            for (int r = q + 1; r < MAXD; ++r) {
+                if (lab[q] == lab[r]) {
+                    sum[q] += wt[r];
+                    sum[r] += wt[q];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MAXD; ++q) sk[q] = lab[q] != kEmptyKey ? sum_key(sum[q]) : 0u;
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < MAXD; ++q) m = sk[q] > m ? sk[q] : m;
+    uint32_t best_k = 0xffffffffu;
+#pragma unroll
+    for (int q = 0; q < MAXD; ++q) {
+        const uint32_t kq = tr.key(lab[q]);
+        if (sk[q] == m && kq < best_k) best_k = kq;
+    }
+    return m != 0u ? tr.label(best_k) : -1;
+}
+
 template <bool NS, int WK, bool BATCH, int MAXD>
 __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
@@ -48,77 +99,92 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
     const bool ident = identity_sweep<false, BATCH>(s);
     const unsigned cnt = iota ? (unsigned)s.N : bv.cnt;
     const unsigned stride = gridDim.x * blockDim.x;
-    constexpr int RUN = 1;                            // async mode uses k_sweep_small_async
-    const unsigned nruns = (cnt + RUN - 1) / RUN;
-    unsigned long long my_changed = 0, my_changed_entries = 0;
-    for (unsigned rbase = blockIdx.x * blockDim.x; rbase < nruns; rbase += stride)
-    for (int step = 0; step < RUN; ++step) {
-        const unsigned run = rbase + threadIdx.x;
-        const unsigned k = run * RUN + step;
-        bool slot = run < nruns && k < cnt;
-        const int32_t v = slot ? (iota ? (int32_t)k : bv.list[k]) : 0;
-        int64_t st = 0;
-        int d = 0;
-        if (iota && slot) {
-            st = s.off[v];
-            const int64_t dd = s.off_end[v] - st;
-            slot = dd >= 1 && dd <= s.small_max;
-            d = slot ? (int)dd : 0;
-        }
-        bool act = slot;
-        if constexpr (BATCH) {
-            if (act && s.done[s.gid[v]]) act = false;
-        }
-        int32_t own = 0;
-        if (slot) own = L.C[v];
-        if (!act) {
-            d = 0;
-        } else if (!iota) {
-            st = s.off[v];
-            d = (int)(s.off_end[v] - st);
-        }
+    const int small_max = s.small_max;
+
+    // Each thread walks the frontier slots k, k + stride, ... as a software
+    // pipeline: while slot k is evaluated (its neighbour labels in flight),
+    // the row of the next slot and the offsets and own label of the one after
+    // are loaded too, so a step waits for about one load latency instead of
+    // the whole chain frontier id -> offsets -> row -> labels.
+    struct Head {
+        int64_t st, en;
+        int32_t v, own, g;
+    };
+    struct Row {
+        int32_t v, own, g, done;
+        int d;
+        bool slot;
         int32_t nb[MAXD];
+        T wt[MAXD];
+    };
+    auto vertex_of = [&](unsigned k) -> int32_t { return k < cnt ? (iota ? (int32_t)k : bv.list[k]) : -1; };
+    auto head_of = [&](int32_t v) -> Head {
+        Head h{0, 0, v, 0, 0};
+        if (v >= 0) {
+            h.st = s.off[v];
+            h.en = s.off_end[v];
+            h.own = L.C[v];
+            if constexpr (BATCH) h.g = s.gid[v];
+        }
+        return h;
+    };
+    auto row_of = [&](const Head& h) -> Row {
+        Row r;
+        r.v = h.v;
+        r.own = h.own;
+        r.g = h.g;
+        const int64_t dd = h.en - h.st;
+        r.slot = h.v >= 0 && (!iota || (dd >= 1 && dd <= small_max));
+        r.d = r.slot ? (int)dd : 0;
+#pragma unroll
+        for (int q = 0; q < MAXD; ++q) {
+            r.nb[q] = q < r.d ? load_index(s.idx, h.st + q) : h.v;
+            r.wt[q] = q < r.d ? load_weight<WK>(s.w, h.st + q) : (T)0;
+        }
+        r.done = 0;
+        if constexpr (BATCH) r.done = r.slot ? s.done[r.g] : 0;
+        return r;
+    };
+
+    const unsigned k0 = blockIdx.x * blockDim.x + threadIdx.x;
+    Row cur = row_of(head_of(vertex_of(k0)));
+    Head nxt = head_of(vertex_of(k0 + stride));
+    int32_t vn = vertex_of(k0 + 2 * stride);
+    unsigned long long my_changed = 0, my_changed_entries = 0;
+    for (unsigned rbase = blockIdx.x * blockDim.x; rbase < cnt; rbase += stride) {
+        const unsigned k = rbase + threadIdx.x;
+        const int32_t v = cur.v;
+        const bool act = cur.slot && !(BATCH && cur.done);
         int32_t lab[MAXD];
         T wt[MAXD];
 #pragma unroll
         for (int q = 0; q < MAXD; ++q) {
-            bool ok = q < d;
-            const int32_t j = ok ? load_index(s.idx, st + q) : v;
-            nb[q] = j;
-            ok = ok && (j != v);
-            lab[q] = ok ? (ident ? j : load_label<false>(L.C, j)) : kEmptyKey;
-            wt[q] = ok ? load_weight<WK>(s.w, st + q) : (T)0;
+            const bool ok = act && q < cur.d && cur.nb[q] != v;
+            lab[q] = ok ? (ident ? cur.nb[q] : load_label<false>(L.C, cur.nb[q])) : kEmptyKey;
+            wt[q] = ok ? cur.wt[q] : (T)0;
         }
+        // the next stages, issued before this slot's labels are consumed
+        const Row r_next = row_of(nxt);
+        const Head h_next = head_of(vn);
+        const int32_t v_next = vertex_of(k + 3 * stride);
+
         const TieRule tr = tie_rule(s, NS && act, sweep, v);
-        bool any = false;
-        T best_w = 0;
-        uint32_t best_k = 0xffffffffu;
-#pragma unroll
-        for (int q = 0; q < MAXD; ++q) {
-            T sum = 0;
-#pragma unroll
-            for (int r = 0; r < MAXD; ++r) sum += (lab[r] == lab[q]) ? wt[r] : (T)0;
-            const uint32_t kq = lab[q] != kEmptyKey ? tr.key(lab[q]) : 0xffffffffu;
-            const bool better = lab[q] != kEmptyKey && (!any || sum > best_w || (sum == best_w && kq < best_k));
-            if (better) {
-                any = true;
-                best_w = sum;
-                best_k = kq;
-            }
-        }
-        const int32_t best = tr.label(best_k);
-        const bool changed = act && any && best != own;
-        if (slot) record_label<false>(L, bv.chg + k, v, own, best, changed);
+        const int32_t best = small_argmax<WK, MAXD>(lab, wt, tr);
+        const bool changed = act && best >= 0 && best != cur.own;
+        if (cur.slot) record_label<false>(L, bv.chg + k, v, cur.own, best, changed);
         if (changed) {
             if (marks) {
 #pragma unroll
                 for (int q = 0; q < MAXD; ++q)
-                    if (q < d && nb[q] != v) s.flags[nb[q]] = 1;
+                    if (q < cur.d && cur.nb[q] != v) s.flags[cur.nb[q]] = 1;
             }
             ++my_changed;
-            my_changed_entries += (unsigned)d;
+            my_changed_entries += (unsigned)cur.d;
         }
         count_graph_changes<BATCH>(s, changed, v);
+        cur = r_next;
+        nxt = h_next;
+        vn = v_next;
     }
     flush_bin_counts(s, 0, my_changed, my_changed_entries);
 }
@@ -195,26 +261,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small_async(DevState s,
                     else wt[q] = ok ? sw[q * SL + pos] : (T)0;
                 }
                 const TieRule tr = tie_rule(s, NS, sweep, v);
-                bool any = false;
-                T best_w = 0;
-                uint32_t best_k = 0xffffffffu;
-#pragma unroll
-                for (int q = 0; q < MAXD; ++q) {
-                    T sum = 0;
-#pragma unroll
-                    for (int r = 0; r < MAXD; ++r) sum += (lab[r] == lab[q]) ? wt[r] : (T)0;
-                    const uint32_t kq = lab[q] != kEmptyKey ? tr.key(lab[q]) : 0xffffffffu;
-                    const bool better =
-                        lab[q] != kEmptyKey && (!any || sum > best_w || (sum == best_w && kq < best_k));
-                    if (better) {
-                        any = true;
-                        best_w = sum;
-                        best_k = kq;
-                    }
-                }
-                const int32_t best = tr.label(best_k);
+                const int32_t best = small_argmax<WK, MAXD>(lab, wt, tr);
                 const int32_t own = sown[pos];
-                changed = any && best != own;
+                changed = best >= 0 && best != own;
                 if (changed) {
                     L.C[v] = best;
                     if (marks) {
@@ -248,6 +297,17 @@ static cudaError_t launch_small_async_t(const DevState& s, int flag, int sms, cu
     return cudaGetLastError();
 }
 
+// One resident wave: each thread runs its pipeline over many slots.
+template <bool NS, int WK, bool BATCH, int MAXD>
+static cudaError_t launch_small_sync_t(const DevState& s, int flag, int sms, cudaStream_t st) {
+    auto kern = k_sweep_small<NS, WK, BATCH, MAXD>;
+    int per_sm = 0;
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSmallThreads, 0);
+    if (err != cudaSuccess) return err;
+    kern<<<sms * (per_sm > 0 ? per_sm : 1), kSmallThreads, 0, st>>>(s, flag);
+    return cudaGetLastError();
+}
+
 template <int WK, bool BATCH, bool NS>
 static cudaError_t launch_small_t(const DevState& s, bool async, int flag, int sms, cudaStream_t st) {
     const bool four = s.small_max <= 4;
@@ -255,9 +315,8 @@ static cudaError_t launch_small_t(const DevState& s, bool async, int flag, int s
         return four ? launch_small_async_t<WK, BATCH, 4, NS>(s, flag, sms, st)
                     : launch_small_async_t<WK, BATCH, 8, NS>(s, flag, sms, st);
     }
-    if (four) k_sweep_small<NS, WK, BATCH, 4><<<sms * 8, kSmallThreads, 0, st>>>(s, flag);
-    else k_sweep_small<NS, WK, BATCH, 8><<<sms * 8, kSmallThreads, 0, st>>>(s, flag);
-    return cudaGetLastError();
+    return four ? launch_small_sync_t<NS, WK, BATCH, 4>(s, flag, sms, st)
+                : launch_small_sync_t<NS, WK, BATCH, 8>(s, flag, sms, st);
 }
 
 template <int WK, bool NS>
