@@ -137,7 +137,6 @@ struct Engine {
     int64_t max_degree = 0;
     int64_t device_bytes = 0;
     lpa_config cfg{4, 128, 512, 2048, 500};
-    int block_grid[kBlockBins] = {0, 0, 0};
     Overflow* ovf = nullptr;
     cudaGraph_t graph[6] = {};         // per mode, strict (0..2) and non-strict (3..5)
     cudaGraphExec_t exec[6] = {};
@@ -191,7 +190,6 @@ void engine_free(Engine& E) {
 // Grid sizes of the block bins, and the overflow list of the last bin (one
 // entry per vertex of that bin at most).
 lpa_status setup_blocks(Engine& E, cudaStream_t st) {
-    for (int b = 0; b < kBlockBins; ++b) E.block_grid[b] = block_grid_for(E.s, b + 2, E.sms);
     std::vector<void*> old;
     if (E.ovf) old.push_back(E.ovf);
     for (void* p : E.ovf_scratch) old.push_back(p);
@@ -404,7 +402,7 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
 cudaError_t launch_bin(Engine& E, int mode, int bin, cudaStream_t st) {
     if (bin == 0) return launch_sweep_small(E.s, mode, st, E.sms);
     if (bin == 1) return launch_sweep_warp(E.s, mode, st, E.sms);
-    return launch_sweep_block(E.s, mode, bin, E.block_grid[bin - 2], st);
+    return launch_sweep_block(E.s, mode, bin, E.sms, st);
 }
 
 // A sweep's frontier is a subset of the static bin lists (same thresholds,

@@ -195,15 +195,18 @@ __device__ __forceinline__ uint32_t slot_of(int32_t label, int log_slots) {
 }
 
 // Open-addressing insert-or-add into a table with 2^log_slots slots whose
-// free slots hold kEmptyKey.  Callers size the table at >= 2 x the distinct
-// labels it can receive, so a free slot always exists; the probe is still
-// bounded by the table size and reports failure instead of looping.
+// free slots hold kEmptyKey, probing at most max_probes slots.  Returns false
+// if the label is not in the probed slots and none of them was free.
+// `created` receives the slot this call claimed for a new label, else -1, so
+// callers can list the slots a row filled and scan only those.
 template <typename T>
-__device__ __forceinline__ bool table_add(int32_t* keys, T* vals, int log_slots, int32_t label, T w) {
+__device__ __forceinline__ bool table_insert(int32_t* keys, T* vals, int log_slots, int32_t label, T w,
+                                             uint32_t max_probes, int& created) {
     const uint32_t mask = (1u << log_slots) - 1u;
     uint32_t h = slot_of(label, log_slots);
     volatile int32_t* vkeys = keys;
-    for (uint32_t p = 0; p <= mask; ++p) {
+    created = -1;
+    for (uint32_t p = 0; p < max_probes; ++p) {
         int32_t k = vkeys[h];
         if (k == label) {
             atomicAdd(vals + h, w);
@@ -212,6 +215,7 @@ __device__ __forceinline__ bool table_add(int32_t* keys, T* vals, int log_slots,
         if (k == kEmptyKey) {
             int32_t old = atomicCAS(keys + h, kEmptyKey, label);
             if (old == kEmptyKey || old == label) {
+                if (old == kEmptyKey) created = (int)h;
                 atomicAdd(vals + h, w);
                 return true;
             }
@@ -219,6 +223,15 @@ __device__ __forceinline__ bool table_add(int32_t* keys, T* vals, int log_slots,
         h = (h + 1u) & mask;
     }
     return false;
+}
+
+// Insert-or-add probing the whole table.  Callers size the table at >= 2 x
+// the distinct labels it can receive, so a free slot always exists; the probe
+// is still bounded by the table size and reports failure instead of looping.
+template <typename T>
+__device__ __forceinline__ bool table_add(int32_t* keys, T* vals, int log_slots, int32_t label, T w) {
+    int created;
+    return table_insert<T>(keys, vals, log_slots, label, w, 1u << log_slots, created);
 }
 
 // Bounded variant: gives up after max_probes occupied slots; returns false if
@@ -227,28 +240,17 @@ __device__ __forceinline__ bool table_add(int32_t* keys, T* vals, int log_slots,
 template <typename T>
 __device__ __forceinline__ bool table_add_bounded(int32_t* keys, T* vals, int log_slots, int32_t label, T w,
                                                   int max_probes) {
-    const uint32_t mask = (1u << log_slots) - 1u;
-    uint32_t h = slot_of(label, log_slots);
-    volatile int32_t* vkeys = keys;
-    for (int p = 0; p < max_probes; ++p) {
-        int32_t k = vkeys[h];
-        if (k == label) {
-            atomicAdd(vals + h, w);
-            return true;
-        }
-        if (k == kEmptyKey) {
-            int32_t old = atomicCAS(keys + h, kEmptyKey, label);
-            if (old == kEmptyKey || old == label) {
-                atomicAdd(vals + h, w);
-                return true;
-            }
-        }
-        h = (h + 1u) & mask;
-    }
-    return false;
+    int created;
+    return table_insert<T>(keys, vals, log_slots, label, w, (uint32_t)max_probes, created);
 }
 
 __device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ unsigned lanes_below() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
 
 // Batched runs: dN of each graph, aggregated over the lanes of a warp that
 // changed a vertex of the same graph.  All 32 lanes must call.

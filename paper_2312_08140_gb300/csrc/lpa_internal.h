@@ -201,10 +201,9 @@ cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, i
                               int32_t* labels_out, int local_ids, cudaStream_t st);
 cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms);
 cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int sms);
-// Block-per-vertex sweep of bin 2, 3 or 4; `blocks` from block_grid_for.
+// Block-per-vertex sweep of bin 2, 3 or 4 (one resident wave over `sms` SMs).
 // For bin 4 this also launches the partitioned rescan of overflowed rows.
-cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int blocks, cudaStream_t st);
-int block_grid_for(const DevState& s, int bin, int sms);
+cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int sms, cudaStream_t st);
 
 // Graph validation (row-wise).  Results accumulate into *res (device).
 struct ValidateResult {

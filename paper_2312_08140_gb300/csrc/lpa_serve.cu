@@ -297,7 +297,7 @@ cudaError_t run_cycle(lpa_server* S) {
         if (e == cudaSuccess) e = launch_sweep_small(s, mode, st, S->sms);
         if (e == cudaSuccess) e = launch_sweep_warp(s, mode, st, S->sms);
         for (int b = 2; b < kBins && e == cudaSuccess; ++b)
-            e = launch_sweep_block(s, mode, b, block_grid_for(s, b, S->sms), st);
+            e = launch_sweep_block(s, mode, b, S->sms, st);
     }
     if (e == cudaSuccess) e = launch_finish(s, mode, kRoleControl, none, 0, st, S->sms);   // apply + control
     if (e == cudaSuccess) e = cudaMemcpyAsync(S->h_done, s.done, (size_t)S->S * 4, cudaMemcpyDeviceToHost, st);

@@ -6,9 +6,10 @@
 //
 // Warps read the row in 32-entry chunks and group equal labels with
 // __match_any_sync as in the warp kernel; group leaders add their sums into a
-// shared-memory open-addressing table; the block then reduces (sum, smallest
-// label) to the winner (Eq. 2; Section 4.1.5) and, on change, marks the
-// neighbours unprocessed (Section 4.1.4).
+// shared-memory open-addressing table and list the slots they fill; the block
+// then scans the listed slots and reduces (sum, smallest label) to the winner
+// (Eq. 2; Section 4.1.5) and, on change, marks the neighbours unprocessed
+// (Section 4.1.4).
 //
 // Last bin (d > large_max): the table has kLargeSlots slots.  Rows longer than
 // kLargeSlots / 2 may carry more distinct labels than it holds; their inserts
@@ -55,15 +56,32 @@ __device__ __forceinline__ uint32_t block_argmax(uint32_t key, uint32_t tie, uin
     return *winner;
 }
 
-// Scans table slots [0, slots) for this thread's best candidate under the
-// row's tie rule (sum key, tie key) and clears the slots it visits.
+// Each warp lists the table slots it fills for the current row in its own
+// segment of `seg_cap` entries (no atomics: the count is the same register in
+// every lane).  All 32 lanes call; entries past the segment are dropped (the
+// count still grows, which sends the scan to the whole table).
+__device__ __forceinline__ void list_filled(int created, uint16_t* seg, unsigned seg_cap, unsigned& wfill) {
+    const unsigned nm = __ballot_sync(kFull, created >= 0);
+    if (created >= 0) {
+        const unsigned pos = wfill + __popc(nm & lanes_below());
+        if (pos < seg_cap) seg[pos] = (uint16_t)created;
+    }
+    wfill += __popc(nm);
+}
+
+// This thread's best candidate of the row's table under the row's tie rule
+// (sum key, tie key); clears the slots it visits.  With `lists` the slots the
+// row filled are read from the warps' segments (wcnt[w] entries of segment w,
+// seg_cap each; wpre holds their prefix sums); without, or when a segment
+// overflowed, all `slots` slots are scanned.
 template <typename T>
-__device__ __forceinline__ void scan_table(int32_t* keys, T* vals, int slots, const TieRule& tr, uint32_t& key,
-                                           uint32_t& tie) {
+__device__ __forceinline__ void scan_table(int32_t* keys, T* vals, int slots, bool lists, const uint16_t* segs,
+                                           unsigned seg_cap, const unsigned* wpre, int nw, const TieRule& tr,
+                                           uint32_t& key, uint32_t& tie) {
     bool any = false;
     T best_w = 0;
     uint32_t best_k = 0xffffffffu;
-    for (int q = threadIdx.x; q < slots; q += blockDim.x) {
+    auto visit = [&](int q) {
         const int32_t kq = keys[q];
         if (kq != kEmptyKey) {
             const T vq = vals[q];
@@ -76,6 +94,16 @@ __device__ __forceinline__ void scan_table(int32_t* keys, T* vals, int slots, co
             keys[q] = kEmptyKey;
             vals[q] = (T)0;
         }
+    };
+    if (lists) {
+        const unsigned total = wpre[nw];
+        for (unsigned f = threadIdx.x; f < total; f += blockDim.x) {
+            int w = 0;
+            while (w + 1 < nw && wpre[w + 1] <= f) ++w;
+            visit(segs[(size_t)w * seg_cap + (f - wpre[w])]);
+        }
+    } else {
+        for (int q = threadIdx.x; q < slots; q += blockDim.x) visit(q);
     }
     key = any ? sum_key(best_w) : 0u;
     tie = best_k;
@@ -90,14 +118,23 @@ __device__ __forceinline__ void mark_neighbours(const DevState& s, int32_t v, in
 
 // U: chunks in flight per warp (4 for the last bin, whose rows span many
 // chunks per warp; 1 for the middle bins, where the SM's 64 warps already
-// overlap the few chunks of each row).
-template <bool ASYNC, int WK, bool BATCH, int U, bool NS>
+// overlap the few chunks of each row).  LISTS: the warps list the slots they
+// fill and the scan reads only those (middle bins; the last bin's rows fill
+// many slots, and its table is scanned whole).
+template <bool ASYNC, int WK, bool BATCH, int U, bool NS, bool LISTS>
 __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int S = s.block_slots[bin - 2];
     int32_t* keys = reinterpret_cast<int32_t*>(smem_raw);
     T* vals = reinterpret_cast<T*>(keys + S);
+    // per-warp lists of the slots a row filled: S / 2 entries in nw segments
+    const unsigned seg_cap = (unsigned)S / 2u / (blockDim.x >> 5);
+    uint16_t* segs = reinterpret_cast<uint16_t*>(vals + S);
+    uint16_t* my_seg = segs + (size_t)(threadIdx.x >> 5) * seg_cap;
+    unsigned wfill = 0;
+    __shared__ unsigned wpre[33];      // [0, nw]: prefix sums of the warps' counts; [32]: the largest count
+    static_assert(kBlockThreads[kBlockBins - 1] / 32 < 32, "wpre holds nw + 1 prefix sums and the maximum");
     __shared__ uint32_t red_key[32];
     __shared__ uint32_t red_tie[32];
     __shared__ int overflow;
@@ -197,18 +234,38 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
                         }
                         lead = ok && lane == (unsigned)(__ffs(peers) - 1);
                     }
+                    int created = -1;
                     if (lead) {
                         if (fits) {
-                            if (!table_add<T>(keys, vals, log_s, lab[u], w)) atomicExch(&s.ctrl->error, 3);
-                        } else if (!table_add_bounded<T>(keys, vals, log_s, lab[u], w, kSharedProbes)) {
+                            if (!table_insert<T>(keys, vals, log_s, lab[u], w, 1u << log_s, created))
+                                atomicExch(&s.ctrl->error, 3);
+                        } else if (!table_insert<T>(keys, vals, log_s, lab[u], w, kSharedProbes, created)) {
                             overflow = 1;
                         }
                     }
+                    if constexpr (LISTS) list_filled(created, my_seg, seg_cap, wfill);
                 }
             }
+            bool lists = false;
+            if constexpr (LISTS) {
+                if (lane == 0) wpre[wib + 1] = wfill;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned acc = 0, mx = 0;
+                    wpre[0] = 0;
+                    for (int w = 1; w <= nw; ++w) {
+                        mx = wpre[w] > mx ? wpre[w] : mx;
+                        acc += wpre[w];
+                        wpre[w] = acc;
+                    }
+                    wpre[32] = mx;
+                }
+                wfill = 0;
+            }
             __syncthreads();
+            if constexpr (LISTS) lists = wpre[32] <= seg_cap;
             uint32_t key, tie;
-            scan_table<T>(keys, vals, 1 << log_s, tr, key, tie);     // also clears the table
+            scan_table<T>(keys, vals, 1 << log_s, lists, segs, seg_cap, wpre, nw, tr, key, tie);   // and clears
             const int ovf = overflow;
             const uint32_t best_tie = block_argmax(key, tie, red_key, red_tie, &winner);
             best_lab = best_tie == 0xffffffffu ? -1 : tr.label(best_tie);
@@ -607,7 +664,7 @@ __global__ void __launch_bounds__(kSliceThreads, 2) k_ovf_parts(DevState s, int 
         __syncthreads();
         const TieRule tr = tie_rule(s, NS, sweep, o.v);
         uint32_t key, tie;
-        scan_table<T>(keys, vals, S, tr, key, tie);
+        scan_table<T>(keys, vals, S, false, nullptr, 0u, nullptr, 0, tr, key, tie);     // the whole table
         const uint32_t part_best = block_argmax(key, tie, red_key, red_tie, &winner);
         fold_partition<ASYNC, BATCH>(s, L, bv, o, tr, marks, key, tie, part_best, my_changed, my_changed_entries);
     }
@@ -689,7 +746,7 @@ __global__ void k_sweep_parts(DevState s, int flag_neighbours) {
         __syncthreads();
         const TieRule tr = tie_rule(s, NS, sweep, o.v);
         uint32_t key, tie;
-        scan_table<T>(keys, vals, S, tr, key, tie);
+        scan_table<T>(keys, vals, S, false, nullptr, 0u, nullptr, 0, tr, key, tie);     // the whole table
         const uint32_t part_best = block_argmax(key, tie, red_key, red_tie, &winner);
         fold_partition<ASYNC, BATCH>(s, L, bv, o, tr, marks, key, tie, part_best, my_changed, my_changed_entries);
     }
@@ -745,22 +802,24 @@ cudaError_t ovf_capacity(const DevState& s, cudaStream_t st, int sms, int64_t* p
     return cudaSuccess;
 }
 
-int block_grid_for(const DevState& s, int bin, int sms) {
-    const int threads = kBlockThreads[bin - 2];
-    const size_t smem = (size_t)s.block_slots[bin - 2] * 8 + 512;
-    int by_smem = (int)((220 * 1024) / smem);
-    int by_threads = 2048 / threads;
-    int per_sm = by_smem < by_threads ? by_smem : by_threads;
-    if (per_sm < 1) per_sm = 1;
-    return sms * per_sm;
+// Dynamic shared memory of a block-bin kernel: the table (S keys, S values)
+// and, in the middle bins, the lists of filled slots (S / 2 two-byte entries).
+static size_t block_smem(const DevState& s, int bin) {
+    return (size_t)s.block_slots[bin - 2] * (bin == kBins - 1 ? 8 : 9);
 }
 
 template <bool ASYNC, int WK, bool BATCH, bool NS>
-static cudaError_t launch_block_t(const DevState& s, int bin, int flag, int blocks, cudaStream_t st) {
-    const size_t smem = (size_t)s.block_slots[bin - 2] * 8;
-    auto kern = bin == kBins - 1 ? k_sweep_block<ASYNC, WK, BATCH, kUnroll, NS> : k_sweep_block<ASYNC, WK, BATCH, 1, NS>;
+static cudaError_t launch_block_t(const DevState& s, int bin, int flag, int sms, cudaStream_t st) {
+    const size_t smem = block_smem(s, bin);
+    auto kern = bin == kBins - 1 ? k_sweep_block<ASYNC, WK, BATCH, kUnroll, NS, false>
+                                 : k_sweep_block<ASYNC, WK, BATCH, 1, NS, true>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
+    // one resident wave: blocks loop over the bin's vertices
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlockThreads[bin - 2], smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = sms * (per_sm > 0 ? per_sm : 1);
     kern<<<blocks, kBlockThreads[bin - 2], smem, st>>>(s, bin, flag);
     err = cudaGetLastError();
     if (err != cudaSuccess || bin != kBins - 1 || !s.ovf_possible) return err;
@@ -787,32 +846,32 @@ static cudaError_t launch_block_t(const DevState& s, int bin, int flag, int bloc
 }
 
 template <bool ASYNC, bool BATCH, bool NS>
-static cudaError_t launch_block_w(const DevState& s, int bin, int flag, int blocks, cudaStream_t st) {
+static cudaError_t launch_block_w(const DevState& s, int bin, int flag, int sms, cudaStream_t st) {
     switch (s.weight_kind) {
-        case W_UNIT: return launch_block_t<ASYNC, W_UNIT, BATCH, NS>(s, bin, flag, blocks, st);
-        case W_U32: return launch_block_t<ASYNC, W_U32, BATCH, NS>(s, bin, flag, blocks, st);
-        case W_U8: return launch_block_t<ASYNC, W_U8, BATCH, NS>(s, bin, flag, blocks, st);
-        default: return launch_block_t<ASYNC, W_F32, BATCH, NS>(s, bin, flag, blocks, st);
+        case W_UNIT: return launch_block_t<ASYNC, W_UNIT, BATCH, NS>(s, bin, flag, sms, st);
+        case W_U32: return launch_block_t<ASYNC, W_U32, BATCH, NS>(s, bin, flag, sms, st);
+        case W_U8: return launch_block_t<ASYNC, W_U8, BATCH, NS>(s, bin, flag, sms, st);
+        default: return launch_block_t<ASYNC, W_F32, BATCH, NS>(s, bin, flag, sms, st);
     }
 }
 
 template <bool NS>
-static cudaError_t launch_block_ns(const DevState& s, bool async, int bin, int flag, int blocks, cudaStream_t st) {
+static cudaError_t launch_block_ns(const DevState& s, bool async, int bin, int flag, int sms, cudaStream_t st) {
     const bool batch = s.G > 1;
     if (async)
-        return batch ? launch_block_w<true, true, NS>(s, bin, flag, blocks, st)
-                     : launch_block_w<true, false, NS>(s, bin, flag, blocks, st);
-    return batch ? launch_block_w<false, true, NS>(s, bin, flag, blocks, st)
-                 : launch_block_w<false, false, NS>(s, bin, flag, blocks, st);
+        return batch ? launch_block_w<true, true, NS>(s, bin, flag, sms, st)
+                     : launch_block_w<true, false, NS>(s, bin, flag, sms, st);
+    return batch ? launch_block_w<false, true, NS>(s, bin, flag, sms, st)
+                 : launch_block_w<false, false, NS>(s, bin, flag, sms, st);
 }
 
-cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int blocks, cudaStream_t st) {
+cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int sms, cudaStream_t st) {
     const bool ns = (mode & kModeNonstrict) != 0;
     mode &= ~kModeNonstrict;
     const bool async = mode == MODE_ASYNC;
     const int flag = mode != MODE_SYNC_FULL;
-    return ns ? launch_block_ns<true>(s, async, bin, flag, blocks, st)
-              : launch_block_ns<false>(s, async, bin, flag, blocks, st);
+    return ns ? launch_block_ns<true>(s, async, bin, flag, sms, st)
+              : launch_block_ns<false>(s, async, bin, flag, sms, st);
 }
 
 }  // namespace lpa

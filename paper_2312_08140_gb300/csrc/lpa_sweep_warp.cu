@@ -10,8 +10,8 @@
 //            (Eq. 2) and the warp takes the argmax directly.
 //   d  > 32: group leaders add their sums into a per-warp open-addressing
 //            table in shared memory sized 2^ceil(log2(2d)) slots (so it can
-//            never fill), then the warp scans the table for the argmax and
-//            clears the slots it used.
+//            never fill) and list the slots they fill; the warp then scans
+//            the listed slots for the argmax and clears them.
 // Ties go to the smallest label id (Section 4.1.5); self-loops are skipped
 // (Algorithm 1).  On change, the warp re-reads the row and marks the
 // neighbours unprocessed (Section 4.1.4).
@@ -55,6 +55,12 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
     const int wib = threadIdx.x >> 5;
     int32_t* keys = reinterpret_cast<int32_t*>(smem_raw) + (size_t)wib * wslots * 2;
     T* vals = reinterpret_cast<T*>(keys + wslots);
+    // slots the current row filled (a row has at most wslots / 2 labels);
+    // `filled` counts them, the same value in every lane
+    uint16_t* filled_slots =
+        reinterpret_cast<uint16_t*>(reinterpret_cast<int32_t*>(smem_raw) + (size_t)kWarpsPerBlock * wslots * 2) +
+        (size_t)wib * (wslots / 2);
+    unsigned filled = 0;
     for (int q = lane; q < wslots; q += 32) {
         keys[q] = kEmptyKey;
         vals[q] = (T)0;
@@ -159,14 +165,19 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                 const int log_slots = ceil_log2(2u * (unsigned)d);
                 auto add_chunk = [&](int32_t lab, T w) {
                     const bool ok = lab != kEmptyKey;
-                    if constexpr (WK == W_F32) {
-                        if (ok && !table_add<T>(keys, vals, log_slots, lab, w)) atomicExch(&s.ctrl->error, 2);
-                    } else {
+                    bool ins = ok;
+                    T add = w;
+                    if constexpr (WK != W_F32) {
                         const unsigned peers = __match_any_sync(kFull, lab);
-                        const T sum = group_sum<WK>(peers, w, lab, ok);
-                        if (ok && lane == (unsigned)(__ffs(peers) - 1) && !table_add<T>(keys, vals, log_slots, lab, sum))
-                            atomicExch(&s.ctrl->error, 2);
+                        add = group_sum<WK>(peers, w, lab, ok);
+                        ins = ok && lane == (unsigned)(__ffs(peers) - 1);
                     }
+                    int created = -1;
+                    if (ins && !table_insert<T>(keys, vals, log_slots, lab, add, 1u << log_slots, created))
+                        atomicExch(&s.ctrl->error, 2);
+                    const unsigned nm = __ballot_sync(kFull, created >= 0);
+                    if (created >= 0) filled_slots[filled + __popc(nm & lanes_below())] = (uint16_t)created;
+                    filled += __popc(nm);
                 };
                 add_chunk(lab_cur, w_cur);                 // first chunk, prefetched
                 for (int64_t e0 = st + 32; e0 < en; e0 += 32 * kWarpUnroll) {
@@ -193,21 +204,20 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                 bool any = false;
                 T best_w = 0;
                 uint32_t best_k = 0xffffffffu;
-                const int slots = 1 << log_slots;
-                for (int q = lane; q < slots; q += 32) {
+                for (unsigned f = lane; f < filled; f += 32) {
+                    const int q = filled_slots[f];
                     const int32_t kq = keys[q];
-                    if (kq != kEmptyKey) {
-                        const T vq = vals[q];
-                        const uint32_t tq = tr.key(kq);
-                        if (!any || vq > best_w || (vq == best_w && tq < best_k)) {
-                            any = true;
-                            best_w = vq;
-                            best_k = tq;
-                        }
-                        keys[q] = kEmptyKey;
-                        vals[q] = (T)0;
+                    const T vq = vals[q];
+                    const uint32_t tq = tr.key(kq);
+                    if (!any || vq > best_w || (vq == best_w && tq < best_k)) {
+                        any = true;
+                        best_w = vq;
+                        best_k = tq;
                     }
+                    keys[q] = kEmptyKey;
+                    vals[q] = (T)0;
                 }
+                filled = 0;
                 __syncwarp();
                 if (any) {
                     key = sum_key(best_w);
@@ -251,7 +261,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
 
 template <bool ASYNC, int WK, bool BATCH, bool NS>
 static cudaError_t launch_warp_t(const DevState& s, int flag, cudaStream_t st, int sms) {
-    const size_t smem = (size_t)kWarpsPerBlock * s.warp_slots * 8;
+    const size_t smem = (size_t)kWarpsPerBlock * s.warp_slots * 9;     // table + list of filled slots
     auto kern = k_sweep_warp<ASYNC, WK, BATCH, NS>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
