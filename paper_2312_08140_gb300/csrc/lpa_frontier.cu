@@ -79,6 +79,7 @@ __global__ void k_init(DevState s) {
         c->pass_changed_entries = 0;
         c->ovf_count = 0;
         for (int b = 0; b < kBins; ++b) {
+            c->row_next[b] = 0;
             c->bin_cnt[0][b] = s.bin_static[b];
             c->bin_entries[0][b] = s.bin_static_entries[b];
             c->bin_cnt[1][b] = 0;
@@ -483,6 +484,7 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
         }
         c->bin_cnt[rd][b] = 0;
         c->bin_entries[rd][b] = 0;
+        c->row_next[b] = 0;
     }
     if (ends_sweep) {
         // Marks are useless when the next pass is dense anyway.  After two

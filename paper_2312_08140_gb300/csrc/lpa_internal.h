@@ -81,6 +81,8 @@ struct Ctrl {
     unsigned int ovf_part_items;
     unsigned int ovf_rescan_items;
     unsigned int ovf_pad;
+    unsigned int row_next[kBins];        // block bins: next list position to take in this pass
+    unsigned int row_next_pad[8 - kBins];
 };
 
 // A last-bin row whose distinct labels overflowed the block's shared table.

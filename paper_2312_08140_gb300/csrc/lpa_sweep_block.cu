@@ -116,13 +116,20 @@ __device__ __forceinline__ void mark_neighbours(const DevState& s, int32_t v, in
     }
 }
 
-// U: chunks in flight per warp (4 for the last bin, whose rows span many
-// chunks per warp; 1 for the middle bins, where the SM's 64 warps already
-// overlap the few chunks of each row).  LISTS: the warps list the slots they
-// fill and the scan reads only those (middle bins; the last bin's rows fill
-// many slots, and its table is scanned whole).
-template <bool ASYNC, int WK, bool BATCH, int U, bool NS, bool LISTS>
-__global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
+// LAST selects the last bin's variant:
+//  * chunks in flight per warp U: 4 in the last bin, whose rows span many
+//    chunks per warp; 1 in the middle bins, where the SM's 64 warps already
+//    overlap the few chunks of each row;
+//  * middle bins list the table slots each warp fills and scan only those;
+//    the last bin's rows fill many slots, and its table is scanned whole;
+//  * the last bin takes rows one at a time from a counter, so a block holding
+//    a long row does not also hold a fixed share of the others (a static split
+//    left the busiest R-MAT block with 2.4x the mean work); the middle bins'
+//    rows are short and bounded, and are split statically.
+template <bool ASYNC, int WK, bool BATCH, bool NS, bool LAST>
+__global__ void __launch_bounds__(512, 4) k_sweep_block(DevState s, int bin, int flag_neighbours) {
+    constexpr int U = LAST ? kUnroll : 1;
+    constexpr bool LISTS = !LAST;
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int S = s.block_slots[bin - 2];
@@ -160,7 +167,21 @@ __global__ void k_sweep_block(DevState s, int bin, int flag_neighbours) {
     const unsigned cnt = bv.cnt;
     const int log_S = ceil_log2((unsigned)S);
     unsigned long long my_changed = 0, my_changed_entries = 0;
-    for (unsigned k = blockIdx.x; k < cnt; k += gridDim.x) {
+    // Last bin: thread 0 fetches the next row's position while the block works
+    // on the current row and publishes it at the top of the next iteration
+    // (two slots: a slot is rewritten only after every thread read it).
+    __shared__ unsigned next_k[2];
+    unsigned fetched = 0;
+    if (LAST && threadIdx.x == 0) fetched = atomicAdd(&s.ctrl->row_next[bin], 1u);
+    for (unsigned it = 0;; ++it) {
+        unsigned k = blockIdx.x + it * gridDim.x;
+        if constexpr (LAST) {
+            if (threadIdx.x == 0) next_k[it & 1u] = fetched;
+            __syncthreads();
+            k = next_k[it & 1u];
+            if (k < cnt && threadIdx.x == 0) fetched = atomicAdd(&s.ctrl->row_next[bin], 1u);
+        }
+        if (k >= cnt) break;
         const int32_t v = bv.list[k];
         const int32_t own = ASYNC ? __ldcg(L.C + v) : L.C[v];
         if constexpr (BATCH) {
@@ -811,8 +832,7 @@ static size_t block_smem(const DevState& s, int bin) {
 template <bool ASYNC, int WK, bool BATCH, bool NS>
 static cudaError_t launch_block_t(const DevState& s, int bin, int flag, int sms, cudaStream_t st) {
     const size_t smem = block_smem(s, bin);
-    auto kern = bin == kBins - 1 ? k_sweep_block<ASYNC, WK, BATCH, kUnroll, NS, false>
-                                 : k_sweep_block<ASYNC, WK, BATCH, 1, NS, true>;
+    auto kern = bin == kBins - 1 ? k_sweep_block<ASYNC, WK, BATCH, NS, true> : k_sweep_block<ASYNC, WK, BATCH, NS, false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     // one resident wave: blocks loop over the bin's vertices
