@@ -392,6 +392,12 @@ def check_async(lpa, g, tau=0.05, iters=20, cfg=None):
         lpa.lpa_graph_destroy(h)
     q_ref_gpu_labels = O.modularity(g.off, g.idx, g.w, got)
     assert abs(q_gpu - q_ref_gpu_labels) <= 1e-6 * max(1.0, abs(q_ref_gpu_labels))
+    # a sweep scans each vertex at most once (Algorithm 1 marks a vertex
+    # processed when it scans it), and the first sweep scans every vertex
+    # that has an entry
+    with_entries = int(np.count_nonzero(np.diff(g.off)))
+    assert info["active"][0] == with_entries, (info["active"][0], with_entries)
+    assert all(a <= with_entries for a in info["active"]), info["active"]
     floor = async_floor(g, tau, iters)
     off_max = O.count_not_local_max(g.off, g.idx, g.w, got)
     print(f"async n={g.n}: Q_gpu={q_gpu:.4f} floor={floor:.4f} sweeps={info['iterations']} "
