@@ -54,28 +54,31 @@ def workload(name):
     if name == "rmat21+grid2048":
         return [("rmat21", lambda: L.rmat(21, 16, seed=1)), ("grid2048", lambda: L.road_grid(2048, 2048, seed=1))]
     if name == "rmat27":
-        return [("rmat27", _rmat27_host)]
+        return [("rmat27", lambda: _rmat_device_host(27))]
+    if name == "rmat25":
+        return [("rmat25", lambda: _rmat_device_host(25))]
     if name == "planted1e4+grid64":
         return [("planted1e4", lambda: L.planted_partition(seed=1)), ("grid64", lambda: L.road_grid(64, 64, seed=1))]
     raise SystemExit(f"unknown workload {name}")
 
 
-def _rmat27_host():
-    """R-MAT scale 27, edge factor 14, drawn on the device (lpa_inputs.device) and
-    copied to host arrays, so the run path starts from host CSR like the others."""
+def _rmat_device_host(scale):
+    """R-MAT of the given scale, edge factor 14, drawn on the device
+    (lpa_inputs.device) and copied to host arrays, so the run path starts from
+    host CSR like the others."""
     import torch
     import lpa_inputs as L
     from lpa_inputs.device import rmat_device
-    g = rmat_device(27, 14, seed=1)
+    g = rmat_device(scale, 14, seed=1)
     host = L.Graph(g.off.cpu().numpy(), g.idx.cpu().numpy(), None,
-                   {"kind": "rmat", "scale": 27, "edge_factor": 14, "generator": "device"})
+                   {"kind": "rmat", "scale": scale, "edge_factor": 14, "generator": "device"})
     del g
     torch.cuda.empty_cache()
     return host
 
 
 # modes each workload runs (every other workload: both)
-WORKLOAD_MODES = {"rmat27": ("async",)}
+WORKLOAD_MODES = {"rmat27": ("async",), "rmat25": ("async",)}
 
 WORKLOAD_TEXT = {
     "rmat22+grid4096": "R-MAT scale 22 edge factor 16 (a,b,c,d=.57,.19,.19,.05; symmetrised, deduplicated, "
@@ -86,6 +89,9 @@ WORKLOAD_TEXT = {
     "rmat27": "R-MAT scale 27 edge factor 14 (a,b,c,d=.57,.19,.19,.05; symmetrised, deduplicated, no "
               "self-loops; unit weights; ~3.7e9 entries, int64 offsets; drawn on the device with torch); "
               "asynchronous mode with pruning; tau=0.05, cap 20",
+    "rmat25": "R-MAT scale 25 edge factor 14 (the generator and mode of the scale-27 workload at a "
+              "quarter of the size: ~0.9e9 entries, a 134 MB label array just above L2; a profiling "
+              "case); asynchronous mode with pruning; tau=0.05, cap 20",
     "planted1e4+grid64": "planted partition 10 x 1000 + 64x64 road-like grid (a seconds-long check of the "
                          "launch path, smaller than L2: not a performance workload); tau=0.05, cap 20",
 }

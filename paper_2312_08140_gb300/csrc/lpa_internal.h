@@ -25,7 +25,8 @@ constexpr int kHighPermille = 900;      // "almost every vertex changed" (see sk
 constexpr int kSliceLen = 4096;         // entries per slice of an overflowing row
 constexpr int kMaxParts = 4096;         // partitions a row may use on the sliced path
 constexpr int kMaxSlices = 4096;        // slices a row may use on the sliced path (with the above: d <= 2^24)
-constexpr int kSliceMinParts = 9;       // rows with fewer partitions are rescanned (at most 8 reads per entry)
+constexpr int kSliceMinParts = 2;       // every overflowing row (>= 2 partitions) takes the sliced path
+                                        // within its limits; the rescan path takes the rest
 constexpr int kLargeSlots = 8192;       // shared table of the last bin (overflowing rows are
                                         // rescanned split over label partitions)
 constexpr int32_t kEmptyKey = -1;       // free slot in label tables; labels are >= 0
@@ -85,11 +86,10 @@ struct Ctrl {
     unsigned int row_next_pad[8 - kBins];
 };
 
-// A last-bin row whose distinct labels overflowed the block's shared table.
-// It is rescanned by `parts` blocks, block p aggregating only the labels whose
-// hash falls in partition p; each block folds its best (sum, label) into
-// `best` and the block that completes the row applies the result.
-// A last-bin row whose labels overflowed the shared table in this pass.
+// A last-bin row whose labels overflowed the shared table in this pass.  Its
+// labels are split over `parts` hash partitions; each partition's block folds
+// its best (sum, label) into `best` and the block that completes the row
+// applies the result.
 // Sliced path (kSliceMinParts <= parts <= kMaxParts, scratch available): blocks over
 // kSliceLen-entry slices group the row's labels by hash partition into
 // scratch, then a block per partition aggregates its share.  Rescan path

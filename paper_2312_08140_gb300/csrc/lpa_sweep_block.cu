@@ -14,12 +14,12 @@
 // Last bin (d > large_max): the table has kLargeSlots slots.  Rows longer than
 // kLargeSlots / 2 may carry more distinct labels than it holds; their inserts
 // probe a bounded number of slots and, if one fails, the block stops and
-// appends the row to an overflow list.  The row's labels are then split over
-// parts = ceil(2d / kLargeSlots) hash partitions (about d / parts distinct
-// labels each at most, half of the table, so an insert always finds a slot):
-// rows of up to 8 partitions are rescanned by one block per partition
-// (k_sweep_parts); longer rows are read once in slices grouped by partition
-// (k_ovf_slices) and aggregated by one block per partition (k_ovf_parts).
+// appends the row to an overflow list.  The row's labels are then split over parts = ceil(2d / kLargeSlots) hash
+// partitions (about d / parts distinct labels each at most, half of the
+// table, so an insert always finds a slot): the row is read once in slices
+// grouped by partition (k_ovf_slices) and aggregated by one block per
+// partition (k_ovf_parts); rows beyond the sliced path's limits are rescanned
+// by one block per partition (k_sweep_parts).
 // Each partition's winner is folded into a 64-bit atomicMax of
 // (sum << 32 | ~tie key) -- larger sum first, then the tie-break -- and the
 // block that completes the row applies the result.  No block waits on another.
