@@ -277,7 +277,16 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     lpa_status rs;
 
-    // CSR
+    // The graph-capture streams double as the copy and helper streams here.
+    LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_top, cudaStreamNonBlocking));
+    LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_body, cudaStreamNonBlocking));
+
+    // CSR.  Host arrays are copied in stages: the offsets first, then indices
+    // and weights in chunks on the copy stream, each chunk's entries checked
+    // as soon as it lands, while the static bin lists (which need only the
+    // offsets) are built on the helper stream -- creation then costs about
+    // the copy alone.
+    const bool staged = !borrow && !dev && nnz > 0;
     int64_t* off_d = nullptr;
     int32_t* idx_d = nullptr;
     float* w_d = nullptr;
@@ -288,11 +297,11 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     } else {
         if ((rs = dalloc_t(E, &off_d, (size_t)n + 1)) != LPA_OK) return rs;
         if ((rs = dalloc_t(E, &idx_d, (size_t)nnz)) != LPA_OK) return rs;
+        if (weights && (rs = dalloc_t(E, &w_d, (size_t)nnz)) != LPA_OK) return rs;
         LPA_CUDA(cudaMemcpyAsync(off_d, offsets, ((size_t)n + 1) * 8, kind, st));
-        if (nnz) LPA_CUDA(cudaMemcpyAsync(idx_d, indices, (size_t)nnz * 4, kind, st));
-        if (weights) {
-            if ((rs = dalloc_t(E, &w_d, (size_t)nnz)) != LPA_OK) return rs;
-            if (nnz) LPA_CUDA(cudaMemcpyAsync(w_d, weights, (size_t)nnz * 4, kind, st));
+        if (!staged && nnz) {
+            LPA_CUDA(cudaMemcpyAsync(idx_d, indices, (size_t)nnz * 4, kind, st));
+            if (weights) LPA_CUDA(cudaMemcpyAsync(w_d, weights, (size_t)nnz * 4, kind, st));
         }
     }
     int64_t* vo_d = nullptr;
@@ -306,14 +315,69 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
         if ((rs = dalloc_t(E, &gid_d, (size_t)std::max<int64_t>(n, 1))) != LPA_OK) return rs;
         LPA_CUDA(launch_fill_gid(vo_d, G, n, gid_d, st, E.sms));
     }
+    E.s.off = off_d;
+    E.s.off_end = off_d + 1;
+    E.s.idx = idx_d;
+    E.s.gid = gid_d;
+    E.s.vtx_off = vo_d;
+    E.s.g_begin = vo_d;
+    E.s.g_end = vo_d + 1;
+
+    // working state
+    const size_t N1 = (size_t)std::max<int64_t>(n, 1);
+    if ((rs = dalloc_t(E, &E.s.lab[0], N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.lab[1], N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.flags, N1 + 16)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.fr_bits, N1 / 16 + 1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.slist, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.flist, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.chg, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.ctrl, 1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.dN, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.done, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.iters, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.exit_reason, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.hist_changed, (size_t)G * kMaxHist)) != LPA_OK) return rs;
+    LPA_CUDA(cudaMemsetAsync(E.s.flags, 0, N1 + 16, st));
+    LPA_CUDA(cudaMemsetAsync(E.s.ctrl, 0, sizeof(Ctrl), st));
+    LPA_CUDA(cudaMemsetAsync(E.s.hist_changed, 0, (size_t)G * kMaxHist * 8, st));
+    apply_config_fields(E);
+    const size_t sblk = (size_t)std::max<int64_t>(static_scratch_blocks(n), 1) * kBins;
+    if ((rs = dalloc_t(E, &E.static_counts, sblk)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.static_ents, sblk)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.cap_scratch, 3)) != LPA_OK) return rs;
 
     // validation (and, for batches, local -> global index rewrite in our copy)
     ValidateResult* vr_d = nullptr;
     if ((rs = dalloc_t(E, &vr_d, 1)) != LPA_OK) return rs;
     LPA_CUDA(cudaMemsetAsync(vr_d, 0, sizeof(ValidateResult), st));
-    if (n > 0)
-        LPA_CUDA(launch_validate(off_d, idx_d, w_d, n, nnz, vo_d, eo_d, gid_d, G, G > 1 ? 1 : 0, idx_d, vr_d, st,
-                                 E.sms));
+    cudaEvent_t ev = nullptr;
+    LPA_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t ce = cudaEventRecord(ev, st);                    // offsets and working state ready
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(E.cap_body, ev, 0);
+    const int rewrite = G > 1 ? 1 : 0;
+    if (staged) {
+        constexpr int64_t kChunk = 1LL << 24;                    // entries per staged copy
+        for (int64_t e0 = 0; e0 < nnz && ce == cudaSuccess; e0 += kChunk) {
+            const int64_t c = std::min<int64_t>(kChunk, nnz - e0);
+            ce = cudaMemcpyAsync(idx_d + e0, indices + e0, (size_t)c * 4, cudaMemcpyHostToDevice, E.cap_top);
+            if (ce == cudaSuccess && weights)
+                ce = cudaMemcpyAsync(w_d + e0, weights + e0, (size_t)c * 4, cudaMemcpyHostToDevice, E.cap_top);
+            if (ce == cudaSuccess) ce = cudaEventRecord(ev, E.cap_top);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(st, ev, 0);
+            if (ce == cudaSuccess)
+                ce = launch_validate_entries(idx_d, w_d, n, nnz, e0, e0 + c, vo_d, eo_d, G, rewrite, idx_d, vr_d, st,
+                                             E.sms);
+        }
+    } else if (ce == cudaSuccess && n > 0) {
+        ce = launch_validate_entries(idx_d, w_d, n, nnz, 0, nnz, vo_d, eo_d, G, rewrite, idx_d, vr_d, st, E.sms);
+    }
+    cudaEventDestroy(ev);                                        // released once its waits have passed
+    LPA_CUDA(ce);
+    // static bin lists on the helper stream, meanwhile (blocks this thread
+    // until they are built; the copies and checks above keep running)
+    LPA_CUDA(build_static_lists(E.s, E.cap_body, E.static_counts, E.static_ents));
+    if (n > 0) LPA_CUDA(launch_validate_rows(off_d, idx_d, w_d, n, nnz, vo_d, eo_d, gid_d, G, vr_d, st, E.sms));
     ValidateResult vr{};
     LPA_CUDA(cudaMemcpyAsync(&vr, vr_d, sizeof(vr), cudaMemcpyDeviceToHost, st));
     LPA_CUDA(cudaStreamSynchronize(st));
@@ -359,42 +423,8 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
         E.exact = vr.c[3] == 0 && vr.c[4] == 0;
         E.s.weight_kind = W_F32;
     }
-    E.s.off = off_d;
-    E.s.off_end = off_d + 1;
-    E.s.idx = idx_d;
     E.s.w = w_d;
-    E.s.gid = gid_d;
-    E.s.vtx_off = vo_d;
-    E.s.g_begin = vo_d;
-    E.s.g_end = vo_d + 1;
-
-    // working state
-    const size_t N1 = (size_t)std::max<int64_t>(n, 1);
-    if ((rs = dalloc_t(E, &E.s.lab[0], N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.lab[1], N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.flags, N1 + 16)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.fr_bits, N1 / 16 + 1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.slist, N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.flist, N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.chg, N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.ctrl, 1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.dN, (size_t)G)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.done, (size_t)G)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.iters, (size_t)G)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.exit_reason, (size_t)G)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.hist_changed, (size_t)G * kMaxHist)) != LPA_OK) return rs;
-    LPA_CUDA(cudaMemsetAsync(E.s.flags, 0, N1 + 16, st));
-    LPA_CUDA(cudaMemsetAsync(E.s.ctrl, 0, sizeof(Ctrl), st));
-    LPA_CUDA(cudaMemsetAsync(E.s.hist_changed, 0, (size_t)G * kMaxHist * 8, st));
-    apply_config_fields(E);
-    const size_t sblk = (size_t)std::max<int64_t>(static_scratch_blocks(n), 1) * kBins;
-    if ((rs = dalloc_t(E, &E.static_counts, sblk)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.static_ents, sblk)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.cap_scratch, 3)) != LPA_OK) return rs;
-    LPA_CUDA(build_static_lists(E.s, st, E.static_counts, E.static_ents));
     if ((rs = setup_blocks(E, st)) != LPA_OK) return rs;
-    LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_top, cudaStreamNonBlocking));
-    LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_body, cudaStreamNonBlocking));
     LPA_CUDA(cudaStreamSynchronize(st));
     return LPA_OK;
 }

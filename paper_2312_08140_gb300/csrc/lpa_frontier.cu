@@ -693,15 +693,16 @@ __device__ __forceinline__ void val_flush(ValAcc& a, ValidateResult* res, unsign
     }
 }
 
-// Entries: block b owns the contiguous chunk [b*chunk, (b+1)*chunk).
+// Entries: block b owns the contiguous chunk [e0 + b*chunk, e0 + (b+1)*chunk)
+// of the range [e0, e1).
 __global__ void __launch_bounds__(kValThreads) k_validate_entries(const int32_t* idx, const float* w, int64_t N,
-                                                                  int64_t E, const int64_t* vtx_off,
-                                                                  const int64_t* edge_off, int32_t G, int rewrite,
-                                                                  int32_t* idx_rw, int64_t chunk,
-                                                                  ValidateResult* res) {
+                                                                  int64_t E, int64_t e0, int64_t e1,
+                                                                  const int64_t* vtx_off, const int64_t* edge_off,
+                                                                  int32_t G, int rewrite, int32_t* idx_rw,
+                                                                  int64_t chunk, ValidateResult* res) {
     ValAcc a{};
-    const int64_t beg = (int64_t)blockIdx.x * chunk;
-    const int64_t end = beg + chunk < E ? beg + chunk : E;
+    const int64_t beg = e0 + (int64_t)blockIdx.x * chunk;
+    const int64_t end = beg + chunk < e1 ? beg + chunk : e1;
     int64_t ge_lo = 0, ge_hi = E, lo = 0, n_local = N;      // entry range, first vertex, size of the graph
     if (rewrite) ge_hi = -1;
     for (int64_t e = beg + threadIdx.x; e < end; e += kValThreads) {
@@ -793,20 +794,24 @@ __global__ void __launch_bounds__(kValThreads) k_validate_rows(const int64_t* of
     val_flush(a, res, &res->desc_row_starts);
 }
 
-cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N, int64_t E,
-                            const int64_t* vtx_off, const int64_t* edge_off, const int32_t* gid, int32_t G,
-                            int rewrite_local_ids, int32_t* idx_rw, ValidateResult* res, cudaStream_t st,
-                            int sms) {
-    if (E > 0) {
-        const int64_t max_blocks = (int64_t)sms * 8;
-        int64_t chunk = (E + max_blocks - 1) / max_blocks;
-        chunk = std::max<int64_t>((chunk + kValThreads - 1) / kValThreads * kValThreads, kValThreads * 4);
-        const int blocks = (int)((E + chunk - 1) / chunk);
-        k_validate_entries<<<blocks, kValThreads, 0, st>>>(idx, w, N, E, vtx_off, edge_off, G, rewrite_local_ids,
-                                                           idx_rw, chunk, res);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+cudaError_t launch_validate_entries(const int32_t* idx, const float* w, int64_t N, int64_t E, int64_t e_begin,
+                                    int64_t e_end, const int64_t* vtx_off, const int64_t* edge_off, int32_t G,
+                                    int rewrite_local_ids, int32_t* idx_rw, ValidateResult* res, cudaStream_t st,
+                                    int sms) {
+    const int64_t cnt = e_end - e_begin;
+    if (cnt <= 0) return cudaSuccess;
+    const int64_t max_blocks = (int64_t)sms * 8;
+    int64_t chunk = (cnt + max_blocks - 1) / max_blocks;
+    chunk = std::max<int64_t>((chunk + kValThreads - 1) / kValThreads * kValThreads, kValThreads * 4);
+    const int blocks = (int)((cnt + chunk - 1) / chunk);
+    k_validate_entries<<<blocks, kValThreads, 0, st>>>(idx, w, N, E, e_begin, e_end, vtx_off, edge_off, G,
+                                                       rewrite_local_ids, idx_rw, chunk, res);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate_rows(const int64_t* off, const int32_t* idx, const float* w, int64_t N, int64_t E,
+                                 const int64_t* vtx_off, const int64_t* edge_off, const int32_t* gid, int32_t G,
+                                 ValidateResult* res, cudaStream_t st, int sms) {
     const int64_t warps = (N + 31) / 32;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((warps + 7) / 8, (int64_t)sms * 8));
     k_validate_rows<<<blocks, kValThreads, 0, st>>>(off, idx, w, N, E, vtx_off, edge_off, gid, G, res);

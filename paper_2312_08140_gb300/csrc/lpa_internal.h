@@ -222,10 +222,18 @@ struct ValidateResult {
     unsigned long long desc_all;
     unsigned long long desc_row_starts;
 };
-cudaError_t launch_validate(const int64_t* off, const int32_t* idx, const float* w, int64_t N,
-                            int64_t E, const int64_t* vtx_off, const int64_t* edge_off,
-                            const int32_t* gid, int32_t G, int rewrite_local_ids, int32_t* idx_rw,
-                            ValidateResult* res, cudaStream_t st, int sms);
+// Entry checks of entries [e_begin, e_end) (indices in range, weights finite
+// and >= 0, integrality, largest weight, descents; for batches the rewrite of
+// local ids to global ones); then, once every entry is in place and checked,
+// the row checks (offsets, degrees, exact weighted degrees, descents at row
+// starts).  Both accumulate into *res.
+cudaError_t launch_validate_entries(const int32_t* idx, const float* w, int64_t N, int64_t E, int64_t e_begin,
+                                    int64_t e_end, const int64_t* vtx_off, const int64_t* edge_off, int32_t G,
+                                    int rewrite_local_ids, int32_t* idx_rw, ValidateResult* res, cudaStream_t st,
+                                    int sms);
+cudaError_t launch_validate_rows(const int64_t* off, const int32_t* idx, const float* w, int64_t N, int64_t E,
+                                 const int64_t* vtx_off, const int64_t* edge_off, const int32_t* gid, int32_t G,
+                                 ValidateResult* res, cudaStream_t st, int sms);
 cudaError_t launch_fill_gid(const int64_t* vtx_off, int32_t G, int64_t N, int32_t* gid,
                             cudaStream_t st, int sms);
 cudaError_t launch_weights_to_u32(float* w, int64_t E, cudaStream_t st, int sms);
