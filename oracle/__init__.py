@@ -13,6 +13,8 @@ Functions and the passages they follow:
                        4.1.2-4.1.3.
   lpa_async(...)       Algorithm 1 with one thread in ascending vertex order,
                        vertex pruning (Section 4.1.4).
+  lpa_async_ex(...)    the same with options, among them the pruning rule of
+                       FLPA (Section 2), and the vertices scanned per sweep.
   modularity(...)      Eq. 1 (Section 3.2), community form, fp64.
   count_labels_outside_component / count_not_local_max: output checkers.
 
@@ -51,7 +53,7 @@ def build(force: bool = False) -> str:
 
 def _bind(lib):
     for name in ("oracle_lpa_sync", "oracle_lpa_async", "oracle_lpa_async_order", "oracle_lpa_sync_nonstrict",
-                 "oracle_lpa_async_nonstrict", "oracle_sync_sweep",
+                 "oracle_lpa_async_nonstrict", "oracle_lpa_async_ex", "oracle_sync_sweep",
                  "oracle_count_labels_outside_component", "oracle_count_not_local_max"):
         getattr(lib, name).restype = _i64
     lib.oracle_pick.restype = ctypes.c_int32
@@ -78,7 +80,7 @@ def load_variant(so_path):
         pass
 
     v = _Variant()
-    for name in ("pick", "sync_sweep", "lpa_sync", "lpa_async", "modularity",
+    for name in ("pick", "sync_sweep", "lpa_sync", "lpa_async", "lpa_async_ex", "modularity",
                  "count_labels_outside_component", "count_not_local_max"):
         fn = globals()[name]
         setattr(v, name, (lambda f: (lambda *a, **k: f(*a, _lib_override=lib, **k)))(fn))
@@ -151,6 +153,24 @@ def lpa_async(off, idx, w=None, tau=0.05, max_iters=20, order=None, nonstrict=Fa
     f = lib.oracle_lpa_async_nonstrict if nonstrict else lib.oracle_lpa_async_order
     fn = lambda n, o, i, ww, t, m, C, h: f(n, o, i, ww, t, m, _p(order), C, h)
     return _run(fn, off, idx, w, tau, max_iters)
+
+
+def lpa_async_ex(off, idx, w=None, tau=0.05, max_iters=20, order=None, nonstrict=False, prune_other=False,
+                 _lib_override=None):
+    """Algorithm 1, one thread, with options: `prune_other` applies the FLPA
+    pruning rule (Section 2: a vertex whose label changes to c marks only the
+    neighbours whose label is not c).  Returns (labels, iterations, changed,
+    active), active = vertices scanned per sweep."""
+    lib = _lib_override or _load()
+    n, off, idx, w = _csr(off, idx, w)
+    C = np.empty(n, dtype=np.int32)
+    hist = np.zeros(max(max_iters, 1), dtype=np.int64)
+    act = np.zeros(max(max_iters, 1), dtype=np.int64)
+    order = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
+    it = _check(lib.oracle_lpa_async_ex(_i64(n), _p(off), _p(idx), _p(w), ctypes.c_double(float(tau)),
+                                        _i64(max_iters), _p(order), ctypes.c_int(int(nonstrict)),
+                                        ctypes.c_int(int(prune_other)), _p(C), _p(hist), _p(act)), "lpa")
+    return C, int(it), hist[:it].copy(), act[:it].copy()
 
 
 def modularity(off, idx, w, C, _lib_override=None) -> float:

@@ -27,6 +27,11 @@
  *                        processed when visited and, when its label changes,
  *                        all of its neighbours other than itself are marked
  *                        unprocessed (vertex pruning, Section 4.1.4).
+ *   - oracle_lpa_async_ex: the same with options: the non-strict tie-break;
+ *                        the pruning rule of FLPA (Section 2), under which a
+ *                        vertex whose label changes to c marks unprocessed
+ *                        only the neighbours whose label is not c; and the
+ *                        number of vertices scanned in each sweep.
  *   - *_nonstrict:       the same with the non-strict tie-break (Section
  *                        4.1.5: a pseudo-random choice among the tied
  *                        labels through a modulo of the label id), read as: in
@@ -275,7 +280,7 @@ int64_t oracle_lpa_sync_nonstrict(int64_t n, const int64_t *off, const int32_t *
  * non-strict tie-break of sweep it + 1.  Returns the number of sweeps. */
 static int64_t lpa_async_impl(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                               double tau, int64_t max_iters, const int64_t *order, int nonstrict,
-                              int32_t *C_out, int64_t *changed_hist) {
+                              int prune_other, int32_t *C_out, int64_t *changed_hist, int64_t *active_hist) {
     if (check_csr(n, off, idx) || !C_out || max_iters < 0 || !(tau >= 0.0)) return ORACLE_BAD_ARG;
     if (order) {                                                     /* must be a permutation */
         uint8_t *hit = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
@@ -295,19 +300,25 @@ static int64_t lpa_async_impl(int64_t n, const int64_t *off, const int32_t *idx,
     if (kv_init(&H, n)) { free(unprocessed); return ORACLE_NO_MEM; }
     int64_t it = 0;
     while (it < max_iters) {
-        int64_t dN = 0;                                              /* lpaMove */
+        int64_t dN = 0, active = 0;                                  /* lpaMove */
         for (int64_t k = 0; k < n; ++k) {
             const int64_t i = order ? order[k] : k;
             if (!unprocessed[i]) continue;
             unprocessed[i] = 0;                                      /* prune */
+            ++active;
             int32_t c = pick_t(&H, n, off, idx, w, C_out, i, nonstrict ? it + 1 : 0);
             if (c == C_out[i]) continue;
             C_out[i] = c;
             ++dN;
-            for (int64_t e = off[i]; e < off[i + 1]; ++e)            /* re-mark neighbours */
-                if ((int64_t)idx[e] != i) unprocessed[idx[e]] = 1;
+            for (int64_t e = off[i]; e < off[i + 1]; ++e) {          /* re-mark neighbours */
+                const int32_t j = idx[e];
+                if ((int64_t)j == i) continue;
+                if (prune_other && C_out[j] == c) continue;          /* FLPA: already in c */
+                unprocessed[j] = 1;
+            }
         }
         if (changed_hist) changed_hist[it] = dN;
+        if (active_hist) active_hist[it] = active;
         ++it;
         if (converged(dN, n, tau)) break;
     }
@@ -331,7 +342,7 @@ int32_t oracle_pick_nonstrict(int64_t n, const int64_t *off, const int32_t *idx,
 int64_t oracle_lpa_async_order(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                double tau, int64_t max_iters, const int64_t *order, int32_t *C_out,
                                int64_t *changed_hist) {
-    return lpa_async_impl(n, off, idx, w, tau, max_iters, order, 0, C_out, changed_hist);
+    return lpa_async_impl(n, off, idx, w, tau, max_iters, order, 0, 0, C_out, changed_hist, NULL);
 }
 
 /* Algorithm 1 by one thread in the given vertex order (NULL: ascending) with
@@ -339,7 +350,18 @@ int64_t oracle_lpa_async_order(int64_t n, const int64_t *off, const int32_t *idx
 int64_t oracle_lpa_async_nonstrict(int64_t n, const int64_t *off, const int32_t *idx, const float *w,
                                    double tau, int64_t max_iters, const int64_t *order, int32_t *C_out,
                                    int64_t *changed_hist) {
-    return lpa_async_impl(n, off, idx, w, tau, max_iters, order, 1, C_out, changed_hist);
+    return lpa_async_impl(n, off, idx, w, tau, max_iters, order, 1, 0, C_out, changed_hist, NULL);
+}
+
+/* Algorithm 1 by one thread in the given vertex order (NULL: ascending),
+ * with the non-strict tie-break if `nonstrict`, the FLPA pruning rule if
+ * `prune_other`, and the vertices scanned per sweep in active_hist (NULL:
+ * not recorded). */
+int64_t oracle_lpa_async_ex(int64_t n, const int64_t *off, const int32_t *idx, const float *w, double tau,
+                            int64_t max_iters, const int64_t *order, int nonstrict, int prune_other,
+                            int32_t *C_out, int64_t *changed_hist, int64_t *active_hist) {
+    return lpa_async_impl(n, off, idx, w, tau, max_iters, order, nonstrict, prune_other, C_out, changed_hist,
+                          active_hist);
 }
 
 /* Algorithm 1 by one thread in ascending vertex order. */

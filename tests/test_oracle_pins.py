@@ -123,10 +123,11 @@ def test_sync_run_is_iterated_sweeps():
             assert Co.tolist() == C.tolist() and it == len(hist) and ho.tolist() == hist
 
 
-def _serial_async_restated(g, tau, cap, order=None):
+def _serial_async_restated(g, tau, cap, order=None, prune_other=False):
     """Algorithm 1 with one thread, written as a worklist of pending vertices
     scanned in increasing id order (or in `order`); each pick is the
-    enumerated Eq. 2."""
+    enumerated Eq. 2.  prune_other: a changed vertex adds only neighbours not
+    already carrying its new label (the FLPA rule, Section 2)."""
     n = g.n
     C = np.arange(n, dtype=np.int32)
     pending = set(range(n))
@@ -142,8 +143,9 @@ def _serial_async_restated(g, tau, cap, order=None):
                     C[i] = c
                     dN += 1
                     for e in range(int(g.off[i]), int(g.off[i + 1])):
-                        if int(g.idx[e]) != i:
-                            pending.add(int(g.idx[e]))
+                        j = int(g.idx[e])
+                        if j != i and not (prune_other and C[j] == c):
+                            pending.add(j)
         hist.append(dN)
         if dN / n <= tau:
             break
@@ -290,7 +292,9 @@ MUTANTS = {
                             "C_out[i] = pick_t(&H, n, off, idx, w, C_out, i, nonstrict ? it + 1 : 0);"),
     "nonstrict_is_strict": ("c = most_weighted_label_rotated(H, n, r);", "c = most_weighted_label(H);"),
     "nonstrict_rotation_reversed": ("int64_t key = ((int64_t)c - (int64_t)r) % n;", "int64_t key = ((int64_t)r - (int64_t)c) % n;"),
-    "async_no_remark": ("if ((int64_t)idx[e] != i) unprocessed[idx[e]] = 1;", "(void)0;"),
+    "async_no_remark": ("                unprocessed[j] = 1;\n", "                (void)j;\n"),
+    "flpa_rule_ignored": ("if (prune_other && C_out[j] == c) continue;", ""),
+    "flpa_rule_inverted": ("if (prune_other && C_out[j] == c) continue;", "if (prune_other && C_out[j] != c) continue;"),
     "async_counts_visits": ("if (c == C_out[i]) continue;", "if (c == C_out[i]) { ++dN; continue; }"),
     "async_order_ignored": ("const int64_t i = order ? order[k] : k;", "const int64_t i = k;"),
     "isolated_takes_zero": ("int32_t c = C[i];\n    if (used) {", "int32_t c = 0;\n    if (used) {"),
@@ -346,6 +350,28 @@ def _nonstrict_pins_pass(mod):
     return True
 
 
+def _flpa_pins_pass(mod):
+    """FLPA pruning rule (Section 2).  Star K_{1,7}, ascending order, worked by
+    hand: the centre takes label 1 (all of its labels tie at weight 1), leaf
+    1 keeps 1, leaves 2..7 take 1: 7 changes, then none.  Every leaf change
+    re-marks the centre under the plain rule (8 then 1 vertices scanned); under
+    FLPA the centre already carries label 1 and is not re-marked (8 then 0).
+    And on random graphs the rule equals the worklist restatement."""
+    g = L.from_undirected_pairs(8, [(0, k) for k in range(1, 8)])
+    for po, act in ((False, [8, 1]), (True, [8, 0])):
+        C, it, ch, a = mod.lpa_async_ex(g.off, g.idx, None, 0.05, 20, prune_other=po)
+        if C.tolist() != [1] * 8 or it != 2 or ch.tolist() != [7, 0] or a.tolist() != act:
+            return False
+    for g, _ in _random_cases(60, seed0=61000):
+        if g.n == 0:
+            continue
+        C, it, h = _serial_async_restated(g, 0.05, 20, prune_other=True)
+        Co, ito, ho, _ = mod.lpa_async_ex(g.off, g.idx, g.w, 0.05, 20, prune_other=True)
+        if Co.tolist() != C.tolist() or ito != it or ho.tolist() != h:
+            return False
+    return True
+
+
 def _pins_pass(mod):
     try:
         for case in _golden_cases():
@@ -364,6 +390,8 @@ def _pins_pass(mod):
             if Co.tolist() != C.tolist() or ito != it:
                 return False
         if not _nonstrict_pins_pass(mod):
+            return False
+        if not _flpa_pins_pass(mod):
             return False
         pairs = [(u, v) for u in range(5) for v in range(u + 1, 5)]
         pairs += [(u + 5, v + 5) for u, v in pairs] + [(4, 5)]
