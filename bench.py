@@ -510,6 +510,9 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=0.5, help="0 skips the serving sample")
     ap.add_argument("--tie", default="strict", choices=["strict", "nonstrict"],
                     help="tie-break among the most weighted labels (Section 4.1.5)")
+    ap.add_argument("--prune", default="paper", choices=["paper", "other"],
+                    help="async pruning: every neighbour of a changed vertex re-marked (Section 4.1.4), or "
+                         "only those not already in its new label (FLPA's rule, Section 2)")
     ap.add_argument("--param-sweep", action="store_true",
                     help="also sweep tau in {0.1, 0.05, 0.01, 1e-5} x cap in {10, 20, 50} per graph (async)")
     ap.add_argument("--batched-full", action="store_true",
@@ -545,6 +548,8 @@ def main():
     modes = WORKLOAD_MODES.get(args.workload, MODES)
     if args.tie == "nonstrict":
         modes = tuple(m + "+nonstrict" for m in modes)
+    if args.prune == "other":
+        modes = tuple(m + "+prune_other" if m.startswith("async") else m for m in modes)
     stream = torch.cuda.current_stream()
     handles = [lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS, stream) for g in graphs]
     outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
@@ -685,7 +690,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD_TEXT[args.workload], "tie_break": args.tie, "inputs_larger_than_l2": True,
+                "config": {"workload": WORKLOAD_TEXT[args.workload], "tie_break": args.tie,
+                           "async_pruning": "FLPA rule" if args.prune == "other" else "every neighbour",
+                           "inputs_larger_than_l2": True,
                            "parallelism": f"replicas x{world}", "tau": TAU, "max_iters": MAX_ITERS},
                 "touched_edges_per_s": touched / (ms / 1e3),
                 "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,

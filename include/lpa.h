@@ -79,6 +79,15 @@ typedef enum {
  * Not accepted by lpa_serve_*. */
 #define LPA_NONSTRICT 0x100
 
+/* Mode flag, LPA_MODE_ASYNC only (LPA_ERR_INVALID_ARG with the synchronous
+ * modes): the pruning rule of FLPA (Section 2), under which a vertex whose
+ * label changes to c marks unprocessed only the neighbours whose label is not
+ * c, instead of every neighbour (Section 4.1.4).  A neighbour already in c
+ * gains weight for c and keeps it in the usual case, so the frontiers shrink;
+ * the results are those of a different (still asynchronous) algorithm.
+ * Not accepted by lpa_serve_*. */
+#define LPA_PRUNE_OTHER 0x200
+
 /* lpa_graph_create / lpa_batch_create flags */
 #define LPA_HOST_PTRS   0u  /* offsets/indices/weights are host memory; the library copies them */
 #define LPA_DEVICE_PTRS 1u  /* they are device memory; the library copies them (unless LPA_BORROW) */

@@ -40,6 +40,7 @@ LPA_HOST_PTRS = 0
 LPA_DEVICE_PTRS = 1
 LPA_BORROW = 2
 LPA_NONSTRICT = 0x100
+LPA_PRUNE_OTHER = 0x200
 
 LPA_MAX_RECORDED_ITERS = 64
 LPA_BINS = 5
@@ -257,14 +258,21 @@ def lpa_graph_set_config(g, cfg: LpaConfig):
     _check(load().lpa_graph_set_config(g, ctypes.byref(cfg)))
 
 
+_MODE_FLAGS = {"nonstrict": LPA_NONSTRICT, "prune_other": LPA_PRUNE_OTHER}
+
+
 def _mode(m):
-    """"sync", "async", "sync_full", each optionally with a "+nonstrict" suffix
-    (LPA_NONSTRICT), or an int."""
+    """"sync", "async", "sync_full", each optionally with "+" suffixes
+    "nonstrict" (LPA_NONSTRICT) and "prune_other" (LPA_PRUNE_OTHER), or an
+    int."""
     if isinstance(m, str):
-        base, _, flag = m.partition("+")
-        if flag not in ("", "nonstrict"):
+        base, *flags = m.split("+")
+        if base not in MODES or any(f not in _MODE_FLAGS for f in flags):
             raise ValueError(f"unknown mode {m!r}")
-        return MODES[base] | (LPA_NONSTRICT if flag else 0)
+        v = MODES[base]
+        for f in flags:
+            v |= _MODE_FLAGS[f]
+        return v
     return int(m)
 
 

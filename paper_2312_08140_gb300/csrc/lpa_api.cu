@@ -540,14 +540,19 @@ lpa_status build_graph(Engine& E, int mode) {
 // pick depends on the neighbours' labels alone); a non-strict pick also
 // depends on the sweep, so the synchronous mode then scans every vertex in
 // every sweep.
-void split_mode(int& mode, int& nonstrict) {
+// LPA_PRUNE_OTHER (FLPA's pruning rule) is taken in the asynchronous mode only.
+void split_mode(int& mode, int& nonstrict, int& prune_other) {
     nonstrict = (mode & (int)LPA_NONSTRICT) ? 1 : 0;
-    mode &= ~(int)LPA_NONSTRICT;
+    prune_other = (mode & (int)LPA_PRUNE_OTHER) ? 1 : 0;
+    mode &= ~((int)LPA_NONSTRICT | (int)LPA_PRUNE_OTHER);
     if (nonstrict && mode == MODE_SYNC) mode = MODE_SYNC_FULL;
 }
 
-lpa_status check_run_args(const Engine& E, int mode, float tol, int32_t max_iters, const int32_t* labels_out) {
+lpa_status check_run_args(const Engine& E, int mode, int prune_other, float tol, int32_t max_iters,
+                          const int32_t* labels_out) {
     if (mode < 0 || mode > 2) return fail(LPA_ERR_INVALID_ARG, "unknown mode %d", mode);
+    if (prune_other && mode != MODE_ASYNC)
+        return fail(LPA_ERR_INVALID_ARG, "LPA_PRUNE_OTHER needs LPA_MODE_ASYNC");
     if (!(tol >= 0.f && tol <= 1.f)) return fail(LPA_ERR_INVALID_ARG, "tolerance must be in [0, 1]");
     if (max_iters < 0 || max_iters > (1 << 20)) return fail(LPA_ERR_INVALID_ARG, "max_iters must be in [0, 2^20]");
     if (E.s.N > 0 && !labels_out) return fail(LPA_ERR_INVALID_ARG, "labels_out is NULL");
@@ -585,9 +590,9 @@ lpa_status collect_info(Engine& E, cudaStream_t st, lpa_run_info* infos, int32_t
 
 lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t* labels_out, cudaStream_t st,
                       lpa_run_info* infos, int local_ids) {
-    int ns = 0;
-    split_mode(mode, ns);
-    lpa_status rs = check_run_args(E, mode, tol, max_iters, labels_out);
+    int ns = 0, po = 0;
+    split_mode(mode, ns, po);
+    lpa_status rs = check_run_args(E, mode, po, tol, max_iters, labels_out);
     if (rs != LPA_OK) return rs;
     if (E.s.N == 0) {
         for (int32_t g = 0; infos && g < E.s.G; ++g) {
@@ -598,7 +603,7 @@ lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t
     }
     const int lm = mode | (ns ? kModeNonstrict : 0);
     if ((rs = build_graph(E, lm)) != LPA_OK) return rs;
-    LPA_CUDA(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, ns, labels_out, local_ids, st));
+    LPA_CUDA(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, ns, po, labels_out, local_ids, st));
     LPA_CUDA(cudaGraphLaunch(E.exec[graph_index(lm)], st));
     ++E.runs_total;
     if (infos) return collect_info(E, st, infos, E.s.G);
@@ -609,9 +614,9 @@ lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t
 lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters, int32_t* labels_out,
                                cudaStream_t st, lpa_run_info* infos, lpa_profile* prof, int local_ids) {
     const int mode_arg = mode;
-    int ns = 0;
-    split_mode(mode, ns);
-    lpa_status rs = check_run_args(E, mode, tol, max_iters, labels_out);
+    int ns = 0, po = 0;
+    split_mode(mode, ns, po);
+    lpa_status rs = check_run_args(E, mode, po, tol, max_iters, labels_out);
     if (rs != LPA_OK) return rs;
     if (!prof) return fail(LPA_ERR_INVALID_ARG, "prof is NULL");
     memset(prof, 0, sizeof(*prof));
@@ -632,7 +637,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
             return cuda_fail(err, #call);    \
         }                                    \
     } while (0)
-    LPA_P(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, ns, labels_out, local_ids, st));
+    LPA_P(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, ns, po, labels_out, local_ids, st));
     LPA_P(cudaEventRecord(ev[0], st));
     LPA_P(launch_init(E.s, st, E.sms));
     LPA_P(launch_init_cond(E.s, none, 0, st));

@@ -19,19 +19,20 @@ namespace lpa {
 constexpr int kFrontThreads = 256;
 constexpr int kVertsPerThread = 16;
 
-__global__ void k_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int nonstrict, int32_t* labels_out,
-                             int local_ids) {
+__global__ void k_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int nonstrict, int prune_other,
+                             int32_t* labels_out, int local_ids) {
     ctrl->tau = tau;
     ctrl->max_iters = max_iters;
     ctrl->mode = mode;
     ctrl->nonstrict = nonstrict;
+    ctrl->prune_other = prune_other;
     ctrl->labels_out = labels_out;
     ctrl->local_ids = local_ids;
 }
 
-cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int nonstrict, int32_t* labels_out,
-                              int local_ids, cudaStream_t st) {
-    k_set_params<<<1, 1, 0, st>>>(ctrl, tau, max_iters, mode, nonstrict, labels_out, local_ids);
+cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int nonstrict, int prune_other,
+                              int32_t* labels_out, int local_ids, cudaStream_t st) {
+    k_set_params<<<1, 1, 0, st>>>(ctrl, tau, max_iters, mode, nonstrict, prune_other, labels_out, local_ids);
     return cudaGetLastError();
 }
 

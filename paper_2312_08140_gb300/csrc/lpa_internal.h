@@ -76,7 +76,7 @@ struct Ctrl {
     long long total_scanned;
     long long total_sweep_launches;      // kernel launches of those sweeps
     int32_t nonstrict;                   // non-strict tie-break for this run (Section 4.1.5)
-    int32_t nonstrict_pad;
+    int32_t prune_other;                 // async: a changed vertex marks only neighbours not in its new label
     unsigned long long ovf_count;        // overflow rows appended in this pass
     unsigned int ovf_slice_items;        // work items of the overflow kernels (set by k_ovf_plan)
     unsigned int ovf_part_items;
@@ -199,7 +199,7 @@ enum FinishRole {
 cudaError_t launch_finish(const DevState& s, int mode, int role, cudaGraphConditionalHandle h, int in_graph,
                           cudaStream_t st, int sms);
 cudaError_t launch_finalize(const DevState& s, cudaStream_t st, int sms);
-cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int nonstrict,
+cudaError_t launch_set_params(Ctrl* ctrl, double tau, int max_iters, int mode, int nonstrict, int prune_other,
                               int32_t* labels_out, int local_ids, cudaStream_t st);
 cudaError_t launch_sweep_small(const DevState& s, int mode, cudaStream_t st, int sms);
 cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int sms);

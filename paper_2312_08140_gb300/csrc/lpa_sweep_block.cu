@@ -109,10 +109,14 @@ __device__ __forceinline__ void scan_table(int32_t* keys, T* vals, int slots, bo
     tie = best_k;
 }
 
-__device__ __forceinline__ void mark_neighbours(const DevState& s, int32_t v, int64_t st, int64_t en) {
+// Marks v's neighbours unprocessed (Section 4.1.4); with FLPA's rule (po)
+// only those whose label is not v's new label `best`.
+template <bool ASYNC>
+__device__ __forceinline__ void mark_neighbours(const DevState& s, int32_t v, int64_t st, int64_t en, bool po,
+                                                int32_t best, const int32_t* C) {
     for (int64_t e = st + threadIdx.x; e < en; e += blockDim.x) {
         const int32_t j = s.idx[e];
-        if (j != v) mark_unprocessed(s.flags, j);
+        if (j != v && !(po && load_label<ASYNC>(C, j) == best)) mark_unprocessed(s.flags, j);
     }
 }
 
@@ -164,6 +168,7 @@ __global__ void __launch_bounds__(512, 4) k_sweep_block(DevState s, int bin, int
     const bool marks = marks_on(s, flag_neighbours);
     const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
     const bool ident = identity_sweep<ASYNC, BATCH>(s);
+    const bool po = ASYNC && s.ctrl->prune_other != 0;               // FLPA's pruning rule
     const unsigned cnt = bv.cnt;
     const int log_S = ceil_log2((unsigned)S);
     unsigned long long my_changed = 0, my_changed_entries = 0;
@@ -316,7 +321,7 @@ __global__ void __launch_bounds__(512, 4) k_sweep_block(DevState s, int bin, int
                 my_changed_entries += (unsigned long long)d;
                 if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
             }
-            if (marks) mark_neighbours(s, v, st, en);
+            if (marks) mark_neighbours<ASYNC>(s, v, st, en, po, best_lab, L.C);
         }
         __syncthreads();    // `winner` / `win_bp` consumed before the next vertex
     }
@@ -573,6 +578,7 @@ __device__ __forceinline__ void fold_partition(const DevState& s, const Labels& 
                                                unsigned long long& my_changed_entries) {
     __shared__ int resolver;
     __shared__ unsigned long long best_packed;
+    const bool po = ASYNC && s.ctrl->prune_other != 0;               // FLPA's pruning rule
     if (threadIdx.x == 0) resolver = 0;
     __syncthreads();
     if (part_best != 0xffffffffu && key != 0 && tie == part_best) {
@@ -604,7 +610,7 @@ __device__ __forceinline__ void fold_partition(const DevState& s, const Labels& 
                 if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
             }
         }
-        if (changed && marks) mark_neighbours(s, v, o.st, o.st + o.d);
+        if (changed && marks) mark_neighbours<ASYNC>(s, v, o.st, o.st + o.d, po, best_lab, L.C);
     }
     __syncthreads();
 }

@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small_async(DevState s,
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
     const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
+    const bool po = s.ctrl->prune_other != 0;                        // FLPA's pruning rule
     const unsigned cnt = bv.cnt;
     unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned tile = blockIdx.x * (unsigned)kTile; tile < cnt; tile += gridDim.x * (unsigned)kTile) {
@@ -270,7 +271,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small_async(DevState s,
 #pragma unroll
                         for (int q = 0; q < MAXD; ++q) {
                             const int32_t j = sidx[q * SL + pos];
-                            if (q < d && j != v) s.flags[j] = 1;
+                            // FLPA's rule: a neighbour already carrying `best` stays unmarked
+                            if (q < d && j != v && !(po && lab[q] == best)) s.flags[j] = 1;
                         }
                     }
                     ++my_changed;

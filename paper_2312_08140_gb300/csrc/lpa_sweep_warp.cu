@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
     const bool marks = marks_on(s, flag_neighbours);
     const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
     const bool ident = identity_sweep<ASYNC, BATCH>(s);
+    const bool po = ASYNC && s.ctrl->prune_other != 0;               // FLPA's pruning rule
     const unsigned cnt = bv.cnt;
     const unsigned nwarps = gridDim.x * kWarpsPerBlock;
     // each warp takes batches of B consecutive frontier entries (B <= 32), B
@@ -82,8 +83,22 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
     unsigned B = (cnt + nwarps - 1) / nwarps;
     if (ASYNC && B < kAsyncMinBatch) B = kAsyncMinBatch;
     B = B < 1u ? 1u : (B > 32u ? 32u : B);
+    // In the asynchronous mode the batches are visited in a scattered order:
+    // batch b is taken as (b * mul) mod nbatch, mul coprime with nbatch.  In
+    // id order, a graph spanning several waves of warps would have its low ids
+    // updated before its high ids -- a coarse ascending sweep that, with the
+    // smallest-id tie-break, lets the smallest labels flood through id-ordered
+    // blocks (a planted partition inside a large batch fell to Q = 0.38).
+    const unsigned nbatch = (cnt + B - 1) / B;
+    unsigned mul = 1;
+    if (ASYNC && nbatch > 2) {
+        mul = (0x9E3779B1u % nbatch) | 1u;
+        for (int tries = 0; tries < 64 && gcd_u32(mul, nbatch) != 1u; ++tries) mul += 2u;
+        if (gcd_u32(mul, nbatch) != 1u) mul = 1;
+    }
     unsigned long long my_changed = 0, my_changed_entries = 0;
-    for (unsigned base = (blockIdx.x * kWarpsPerBlock + wib) * B; base < cnt; base += nwarps * B) {
+    for (unsigned bi = blockIdx.x * kWarpsPerBlock + wib; bi < nbatch; bi += nwarps) {
+        const unsigned base = (unsigned)(((unsigned long long)bi * mul) % nbatch) * B;
         // Metadata of up to B consecutive frontier entries, one per lane, loaded
         // together so their latencies overlap.
         const unsigned kl = base + lane;
@@ -131,6 +146,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
             const int d = (int)(en - st);
             const TieRule tr = tie_rule(s, NS && act, sweep, v);
             const int32_t j = j_cur;
+            const int32_t lab_row = lab_cur;        // this row's first-chunk labels
             const int32_t j_nn = first_index(i + 2);
             int32_t lab_nxt;
             T w_nxt;
@@ -239,12 +255,13 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
             }
             if (changed) {
                 if (marks) {
+                    // FLPA's rule: a neighbour already carrying `best` stays unmarked
                     if (d <= 32) {                   // this row's indices are still in j
-                        if ((int)lane < d && j != v) mark_unprocessed(s.flags, j);
+                        if ((int)lane < d && j != v && !(po && lab_row == best)) mark_unprocessed(s.flags, j);
                     } else {
                         for (int64_t e = st + lane; e < en; e += 32) {
                             const int32_t jj = s.idx[e];
-                            if (jj != v) mark_unprocessed(s.flags, jj);
+                            if (jj != v && !(po && load_label<ASYNC>(L.C, jj) == best)) mark_unprocessed(s.flags, jj);
                         }
                     }
                 }

@@ -28,4 +28,5 @@ def test_async_invariants():
         got, it, _ = CP.run(g.off, g.idx, g.w, "async", n_threads=4)
         assert 1 <= it <= 20
         assert O.count_labels_outside_component(g.off, g.idx, got) == 0
-        assert O.modularity(g.off, g.idx, g.w, got) >= async_floor(g), g.n
+        # the paper's chunked ascending design can end like a monotone serial run
+        assert O.modularity(g.off, g.idx, g.w, got) >= async_floor(g, include_monotone=True), g.n

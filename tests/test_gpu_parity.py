@@ -362,6 +362,61 @@ def test_nonstrict_async_invariants(lpa):
         assert 1 <= info["iterations"] <= 20
 
 
+def test_prune_other_needs_async(lpa):
+    """LPA_PRUNE_OTHER (FLPA's pruning rule, Section 2) changes the algorithm,
+    so the synchronous modes refuse it."""
+    g = L.planted_partition(n=500, blocks=5, seed=3)
+    h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w)
+    try:
+        for mode in ("sync+prune_other", "sync_full+prune_other", "sync+nonstrict+prune_other"):
+            with pytest.raises(lpa.LpaError) as e:
+                lpa.lpa_run(h, mode, 0.05, 20, None)
+            assert e.value.status == lpa.LPA_ERR_INVALID_ARG
+    finally:
+        lpa.lpa_graph_destroy(h)
+
+
+def test_prune_other_async_invariants(lpa):
+    """Asynchronous runs under FLPA's pruning rule (a vertex whose label
+    changes to c marks only the neighbours not already in c): labels inside
+    components, the GPU's modularity equal to the oracle's on the same labels
+    and at least the floor of serial runs under the same rule, each vertex
+    scanned at most once per sweep, every vertex with an entry scanned in the
+    first sweep; batched graphs too."""
+    import torch
+    graphs = [L.planted_partition(n=3000, blocks=6, seed=31), L.road_grid(120, 90, seed=6),
+              L.rmat(14, 16, seed=7), hub_graph(40000)]
+    for g in graphs:
+        got, info, h = run_gpu(lpa, g, "async+prune_other")
+        try:
+            q_gpu = lpa.lpa_modularity(h, torch.from_numpy(got).cuda())
+        finally:
+            lpa.lpa_graph_destroy(h)
+        assert O.count_labels_outside_component(g.off, g.idx, got) == 0
+        q = O.modularity(g.off, g.idx, g.w, got)
+        assert abs(q_gpu - q) <= 1e-6 * max(1.0, abs(q))
+        with_entries = int(np.count_nonzero(np.diff(g.off)))
+        assert info["active"][0] == with_entries and all(a <= with_entries for a in info["active"])
+        floor = async_floor(g, prune_other=True)
+        print(f"prune_other n={g.n}: Q={q:.4f} floor={floor:.4f} sweeps={info['iterations']} "
+              f"scanned={sum(info['active'])}")
+        assert q >= floor, (q, floor)
+    batch = [L.batched_sbm_graph(gi, n_max=4000) for gi in range(8)]
+    vo, eo, off, idx, w = _batch_inputs(batch)
+    b = lpa.lpa_batch_create(len(batch), vo, eo, off, idx, w)
+    out = torch.empty(int(vo[-1]), dtype=torch.int32, device="cuda")
+    try:
+        lpa.lpa_batch_run(b, len(batch), "async+prune_other", 0.05, 20, out, info=False)
+        got = out.cpu().numpy()
+        for k, gr in enumerate(batch):
+            lab = got[vo[k]:vo[k + 1]]
+            assert O.count_labels_outside_component(gr.off, gr.idx, lab) == 0, k
+            assert O.modularity(gr.off, gr.idx, gr.w, lab) >= async_floor(gr, prune_other=True,
+                                                                          include_monotone=True), k
+    finally:
+        lpa.lpa_batch_destroy(b)
+
+
 def test_pool_reuse_and_release(lpa):
     """Graph memory comes from the library's pool: graphs created after others
     were destroyed (reusing their pages), and after the cache was released,
@@ -379,9 +434,9 @@ def check_async(lpa, g, tau=0.05, iters=20, cfg=None):
     """Async run held to: labels in range and inside the vertex's component;
     GPU modularity equal to the fp64 oracle's on the same labels (1e-6 rel);
     modularity at least async_floor(g): the lowest of serial runs of
-    Algorithm 1 in several vertex orders less 0.01, or, above 300K vertices,
-    the ascending serial run less 0.02; vertices off their local argmax
-    reported."""
+    Algorithm 1 in seeded random vertex orders less 0.03, or, above 300K
+    vertices, the ascending serial run less 0.02; vertices off their local
+    argmax reported."""
     import torch
     got, info, h = run_gpu(lpa, g, "async", tau, iters, cfg)
     try:
