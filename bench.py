@@ -482,9 +482,16 @@ def kernel_bytes(prof, wbytes, sync, passes, rows_distinct=False):
     labels are still the vertex ids); per changed vertex 4 B label write (+4 B
     changed-list entry in sync mode) and 1 B flag per entry of its row."""
     out = {b: {"bytes": 0.0, "ms": 0.0, "launches": 0} for b in BIN_KERNELS}
+    if not prof["iterations"]:
+        return out
+    # the first sweep scans every vertex with an entry: a bin empty then is
+    # statically empty and never launched
+    launched = [prof["bin_vertices"][0][bi] > 0 for bi in range(len(BIN_KERNELS))]
     for t in range(min(prof["iterations"], 64)):
         gather = 0 if (sync and rows_distinct and t == 0) else 4
         for bi, b in enumerate(BIN_KERNELS):
+            if not launched[bi]:
+                continue
             v = prof["bin_vertices"][t][bi]
             e = prof["bin_entries"][t][bi]
             c = prof["bin_changed"][t][bi]
