@@ -19,8 +19,9 @@ CPU design walks contiguous chunks in ascending order and can end the same
 way (cpu_parallel: Q = 0 with 1 or 16 threads on a 3000-vertex planted
 partition), so its test keeps the monotone orders (include_monotone), and so
 do the tests of batched and served runs: inside a batch, a graph's
-asynchronous run can fall well below its run alone (graph 0 of a batch of
-eight 140K-vertex planted partitions: Q 0.45-0.52 against 0.74 alone).
+asynchronous runs spread much more widely than alone (graph 0 of a batch of
+eight 140K-vertex planted partitions: Q 0.45-0.76 across runs, 0.73-0.76
+alone).
 """
 import numpy as np
 
