@@ -53,6 +53,15 @@ def test_pure_host_entry_points(lib_path):
     assert e.value.status == lpa.LPA_ERR_INVALID_ARG
     with pytest.raises(lpa.LpaError):
         lpa.lpa_graph_destroy(None)
+    # the server takes plain modes only: the non-strict and FLPA flags are refused
+    for mode in ("async+prune_other", "sync+nonstrict"):
+        with pytest.raises(lpa.LpaError) as e:
+            lpa.lpa_serve_create(1 << 30, 1000, 10000, mode=mode)
+        assert e.value.status == lpa.LPA_ERR_INVALID_ARG
+    # mode strings: flags combine with "+", unknown ones are refused in the binding
+    assert lpa._mode("async+nonstrict+prune_other") == lpa.MODES["async"] | lpa.LPA_NONSTRICT | lpa.LPA_PRUNE_OTHER
+    with pytest.raises(ValueError):
+        lpa._mode("async+bogus")
 
 
 def test_struct_layouts_match_c(lib_path):
