@@ -438,8 +438,19 @@ cudaError_t launch_bin(Engine& E, int mode, int bin, cudaStream_t st) {
 // A sweep's frontier is a subset of the static bin lists (same thresholds,
 // vertices with no entries never join), so a bin that is statically empty is
 // not launched at all.
+// Launch order of the bins in a pass.  Asynchronous passes run the last bin
+// first: in the first sweep every neighbour of its rows is then still
+// unprocessed, so those rows read initial labels (their vertex ids) -- a
+// valid interleaving of the parallel loop -- and take the max-over-row path
+// on graphs whose rows repeat no neighbour.
+int bin_at(int mode, int k) {
+    if ((mode & ~kModeNonstrict) == MODE_ASYNC) return k == 0 ? kBins - 1 : k - 1;
+    return k;
+}
+
 cudaError_t enqueue_pass(Engine& E, int mode, cudaStream_t st) {
-    for (int b = 0; b < kBins; ++b) {
+    for (int k = 0; k < kBins; ++k) {
+        const int b = bin_at(mode, k);
         if (E.s.bin_static[b] == 0) continue;
         cudaError_t err = launch_bin(E, mode, b, st);
         if (err != cudaSuccess) return err;
@@ -652,17 +663,18 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
         float sweep_ms[kBins] = {0.f}, fin_ms = 0.f;
         const int passes = mode == MODE_ASYNC ? 2 : 1;
         for (int p = 0; p < passes; ++p) {
-            for (int b = 0; b < kBins; ++b) {
-                LPA_P(cudaEventRecord(ev[b], st));
+            for (int k = 0; k < kBins; ++k) {
+                const int b = bin_at(mode, k);
+                LPA_P(cudaEventRecord(ev[k], st));
                 if (E.s.bin_static[b]) LPA_P(launch_bin(E, mode | (ns ? kModeNonstrict : 0), b, st));
             }
             LPA_P(cudaEventRecord(ev[kBins], st));
             LPA_P(launch_finish(E.s, mode, p + 1 < passes ? kRoleCatchUp : kRoleEndSweep, none, 0, st, E.sms));
             LPA_P(cudaEventRecord(ev[kBins + 1], st));
             LPA_P(cudaEventSynchronize(ev[kBins + 1]));
-            for (int b = 0; b < kBins; ++b) {
-                LPA_P(cudaEventElapsedTime(&ms, ev[b], ev[b + 1]));
-                sweep_ms[b] += ms;
+            for (int k = 0; k < kBins; ++k) {
+                LPA_P(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+                sweep_ms[bin_at(mode, k)] += ms;
             }
             LPA_P(cudaEventElapsedTime(&ms, ev[kBins], ev[kBins + 1]));
             fin_ms += ms;

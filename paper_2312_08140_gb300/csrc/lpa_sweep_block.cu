@@ -167,7 +167,12 @@ __global__ void __launch_bounds__(512, 4) k_sweep_block(DevState s, int bin, int
     const Labels L = labels_of(s);
     const bool marks = marks_on(s, flag_neighbours);
     const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
-    const bool ident = identity_sweep<ASYNC, BATCH>(s);
+    // Max-over-row path: the first synchronous sweep of a repeat-free graph;
+    // and in the asynchronous mode, the last bin of the first sweep's main
+    // pass, which runs before every other bin (its rows then read initial
+    // labels, as if processed before their neighbours).
+    bool ident = identity_sweep<ASYNC, BATCH>(s);
+    if constexpr (ASYNC && !BATCH && LAST) ident = s.rows_distinct && s.ctrl->iter == 0 && L.dense;
     const bool po = ASYNC && s.ctrl->prune_other != 0;               // FLPA's pruning rule
     const unsigned cnt = bv.cnt;
     const int log_S = ceil_log2((unsigned)S);
