@@ -186,15 +186,6 @@ __device__ __forceinline__ uint32_t warp_argmax_tie(uint32_t key, uint32_t tie) 
     return __reduce_min_sync(kFull, key == m ? tie : 0xffffffffu);
 }
 
-__device__ __forceinline__ uint32_t gcd_u32(uint32_t a, uint32_t b) {
-    while (b) {
-        const uint32_t t = a % b;
-        a = b;
-        b = t;
-    }
-    return a;
-}
-
 __device__ __forceinline__ int ceil_log2(uint32_t x) {  // x >= 1
     return x <= 1 ? 0 : 32 - __clz(x - 1);
 }

@@ -23,6 +23,7 @@ constexpr int kWarpThreads = 256;
 constexpr int kWarpsPerBlock = kWarpThreads / 32;
 constexpr int kWarpUnroll = 3;      // chunks of 32 entries in flight per warp beyond the first
 constexpr unsigned kAsyncMinBatch = 8;
+constexpr unsigned kScatterWindow = 4096;   // batches per scattered window (a power of two)
 
 // Combined weight of the lanes in `peers` (all hold the same label).
 template <int WK>
@@ -83,22 +84,22 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
     unsigned B = (cnt + nwarps - 1) / nwarps;
     if (ASYNC && B < kAsyncMinBatch) B = kAsyncMinBatch;
     B = B < 1u ? 1u : (B > 32u ? 32u : B);
-    // In the asynchronous mode the batches are visited in a scattered order:
-    // batch b is taken as (b * mul) mod nbatch, mul coprime with nbatch.  In
-    // id order, a graph spanning several waves of warps would have its low ids
+    // In the asynchronous mode the batches are visited in a scattered order
+    // within windows of kScatterWindow batches (an odd multiplier modulo the
+    // window's power-of-two size; the last, partial window in order).  In id
+    // order, a graph spanning several waves of warps would have its low ids
     // updated before its high ids -- a coarse ascending sweep that, with the
     // smallest-id tie-break, lets the smallest labels flood through id-ordered
-    // blocks (a planted partition inside a large batch fell to Q = 0.38).
+    // blocks.  The windows keep the labels being gathered at a time to a few
+    // graphs' worth (L2-resident) in large batches.
     const unsigned nbatch = (cnt + B - 1) / B;
-    unsigned mul = 1;
-    if (ASYNC && nbatch > 2) {
-        mul = (0x9E3779B1u % nbatch) | 1u;
-        for (int tries = 0; tries < 64 && gcd_u32(mul, nbatch) != 1u; ++tries) mul += 2u;
-        if (gcd_u32(mul, nbatch) != 1u) mul = 1;
-    }
+    const unsigned full_windows = nbatch / kScatterWindow;
     unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned bi = blockIdx.x * kWarpsPerBlock + wib; bi < nbatch; bi += nwarps) {
-        const unsigned base = (unsigned)(((unsigned long long)bi * mul) % nbatch) * B;
+        unsigned pb = bi;
+        if (ASYNC && bi / kScatterWindow < full_windows)
+            pb = (bi & ~(kScatterWindow - 1u)) | ((bi * 0x9E3779B1u) & (kScatterWindow - 1u));
+        const unsigned base = pb * B;
         // Metadata of up to B consecutive frontier entries, one per lane, loaded
         // together so their latencies overlap.
         const unsigned kl = base + lane;
