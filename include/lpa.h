@@ -54,10 +54,12 @@ typedef enum {
  * LPA_MODE_ASYNC      Algorithm 1 as the paper runs it (Section 4.1): labels
  *                     are updated in place while other vertices read them,
  *                     with vertex pruning.  Each sweep scans the unprocessed
- *                     vertices, then once more the vertices re-marked during
- *                     that scan (as the serial loop scans a re-marked vertex
- *                     again later in the same sweep); dN counts both.  Results
- *                     depend on timing.
+ *                     vertices, then the vertices marked during that scan
+ *                     that were not in it (the serial loop reaches those later
+ *                     in the same sweep); a vertex is scanned at most once per
+ *                     sweep, and one already scanned keeps a new mark for the
+ *                     next sweep.  dN counts both passes.  Results depend on
+ *                     timing.
  * LPA_MODE_SYNC_FULL  LPA_MODE_SYNC without pruning: every vertex is scanned
  *                     in every sweep.  Same labels as LPA_MODE_SYNC. */
 typedef enum {
