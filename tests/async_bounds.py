@@ -7,8 +7,9 @@ graphs by several hundredths.  A parallel run is one more interleaving.  The
 tests hold it to the lowest modularity among serial runs in seeded random
 vertex orders, less a slack (a parallel pass updates many vertices at once
 and lands 0.01-0.03 below the serial runs on planted partitions); above max_n
-vertices, where several serial runs take minutes, to the ascending run less a
-wider slack.
+vertices, where several serial runs take minutes, to the ascending run less
+the same slack (the 4096x4096 grid's async runs that stop after 3 sweeps
+reach 0.633 against the ascending run's 0.648).
 
 Serial runs in monotone id order (ascending or descending) are left out of
 the floor when random orders are available: with the smallest-id tie-break a
@@ -28,7 +29,7 @@ import numpy as np
 import oracle as O
 
 SLACK_ORDERS = 0.03
-SLACK_ASCENDING = 0.02
+SLACK_ASCENDING = 0.03
 
 
 def async_floor(g, tau=0.05, iters=20, random_orders=6, seed=0, max_n=300_000, prune_other=False,
