@@ -142,11 +142,11 @@ typedef struct {
  *   mid_max   < d <= large_max      one 256-thread block per vertex, shared table
  *   d > large_max                   one 512-thread block per vertex, 8192-slot shared
  *                                   table; a row whose distinct labels overflow it is
- *                                   split over hash partitions of its labels: rows of
- *                                   up to 8 partitions are rescanned by one block per
- *                                   partition, longer rows are read once in slices
- *                                   grouped by partition, then aggregated by one
- *                                   block per partition
+ *                                   split over hash partitions of its labels: it is
+ *                                   read once in slices grouped by partition, then
+ *                                   aggregated by one block per partition (rows
+ *                                   beyond that path's limits are rescanned by one
+ *                                   block per partition)
  * A sweep is "dense" (every vertex with an entry is scanned, no frontier
  * compaction) when the vertices changed since the previous compaction hold
  * at least dense_permille / 1000 of all entries; the first sweep is always
