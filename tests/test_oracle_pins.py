@@ -5,7 +5,8 @@
 - invariants any label propagation run has (labels travel along edges only;
   a synchronous fixed point is stable),
 - modularity (Eq. 1) closed forms and the networkx library routine,
-- connected components from scipy for the component checker,
+- connected components from scipy for the component checker, and enumerated
+  Eq. 2 sums for the local-maximum checker,
 - planted mistakes: broken copies of the oracle source must fail these pins.
 """
 import json
@@ -218,6 +219,49 @@ def test_local_max_checker_closed_cases():
     assert O.count_not_local_max(g.off, g.idx, None, np.zeros(n, dtype=np.int32)) == 0
 
 
+def _enumerated_not_local_max(g, C):
+    """Vertices whose own label's weight K_{i->C_i} is below the best label's
+    (Eq. 2's sums, enumerated); a label outside [0, n) counts, a vertex with no
+    neighbour but itself does not."""
+    bad = 0
+    for i in range(g.n):
+        if not 0 <= int(C[i]) < g.n:
+            bad += 1
+            continue
+        sums = _label_sums(g, C, i)
+        if sums and sums.get(int(C[i]), 0.0) < max(sums.values()):
+            bad += 1
+    return bad
+
+
+def test_local_max_checker_matches_enumeration():
+    rng = np.random.default_rng(11)
+    checked = 0
+    for g, C in _random_cases(600, seed0=70000):
+        if g.n == 0:
+            continue
+        # few distinct labels make ties common, which a tie-sensitive checker would miscount
+        for lab in (C, rng.integers(0, min(g.n, 3), size=g.n).astype(np.int32),
+                    O.lpa_sync(g.off, g.idx, g.w, tau=0.0, max_iters=2)[0]):
+            assert O.count_not_local_max(g.off, g.idx, g.w, lab) == _enumerated_not_local_max(g, lab)
+            checked += 1
+    assert checked > 1500
+
+
+def _checker_pins_pass(mod):
+    rng = np.random.default_rng(13)
+    for g, C in _random_cases(150, seed0=80000):
+        if g.n == 0:
+            continue
+        if mod.count_labels_outside_component(g.off, g.idx, C) != int(np.sum(_component_ids(g)[C] != _component_ids(g))):
+            return False
+        few = rng.integers(0, min(g.n, 3), size=g.n).astype(np.int32)
+        for lab in (C, few):
+            if mod.count_not_local_max(g.off, g.idx, g.w, lab) != _enumerated_not_local_max(g, lab):
+                return False
+    return True
+
+
 # ----------------------------------------------------------- modularity --
 def test_modularity_closed_forms():
     # K_n, all singletons: sigma = 0, Sigma_c = n-1 each: Q = -n (n-1)^2 / (n(n-1))^2 = -1/n
@@ -300,6 +344,8 @@ MUTANTS = {
     "isolated_takes_zero": ("int32_t c = C[i];\n    if (used) {", "int32_t c = 0;\n    if (used) {"),
     "modularity_null_term_dropped": ("q = sigma / two_m - null_term;", "q = sigma / two_m;"),
     "modularity_sigma_by_other_end": ("Sigma[C[i]] += K_i;", "Sigma[C[idx[off[i]]]] += K_i;"),
+    "local_max_tie_sensitive": ("if (own < H.val[best]) ++bad;", "if (own <= H.val[best] && C[i] != best) ++bad;"),
+    "component_union_dropped": ("if (a != b) parent[a < b ? b : a] = (a < b ? a : b);", "(void)a; (void)b;"),
     "cap_off_by_one": ("while (it < max_iters) {\n        memcpy", "while (it <= max_iters) {\n        memcpy"),
 }
 
@@ -392,6 +438,8 @@ def _pins_pass(mod):
         if not _nonstrict_pins_pass(mod):
             return False
         if not _flpa_pins_pass(mod):
+            return False
+        if not _checker_pins_pass(mod):
             return False
         pairs = [(u, v) for u in range(5) for v in range(u + 1, 5)]
         pairs += [(u + 5, v + 5) for u, v in pairs] + [(4, 5)]
