@@ -3,6 +3,7 @@ entry point include/lpa.h declares; the Python binding covers the same names."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -72,3 +73,46 @@ def test_struct_layouts_match_c(lib_path):
     assert ctypes.sizeof(lpa.LpaConfig) == 20
     B = lpa.LPA_BINS
     assert ctypes.sizeof(lpa.LpaProfile) == 16 + 4 * H + 4 * B * H + 4 * B * 8 * H
+
+
+_C_STRUCTS = {"LpaRunInfo": "lpa_run_info", "LpaGraphProps": "lpa_graph_props", "LpaConfig": "lpa_config",
+              "LpaProfile": "lpa_profile", "LpaServeConfig": "lpa_serve_config",
+              "LpaServeStats": "lpa_serve_stats_t"}
+
+
+def test_header_is_plain_c_and_layouts_match_the_binding(lib_path, tmp_path):
+    """A C11 program (no C++) includes lpa.h, links liblpa.so, prints every
+    struct's size and field offsets, and calls the host-only entry points: the
+    binding's ctypes layouts must agree field by field."""
+    import paper_2312_08140_gb300 as lpa
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include <string.h>', '#include "lpa.h"',
+             'int main(void) {']
+    for py, c in _C_STRUCTS.items():
+        lines.append(f'    printf("{py} . %zu\\n", sizeof({c}));')
+        for f, _ in getattr(lpa, py)._fields_:
+            lines.append(f'    printf("{py} {f} %zu\\n", offsetof({c}, {f}));')
+    lines += ['    lpa_graph_t g = 0;',
+              '    if (lpa_graph_create(-1, 0, 0, 0, 0, LPA_HOST_PTRS, 0, &g) != LPA_ERR_INVALID_ARG) return 2;',
+              '    if (strcmp(lpa_status_string(LPA_ERR_INVALID_GRAPH), "invalid graph") != 0) return 3;',
+              '    printf("version %s\\n", lpa_version());',
+              '    return 0;', '}']
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    libdir = os.path.dirname(lib_path)
+    subprocess.check_call(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                           "-L", libdir, "-l:" + os.path.basename(lib_path), "-Wl,-rpath," + libdir])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    *layout, version = out.stdout.rstrip().splitlines()
+    assert version.startswith("version lpa-gb300")
+    got = {}
+    for ln in layout:
+        a, b, v = ln.split(" ")
+        got[(a, b)] = v
+    for py in _C_STRUCTS:
+        cls = getattr(lpa, py)
+        assert int(got[(py, ".")]) == ctypes.sizeof(cls), py
+        for f, _ in cls._fields_:
+            assert int(got[(py, f)]) == getattr(cls, f).offset, (py, f)
