@@ -1,6 +1,7 @@
-"""Host logic of bench.py's roofline accounting (kernel_bytes): the
+"""Host logic of bench.py: the roofline accounting (kernel_bytes: the
 algorithmic bytes per launch of each degree-bin kernel from the per-sweep
-counts of a profiled run, worked by hand on a two-sweep profile."""
+counts of a profiled run, worked by hand on a two-sweep profile), the
+validity of the recorded ncu traffic, and the clock summary."""
 import os
 import sys
 
@@ -45,3 +46,40 @@ def test_async_counts_two_passes_and_4_byte_changes():
     # async: labels are always gathered, a change writes 4 B
     warp = (5 * 24 + 100 * 8 + 5 * 4 + 100) + (5 * 24 + 100 * 8)
     assert out["k_sweep_warp"]["bytes"] == warp and out["k_sweep_warp"]["launches"] == 4
+
+
+def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
+    """The ncu DRAM bytes stand for the kernel sources they were captured
+    from: any edit to those files (another sha1) turns them into null."""
+    assert bench.measured_traffic("k_no_such_kernel") is None
+    rec = dict(bench.TRAFFIC["k_sweep_small"])
+    got = bench.measured_traffic("k_sweep_small")
+    assert got is None or got == rec["bytes_per_launch"]
+    monkeypatch.setitem(bench.TRAFFIC, "k_sweep_small", dict(rec, sha1="0" * 40))
+    assert bench.measured_traffic("k_sweep_small") is None
+
+
+def test_clock_summary_takes_the_median_and_every_active_reason():
+    """nvidia-smi CSV rows (index, sm, max sm, power, active mask, then four
+    reasons) become the median SM clock and the set of reasons seen Active;
+    malformed rows are skipped."""
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+        def join(self, timeout=None):
+            pass
+
+    cs = bench.ClockSampler(0)
+    cs.proc, cs.thread = _Done(), _Done()
+    cs.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+                "0, 2040, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "garbled",
+                "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    got = cs.stop()
+    assert got == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.ClockSampler(0).stop() is None
