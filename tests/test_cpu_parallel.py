@@ -1,7 +1,8 @@
 """The multi-core CPU baseline (cpu_parallel, the paper's OpenMP design):
 its synchronous runs must equal the oracle's exactly (pruning and thread
 interleaving cannot change a Jacobi sweep with the strict tie-break), and its
-asynchronous runs must meet the invariants and modularity floor the GPU's do."""
+asynchronous runs must meet the invariants and modularity floor the GPU's do,
+and on one thread equal the serial ascending run."""
 import numpy as np
 
 import cpu_parallel as CP
@@ -30,3 +31,17 @@ def test_async_invariants():
         assert O.count_labels_outside_component(g.off, g.idx, got) == 0
         # the paper's chunked ascending design can end like a monotone serial run
         assert O.modularity(g.off, g.idx, g.w, got) >= async_floor(g, include_monotone=True), g.n
+
+
+def test_async_on_one_thread_is_the_serial_ascending_run():
+    """One thread walks the chunks in ascending order, updating in place, so it
+    is the serial ascending execution of Algorithm 1: labels, sweep count and
+    per-sweep changes equal the oracle's exactly."""
+    rng = np.random.default_rng(5)
+    graphs = _graphs() + [L.random_small(int(rng.integers(1, 40)), float(rng.uniform(0.05, 0.6)), seed=s,
+                                         wmax=int(rng.integers(0, 5)), self_loops=0.2, multi=bool(s % 2))
+                          for s in range(200)]
+    for g in graphs:
+        ref, it, ch = O.lpa_async(g.off, g.idx, g.w)
+        got, it2, ch2 = CP.run(g.off, g.idx, g.w, "async", n_threads=1)
+        assert np.array_equal(got, ref) and it2 == it and ch2.tolist() == ch.tolist(), g.n
