@@ -377,6 +377,8 @@ lpa_status lpa_serve_fetch(lpa_server_t s, uint64_t ticket, int32_t *labels_host
 /* Forgets a finished request's result. */
 lpa_status lpa_serve_release(lpa_server_t s, uint64_t ticket);
 
+/* Snapshot of the server's counters into a host struct; takes the server's
+ * lock but never waits on the device.  LPA_ERR_INVALID_ARG if s or out is NULL. */
 lpa_status lpa_serve_stats(lpa_server_t s, lpa_serve_stats_t *out);
 
 /* Stops the workers (requests not finished are dropped) and frees the arena. */
