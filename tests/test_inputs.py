@@ -1,4 +1,5 @@
-"""The seeded generators give symmetric, sorted CSR of the advertised shape."""
+"""The seeded generators give symmetric, sorted CSR of the advertised shape and
+the advertised distributions (R-MAT quadrant rates, grid drop and shortcut rates)."""
 import numpy as np
 import pytest
 
@@ -77,3 +78,36 @@ def test_batched_params_and_pack():
     assert vo[-1] == sum(gr.n for gr in graphs) and off[-1] == eo[-1]
     for k, gr in enumerate(graphs):
         assert np.array_equal(idx[eo[k]:eo[k + 1]] - vo[k], gr.idx)
+
+
+def test_rmat_quadrant_probabilities():
+    """Each recursion level of R-MAT picks quadrant (row bit, column bit) =
+    (0,0), (0,1), (1,0), (1,1) with a, b, c, d; the raw symmetrised entries
+    show those rates at every bit level (the mirrored half swaps b and c)."""
+    scale = 14
+    raw = L.rmat(scale, 16, seed=3, dedup=False, drop_self=False)
+    src = np.repeat(np.arange(raw.n, dtype=np.int64), np.diff(raw.off))
+    dst = raw.idx.astype(np.int64)
+    a, b, c, d = 0.57, 0.19, 0.19, 0.05
+    for level in (scale - 1, scale // 2, 0):
+        rs, cs = (src >> level) & 1, (dst >> level) & 1
+        got = [np.mean((rs == r) & (cs == q)) for r, q in ((0, 0), (0, 1), (1, 0), (1, 1))]
+        want = [a, (b + c) / 2, (b + c) / 2, d]
+        assert np.allclose(got, want, atol=0.01), (level, got)
+
+
+def test_road_grid_drop_and_shortcut_rates():
+    """About 90% of the 4-neighbour lattice edges are kept, and 0.1% of that
+    count is added as shortcuts (non-lattice pairs)."""
+    rows, cols = 256, 256
+    g = L.road_grid(rows, cols, seed=4)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.off))
+    dst = g.idx.astype(np.int64)
+    up = src < dst
+    s, t = src[up], dst[up]
+    lattice = ((t - s == 1) & (s // cols == t // cols)) | (t - s == cols)
+    n_lattice = rows * (cols - 1) + cols * (rows - 1)
+    kept = int(lattice.sum())
+    assert abs(kept / n_lattice - 0.90) < 0.01
+    shortcuts = int((~lattice).sum())
+    assert abs(shortcuts - 0.001 * kept) <= max(5, 0.2 * 0.001 * kept)
