@@ -182,18 +182,48 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- oracle arm
+def oracle_run(g, mode, max_iters):
+    """The oracle's run for a mode string of the library ("sync", "async",
+    "sync_full", with "+nonstrict" / "+prune_other"); returns (labels,
+    iterations, changed)."""
+    import oracle as O
+    base, *flags = mode.split("+")
+    nonstrict = "nonstrict" in flags
+    if base in ("sync", "sync_full"):
+        return O.lpa_sync(g.off, g.idx, g.w, TAU, max_iters, nonstrict=nonstrict)
+    if "prune_other" in flags:
+        return O.lpa_async_ex(g.off, g.idx, g.w, TAU, max_iters, nonstrict=nonstrict, prune_other=True)[:3]
+    return O.lpa_async(g.off, g.idx, g.w, TAU, max_iters, nonstrict=nonstrict)
+
+
 def oracle_sample(graphs, pairs):
     """Times one oracle sweep per (graph, mode) pair; returns (edges, seconds)."""
-    import oracle as O
     edges, secs = 0, 0.0
     for gi, mode in pairs:
         g = graphs[gi]
-        fn = O.lpa_sync if mode == "sync" else O.lpa_async
         t0 = time.perf_counter()
-        _, it, _ = fn(g.off, g.idx, g.w, TAU, 1)
+        _, it, _ = oracle_run(g, mode, 1)
         secs += time.perf_counter() - t0
         edges += g.nnz * it
     return edges, secs
+
+
+def workload_modes(args):
+    """The mode strings one step runs on each graph of the workload."""
+    modes = WORKLOAD_MODES.get(args.workload, MODES)
+    if args.tie == "nonstrict":
+        modes = tuple(m + "+nonstrict" for m in modes)
+    if args.prune == "other":
+        modes = tuple(m + "+prune_other" if m.startswith("async") else m for m in modes)
+    return modes
+
+
+def run_config(args, world):
+    """The JSON line's config object, the same for both arms."""
+    return {"workload": WORKLOAD_TEXT[args.workload], "tie_break": args.tie,
+            "async_pruning": "FLPA rule" if args.prune == "other" else "every neighbour",
+            "inputs_larger_than_l2": True,
+            "parallelism": f"replicas x{world}", "tau": TAU, "max_iters": MAX_ITERS}
 
 
 def param_sweep(lpa, torch, stream, names, graphs, handles, outs, mode="async", reps=3):
@@ -248,7 +278,7 @@ def run_reference(args, rank, world):
     O.build()
     wl = workload(args.workload)
     graphs = [make() for _, make in wl]
-    modes = WORKLOAD_MODES.get(args.workload, MODES)
+    modes = workload_modes(args)
     pairs = [(gi, m) for gi in range(len(graphs)) for m in modes]
     for s in range(args.warmup):
         oracle_sample(graphs, [pairs[s % len(pairs)]])
@@ -265,7 +295,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_TEXT[args.workload]},
+            "data": "synthetic", "config": run_config(args, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -552,11 +582,7 @@ def main():
 
     wl = workload(args.workload)
     graphs = [make() for _, make in wl]
-    modes = WORKLOAD_MODES.get(args.workload, MODES)
-    if args.tie == "nonstrict":
-        modes = tuple(m + "+nonstrict" for m in modes)
-    if args.prune == "other":
-        modes = tuple(m + "+prune_other" if m.startswith("async") else m for m in modes)
+    modes = workload_modes(args)
     stream = torch.cuda.current_stream()
     handles = [lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS, stream) for g in graphs]
     outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
@@ -697,10 +723,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": {"workload": WORKLOAD_TEXT[args.workload], "tie_break": args.tie,
-                           "async_pruning": "FLPA rule" if args.prune == "other" else "every neighbour",
-                           "inputs_larger_than_l2": True,
-                           "parallelism": f"replicas x{world}", "tau": TAU, "max_iters": MAX_ITERS},
+                "config": run_config(args, world),
                 "touched_edges_per_s": touched / (ms / 1e3),
                 "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},

@@ -1,7 +1,8 @@
 """Host logic of bench.py: the roofline accounting (kernel_bytes: the
 algorithmic bytes per launch of each degree-bin kernel from the per-sweep
 counts of a profiled run, worked by hand on a two-sweep profile), the
-validity of the recorded ncu traffic, and the clock summary."""
+validity of the recorded ncu traffic, the clock summary, and the modes and
+config the two arms share."""
 import os
 import sys
 
@@ -83,3 +84,28 @@ def test_clock_summary_takes_the_median_and_every_active_reason():
     got = cs.stop()
     assert got == {"sm_mhz": 2040.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     assert bench.ClockSampler(0).stop() is None
+
+
+def test_both_arms_share_modes_and_config():
+    """The oracle arm runs the same mode strings as the GPU arm, each through
+    the matching oracle function, and prints the same config object."""
+    import argparse
+
+    import lpa_inputs as L
+    import oracle as O
+    args = argparse.Namespace(workload="rmat22+grid4096", tie="strict", prune="paper")
+    assert bench.workload_modes(args) == ("sync", "async")
+    assert bench.run_config(args, 1)["tie_break"] == "strict"
+    args = argparse.Namespace(workload="rmat22+grid4096", tie="nonstrict", prune="other")
+    assert bench.workload_modes(args) == ("sync+nonstrict", "async+nonstrict+prune_other")
+    cfg = bench.run_config(args, 2)
+    assert cfg["async_pruning"] == "FLPA rule" and cfg["parallelism"] == "replicas x2"
+    g = L.planted_partition(n=600, blocks=6, intra=10.0, inter=1.0, seed=2)
+    want = {"sync": O.lpa_sync(g.off, g.idx, g.w, bench.TAU, 20),
+            "sync+nonstrict": O.lpa_sync(g.off, g.idx, g.w, bench.TAU, 20, nonstrict=True),
+            "async": O.lpa_async(g.off, g.idx, g.w, bench.TAU, 20),
+            "async+nonstrict": O.lpa_async(g.off, g.idx, g.w, bench.TAU, 20, nonstrict=True),
+            "async+prune_other": O.lpa_async_ex(g.off, g.idx, g.w, bench.TAU, 20, prune_other=True)[:3]}
+    for mode, (C, it, ch) in want.items():
+        C2, it2, ch2 = bench.oracle_run(g, mode, 20)
+        assert C2.tolist() == C.tolist() and it2 == it and ch2.tolist() == ch.tolist(), mode
