@@ -694,9 +694,11 @@ lpa_status lpa_serve_submit(lpa_server_t S, int64_t n, int64_t nnz, const int64_
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(r->ready, st);
     // Page-locked inputs are read by DMA after this call is enqueued: wait for
-    // the copies so the caller may reuse its buffers on return.  (Pageable
-    // inputs were staged by the copies themselves before they returned.)
-    if (e == cudaSuccess && host_pinned(offsets)) e = cudaEventSynchronize(r->ready);
+    // the copies when any of the three arrays is page-locked, so the caller
+    // may reuse its buffers on return.  (Pageable inputs were staged by the
+    // copies themselves before they returned.)
+    if (e == cudaSuccess && (host_pinned(offsets) || host_pinned(indices) || host_pinned(weights)))
+        e = cudaEventSynchronize(r->ready);
     std::lock_guard<std::mutex> lock(S->mu);
     if (e != cudaSuccess) {
         S->vfree.release(r->v0, n);
