@@ -370,8 +370,12 @@ lpa_status lpa_serve_submit(lpa_server_t s, int64_t n, int64_t nnz, const int64_
 lpa_status lpa_serve_poll(lpa_server_t s, uint64_t *done, int32_t cap, int32_t *n_done);
 
 /* Copies a finished request's labels (host int32[n], nullable) and run info
- * (nullable).  LPA_ERR_NOT_READY while it runs, LPA_ERR_NOT_FOUND if unknown,
- * the request's own error (e.g. LPA_ERR_INVALID_GRAPH) if it failed. */
+ * (nullable).  An arena request's info holds iterations, exit_reason and
+ * changed[]; its active[], scanned[] and edges_touched stay 0 (the arena
+ * counts scanned work per cycle, not per request).  A solo-lane request's
+ * info is that of its lpa_run.  LPA_ERR_NOT_READY while it runs,
+ * LPA_ERR_NOT_FOUND if unknown, the request's own error (e.g.
+ * LPA_ERR_INVALID_GRAPH) if it failed. */
 lpa_status lpa_serve_fetch(lpa_server_t s, uint64_t ticket, int32_t *labels_host, lpa_run_info *info);
 
 /* Forgets a finished request's result. */
