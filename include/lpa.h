@@ -372,7 +372,7 @@ lpa_status lpa_serve_poll(lpa_server_t s, uint64_t *done, int32_t cap, int32_t *
 /* Copies a finished request's labels (host int32[n], nullable) and run info
  * (nullable).  An arena request's info holds iterations, exit_reason and
  * changed[]; its active[], scanned[] and edges_touched stay 0 (the arena
- * counts scanned work per cycle, not per request).  A solo-lane request's
+ * keeps no per-request scan counts).  A solo-lane request's
  * info is that of its lpa_run.  LPA_ERR_NOT_READY while it runs,
  * LPA_ERR_NOT_FOUND if unknown, the request's own error (e.g.
  * LPA_ERR_INVALID_GRAPH) if it failed. */
