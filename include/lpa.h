@@ -206,8 +206,10 @@ const char *lpa_last_error(void);
  *   flags     LPA_HOST_PTRS | LPA_DEVICE_PTRS, optionally | LPA_BORROW
  * Validates the CSR on the device (returns LPA_ERR_INVALID_GRAPH on failure)
  * and synchronises `stream` before returning.  Device memory: the CSR copy
- * (unless borrowed) plus about 17 bytes per vertex of working state, taken
- * from the library's per-device memory pool. */
+ * (unless borrowed) plus about 21 bytes per vertex of working state (two
+ * label buffers, flags, the frontier bitmap, bin lists and change marks) and
+ * 8 more per vertex once lpa_modularity has been called, taken from the
+ * library's per-device memory pool; lpa_graph_props reports the total. */
 lpa_status lpa_graph_create(int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *indices,
                             const float *weights, uint32_t flags, void *stream, lpa_graph_t *out);
 
