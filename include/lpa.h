@@ -310,7 +310,11 @@ lpa_status lpa_batch_props_get(lpa_batch_t b, lpa_graph_props *out);
 
 /* Run every graph of the batch: labels_out is device int32[N] with LOCAL ids
  * (graph g's labels lie in [0, n_g)); infos is host lpa_run_info[G] or NULL
- * (non-NULL makes the call wait, as in lpa_run). */
+ * (non-NULL makes the call wait, as in lpa_run).  Each graph's info holds its
+ * own iterations, exit_reason and changed[]; the scan counts (active[],
+ * scanned[], edges_touched) are kept for the whole batch only and stay 0 in
+ * the per-graph infos when G > 1 (lpa_batch_props_get reports the batch's
+ * scanned_total). */
 lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, float tolerance, int32_t max_iters,
                          int32_t *labels_out, void *stream, lpa_run_info *infos);
 
