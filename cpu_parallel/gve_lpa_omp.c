@@ -21,6 +21,7 @@
  * writes a second buffer (a Jacobi reading; with the strict tie-break pruning
  * does not change its result).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -31,6 +32,7 @@
 typedef struct {
     int32_t *keys;
     double *val;
+    uint8_t *seen;      /* label already listed in keys (a zero weight leaves val at 0) */
     int64_t nkeys;
 } table_t;
 
@@ -41,7 +43,10 @@ static int32_t pick(table_t *T, const int64_t *off, const int32_t *idx, const fl
         const int32_t j = idx[e];
         if ((int64_t)j == i) continue;
         const int32_t c = C[j];
-        if (T->val[c] == 0.0) T->keys[T->nkeys++] = c;
+        if (!T->seen[c]) {
+            T->seen[c] = 1;
+            T->keys[T->nkeys++] = c;
+        }
         T->val[c] += w ? (double)w[e] : 1.0;
     }
     if (T->nkeys == 0) return C[i];
@@ -55,6 +60,7 @@ static int32_t pick(table_t *T, const int64_t *off, const int32_t *idx, const fl
             best_w = v;
         }
         T->val[c] = 0.0;
+        T->seen[c] = 0;
     }
     return best;
 }
@@ -81,7 +87,8 @@ int64_t cpu_lpa_run(int64_t n, const int64_t *off, const int32_t *idx, const flo
         const int t = omp_get_thread_num();
         T[t].keys = (int32_t *)malloc((size_t)(n > 0 ? n : 1) * 4);
         T[t].val = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
-        if (!T[t].keys || !T[t].val) {
+        T[t].seen = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+        if (!T[t].keys || !T[t].val || !T[t].seen) {
 #pragma omp atomic write
             fail = 1;
         }
@@ -128,12 +135,13 @@ int64_t cpu_lpa_run(int64_t n, const int64_t *off, const int32_t *idx, const flo
             }
             if (changed_hist) changed_hist[it] = dN;
             ++it;
-            if ((double)dN / (double)n <= tau) break;
+            if ((double)dN <= floor(tau * (double)n)) break;    /* dN <= floor(tau N), product in fp64 */
         }
     }
     for (int t = 0; t < nt; ++t) {
         free(T[t].keys);
         free(T[t].val);
+        free(T[t].seen);
     }
     free(T);
     free(flag);

@@ -191,6 +191,15 @@ const char *lpa_status_string(lpa_status st);
 /* Reason for the last non-OK status returned on this thread ("" if none). */
 const char *lpa_last_error(void);
 
+/* The tolerance test of Algorithm 1 (Section 4.1.3), dN / N <= tolerance,
+ * as the integer every run compares dN against: a sweep of a graph with n
+ * vertices meets the tolerance when dN <= *out = floor(tolerance * n), the
+ * product rounded once to fp64 (for decimal tolerances such as 0.05 and
+ * n < 2^31 this equals the exact floor of the decimal times n).  Host only:
+ * needs no GPU.  LPA_ERR_INVALID_ARG unless 0 <= tolerance <= 1,
+ * 0 <= n <= 2^31 - 1 and out != NULL. */
+lpa_status lpa_tolerance_threshold(double tolerance, int64_t n, int64_t *out);
+
 /* ---------------------------------------------------------------- graphs */
 
 /* Build a graph handle from CSR (Section 3: undirected, w_ij = w_ji).
@@ -235,7 +244,8 @@ lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config *cfg);
  * dN/N <= tolerance (Section 4.1.3; the paper uses 0.05) or max_iters sweeps
  * (Section 4.1.2; the paper uses 20).
  *   mode        lpa_mode
- *   tolerance   in [0, 1]
+ *   tolerance   in [0, 1]; a sweep meets it when dN <= floor(tolerance * N)
+ *               (lpa_tolerance_threshold)
  *   max_iters   in [0, 1 << 20]
  *   labels_out  device int32[n], caller-owned; receives C
  *   info        host pointer or NULL.  When non-NULL the call waits for the
@@ -243,13 +253,13 @@ lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config *cfg);
  *               work on `stream` and returns.
  * The whole loop runs on the device (a CUDA graph with a device-side loop
  * condition): no host round trip per sweep. */
-lpa_status lpa_run(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters,
+lpa_status lpa_run(lpa_graph_t g, lpa_mode mode, double tolerance, int32_t max_iters,
                    int32_t *labels_out, void *stream, lpa_run_info *info);
 
 /* Same result as lpa_run, but every launch is issued from the host and timed
  * with CUDA events; per-phase times and per-bin counts go to *prof (host).
  * Blocks until done.  For profiling only: slower than lpa_run. */
-lpa_status lpa_run_profiled(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters,
+lpa_status lpa_run_profiled(lpa_graph_t g, lpa_mode mode, double tolerance, int32_t max_iters,
                             int32_t *labels_out, void *stream, lpa_run_info *info, lpa_profile *prof);
 
 /* Modularity Q of a labelling (Eq. 1, Section 3.2, community form):
@@ -266,7 +276,7 @@ lpa_status lpa_modularity(lpa_graph_t g, const int32_t *labels, double *q_out, v
  * given tolerance and cap, best time kept).  Applies the winner to the handle
  * and copies it to *chosen (host, nullable).  Synchronous; the graph's labels
  * scratch is used, no caller buffer is touched. */
-lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters,
+lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, double tolerance, int32_t max_iters,
                         int32_t trials, void *stream, lpa_config *chosen);
 
 /* Modularity of a labelling, as lpa_modularity, for callers that cannot let
@@ -274,15 +284,16 @@ lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t m
  * arrays (same rules as lpa_graph_create; not validated here) and the working
  * memory is a fixed array inside the library, sized for at most 1,048,576
  * vertices (larger n returns LPA_ERR_INVALID_ARG).  The paper has no
- * counterpart to this entry point; it exists for code that runs where
- * cudaMalloc is not available to it (a host framework's memory pool, a
- * latency-critical loop, an ongoing stream capture).
+ * counterpart to this entry point; it exists for code that may not call
+ * cudaMalloc: a plugin whose host framework owns all device memory through
+ * its own pool, or a latency-critical loop that cannot afford an allocation.
  *   n, nnz, offsets, indices, weights   device CSR (weights NULL = unit)
  *   labels   device int32[n], each in [0, n)
  *   q_out    host double; the call synchronises `stream` before returning.
- * Allocates nothing.  The first call on each device looks up the array's
- * device address; make it before any stream capture.  Every call uses the
- * same array: calls that run concurrently on the GPU race. */
+ * Allocates nothing.  The first call on each device (and again after that
+ * device's context is recreated) looks up the array's device address; make
+ * it before any stream capture.  Every call uses the same array and clears
+ * what must start at zero: calls that run concurrently on the GPU race. */
 lpa_status lpa_modularity_noalloc(int64_t n, int64_t nnz, const int64_t *offsets, const int32_t *indices,
                                   const float *weights, const int32_t *labels, double *q_out, void *stream);
 
@@ -315,7 +326,7 @@ lpa_status lpa_batch_props_get(lpa_batch_t b, lpa_graph_props *out);
  * scanned[], edges_touched) are kept for the whole batch only and stay 0 in
  * the per-graph infos when G > 1 (lpa_batch_props_get reports the batch's
  * scanned_total). */
-lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, float tolerance, int32_t max_iters,
+lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, double tolerance, int32_t max_iters,
                          int32_t *labels_out, void *stream, lpa_run_info *infos);
 
 /* Modularity of graph g of the batch for LOCAL labels (device int32[n_g]). */
@@ -339,7 +350,7 @@ typedef struct {
     int64_t arena_entries;      /* CSR entry capacity of the shared arena (>= 1) */
     int32_t max_slots;          /* requests in the arena at once (>= 2) */
     int32_t mode;               /* lpa_mode; LPA_MODE_SYNC_FULL is run as LPA_MODE_SYNC */
-    float   tolerance;          /* in [0, 1] */
+    double  tolerance;          /* in [0, 1] */
     int32_t max_iters;          /* in [0, 1 << 20] */
     int64_t solo_min_entries;   /* requests with at least this many entries use the solo lane; 0 = never */
 } lpa_serve_config;

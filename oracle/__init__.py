@@ -16,6 +16,8 @@ Functions and the passages they follow:
   lpa_async_ex(...)    the same with options, among them the pruning rule of
                        FLPA (Section 2), and the vertices scanned per sweep.
   modularity(...)      Eq. 1 (Section 3.2), community form, fp64.
+  converged(...)       the tolerance test dN / N <= tau of Algorithm 1
+                       (Section 4.1.3), decided exactly.
   count_labels_outside_component / count_not_local_max: output checkers.
 
 Parity status: pick, lpa_sync, lpa_async and modularity are pinned by the
@@ -46,7 +48,7 @@ def build(force: bool = False) -> str:
     """Compile lpa_oracle.c into liblpa_oracle.so next to it (gcc -O2)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -54,7 +56,7 @@ def build(force: bool = False) -> str:
 def _bind(lib):
     for name in ("oracle_lpa_sync", "oracle_lpa_async", "oracle_lpa_async_order", "oracle_lpa_sync_nonstrict",
                  "oracle_lpa_async_nonstrict", "oracle_lpa_async_ex", "oracle_sync_sweep",
-                 "oracle_count_labels_outside_component", "oracle_count_not_local_max"):
+                 "oracle_count_labels_outside_component", "oracle_count_not_local_max", "oracle_converged"):
         getattr(lib, name).restype = _i64
     lib.oracle_pick.restype = ctypes.c_int32
     lib.oracle_pick_nonstrict.restype = ctypes.c_int32
@@ -81,7 +83,7 @@ def load_variant(so_path):
 
     v = _Variant()
     for name in ("pick", "sync_sweep", "lpa_sync", "lpa_async", "lpa_async_ex", "modularity",
-                 "count_labels_outside_component", "count_not_local_max"):
+                 "count_labels_outside_component", "count_not_local_max", "converged"):
         fn = globals()[name]
         setattr(v, name, (lambda f: (lambda *a, **k: f(*a, _lib_override=lib, **k)))(fn))
     return v
@@ -103,6 +105,13 @@ def _check(ret, what):
     if ret < 0:
         raise ValueError(f"oracle {what} rejected its input (code {ret})")
     return ret
+
+
+def converged(dN, n, tau, _lib_override=None) -> bool:
+    """The tolerance test of Algorithm 1 (Section 4.1.3), dN / N <= tau,
+    decided exactly for the binary64 value of tau."""
+    lib = _lib_override or _load()
+    return bool(_check(lib.oracle_converged(_i64(int(dN)), _i64(int(n)), ctypes.c_double(float(tau))), "converged"))
 
 
 def pick(off, idx, w, C, i, sweep=None, _lib_override=None) -> int:

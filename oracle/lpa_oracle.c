@@ -49,6 +49,7 @@
  *
  * Every function returns a negative value on invalid input and never aborts.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -200,9 +201,22 @@ static int check_csr(int64_t n, const int64_t *off, const int32_t *idx) {
     return 0;
 }
 
-/* Convergence test of Algorithm 1: dN / N <= tau, in fp64. */
+/* Convergence test of Algorithm 1: dN / N <= tau, read as the integer test
+ * dN <= floor(tau * N) with the product tau * N rounded once to fp64.  For
+ * the tolerances one writes as decimals (0.05, 0.1, 1e-5 ...) and N < 2^31
+ * this threshold is floor of the exact decimal tau times N: the fp64 error
+ * of tau * N (a few 1e-9 at most) never crosses an integer that the exact
+ * product does not reach.  A threshold is one integer per graph, so every
+ * implementation that forms it the same way stops after the same sweep. */
 static int converged(int64_t dN, int64_t n, double tau) {
-    return (double)dN / (double)n <= tau;
+    const double thr = floor(tau * (double)n);
+    return (double)dN <= thr;
+}
+
+/* The tolerance test above as an entry point (1: dN / N <= tau). */
+int64_t oracle_converged(int64_t dN, int64_t n, double tau) {
+    if (dN < 0 || n < 0 || !(tau >= 0.0)) return ORACLE_BAD_ARG;
+    return converged(dN, n, tau);
 }
 
 /* One label for vertex i given labels C (Eq. 2 with the strict tie-break). */

@@ -100,7 +100,7 @@ class LpaProfile(ctypes.Structure):
 class LpaServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("arena_vertices", ctypes.c_int64),
                 ("arena_entries", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("tolerance", ctypes.c_float), ("max_iters", ctypes.c_int32),
+                ("tolerance", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("solo_min_entries", ctypes.c_int64)]
 
 
@@ -128,7 +128,7 @@ _V = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int32
 _U32 = ctypes.c_uint32
-_F = ctypes.c_float
+_D = ctypes.c_double
 _P = ctypes.POINTER
 
 _SIGS = {
@@ -141,15 +141,16 @@ _SIGS = {
     "lpa_graph_props_get": ([_V, _P(LpaGraphProps)], ctypes.c_int),
     "lpa_graph_get_config": ([_V, _P(LpaConfig)], ctypes.c_int),
     "lpa_graph_set_config": ([_V, _P(LpaConfig)], ctypes.c_int),
-    "lpa_run": ([_V, ctypes.c_int, _F, _I32, _V, _V, _P(LpaRunInfo)], ctypes.c_int),
-    "lpa_run_profiled": ([_V, ctypes.c_int, _F, _I32, _V, _V, _P(LpaRunInfo), _P(LpaProfile)], ctypes.c_int),
+    "lpa_tolerance_threshold": ([_D, _I64, _P(_I64)], ctypes.c_int),
+    "lpa_run": ([_V, ctypes.c_int, _D, _I32, _V, _V, _P(LpaRunInfo)], ctypes.c_int),
+    "lpa_run_profiled": ([_V, ctypes.c_int, _D, _I32, _V, _V, _P(LpaRunInfo), _P(LpaProfile)], ctypes.c_int),
     "lpa_modularity": ([_V, _V, _P(ctypes.c_double), _V], ctypes.c_int),
     "lpa_modularity_noalloc": ([_I64, _I64, _V, _V, _V, _V, _P(ctypes.c_double), _V], ctypes.c_int),
-    "lpa_autotune": ([_V, ctypes.c_int, _F, _I32, _I32, _V, _P(LpaConfig)], ctypes.c_int),
+    "lpa_autotune": ([_V, ctypes.c_int, _D, _I32, _I32, _V, _P(LpaConfig)], ctypes.c_int),
     "lpa_batch_create": ([_I32, _V, _V, _V, _V, _V, _U32, _V, _P(_V)], ctypes.c_int),
     "lpa_batch_destroy": ([_V], ctypes.c_int),
     "lpa_batch_props_get": ([_V, _P(LpaGraphProps)], ctypes.c_int),
-    "lpa_batch_run": ([_V, ctypes.c_int, _F, _I32, _V, _V, _P(LpaRunInfo)], ctypes.c_int),
+    "lpa_batch_run": ([_V, ctypes.c_int, _D, _I32, _V, _V, _P(LpaRunInfo)], ctypes.c_int),
     "lpa_batch_modularity": ([_V, _I32, _V, _P(ctypes.c_double), _V], ctypes.c_int),
     "lpa_serve_create": ([_P(LpaServeConfig), _P(_V)], ctypes.c_int),
     "lpa_serve_submit": ([_V, _I64, _I64, _V, _V, _V, _P(ctypes.c_uint64)], ctypes.c_int),
@@ -225,6 +226,14 @@ def lpa_status_string(st: int) -> str:
 
 def lpa_last_error() -> str:
     return load().lpa_last_error().decode()
+
+
+def lpa_tolerance_threshold(tolerance, n) -> int:
+    """floor(tolerance * n) as the runs compute it: the largest dN that meets
+    the tolerance test of Algorithm 1 on an n-vertex graph (no GPU needed)."""
+    out = _I64()
+    _check(load().lpa_tolerance_threshold(float(tolerance), int(n), ctypes.byref(out)))
+    return out.value
 
 
 def lpa_graph_create(n, nnz, offsets, indices, weights=None, flags=LPA_HOST_PTRS, stream=None):

@@ -559,12 +559,12 @@ void split_mode(int& mode, int& nonstrict, int& prune_other) {
     if (nonstrict && mode == MODE_SYNC) mode = MODE_SYNC_FULL;
 }
 
-lpa_status check_run_args(const Engine& E, int mode, int prune_other, float tol, int32_t max_iters,
+lpa_status check_run_args(const Engine& E, int mode, int prune_other, double tol, int32_t max_iters,
                           const int32_t* labels_out) {
     if (mode < 0 || mode > 2) return fail(LPA_ERR_INVALID_ARG, "unknown mode %d", mode);
     if (prune_other && mode != MODE_ASYNC)
         return fail(LPA_ERR_INVALID_ARG, "LPA_PRUNE_OTHER needs LPA_MODE_ASYNC");
-    if (!(tol >= 0.f && tol <= 1.f)) return fail(LPA_ERR_INVALID_ARG, "tolerance must be in [0, 1]");
+    if (!(tol >= 0.0 && tol <= 1.0)) return fail(LPA_ERR_INVALID_ARG, "tolerance must be in [0, 1]");
     if (max_iters < 0 || max_iters > (1 << 20)) return fail(LPA_ERR_INVALID_ARG, "max_iters must be in [0, 2^20]");
     if (E.s.N > 0 && !labels_out) return fail(LPA_ERR_INVALID_ARG, "labels_out is NULL");
     return LPA_OK;
@@ -599,7 +599,7 @@ lpa_status collect_info(Engine& E, cudaStream_t st, lpa_run_info* infos, int32_t
     return LPA_OK;
 }
 
-lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t* labels_out, cudaStream_t st,
+lpa_status engine_run(Engine& E, int mode, double tol, int32_t max_iters, int32_t* labels_out, cudaStream_t st,
                       lpa_run_info* infos, int local_ids) {
     int ns = 0, po = 0;
     split_mode(mode, ns, po);
@@ -614,7 +614,7 @@ lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t
     }
     const int lm = mode | (ns ? kModeNonstrict : 0);
     if ((rs = build_graph(E, lm)) != LPA_OK) return rs;
-    LPA_CUDA(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, ns, po, labels_out, local_ids, st));
+    LPA_CUDA(launch_set_params(E.s.ctrl, tol, max_iters, mode, ns, po, labels_out, local_ids, st));
     LPA_CUDA(cudaGraphLaunch(E.exec[graph_index(lm)], st));
     ++E.runs_total;
     if (infos) return collect_info(E, st, infos, E.s.G);
@@ -622,7 +622,7 @@ lpa_status engine_run(Engine& E, int mode, float tol, int32_t max_iters, int32_t
 }
 
 // Host-driven run with an event pair around every launch.
-lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters, int32_t* labels_out,
+lpa_status engine_run_profiled(Engine& E, int mode, double tol, int32_t max_iters, int32_t* labels_out,
                                cudaStream_t st, lpa_run_info* infos, lpa_profile* prof, int local_ids) {
     const int mode_arg = mode;
     int ns = 0, po = 0;
@@ -648,7 +648,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, float tol, int32_t max_iters
             return cuda_fail(err, #call);    \
         }                                    \
     } while (0)
-    LPA_P(launch_set_params(E.s.ctrl, (double)tol, max_iters, mode, ns, po, labels_out, local_ids, st));
+    LPA_P(launch_set_params(E.s.ctrl, tol, max_iters, mode, ns, po, labels_out, local_ids, st));
     LPA_P(cudaEventRecord(ev[0], st));
     LPA_P(launch_init(E.s, st, E.sms));
     LPA_P(launch_init_cond(E.s, none, 0, st));
@@ -786,6 +786,14 @@ const char* lpa_status_string(lpa_status st) {
 
 const char* lpa_last_error(void) { return g_last_error.c_str(); }
 
+lpa_status lpa_tolerance_threshold(double tolerance, int64_t n, int64_t* out) {
+    if (!out) return fail(LPA_ERR_INVALID_ARG, "out is NULL");
+    if (!(tolerance >= 0.0 && tolerance <= 1.0)) return fail(LPA_ERR_INVALID_ARG, "tolerance must be in [0, 1]");
+    if (n < 0 || n > 0x7fffffffLL) return fail(LPA_ERR_INVALID_ARG, "n out of range [0, 2^31-1]");
+    *out = (int64_t)dn_threshold(tolerance, n);
+    return LPA_OK;
+}
+
 lpa_status lpa_graph_create(int64_t n, int64_t nnz, const int64_t* offsets, const int32_t* indices,
                             const float* weights, uint32_t flags, void* stream, lpa_graph_t* out) {
     g_last_error.clear();
@@ -840,13 +848,13 @@ lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config* cfg) {
     return set_config(g->e, cfg);
 }
 
-lpa_status lpa_run(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters, int32_t* labels_out,
+lpa_status lpa_run(lpa_graph_t g, lpa_mode mode, double tolerance, int32_t max_iters, int32_t* labels_out,
                    void* stream, lpa_run_info* info) {
     if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
     return engine_run(g->e, (int)mode, tolerance, max_iters, labels_out, static_cast<cudaStream_t>(stream), info, 0);
 }
 
-lpa_status lpa_run_profiled(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters, int32_t* labels_out,
+lpa_status lpa_run_profiled(lpa_graph_t g, lpa_mode mode, double tolerance, int32_t max_iters, int32_t* labels_out,
                             void* stream, lpa_run_info* info, lpa_profile* prof) {
     if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
     return engine_run_profiled(g->e, (int)mode, tolerance, max_iters, labels_out, static_cast<cudaStream_t>(stream),
@@ -858,7 +866,7 @@ lpa_status lpa_modularity(lpa_graph_t g, const int32_t* labels, double* q_out, v
     return engine_modularity(g->e, 0, g->e.s.N, labels, q_out, static_cast<cudaStream_t>(stream));
 }
 
-lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, float tolerance, int32_t max_iters, int32_t trials,
+lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, double tolerance, int32_t max_iters, int32_t trials,
                         void* stream, lpa_config* chosen) {
     if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
     if (trials < 1 || trials > 100) return fail(LPA_ERR_INVALID_ARG, "trials must be in [1, 100]");
@@ -969,7 +977,7 @@ lpa_status lpa_batch_props_get(lpa_batch_t b, lpa_graph_props* out) {
     return fill_props(b->e, out);
 }
 
-lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, float tolerance, int32_t max_iters, int32_t* labels_out,
+lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, double tolerance, int32_t max_iters, int32_t* labels_out,
                          void* stream, lpa_run_info* infos) {
     if (!b) return fail(LPA_ERR_INVALID_ARG, "batch is NULL");
     return engine_run(b->e, (int)mode, tolerance, max_iters, labels_out, static_cast<cudaStream_t>(stream), infos,

@@ -1,9 +1,11 @@
 // lpa_device.cuh -- device helpers shared by the sweep kernels.
 //
-// Weight sums: for graphs whose weights are integers (or unit) the per-label
-// sums K_{i->c} are accumulated in uint32 (exact, any order, as long as every
-// weighted degree is < 2^24 -- checked at graph creation).  Otherwise they
-// are accumulated in fp32.
+// Weight sums: for graphs whose weights are integers (or unit) in the
+// library's own copy, the per-label sums K_{i->c} are accumulated in uint32
+// (exact in any order while every weighted degree is < 2^31, checked at graph
+// creation).  Otherwise (non-integer or borrowed weights) they are
+// accumulated in fp32, exact for integer weights while every weighted degree
+// is < 2^24.
 //
 // Argmax with the strict tie-break (Section 4.1.5: smallest label id among the
 // most weighted): a candidate is encoded as key = sum + 1 (uint32; 0 means "no

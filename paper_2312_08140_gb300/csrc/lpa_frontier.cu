@@ -422,7 +422,7 @@ __device__ void control_step(const DevState& s, int mode, int role, int dense_ne
                 if (it <= kMaxHist) s.hist_changed[g * kMaxHist + it - 1] = (long long)dn;
                 s.iters[g] = it;
                 const int64_t ng = s.g_end[g] - s.g_begin[g];
-                if ((double)dn / (double)ng <= tau) {            // Algorithm 1: dN / N <= tau
+                if ((long long)dn <= dn_threshold(tau, ng)) {     // Algorithm 1: dN / N <= tau
                     s.done[g] = 1;
                     s.exit_reason[g] = 0;
                 } else if (it >= max_iters) {

@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace lpa {
@@ -30,6 +31,14 @@ constexpr int kSliceMinParts = 2;       // every overflowing row (>= 2 partition
 constexpr int kLargeSlots = 8192;       // shared table of the last bin (overflowing rows are
                                         // rescanned split over label partitions)
 constexpr int32_t kEmptyKey = -1;       // free slot in label tables; labels are >= 0
+
+// Tolerance test of Algorithm 1 (Section 4.1.3), dN / N <= tau, as one
+// integer threshold per graph: a sweep with dN <= floor(tau * N) meets it,
+// the product rounded once to fp64.  IEEE round-to-nearest multiplication
+// gives the same threshold on the host and on the device.
+__host__ __device__ inline long long dn_threshold(double tau, long long n) {
+    return (long long)floor(tau * (double)n);
+}
 
 // Weight storage: none (unit weights), integer weights as uint32 or, when all
 // are at most 255, as uint8 (sums are uint32 in both), or float.

@@ -493,7 +493,7 @@ lpa_status lpa_serve_create(const lpa_serve_config* cfg, lpa_server_t* out) {
         return err(LPA_ERR_INVALID_ARG, "arena_vertices and arena_entries must be >= 1, max_slots >= 2");
     if (cfg->arena_vertices > 0x7fffffffLL) return err(LPA_ERR_INVALID_ARG, "arena_vertices above 2^31-1");
     if (cfg->mode < 0 || cfg->mode > 2) return err(LPA_ERR_INVALID_ARG, "unknown mode");
-    if (!(cfg->tolerance >= 0.f && cfg->tolerance <= 1.f)) return err(LPA_ERR_INVALID_ARG, "tolerance must be in [0, 1]");
+    if (!(cfg->tolerance >= 0.0 && cfg->tolerance <= 1.0)) return err(LPA_ERR_INVALID_ARG, "tolerance must be in [0, 1]");
     if (cfg->max_iters < 0 || cfg->max_iters > (1 << 20)) return err(LPA_ERR_INVALID_ARG, "max_iters out of range");
     lpa_server* S = new (std::nothrow) lpa_server();
     if (!S) return err(LPA_ERR_OUT_OF_MEMORY, "host allocation");
@@ -568,7 +568,7 @@ lpa_status lpa_serve_create(const lpa_serve_config* cfg, lpa_server_t* out) {
         s.bin_static_entries[b] = 0;
     }
     s.active_entries = S->E;
-    k_ctrl_init<<<1, 1>>>(s.ctrl, (double)cfg->tolerance, cfg->max_iters,
+    k_ctrl_init<<<1, 1>>>(s.ctrl, cfg->tolerance, cfg->max_iters,
                           cfg->mode == LPA_MODE_ASYNC ? MODE_ASYNC : MODE_SYNC);
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(err(LPA_ERR_CUDA, "control initialisation failed"));
     if (cudaMallocHost(&S->h_done, G * 4) != cudaSuccess) return bail(err(LPA_ERR_OUT_OF_MEMORY, "pinned buffer"));

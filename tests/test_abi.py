@@ -65,6 +65,40 @@ def test_pure_host_entry_points(lib_path):
         lpa._mode("async+bogus")
 
 
+def test_tolerance_threshold_is_one_integer_on_both_sides(lib_path):
+    """The tolerance test of Algorithm 1 (Section 4.1.3), dN / N <= tau, is
+    one integer threshold per graph, floor(tau * N): the library's helper
+    (the same inline function the device's loop control calls) equals the
+    exact floor of the decimal tolerance times N and agrees with the oracle's
+    test on both sides of it.  At N = 100,000,019 and tau = 0.05 (0.05 N =
+    5,000,000.95) dN = 5,000,001 must not stop a run; the fp32 value of 0.05
+    would have stopped it."""
+    from fractions import Fraction
+
+    import numpy as np
+
+    import oracle as O
+    import paper_2312_08140_gb300 as lpa
+    lpa.load(lib_path)
+    n = 100_000_019
+    assert lpa.lpa_tolerance_threshold(0.05, n) == 5_000_000
+    assert O.converged(5_000_000, n, 0.05) and not O.converged(5_000_001, n, 0.05)
+    assert int(np.floor(float(np.float32(0.05)) * n)) == 5_000_001
+    assert lpa.lpa_tolerance_threshold(0.0, 12) == 0 and lpa.lpa_tolerance_threshold(1.0, 12) == 12
+    assert lpa.lpa_tolerance_threshold(0.05, 0) == 0
+    rng = np.random.default_rng(12)
+    for text in ("0.05", "0.1", "0.01", "0.00001", "0.3"):
+        tau = float(text)
+        for N in [1, 19, 20, 21, 2**31 - 1] + rng.integers(1, 2**31 - 1, size=300).tolist():
+            thr = lpa.lpa_tolerance_threshold(tau, int(N))
+            assert thr == int(Fraction(text) * int(N)), (text, N)
+            assert O.converged(thr, int(N), tau) and (thr + 1 > N or not O.converged(thr + 1, int(N), tau))
+    for bad in ((-0.1, 5), (1.5, 5), (float("nan"), 5), (0.05, -1), (0.05, 2**31)):
+        with pytest.raises(lpa.LpaError) as e:
+            lpa.lpa_tolerance_threshold(*bad)
+        assert e.value.status == lpa.LPA_ERR_INVALID_ARG
+
+
 def test_struct_layouts_match_c(lib_path):
     import paper_2312_08140_gb300 as lpa
     H = lpa.LPA_MAX_RECORDED_ITERS

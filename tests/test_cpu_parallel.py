@@ -45,3 +45,20 @@ def test_async_on_one_thread_is_the_serial_ascending_run():
         ref, it, ch = O.lpa_async(g.off, g.idx, g.w)
         got, it2, ch2 = CP.run(g.off, g.idx, g.w, "async", n_threads=1)
         assert np.array_equal(got, ref) and it2 == it and ch2.tolist() == ch.tolist(), g.n
+
+
+def test_zero_weight_label_repeated_more_than_n_times():
+    """A row that lists a zero-weight neighbour many times over (more entries
+    than the graph has vertices) lists its label once in the per-thread key
+    list: the run equals the oracle's and writes nothing out of bounds."""
+    n = 3
+    rows = [[1] * 40 + [2], [0] * 40, [0]]
+    wts = [[0.0] * 40 + [1.0], [0.0] * 40, [1.0]]
+    off = np.zeros(n + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(r) for r in rows])
+    idx = np.array([j for r in rows for j in r], dtype=np.int32)
+    w = np.array([x for r in wts for x in r], dtype=np.float32)
+    for mode, ref_fn in (("sync", O.lpa_sync), ("async", O.lpa_async)):
+        ref, it, ch = ref_fn(off, idx, w)
+        got, it2, ch2 = CP.run(off, idx, w, mode, n_threads=1)
+        assert np.array_equal(got, ref) and it2 == it and ch2.tolist() == ch.tolist(), mode

@@ -13,6 +13,8 @@ import json
 import os
 import subprocess
 
+from fractions import Fraction
+
 import numpy as np
 import pytest
 
@@ -118,7 +120,7 @@ def test_sync_run_is_iterated_sweeps():
                 Cn = np.array([_enumerated_pick(g, C, i) for i in range(g.n)], dtype=np.int32)
                 hist.append(int(np.sum(Cn != C)))
                 C = Cn
-                if hist[-1] / g.n <= tau:
+                if Fraction(hist[-1]) <= Fraction(str(tau)) * g.n:
                     break
             Co, it, ho = O.lpa_sync(g.off, g.idx, g.w, tau=tau, max_iters=cap)
             assert Co.tolist() == C.tolist() and it == len(hist) and ho.tolist() == hist
@@ -148,7 +150,7 @@ def _serial_async_restated(g, tau, cap, order=None, prune_other=False):
                         if j != i and not (prune_other and C[j] == c):
                             pending.add(j)
         hist.append(dN)
-        if dN / n <= tau:
+        if Fraction(dN) <= Fraction(str(tau)) * n:
             break
     return C, len(hist), hist
 
@@ -330,7 +332,9 @@ def test_planted_partition_true_blocks_modularity():
 MUTANTS = {
     "self_loops_counted": ("if ((int64_t)j == i) continue;            /* self-loops are skipped */", ""),
     "tie_to_largest": ("(v == best_w && c < best)", "(v == best_w && c > best)"),
-    "strict_tolerance": ("return (double)dN / (double)n <= tau;", "return (double)dN / (double)n < tau;"),
+    "strict_tolerance": ("return (double)dN <= thr;", "return (double)dN < thr;"),
+    "tolerance_in_fp32": ("floor(tau * (double)n)", "floor((double)(float)tau * (double)n)"),
+    "tolerance_rounded_up": ("floor(tau * (double)n)", "ceil(tau * (double)n)"),
     "unit_weights_ignored": ("return w ? (double)w[e] : 1.0;", "return 1.0;"),
     "sync_reads_in_place": ("C_out[i] = pick_t(&H, n, off, idx, w, prev, i, nonstrict ? it + 1 : 0);",
                             "C_out[i] = pick_t(&H, n, off, idx, w, C_out, i, nonstrict ? it + 1 : 0);"),
@@ -418,6 +422,32 @@ def _flpa_pins_pass(mod):
     return True
 
 
+def _tolerance_pins_pass(mod):
+    """The tolerance test of Algorithm 1 (Section 4.1.3), dN / N <= tau,
+    against exact rational arithmetic on the decimal tolerance as written
+    (Fraction("0.05") is exactly 1/20): random N below 2^31 and dN on both
+    sides of the threshold for the paper's 0.05 and the sweep's 0.1, 0.01,
+    1e-5; the paper's 0.05 at N = 100,000,019 (0.05 N = 5,000,000.95: dN =
+    5,000,000 stops, 5,000,001 does not -- the fp32 value of 0.05 would stop
+    there); and the ends tau = 0 and tau = 1 (inclusive)."""
+    from fractions import Fraction
+    n = 100_000_019
+    if not mod.converged(5_000_000, n, 0.05) or mod.converged(5_000_001, n, 0.05):
+        return False
+    if not mod.converged(0, 7, 0.0) or mod.converged(1, 7, 0.0) or not mod.converged(7, 7, 1.0):
+        return False
+    rng = np.random.default_rng(4)
+    for text in ("0.05", "0.1", "0.01", "0.00001", "0.25", "0.3"):
+        tau_q, tau = Fraction(text), float(text)
+        for _ in range(500):
+            N = int(rng.integers(1, 2**31 - 1))
+            base = int(tau_q * N)                     # floor(tau N), exact
+            for dN in (base - 1, base, base + 1):
+                if 0 <= dN <= N and mod.converged(dN, N, tau) != (dN <= tau_q * N):
+                    return False
+    return True
+
+
 def _pins_pass(mod):
     try:
         for case in _golden_cases():
@@ -440,6 +470,8 @@ def _pins_pass(mod):
         if not _flpa_pins_pass(mod):
             return False
         if not _checker_pins_pass(mod):
+            return False
+        if not _tolerance_pins_pass(mod):
             return False
         pairs = [(u, v) for u in range(5) for v in range(u + 1, 5)]
         pairs += [(u + 5, v + 5) for u, v in pairs] + [(4, 5)]
@@ -466,7 +498,7 @@ def test_planted_mistake_is_caught(name, tmp_path):
     path = tmp_path / "mutant.c"
     path.write_text(src.replace(old, new))
     so = tmp_path / f"lib_{name}.so"
-    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(path)])
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-o", str(so), str(path), "-lm"])
     assert not _pins_pass(O.load_variant(str(so)))
 
 

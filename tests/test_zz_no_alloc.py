@@ -1,8 +1,8 @@
 """lpa_modularity_noalloc: the entry point for callers that may not allocate
-device memory (a host framework that owns the device memory pool, a
-latency-critical loop, code running during a stream capture).  It must give
-the same modularity as lpa_modularity on a graph handle, call after call, even
-though every call reuses the same fixed working array inside the library.
+device memory (a plugin whose host framework owns the device memory pool, a
+latency-critical loop).  It must give the same modularity as lpa_modularity
+on a graph handle and as the fp64 oracle, call after call, even though every
+call reuses the same fixed working array inside the library.
 
 Collected last on purpose: if it fails, a run that stops at the first failure
 has already run every other test."""
@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import lpa_inputs as L
+import oracle as O
 
 pytestmark = pytest.mark.gpu
 
@@ -35,9 +36,11 @@ def test_noalloc_modularity_matches_handle_entry_point():
             off_d, idx_d, w_d = _device(g.off), _device(g.idx), _device(g.w)
             for labels in (run_labels, rand_labels):
                 q_ref = lpa.lpa_modularity(h, labels)
+                q_oracle = O.modularity(g.off, g.idx, g.w, labels.cpu().numpy())
                 for _ in range(2):                       # two calls in a row share the array
                     q = lpa.lpa_modularity_noalloc(g.n, g.nnz, off_d, idx_d, w_d, labels)
                     assert abs(q - q_ref) <= 1e-6 * max(1.0, abs(q_ref)), (q, q_ref)
+                    assert abs(q - q_oracle) <= 1e-6 * max(1.0, abs(q_oracle)), (q, q_oracle)
         finally:
             lpa.lpa_graph_destroy(h)
 
