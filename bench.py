@@ -1,30 +1,40 @@
 #!/usr/bin/env python3
 """Label propagation throughput on one GB300 (or N replicas under torchrun).
 
-Workload (default "rmat22+grid4096"): R-MAT scale 22, edge factor 16,
-(a,b,c,d) = (.57,.19,.19,.05), symmetrised, de-duplicated, self-loops removed,
-unit weights; and a 4096 x 4096 4-neighbour lattice with 10% of edges dropped,
-0.1% random shortcuts and integer weights 1..8.  One step = four runs of the
-whole hot path (initialisation, sweeps with pruning until dN/N <= 0.05 or 20
-sweeps, labels out): each graph in the synchronous and the asynchronous mode.
+Headline workload (default "rmat27"): the paper-scale single graph, R-MAT
+scale 27 with edge factor 14, (a,b,c,d) = (.57,.19,.19,.05), symmetrised,
+de-duplicated, self-loops removed, unit weights, int64 offsets (134,217,728
+vertices, ~3.7e9 stored entries), drawn on the device and handed to the
+library as host CSR.  One step = one run of the whole hot path in the
+paper's asynchronous mode with vertex pruning (initialisation, sweeps until
+dN/N <= 0.05 or 20 sweeps, labels out).
 
 Metric: LPA edges/s = sum over runs of nnz x sweeps / time.  Every rank runs
 the same workload on its own GPU (replicas, no collective on the data path);
 value = all ranks' edges / the slowest rank's time.
 
-Also reported:
+Also reported on the same line:
   e2e          the same metric through the public C ABI from pinned host
-               buffers: graph creation (H2D copy + validation), both runs,
-               labels copied back, all inside the timed region;
+               buffers: graph creation (H2D copy + validation), the run and
+               the labels copied back, all inside the timed region;
   roofline     algorithmic bytes of the dominant kernel per launch / its mean
                launch time, from CUDA events around every launch of the
-               profiled run path, against the measured HBM copy bandwidth;
-  cpu_baseline the single-threaded CPU oracle on a bounded sample;
-  cpu_parallel the paper's own multi-core CPU design on the host cores;
+               profiled run path, against the measured HBM copy bandwidth
+               (and the same for all sweep kernels together);
+  cpu_baseline the single-threaded CPU oracle on a bounded sample of the
+               same graph: its first serial sweep over a contiguous range of
+               rows (lpa_inputs.row_range_sample);
+  extras       R-MAT 22 + the road-like 4096^2 grid in both modes, with the
+               paper's multi-core CPU design on the host cores and the
+               tolerance / iteration-cap sweep (Sections 4.1.2-4.1.3);
+  batched      the 4,096-graph planted-partition batch in one device loop
+               against one lpa_run per graph;
+  serving      continuous batching at 2,000 req/s with an R-MAT scale 24
+               request every 500, against an unbatched FIFO;
   clocks       nvidia-smi samples taken during the timed region.
 
 --impl reference times the CPU oracle (the reference arm of this method) on
-the same workload: each step is one oracle sweep of one (graph, mode) pair.
+the same workload: each step is one oracle sweep over a bounded sample.
 """
 import argparse
 import json
@@ -43,7 +53,9 @@ UNIT = "edges/s"
 TAU = 0.05
 MAX_ITERS = 20
 MODES = ("sync", "async")
-BIN_KERNELS = ("k_sweep_small", "k_sweep_warp", "k_sweep_block128", "k_sweep_block256", "k_sweep_block512")
+# the sweep kernel of each degree bin (the low-degree bin's asynchronous
+# passes run k_sweep_small_async)
+BIN_KERNELS = ("k_sweep_small", "k_sweep_warp", "k_sweep_rows<128>", "k_sweep_rows<256>", "k_sweep_rows<512>")
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -208,6 +220,45 @@ def oracle_sample(graphs, pairs):
     return edges, secs
 
 
+def host_cpu():
+    """Cores and model of the host that runs the CPU legs."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() in ("Model name", "Model Name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "lscpu_model": model}
+
+
+def oracle_rows_sample(g, mode, v0, entries):
+    """One oracle sweep (the first sweep of the mode's run) over the rows of g
+    starting at v0 and holding about `entries` entries
+    (lpa_inputs.row_range_sample: the rows and their neighbours, relabelled in
+    order, the neighbours' rows empty).  Returns (entries scanned, seconds,
+    (v0, v1))."""
+    import lpa_inputs as L
+    sg, v1, _ = L.row_range_sample(g, v0, entries)
+    t0 = time.perf_counter()
+    oracle_run(sg, mode, 1)
+    return sg.nnz, time.perf_counter() - t0, (int(v0), int(v1))
+
+
+def oracle_rows_baseline(g, mode, target_s=12.0):
+    """The oracle on a bounded sample of a graph too large to sweep whole on
+    one core: rows from the middle of the id range, sized from a short first
+    sample so that the timed sample takes about target_s seconds."""
+    v0 = g.n // 3
+    e, t, _ = oracle_rows_sample(g, mode, v0, 1 << 22)
+    rate = e / max(t, 1e-6)
+    want = int(min(max(rate * target_s, 1 << 22), 1 << 30))
+    e, t, rows = oracle_rows_sample(g, mode, v0, want)
+    return e, t, rows
+
+
 def workload_modes(args):
     """The mode strings one step runs on each graph of the workload."""
     modes = WORKLOAD_MODES.get(args.workload, MODES)
@@ -271,6 +322,10 @@ def cpu_parallel_sample(graphs, modes):
             "sample": f"one full run of each (graph, mode) pair of the workload ({secs:.1f} s)"}
 
 
+LARGE_NNZ = 400_000_000       # above this a whole oracle sweep of a graph takes minutes: time row samples
+REF_SAMPLE_ENTRIES = 1 << 24  # entries per reference-arm step on a large graph
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -280,23 +335,40 @@ def run_reference(args, rank, world):
     graphs = [make() for _, make in wl]
     modes = workload_modes(args)
     pairs = [(gi, m) for gi in range(len(graphs)) for m in modes]
+    large = any(g.nnz > LARGE_NNZ for g in graphs)
+    total = args.warmup + args.steps
+
+    def one(step):
+        gi, m = pairs[step % len(pairs)]
+        g = graphs[gi]
+        if g.nnz > LARGE_NNZ:
+            e, t, _ = oracle_rows_sample(g, m, (g.n * (step + 1)) // (total + 1), REF_SAMPLE_ENTRIES)
+            return e, t
+        return oracle_sample(graphs, [(gi, m)])
+
     for s in range(args.warmup):
-        oracle_sample(graphs, [pairs[s % len(pairs)]])
+        one(s)
     edges, secs = 0, 0.0
     t_all = time.perf_counter()
     for s in range(args.steps):
-        e, t = oracle_sample(graphs, [pairs[s % len(pairs)]])
+        e, t = one(args.warmup + s)
         edges += e
         secs += t
     wall = time.perf_counter() - t_all
     value = edges / secs
-    sample = (f"each step: one CPU-oracle sweep of one (graph, mode) pair, rotating over "
-              f"{[(wl[g][0], m) for g, m in pairs]}")
+    if large:
+        sample = (f"each step: the CPU oracle's first sweep over a range of about {REF_SAMPLE_ENTRIES} entries "
+                  f"of rows of {[wl[g][0] for g, _ in pairs]} ({[m for _, m in pairs]} mode), the range moving "
+                  f"through the vertex ids from step to step (rows and their neighbours relabelled in order)")
+    else:
+        sample = (f"each step: one CPU-oracle sweep of one (graph, mode) pair, rotating over "
+                  f"{[(wl[g][0], m) for g, m in pairs]}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": run_config(args, world),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             **host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -533,29 +605,74 @@ def kernel_bytes(prof, wbytes, sync, passes, rows_distinct=False):
     return out
 
 
+def release(lpa, torch, handles):
+    for h in handles:
+        lpa.lpa_graph_destroy(h)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    lpa.lpa_release_cached_memory()
+
+
+def run_extras(lpa, torch, stream, tie, prune, reps=5):
+    """R-MAT 22 + the road-like 4096^2 grid (config 2) in both modes: device
+    edges/s per (graph, mode), the paper's multi-core CPU design on the host
+    cores, and the tolerance / cap sweep per graph class."""
+    args = argparse.Namespace(workload="rmat22+grid4096", tie=tie, prune=prune)
+    wl = workload(args.workload)
+    graphs = [make() for _, make in wl]
+    modes = workload_modes(args)
+    handles = [lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS, stream) for g in graphs]
+    outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    runs = []
+    edges_all, ms_all = 0, 0.0
+    for (name, _), g, h, o in zip(wl, graphs, handles, outs):
+        for m in modes:
+            info = lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=True)
+            for _ in range(2):
+                lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(reps):
+                lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1) / reps
+            edges_all += g.nnz * info.iterations
+            ms_all += ms
+            runs.append({"graph": name, "mode": m, "n": g.n, "nnz": g.nnz, "iterations": info.iterations,
+                         "exit_reason": info.exit_reason, "ms": ms, "edges_per_s": g.nnz * info.iterations / (ms / 1e3),
+                         "touched_per_s": info.edges_touched / (ms / 1e3),
+                         "modularity": lpa.lpa_modularity(h, o)})
+    res = {"workload": WORKLOAD_TEXT[args.workload], "edges_per_s": edges_all / (ms_all / 1e3), "runs": runs,
+           "param_sweep": param_sweep(lpa, torch, stream, [n for n, _ in wl], graphs, handles, outs),
+           "cpu_parallel": cpu_parallel_sample(graphs, modes)}
+    release(lpa, torch, handles)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gvelpa", choices=["gvelpa", "reference"])
-    ap.add_argument("--workload", default="rmat22+grid4096", choices=sorted(WORKLOAD_TEXT))
+    ap.add_argument("--workload", default="rmat27", choices=sorted(WORKLOAD_TEXT))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip the event-timed roofline pass")
-    ap.add_argument("--e2e-steps", type=int, default=10)
-    ap.add_argument("--batched-graphs", type=int, default=128, help="0 skips the batched sample")
-    ap.add_argument("--serving-seconds", type=float, default=0.5, help="0 skips the serving sample")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the R-MAT 22 + grid runs, the paper's CPU design and the tau / cap sweep")
+    ap.add_argument("--batched-graphs", type=int, default=4096,
+                    help="4096: the full batch drawn on the device; other N: N host-drawn graphs; 0 skips it")
+    ap.add_argument("--serving-requests", type=int, default=10_000, help="0 skips the serving sample")
+    ap.add_argument("--serving-big-every", type=int, default=500,
+                    help="an R-MAT scale 24 request every this many requests (0: none)")
     ap.add_argument("--tie", default="strict", choices=["strict", "nonstrict"],
                     help="tie-break among the most weighted labels (Section 4.1.5)")
     ap.add_argument("--prune", default="paper", choices=["paper", "other"],
                     help="async pruning: every neighbour of a changed vertex re-marked (Section 4.1.4), or "
                          "only those not already in its new label (FLPA's rule, Section 2)")
-    ap.add_argument("--param-sweep", action="store_true",
-                    help="also sweep tau in {0.1, 0.05, 0.01, 1e-5} x cap in {10, 20, 50} per graph (async)")
-    ap.add_argument("--batched-full", action="store_true",
-                    help="batched sample on the full workload: 4,096 graphs drawn on the device")
-    ap.add_argument("--serving-full", action="store_true",
-                    help="serving sample with an R-MAT scale 24 request every 500 requests")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -688,36 +805,63 @@ def main():
                     "frac": d["GB_per_s"] / hbm, "peak_kind": hbm_kind, "traffic": measured_traffic(dom),
                     "bytes_per_launch": d["bytes_per_launch"],
                     "mean_launch_ms": d["ms_per_step"] / d["launches_per_step"]}
+        tot_b = sum(a["bytes"] for a in agg.values())
+        tot_ms = sum(a["ms"] for a in agg.values())
+        if tot_ms > 0:
+            roofline["all_sweep_kernels"] = {"achieved": tot_b / (tot_ms / 1e3) / 1e9, "unit": "GB/s",
+                                             "frac": tot_b / (tot_ms / 1e3) / 1e9 / hbm,
+                                             "bytes_per_step": tot_b, "ms_per_step": tot_ms}
 
-    if args.batched_full:
-        batched = batched_sample_full(lpa, torch, stream)
-    else:
-        batched = batched_sample(lpa, torch, stream, args.batched_graphs) if args.batched_graphs > 0 else None
-    serving = None
-    if args.serving_seconds > 0:
-        import lpa_inputs as L
-        big = L.rmat(24, 16, seed=3) if args.serving_full else None
-        serving = serving_sample(lpa, torch, stream, rate=2000.0, seconds=args.serving_seconds, pool_size=48,
-                                 big=big, big_every=500 if big is not None else 0)
-        serving["sample"] = ("Poisson arrivals at 2000 req/s, graphs of the batched distribution (pool of 48)" +
-                             ("; an R-MAT scale 24 request every 500" if big is not None else
-                              "; without the R-MAT scale 24 request of the full serving config (--serving-full)"))
-
+    # the CPU oracle on the host cores: a bounded sample of the same workload
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and sum(g.nnz for g in graphs) <= 400_000_000:
-        pairs = [(gi, m) for gi in range(len(graphs)) for m in modes]
-        e, s = oracle_sample(graphs, pairs + pairs)
-        cpu = {"value": e / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "CPU oracle, one sweep of each (graph, mode) pair of the workload, twice "
-                         f"({s:.1f} s of single-thread CPU work)"}
-
-    sweep_rows = None
-    if args.param_sweep:
-        sweep_rows = param_sweep(lpa, torch, stream, [n for n, _ in wl], graphs, handles, outs)
-
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        if any(g.nnz > LARGE_NNZ for g in graphs):
+            e_all, s_all, parts = 0, 0.0, []
+            for (name, _), g in zip(wl, graphs):
+                for m in modes:
+                    e, t, rows = oracle_rows_baseline(g, m)
+                    e_all += e
+                    s_all += t
+                    parts.append(f"{name} {m}: rows [{rows[0]}, {rows[1]}), {e} entries, {t:.1f} s")
+            cpu = {"value": e_all / s_all, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "the CPU oracle's first sweep over a contiguous range of rows (the rows and their "
+                             "neighbours relabelled in order, neighbours' rows empty): " + "; ".join(parts),
+                   **host_cpu()}
+        else:
+            pairs = [(gi, m) for gi in range(len(graphs)) for m in modes]
+            e, s_ = oracle_sample(graphs, pairs + pairs)
+            cpu = {"value": e / s_, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "CPU oracle, one sweep of each (graph, mode) pair of the workload, twice "
+                             f"({s_:.1f} s of single-thread CPU work)", **host_cpu()}
     cpu_par = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and sum(g.nnz for g in graphs) <= 400_000_000:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and sum(g.nnz for g in graphs) <= LARGE_NNZ:
         cpu_par = cpu_parallel_sample(graphs, modes)
+
+    # the headline graphs are freed before the other samples
+    del pinned
+    release(lpa, torch, handles)
+    del graphs, outs
+    torch.cuda.empty_cache()
+
+    extras = None
+    if args.workload == "rmat27" and not args.no_extras:
+        extras = run_extras(lpa, torch, stream, args.tie, args.prune)
+    batched = None
+    if args.batched_graphs == 4096:
+        batched = batched_sample_full(lpa, torch, stream)
+    elif args.batched_graphs > 0:
+        batched = batched_sample(lpa, torch, stream, args.batched_graphs)
+    serving = None
+    if args.serving_requests > 0:
+        import lpa_inputs as L
+        big = L.rmat(24, 16, seed=3) if args.serving_big_every > 0 else None
+        serving = serving_sample(lpa, torch, stream, rate=2000.0, seconds=args.serving_requests / 2000.0,
+                                 pool_size=48, big=big, big_every=args.serving_big_every if big is not None else 0)
+        serving["sample"] = (f"{args.serving_requests} requests, Poisson arrivals at 2000 req/s, graphs of the "
+                             "batched distribution (pool of 48)" +
+                             (f"; an R-MAT scale 24 edge-factor-16 request every {args.serving_big_every}"
+                              if big is not None else "; no R-MAT scale 24 request"))
+        del big
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -728,11 +872,9 @@ def main():
                 "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},
                 "gpu_launches": int(launches), "clocks": clocks, "roofline": roofline, "kernels": kernels,
-                "cpu_baseline": cpu, "cpu_parallel": cpu_par, "batched": batched, "serving": serving,
-                "param_sweep": sweep_rows, "per_run": per_run}
+                "cpu_baseline": cpu, "cpu_parallel": cpu_par, "per_run": per_run, "extras": extras,
+                "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
-    for h in handles:
-        lpa.lpa_graph_destroy(h)
     if dist:
         dist.destroy_process_group()
 

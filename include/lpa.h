@@ -94,7 +94,9 @@ typedef enum {
 #define LPA_HOST_PTRS   0u  /* offsets/indices/weights are host memory; the library copies them */
 #define LPA_DEVICE_PTRS 1u  /* they are device memory; the library copies them (unless LPA_BORROW) */
 #define LPA_BORROW      2u  /* with LPA_DEVICE_PTRS: use the caller's device arrays in place; they
-                               must stay alive and unchanged until *_destroy */
+                               must stay alive and unchanged until *_destroy.  Indices that are not
+                               16-byte aligned are copied all the same (the sweeps move index rows
+                               with 16-byte bulk copies) */
 
 /* Per-sweep history kept in lpa_run_info (sweeps beyond this are still run). */
 #define LPA_MAX_RECORDED_ITERS 64
@@ -271,13 +273,39 @@ lpa_status lpa_run_profiled(lpa_graph_t g, lpa_mode mode, double tolerance, int3
  *   q_out   host double; the call synchronises `stream` before returning. */
 lpa_status lpa_modularity(lpa_graph_t g, const int32_t *labels, double *q_out, void *stream);
 
-/* Pick a faster lpa_config for this graph and mode by timing candidate
- * configurations on it (each candidate: `trials` runs of lpa_run with the
- * given tolerance and cap, best time kept).  Applies the winner to the handle
- * and copies it to *chosen (host, nullable).  Synchronous; the graph's labels
- * scratch is used, no caller buffer is touched. */
+/* What an autotuner call did (host struct). */
+typedef struct {
+    int32_t cached;         /* 1: the configuration came from the process-wide cache; nothing was timed */
+    int32_t candidates;     /* configurations timed, the one in force before the call included */
+    float   search_ms;      /* wall time of the call */
+    float   default_ms;     /* best timed run of the configuration in force before the call (on the sample) */
+    float   chosen_ms;      /* best timed run of the chosen configuration (on the sample) */
+    int32_t sample_graphs;  /* graphs in the timed sample */
+    int32_t reserved;
+} lpa_autotune_info;
+
+/* Pick the degree-bin launch parameters (lpa_config) for this graph and run
+ * mode -- the GPU counterpart of the paper's scheduling choice (Section
+ * 4.1.1: OpenMP dynamic scheduling in chunks of 2048 vertices).  A log2
+ * degree histogram of the graph, taken on the device, bins the vertices under
+ * every candidate (limits are powers of two); candidates that bin them as an
+ * earlier one does are skipped.  One pass of coordinate descent over
+ * warp_max, mid_max, small_max, large_max and dense_permille, starting from
+ * the configuration in force (itself a candidate), times each candidate with
+ * `trials` runs of lpa_run (best kept, after one untimed run).  The winner is
+ * applied to the handle and copied to *chosen (host, nullable); *info (host,
+ * nullable) receives what the call did.  Choices are cached for the life of
+ * the process, keyed by mode, weight storage and the histogram rounded to
+ * 1/64 of the vertices and of the entries per bucket: a later call on a
+ * workload of the same shape applies the cached choice without timing.
+ * Results do not depend on the configuration (it moves work between
+ * kernels, not the arithmetic), so LPA_MODE_SYNC labels stay the same.
+ * Synchronous; uses a label buffer of its own, no caller buffer is touched. */
 lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, double tolerance, int32_t max_iters,
-                        int32_t trials, void *stream, lpa_config *chosen);
+                        int32_t trials, void *stream, lpa_config *chosen, lpa_autotune_info *info);
+
+/* Forgets every cached autotuner choice. */
+lpa_status lpa_autotune_cache_clear(void);
 
 /* Modularity of a labelling, as lpa_modularity, for callers that cannot let
  * the library allocate device memory: the CSR stays in the caller's device
@@ -328,6 +356,20 @@ lpa_status lpa_batch_props_get(lpa_batch_t b, lpa_graph_props *out);
  * scanned_total). */
 lpa_status lpa_batch_run(lpa_batch_t b, lpa_mode mode, double tolerance, int32_t max_iters,
                          int32_t *labels_out, void *stream, lpa_run_info *infos);
+
+/* Degree-bin launch parameters of a batch (as lpa_graph_get_config /
+ * lpa_graph_set_config). */
+lpa_status lpa_batch_get_config(lpa_batch_t b, lpa_config *out);
+lpa_status lpa_batch_set_config(lpa_batch_t b, const lpa_config *cfg);
+
+/* lpa_autotune for a batch: the same search, each candidate timed on a
+ * sample of the batch -- the shortest prefix of its graphs holding at least
+ * sample_permille / 1000 of its entries (1..1000; 1000 = the whole batch),
+ * run as a batch of its own that reads the parent's CSR in place (the graphs
+ * of a batch are independent draws, so a prefix is a sample of them).  The
+ * histogram and the cache key are the whole batch's. */
+lpa_status lpa_batch_autotune(lpa_batch_t b, lpa_mode mode, double tolerance, int32_t max_iters, int32_t trials,
+                              int32_t sample_permille, void *stream, lpa_config *chosen, lpa_autotune_info *info);
 
 /* Modularity of graph g of the batch for LOCAL labels (device int32[n_g]). */
 lpa_status lpa_batch_modularity(lpa_batch_t b, int32_t g, const int32_t *labels, double *q_out,

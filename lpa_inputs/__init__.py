@@ -265,3 +265,29 @@ def random_small(n, p, seed, wmax=0, self_loops=0.0, multi=False) -> Graph:
     g = from_undirected_pairs(n, pairs, weights)
     g.meta.update(kind="random_small", seed=seed, p=p)
     return g
+
+
+def row_range_sample(g, v0, min_entries):
+    """A bounded sample of a large graph for timing CPU code on its rows: the
+    rows [v0, v1) of g, v1 the first row boundary at least min_entries entries
+    past off[v0] (or the end), as a graph of their own.  Its vertices are the
+    sampled vertices and every neighbour of theirs, numbered in increasing
+    order of their ids in g; only the sampled rows keep their entries (the
+    neighbours' rows are empty).  Returns (graph, v1, ids) with ids[k] the id
+    in g of vertex k."""
+    n = g.n
+    v0 = int(min(max(v0, 0), max(n - 1, 0)))
+    e0 = int(g.off[v0])
+    v1 = int(np.searchsorted(g.off, e0 + int(min_entries), side="left"))
+    v1 = min(max(v1, v0 + 1), n)
+    e1 = int(g.off[v1])
+    nb = g.idx[e0:e1]
+    ids = np.union1d(np.arange(v0, v1, dtype=np.int64), nb.astype(np.int64))
+    deg = np.zeros(ids.size, dtype=np.int64)
+    deg[np.searchsorted(ids, np.arange(v0, v1, dtype=np.int64))] = np.diff(g.off[v0:v1 + 1])
+    off = np.zeros(ids.size + 1, dtype=np.int64)
+    np.cumsum(deg, out=off[1:])
+    idx = np.searchsorted(ids, nb.astype(np.int64)).astype(np.int32)
+    w = None if g.w is None else np.ascontiguousarray(g.w[e0:e1])
+    meta = dict(g.meta, sample_rows=(v0, v1), sample_entries=e1 - e0)
+    return Graph(off, idx, w, meta), v1, ids

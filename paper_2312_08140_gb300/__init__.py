@@ -97,6 +97,15 @@ class LpaProfile(ctypes.Structure):
                 "bin_changed_entries": [list(self.bin_changed_entries[t]) for t in range(it)]}
 
 
+class LpaAutotuneInfo(ctypes.Structure):
+    _fields_ = [("cached", ctypes.c_int32), ("candidates", ctypes.c_int32), ("search_ms", ctypes.c_float),
+                ("default_ms", ctypes.c_float), ("chosen_ms", ctypes.c_float), ("sample_graphs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class LpaServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("arena_vertices", ctypes.c_int64),
                 ("arena_entries", ctypes.c_int64), ("max_slots", ctypes.c_int32), ("mode", ctypes.c_int32),
@@ -146,7 +155,12 @@ _SIGS = {
     "lpa_run_profiled": ([_V, ctypes.c_int, _D, _I32, _V, _V, _P(LpaRunInfo), _P(LpaProfile)], ctypes.c_int),
     "lpa_modularity": ([_V, _V, _P(ctypes.c_double), _V], ctypes.c_int),
     "lpa_modularity_noalloc": ([_I64, _I64, _V, _V, _V, _V, _P(ctypes.c_double), _V], ctypes.c_int),
-    "lpa_autotune": ([_V, ctypes.c_int, _D, _I32, _I32, _V, _P(LpaConfig)], ctypes.c_int),
+    "lpa_autotune": ([_V, ctypes.c_int, _D, _I32, _I32, _V, _P(LpaConfig), _P(LpaAutotuneInfo)], ctypes.c_int),
+    "lpa_autotune_cache_clear": ([], ctypes.c_int),
+    "lpa_batch_autotune": ([_V, ctypes.c_int, _D, _I32, _I32, _I32, _V, _P(LpaConfig), _P(LpaAutotuneInfo)],
+                           ctypes.c_int),
+    "lpa_batch_get_config": ([_V, _P(LpaConfig)], ctypes.c_int),
+    "lpa_batch_set_config": ([_V, _P(LpaConfig)], ctypes.c_int),
     "lpa_batch_create": ([_I32, _V, _V, _V, _V, _V, _U32, _V, _P(_V)], ctypes.c_int),
     "lpa_batch_destroy": ([_V], ctypes.c_int),
     "lpa_batch_props_get": ([_V, _P(LpaGraphProps)], ctypes.c_int),
@@ -315,10 +329,34 @@ def lpa_modularity_noalloc(n, nnz, offsets, indices, weights, labels, stream=Non
     return q.value
 
 
-def lpa_autotune(g, mode, tolerance, max_iters, trials=2, stream=None) -> LpaConfig:
+def lpa_autotune(g, mode, tolerance, max_iters, trials=2, stream=None):
+    """Returns (LpaConfig chosen, dict of LpaAutotuneInfo)."""
+    c, inf = LpaConfig(), LpaAutotuneInfo()
+    _check(load().lpa_autotune(g, _mode(mode), tolerance, max_iters, trials, _stream(stream), ctypes.byref(c),
+                               ctypes.byref(inf)))
+    return c, inf.as_dict()
+
+
+def lpa_batch_autotune(b, mode, tolerance, max_iters, trials=2, sample_permille=125, stream=None):
+    """Returns (LpaConfig chosen, dict of LpaAutotuneInfo)."""
+    c, inf = LpaConfig(), LpaAutotuneInfo()
+    _check(load().lpa_batch_autotune(b, _mode(mode), tolerance, max_iters, trials, sample_permille,
+                                     _stream(stream), ctypes.byref(c), ctypes.byref(inf)))
+    return c, inf.as_dict()
+
+
+def lpa_autotune_cache_clear():
+    _check(load().lpa_autotune_cache_clear())
+
+
+def lpa_batch_get_config(b) -> LpaConfig:
     c = LpaConfig()
-    _check(load().lpa_autotune(g, _mode(mode), tolerance, max_iters, trials, _stream(stream), ctypes.byref(c)))
+    _check(load().lpa_batch_get_config(b, ctypes.byref(c)))
     return c
+
+
+def lpa_batch_set_config(b, cfg: LpaConfig):
+    _check(load().lpa_batch_set_config(b, ctypes.byref(cfg)))
 
 
 def lpa_batch_create(G, graph_vtx_off, graph_edge_off, offsets, indices, weights=None, flags=LPA_HOST_PTRS,

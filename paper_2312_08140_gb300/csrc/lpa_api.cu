@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <chrono>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -146,6 +148,9 @@ struct Engine {
     ModAccum* acc = nullptr;
     // host mirrors
     std::vector<int64_t> vtx_off_host;
+    std::vector<int64_t> edge_off_host;
+    unsigned long long* hist_d = nullptr;          // degree histogram scratch (autotuner)
+    int32_t* tune_out = nullptr;                   // labels of the autotuner's timed runs
     int64_t runs_total = 0;          // lpa_run calls that launched the device loop
 };
 
@@ -252,6 +257,38 @@ lpa_status check_config(const lpa_config& c) {
     return LPA_OK;
 }
 
+// Working state of an engine whose N, G and CSR fields are set: label
+// buffers, flags, frontier bitmap and lists, change marks, control block and
+// per-graph counters, and the static-list scratch.
+lpa_status alloc_state(Engine& E, cudaStream_t st) {
+    lpa_status rs;
+    const int64_t n = E.s.N;
+    const int32_t G = E.s.G;
+    const size_t N1 = (size_t)std::max<int64_t>(n, 1);
+    if ((rs = dalloc_t(E, &E.s.lab[0], N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.lab[1], N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.flags, N1 + 16)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.fr_bits, N1 / 16 + 1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.slist, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.flist, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.chg, N1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.ctrl, 1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.dN, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.done, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.iters, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.exit_reason, (size_t)G)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.s.hist_changed, (size_t)G * kMaxHist)) != LPA_OK) return rs;
+    LPA_CUDA(cudaMemsetAsync(E.s.flags, 0, N1 + 16, st));
+    LPA_CUDA(cudaMemsetAsync(E.s.ctrl, 0, sizeof(Ctrl), st));
+    LPA_CUDA(cudaMemsetAsync(E.s.hist_changed, 0, (size_t)G * kMaxHist * 8, st));
+    apply_config_fields(E);
+    const size_t sblk = (size_t)std::max<int64_t>(static_scratch_blocks(n), 1) * kBins;
+    if ((rs = dalloc_t(E, &E.static_counts, sblk)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.static_ents, sblk)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &E.cap_scratch, 3)) != LPA_OK) return rs;
+    return LPA_OK;
+}
+
 // Common creation path: G graphs (G == 1 for lpa_graph_create).
 lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const int64_t* edge_off_h, int64_t n,
                          int64_t nnz, const int64_t* offsets, const int32_t* indices, const float* weights,
@@ -274,6 +311,7 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     E.weighted = weights != nullptr;
     E.borrowed = borrow;
     E.vtx_off_host.assign(vtx_off_h, vtx_off_h + G + 1);
+    E.edge_off_host.assign(edge_off_h, edge_off_h + G + 1);
     const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     lpa_status rs;
 
@@ -286,6 +324,9 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     // as soon as it lands, while the static bin lists (which need only the
     // offsets) are built on the helper stream -- creation then costs about
     // the copy alone.
+    // The sweep kernels copy index rows with 16-byte bulk copies: borrowed
+    // indices that are not 16-byte aligned are copied like unborrowed ones.
+    const bool idx_copy = borrow && nnz > 0 && (reinterpret_cast<uintptr_t>(indices) & 15u) != 0;
     const bool staged = !borrow && !dev && nnz > 0;
     int64_t* off_d = nullptr;
     int32_t* idx_d = nullptr;
@@ -294,6 +335,10 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
         off_d = const_cast<int64_t*>(offsets);
         idx_d = const_cast<int32_t*>(indices);
         w_d = const_cast<float*>(weights);
+        if (idx_copy) {
+            if ((rs = dalloc_t(E, &idx_d, (size_t)nnz)) != LPA_OK) return rs;
+            LPA_CUDA(cudaMemcpyAsync(idx_d, indices, (size_t)nnz * 4, cudaMemcpyDeviceToDevice, st));
+        }
     } else {
         if ((rs = dalloc_t(E, &off_d, (size_t)n + 1)) != LPA_OK) return rs;
         if ((rs = dalloc_t(E, &idx_d, (size_t)nnz)) != LPA_OK) return rs;
@@ -323,29 +368,7 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
     E.s.g_begin = vo_d;
     E.s.g_end = vo_d + 1;
 
-    // working state
-    const size_t N1 = (size_t)std::max<int64_t>(n, 1);
-    if ((rs = dalloc_t(E, &E.s.lab[0], N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.lab[1], N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.flags, N1 + 16)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.fr_bits, N1 / 16 + 1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.slist, N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.flist, N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.chg, N1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.ctrl, 1)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.dN, (size_t)G)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.done, (size_t)G)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.iters, (size_t)G)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.exit_reason, (size_t)G)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.s.hist_changed, (size_t)G * kMaxHist)) != LPA_OK) return rs;
-    LPA_CUDA(cudaMemsetAsync(E.s.flags, 0, N1 + 16, st));
-    LPA_CUDA(cudaMemsetAsync(E.s.ctrl, 0, sizeof(Ctrl), st));
-    LPA_CUDA(cudaMemsetAsync(E.s.hist_changed, 0, (size_t)G * kMaxHist * 8, st));
-    apply_config_fields(E);
-    const size_t sblk = (size_t)std::max<int64_t>(static_scratch_blocks(n), 1) * kBins;
-    if ((rs = dalloc_t(E, &E.static_counts, sblk)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.static_ents, sblk)) != LPA_OK) return rs;
-    if ((rs = dalloc_t(E, &E.cap_scratch, 3)) != LPA_OK) return rs;
+    if ((rs = alloc_state(E, st)) != LPA_OK) return rs;
 
     // validation (and, for batches, local -> global index rewrite in our copy)
     ValidateResult* vr_d = nullptr;
@@ -424,6 +447,38 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
         E.s.weight_kind = W_F32;
     }
     E.s.w = w_d;
+    if ((rs = setup_blocks(E, st)) != LPA_OK) return rs;
+    LPA_CUDA(cudaStreamSynchronize(st));
+    return LPA_OK;
+}
+
+// An engine over the first K graphs of `par` (K >= 1), reading the parent's
+// CSR (already validated, weights already narrowed) in place and holding its
+// own working state: the timed sample of the autotuner.
+lpa_status engine_view(Engine& E, const Engine& par, int32_t K, const lpa_config& cfg, cudaStream_t st) {
+    E.device = par.device;
+    E.sms = par.sms;
+    E.s = par.s;
+    E.s.G = K;
+    E.s.N = par.vtx_off_host[K];
+    E.s.E = 0;
+    E.s.rows_distinct = par.s.G == 1 ? par.s.rows_distinct : 0;
+    if (K == 1) E.s.gid = nullptr;
+    E.weighted = par.weighted;
+    E.borrowed = true;
+    E.exact = par.exact;
+    E.max_degree = par.max_degree;
+    E.vtx_off_host.assign(par.vtx_off_host.begin(), par.vtx_off_host.begin() + K + 1);
+    E.edge_off_host.assign(par.edge_off_host.begin(), par.edge_off_host.begin() + K + 1);
+    E.cfg = cfg;
+    E.owned.clear();
+    E.device_bytes = 0;
+    LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_top, cudaStreamNonBlocking));
+    LPA_CUDA(cudaStreamCreateWithFlags(&E.cap_body, cudaStreamNonBlocking));
+    E.s.E = par.edge_off_host[K];
+    lpa_status rs = alloc_state(E, st);
+    if (rs != LPA_OK) return rs;
+    LPA_CUDA(build_static_lists(E.s, st, E.static_counts, E.static_ents));
     if ((rs = setup_blocks(E, st)) != LPA_OK) return rs;
     LPA_CUDA(cudaStreamSynchronize(st));
     return LPA_OK;
@@ -580,6 +635,7 @@ lpa_status collect_info(Engine& E, cudaStream_t st, lpa_run_info* infos, int32_t
     LPA_CUDA(cudaMemcpyAsync(hist.data(), E.s.hist_changed, hist.size() * 8, cudaMemcpyDeviceToHost, st));
     LPA_CUDA(cudaMemcpyAsync(&c, E.s.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     LPA_CUDA(cudaStreamSynchronize(st));
+    if (c.error == 5) return fail(LPA_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up (code 5)");
     if (c.error) return fail(LPA_ERR_CUDA, "device-side check failed (code %d)", c.error);
     for (int32_t g = 0; g < count; ++g) {
         lpa_run_info& I = infos[g];
@@ -699,6 +755,7 @@ lpa_status engine_run_profiled(Engine& E, int mode, double tol, int32_t max_iter
 #undef LPA_P
     cleanup();
     if (infos) return collect_info(E, st, infos, E.s.G);
+    if (c.error == 5) return fail(LPA_ERR_TIMEOUT, "a bounded wait on a bulk copy gave up (code 5)");
     if (c.error) return fail(LPA_ERR_CUDA, "device-side check failed (code %d)", c.error);
     return LPA_OK;
 }
@@ -745,6 +802,223 @@ lpa_status fill_props(const Engine& E, lpa_graph_props* p) {
     p->max_degree = E.max_degree;
     p->rows_distinct = E.s.rows_distinct;
     p->device_bytes = E.device_bytes + (int64_t)std::max<size_t>(E.s.bin_static[kBins - 1], 1) * sizeof(Overflow);
+    return LPA_OK;
+}
+
+// ------------------------------------------------------------- autotuner --
+// Launch parameters per degree bin (lpa_config) picked for a workload: the
+// GPU counterpart of the paper's scheduling choice (Section 4.1.1, OpenMP
+// dynamic chunks of 2048 vertices).  Candidate limits are powers of two, so a
+// log2 degree histogram gives every candidate's bin of every vertex exactly;
+// candidates that bin the workload's vertices the same way as one already
+// timed are skipped.  The search is one pass of coordinate descent from the
+// configuration in force (always a candidate), each candidate timed on a
+// sample of the workload (a prefix of a batch's graphs sharing its CSR).
+// Choices are cached per process, keyed by mode, weight storage and the
+// histogram rounded to 1/64 of the vertices and of the entries per bucket.
+std::mutex g_tune_mu;
+std::map<std::string, lpa_config> g_tune_cache;
+
+lpa_status set_config(Engine& E, const lpa_config* cfg) {
+    if (!cfg) return fail(LPA_ERR_INVALID_ARG, "cfg is NULL");
+    lpa_status rs = check_config(*cfg);
+    if (rs != LPA_OK) return rs;
+    LPA_CUDA(cudaDeviceSynchronize());
+    destroy_graphs(E);
+    E.cfg = *cfg;
+    apply_config_fields(E);
+    LPA_CUDA(build_static_lists(E.s, 0, E.static_counts, E.static_ents));
+    return setup_blocks(E, 0);
+}
+
+lpa_status degree_histogram(Engine& E, std::vector<unsigned long long>& h, cudaStream_t st) {
+    lpa_status rs;
+    if (!E.hist_d && (rs = dalloc_t(E, &E.hist_d, 2 * kDegBuckets)) != LPA_OK) return rs;
+    LPA_CUDA(launch_degree_hist(E.s, E.hist_d, st, E.sms));
+    h.assign(2 * kDegBuckets, 0ull);
+    LPA_CUDA(cudaMemcpyAsync(h.data(), E.hist_d, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    LPA_CUDA(cudaStreamSynchronize(st));
+    return LPA_OK;
+}
+
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// Bin (0..4) of a bucket of degrees (2^(b-1), 2^b] under power-of-two limits.
+int bucket_bin(const lpa_config& c, int b) {
+    const int64_t hi = (int64_t)1 << b;      // the bucket's largest degree
+    return hi <= c.small_max ? 0 : hi <= c.warp_max ? 1 : hi <= c.mid_max ? 2 : hi <= c.large_max ? 3 : 4;
+}
+
+// What a configuration does to the workload: the bin of each non-empty
+// bucket, and the dense threshold.  Equal signatures launch the same kernels
+// on the same vertices.
+std::string tune_signature(const lpa_config& c, const std::vector<unsigned long long>& h) {
+    std::string sig;
+    for (int b = 0; b < kDegBuckets; ++b)
+        if (h[b]) sig += (char)('0' + bucket_bin(c, b));
+    sig += ":" + std::to_string(c.dense_permille);
+    return sig;
+}
+
+std::string tune_key(const Engine& E, int mode, const std::vector<unsigned long long>& h) {
+    unsigned long long nv = 0, ne = 0;
+    for (int b = 0; b < kDegBuckets; ++b) {
+        nv += h[b];
+        ne += h[kDegBuckets + b];
+    }
+    std::string key = "m" + std::to_string(mode) + "w" + std::to_string(E.s.weight_kind) + (E.s.G > 1 ? "b" : "s");
+    for (int b = 0; b < kDegBuckets; ++b) {
+        const long qv = nv ? std::lround(64.0 * (double)h[b] / (double)nv) : 0;
+        const long qe = ne ? std::lround(64.0 * (double)h[kDegBuckets + b] / (double)ne) : 0;
+        if (qv || qe) key += "," + std::to_string(b) + ":" + std::to_string(qv) + "/" + std::to_string(qe);
+    }
+    return key;
+}
+
+// Best of `trials` timed runs (after one untimed run) of engine T under cfg.
+lpa_status time_config(Engine& T, const lpa_config& cfg, int mode, double tol, int32_t max_iters, int32_t trials,
+                       cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float* best_ms) {
+    lpa_status rs = set_config(T, &cfg);
+    if (rs != LPA_OK) return rs;
+    float best = 1e30f;
+    for (int r = 0; r <= trials; ++r) {
+        LPA_CUDA(cudaEventRecord(e0, st));
+        if ((rs = engine_run(T, mode, tol, max_iters, T.tune_out, st, nullptr, T.s.G > 1 ? 1 : 0)) != LPA_OK)
+            return rs;
+        LPA_CUDA(cudaEventRecord(e1, st));
+        LPA_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        LPA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0) best = std::min(best, ms);
+    }
+    *best_ms = best;
+    return LPA_OK;
+}
+
+lpa_status autotune_engine(Engine& E, int mode, double tol, int32_t max_iters, int32_t trials,
+                           int32_t sample_permille, cudaStream_t st, lpa_config* chosen, lpa_autotune_info* info) {
+    if (trials < 1 || trials > 100) return fail(LPA_ERR_INVALID_ARG, "trials must be in [1, 100]");
+    if (sample_permille < 1 || sample_permille > 1000)
+        return fail(LPA_ERR_INVALID_ARG, "sample_permille must be in [1, 1000]");
+    int ns = 0, po = 0, base = mode;
+    split_mode(base, ns, po);
+    if (base < 0 || base > 2) return fail(LPA_ERR_INVALID_ARG, "unknown mode %d", base);
+    if (po && base != MODE_ASYNC) return fail(LPA_ERR_INVALID_ARG, "LPA_PRUNE_OTHER needs LPA_MODE_ASYNC");
+    if (!(tol >= 0.0 && tol <= 1.0)) return fail(LPA_ERR_INVALID_ARG, "tolerance must be in [0, 1]");
+    if (max_iters < 0 || max_iters > (1 << 20)) return fail(LPA_ERR_INVALID_ARG, "max_iters must be in [0, 2^20]");
+    lpa_status rs = LPA_OK;
+    lpa_autotune_info inf{};
+    const auto t_start = std::chrono::steady_clock::now();
+    const lpa_config start = E.cfg;
+    if (E.s.N == 0) {
+        if (chosen) *chosen = start;
+        if (info) *info = inf;
+        return LPA_OK;
+    }
+    std::vector<unsigned long long> h;
+    if ((rs = degree_histogram(E, h, st)) != LPA_OK) return rs;
+    const std::string key = tune_key(E, mode, h);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            const lpa_config c = it->second;
+            if ((rs = set_config(E, &c)) != LPA_OK) return rs;
+            inf.cached = 1;
+            inf.search_ms = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                                              t_start).count();
+            if (chosen) *chosen = c;
+            if (info) *info = inf;
+            return LPA_OK;
+        }
+    }
+    // the timed sample: the shortest prefix of graphs holding sample_permille
+    // of the entries (the whole workload for a single graph)
+    int32_t K = E.s.G;
+    if (E.s.G > 1) {
+        const double want = (double)E.edge_off_host[E.s.G] * sample_permille / 1000.0;
+        K = 1;
+        while (K < E.s.G && (double)E.edge_off_host[K] < want) ++K;
+    }
+    Engine view;
+    Engine* T = &E;
+    if (K < E.s.G) {
+        if ((rs = engine_view(view, E, K, start, st)) != LPA_OK) {
+            engine_free(view);
+            return rs;
+        }
+        T = &view;
+    }
+    if (!T->tune_out && (rs = dalloc_t(*T, &T->tune_out, (size_t)std::max<int64_t>(T->s.N, 1))) != LPA_OK) {
+        if (T != &E) engine_free(view);
+        return rs;
+    }
+    inf.sample_graphs = K;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool exact_bins = pow2(start.small_max) && pow2(start.warp_max) && pow2(start.mid_max) &&
+                            pow2(start.large_max);
+    std::vector<std::string> seen;
+    lpa_config best = start;
+    float best_ms = 0.f;
+    rs = time_config(*T, start, mode, tol, max_iters, trials, st, e0, e1, &best_ms);
+    inf.default_ms = best_ms;
+    inf.candidates = 1;
+    if (exact_bins) seen.push_back(tune_signature(start, h));
+    static const int kSmall[] = {1, 2, 4, 8};
+    static const int kWarp[] = {16, 32, 64, 128, 256};
+    static const int kMid[] = {256, 512, 1024, 2048};
+    static const int kLarge[] = {1024, 2048, 4096};
+    static const int kDense[] = {300, 500, 700, 1001};
+    struct Axis {
+        int lpa_config::*field;
+        const int* vals;
+        int n;
+    };
+    const Axis axes[] = {{&lpa_config::warp_max, kWarp, 5}, {&lpa_config::mid_max, kMid, 4},
+                         {&lpa_config::small_max, kSmall, 4}, {&lpa_config::large_max, kLarge, 3},
+                         {&lpa_config::dense_permille, kDense, 4}};
+    for (const Axis& ax : axes) {
+        if (rs != LPA_OK) break;
+        const lpa_config centre = best;
+        for (int q = 0; q < ax.n && rs == LPA_OK; ++q) {
+            lpa_config c = centre;
+            c.*(ax.field) = ax.vals[q];
+            if (c.*(ax.field) == centre.*(ax.field)) continue;
+            if (c.small_max >= c.warp_max || c.warp_max >= c.mid_max || c.mid_max >= c.large_max) continue;
+            if (check_config(c) != LPA_OK) continue;
+            if (exact_bins) {
+                const std::string sig = tune_signature(c, h);
+                if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+                seen.push_back(sig);
+            }
+            float ms = 0.f;
+            rs = time_config(*T, c, mode, tol, max_iters, trials, st, e0, e1, &ms);
+            ++inf.candidates;
+            if (rs == LPA_OK && ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (T != &E) engine_free(view);
+    if (rs != LPA_OK) {
+        set_config(E, &start);
+        return rs;
+    }
+    if ((rs = set_config(E, &best)) != LPA_OK) return rs;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    inf.chosen_ms = best_ms;
+    inf.search_ms =
+        (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (chosen) *chosen = best;
+    if (info) *info = inf;
     return LPA_OK;
 }
 
@@ -831,18 +1105,6 @@ lpa_status lpa_graph_get_config(lpa_graph_t g, lpa_config* out) {
     return LPA_OK;
 }
 
-static lpa_status set_config(Engine& E, const lpa_config* cfg) {
-    if (!cfg) return fail(LPA_ERR_INVALID_ARG, "cfg is NULL");
-    lpa_status rs = check_config(*cfg);
-    if (rs != LPA_OK) return rs;
-    LPA_CUDA(cudaDeviceSynchronize());
-    destroy_graphs(E);
-    E.cfg = *cfg;
-    apply_config_fields(E);
-    LPA_CUDA(build_static_lists(E.s, 0, E.static_counts, E.static_ents));
-    return setup_blocks(E, 0);
-}
-
 lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config* cfg) {
     if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
     return set_config(g->e, cfg);
@@ -867,64 +1129,34 @@ lpa_status lpa_modularity(lpa_graph_t g, const int32_t* labels, double* q_out, v
 }
 
 lpa_status lpa_autotune(lpa_graph_t g, lpa_mode mode, double tolerance, int32_t max_iters, int32_t trials,
-                        void* stream, lpa_config* chosen) {
+                        void* stream, lpa_config* chosen, lpa_autotune_info* info) {
     if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
-    if (trials < 1 || trials > 100) return fail(LPA_ERR_INVALID_ARG, "trials must be in [1, 100]");
-    Engine& E = g->e;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (E.s.N == 0) {
-        if (chosen) *chosen = E.cfg;
-        return LPA_OK;
-    }
-    int32_t* out = nullptr;
-    LPA_CUDA(cudaMalloc(&out, (size_t)E.s.N * 4));
-    std::vector<lpa_config> cands;
-    const int smalls[] = {4, 8};
-    const int warps[] = {64, 128, 256};
-    const int mids[] = {512, 1024};
-    const int larges[] = {2048, 4096};
-    const int denses[] = {300, 600, 1001};
-    for (int sm : smalls)
-        for (int wm : warps)
-            for (int md : mids)
-                for (int lg : larges)
-                    for (int dp : denses) cands.push_back(lpa_config{sm, wm, md, lg, dp});
-    cudaEvent_t e0, e1;
-    LPA_CUDA(cudaEventCreate(&e0));
-    LPA_CUDA(cudaEventCreate(&e1));
-    const lpa_config orig = E.cfg;
-    lpa_config best = orig;
-    float best_ms = 1e30f;
-    lpa_status rs = LPA_OK;
-    for (const lpa_config& c : cands) {
-        if ((rs = set_config(E, &c)) != LPA_OK) break;
-        float tmin = 1e30f;
-        for (int r = 0; r <= trials; ++r) {   // first run warms up and builds the graph
-            cudaEventRecord(e0, st);
-            rs = engine_run(E, (int)mode, tolerance, max_iters, out, st, nullptr, 0);
-            if (rs != LPA_OK) break;
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (r > 0) tmin = std::min(tmin, ms);
-        }
-        if (rs != LPA_OK) break;
-        if (tmin < best_ms) {
-            best_ms = tmin;
-            best = c;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(out);
-    if (rs != LPA_OK) {
-        set_config(E, &orig);
-        return rs;
-    }
-    if ((rs = set_config(E, &best)) != LPA_OK) return rs;
-    if (chosen) *chosen = best;
+    return autotune_engine(g->e, (int)mode, tolerance, max_iters, trials, 1000, static_cast<cudaStream_t>(stream),
+                           chosen, info);
+}
+
+lpa_status lpa_batch_autotune(lpa_batch_t b, lpa_mode mode, double tolerance, int32_t max_iters, int32_t trials,
+                              int32_t sample_permille, void* stream, lpa_config* chosen, lpa_autotune_info* info) {
+    if (!b) return fail(LPA_ERR_INVALID_ARG, "batch is NULL");
+    return autotune_engine(b->e, (int)mode, tolerance, max_iters, trials, sample_permille,
+                           static_cast<cudaStream_t>(stream), chosen, info);
+}
+
+lpa_status lpa_autotune_cache_clear(void) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.clear();
     return LPA_OK;
+}
+
+lpa_status lpa_batch_get_config(lpa_batch_t b, lpa_config* out) {
+    if (!b || !out) return fail(LPA_ERR_INVALID_ARG, "NULL argument");
+    *out = b->e.cfg;
+    return LPA_OK;
+}
+
+lpa_status lpa_batch_set_config(lpa_batch_t b, const lpa_config* cfg) {
+    if (!b) return fail(LPA_ERR_INVALID_ARG, "batch is NULL");
+    return set_config(b->e, cfg);
 }
 
 // ------------------------------------------------------------------ batches

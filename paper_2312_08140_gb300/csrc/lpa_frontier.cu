@@ -860,6 +860,36 @@ cudaError_t launch_weights_to_u8(const float* w, unsigned char* out, int64_t E, 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- degree histogram --
+// Vertices and entries per degree bucket b = ceil(log2(d)) (d >= 1; b = 0 for
+// d = 1), over vertices [0, N): hist[b] vertices, hist[kDegBuckets + b]
+// entries.  With bin limits that are powers of two the bucket counts give the
+// bin counts of any lpa_config exactly.
+__global__ void k_degree_hist(const int64_t* off, const int64_t* off_end, int64_t N, unsigned long long* hist) {
+    __shared__ unsigned long long sh[2 * kDegBuckets];
+    for (int q = threadIdx.x; q < 2 * kDegBuckets; q += blockDim.x) sh[q] = 0ull;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < N; v += stride) {
+        const int64_t d = off_end[v] - off[v];
+        if (d > 0) {
+            const int b = d <= 1 ? 0 : 64 - __clzll((unsigned long long)(d - 1));
+            atomicAdd(&sh[b], 1ull);
+            atomicAdd(&sh[kDegBuckets + b], (unsigned long long)d);
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 2 * kDegBuckets; q += blockDim.x)
+        if (sh[q]) atomicAdd(&hist[q], sh[q]);
+}
+
+cudaError_t launch_degree_hist(const DevState& s, unsigned long long* hist, cudaStream_t st, int sms) {
+    cudaError_t e = cudaMemsetAsync(hist, 0, 2 * kDegBuckets * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    k_degree_hist<<<sms * 2, 256, 0, st>>>(s.off, s.off_end, s.N, hist);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ modularity --
 __device__ __forceinline__ double weight_f64(const DevState& s, int64_t e) {
     if (s.weight_kind == W_UNIT) return 1.0;

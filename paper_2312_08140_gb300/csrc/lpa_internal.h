@@ -215,6 +215,16 @@ cudaError_t launch_sweep_warp(const DevState& s, int mode, cudaStream_t st, int 
 // Block-per-vertex sweep of bin 2, 3 or 4 (one resident wave over `sms` SMs).
 // For bin 4 this also launches the partitioned rescan of overflowed rows.
 cudaError_t launch_sweep_block(const DevState& s, int mode, int bin, int sms, cudaStream_t st);
+// The block-per-row kernel of bins 2..4 (lpa_sweep_rows.cu); *blocks receives
+// its grid size.
+template <bool ASYNC, int WK, bool BATCH, bool NS>
+cudaError_t launch_rows(const DevState& s, int bin, int flag, int sms, cudaStream_t st, int* blocks);
+
+// Degree histogram of vertices [0, s.N): kDegBuckets buckets b = ceil(log2 d)
+// of vertex counts, then of entry counts (device unsigned long long[2 x
+// kDegBuckets], cleared here).
+constexpr int kDegBuckets = 40;
+cudaError_t launch_degree_hist(const DevState& s, unsigned long long* hist, cudaStream_t st, int sms);
 
 // Graph validation (row-wise).  Results accumulate into *res (device).
 struct ValidateResult {

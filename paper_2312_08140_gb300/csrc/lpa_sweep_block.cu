@@ -842,17 +842,9 @@ static size_t block_smem(const DevState& s, int bin) {
 
 template <bool ASYNC, int WK, bool BATCH, bool NS>
 static cudaError_t launch_block_t(const DevState& s, int bin, int flag, int sms, cudaStream_t st) {
-    const size_t smem = block_smem(s, bin);
-    auto kern = bin == kBins - 1 ? k_sweep_block<ASYNC, WK, BATCH, NS, true> : k_sweep_block<ASYNC, WK, BATCH, NS, false>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    // one resident wave: blocks loop over the bin's vertices
-    int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlockThreads[bin - 2], smem);
-    if (err != cudaSuccess) return err;
-    const int blocks = sms * (per_sm > 0 ? per_sm : 1);
-    kern<<<blocks, kBlockThreads[bin - 2], smem, st>>>(s, bin, flag);
-    err = cudaGetLastError();
+    // one resident wave: blocks stream the bin's rows (lpa_sweep_rows.cu)
+    int blocks = sms;
+    cudaError_t err = launch_rows<ASYNC, WK, BATCH, NS>(s, bin, flag, sms, st, &blocks);
     if (err != cudaSuccess || bin != kBins - 1 || !s.ovf_possible) return err;
     // overflowing rows: plan, sliced path (slices, then partitions), rescan path
     k_ovf_plan<<<1, 1024, 0, st>>>(s);

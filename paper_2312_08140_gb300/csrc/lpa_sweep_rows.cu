@@ -1,0 +1,648 @@
+// lpa_sweep_rows.cu -- sweep for vertices with degree above warp_max: one
+// thread block per frontier row (128 threads up to mid_max, 256 up to
+// large_max, 512 above), rows streamed through a block-wide pipeline.
+//
+// Per row the work is Eq. 2 (Section 3.3): gather the label of every
+// neighbour, sum the weights per label, take the most weighted label (ties:
+// Section 4.1.5) and, on change, mark the neighbours unprocessed (Section
+// 4.1.4).  The gathers are random 4-byte reads, so the kernel is bound by how
+// many of them are in flight.  It keeps them in flight across the whole pass:
+//
+//   * a row is cut into tiles of TILE = NT x P entries.  Warp 0 produces the
+//     tile sequence of the block (rows taken from a per-bin counter in
+//     batches of 32, their metadata loaded by the 32 lanes in parallel) two
+//     tiles ahead, and copies each tile's neighbour ids into one of two
+//     shared-memory buffers with one bulk asynchronous copy (cp.async.bulk,
+//     completion counted on an mbarrier);
+//   * in step k every thread reads its P ids of tile k+1 from shared memory
+//     and issues their label gathers into registers, then aggregates tile k
+//     (whose labels arrived during step k-1): lanes holding the same label
+//     are grouped with __match_any_sync and the group leader adds the group's
+//     weight into a shared-memory open-addressing table, listing the slots it
+//     fills;
+//   * after a row's last tile the block scans the listed slots, reduces
+//     (sum, tie key) to the winner, records it and marks the neighbours.
+//     The next row's gathers are already in flight at that point.
+//
+// Rows whose distinct labels overflow the last bin's table (bounded probing
+// fails) are appended to the overflow list and finished by the partitioned
+// kernels of lpa_sweep_block.cu, as before.  The first synchronous sweep of a
+// repeat-free graph, and the last bin of the first asynchronous sweep, take
+// the max-over-row path (every label is still its vertex's id): no gathers,
+// a max of (weight key, tie key) over the ids in shared memory.
+//
+// Every wait on an mbarrier is bounded (2 s of GPU time); a wait that gives
+// up sets error code 5 in the control block and the block leaves after its
+// copies in flight have landed (again waited for with a bound).
+#include "lpa_device.cuh"
+
+namespace lpa {
+
+constexpr int kRowBatch = 32;                  // rows taken from the counter at a time
+constexpr int kStages = 4;                     // index buffers: a tile's copy starts three steps ahead
+constexpr int kSharedProbes = 16;              // probe bound of rows that may overflow the table
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+// ---- PTX wrappers: mbarrier and bulk asynchronous copy --------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Orders this thread's earlier generic-proxy accesses of shared memory before
+// later async-proxy (bulk copy) writes to it.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// dst (shared, 16-byte aligned) <- src (global, 16-byte aligned), bytes a
+// multiple of 16; completion adds `bytes` to the mbarrier's transaction count.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits until phase `parity` of the mbarrier has completed, for at most
+// kWaitNs.  Returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned polls = 1;; ++polls) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((polls & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// ---- per-block shared state -----------------------------------------------
+// One tile: entries [e0, e1) of one row.  Written by warp 0 two steps before
+// it is aggregated.
+struct Tile {
+    int64_t e0, e1;        // entry range of the tile
+    int64_t a0;            // first entry held by the tile's buffer (e0 rounded down to 4)
+    int64_t st, en;        // the row
+    int32_t v;             // vertex (-1: no tile, the pass is over for this block)
+    int32_t own;           // its label before the sweep
+    uint32_t k;            // its slot in the bin's frontier list
+    int32_t last;          // last tile of the row
+    int32_t skip;          // batches: the vertex's graph is done; the row is left as it is
+    int32_t pad;
+};
+
+// Entries per thread per tile, entries per tile, and one index buffer.  The
+// unit-weight kernels of the wider blocks keep 8 gathers per thread in
+// flight (1 block of 512 or 2 of 256 threads per SM, no register spills).
+template <int NT, int WK>
+struct RowsShape {
+    static constexpr int P = (NT >= 256 && WK == W_UNIT) ? 8 : 4;
+    static constexpr int TILE = NT * P;
+    static constexpr int BUF = TILE + 8;       // + up to 3 entries of alignment slack on each side
+};
+
+// Blocks of NT threads the launch bounds ask to fit on one SM (registers per
+// thread follow from it).  Measured on R-MAT 27: one 512-thread block per SM
+// for the last bin and two 256-thread blocks for the bin before it ran the
+// run in 107 ms; two and four blocks (64 registers, 4 gathers per thread)
+// took 154 ms, and with 8 gathers per thread (spilling) 136 ms.
+template <int NT>
+struct RowsOccupancy {
+    static constexpr int kBlocks = NT >= 512 ? 1 : NT >= 256 ? 2 : 8;
+};
+
+// Metadata of one row of the current batch.
+struct RowMeta {
+    int64_t st, en;        // the row
+    int32_t v;             // vertex (-1: past the end of the bin)
+    int32_t own;           // its label before the sweep
+    int32_t skip;          // batches: the vertex's graph is done
+    uint32_t k;            // its slot in the bin's frontier list
+};
+
+// Production cursor of warp 0.
+struct ProdState {
+    int64_t pe, pen;       // next entry of the row being cut into tiles, and its end
+    int32_t bpos;          // next row of the batch
+    int32_t prow;          // the row being cut into tiles
+    int32_t exhausted;     // no rows left for this block
+    int32_t pad;
+};
+
+// Block-wide argmax of (sum key, tie key), as in lpa_sweep_block.cu.
+__device__ __forceinline__ uint32_t rows_block_argmax(uint32_t key, uint32_t tie, uint32_t* red_key,
+                                                      uint32_t* red_tie, uint32_t* winner) {
+    const unsigned lane = lane_id();
+    const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t m = __reduce_max_sync(kFull, key);
+    const uint32_t c = __reduce_min_sync(kFull, (m != 0 && key == m) ? tie : 0xffffffffu);
+    if (lane == 0) {
+        red_key[wib] = m;
+        red_tie[wib] = c;
+    }
+    __syncthreads();
+    if (wib == 0) {
+        const uint32_t kk = (int)lane < nw ? red_key[lane] : 0u;
+        const uint32_t tt = (int)lane < nw ? red_tie[lane] : 0xffffffffu;
+        const uint32_t w = warp_argmax_tie(kk, tt);
+        if (lane == 0) *winner = w;
+    }
+    __syncthreads();
+    return *winner;
+}
+
+template <bool ASYNC, int WK, bool BATCH, bool NS, int NT>
+__global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(DevState s, int bin,
+                                                                            int flag_neighbours) {
+    using T = typename Acc<WK>::T;
+    using Sh = RowsShape<NT, WK>;
+    constexpr int P = Sh::P;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // layout: kStages index buffers | table keys | table values | filled-slot lists
+    int32_t* ibuf = reinterpret_cast<int32_t*>(smem_raw);                   // [kStages][BUF]
+    const int S = s.block_slots[bin - 2];
+    int32_t* keys = ibuf + kStages * Sh::BUF;
+    T* vals = reinterpret_cast<T*>(keys + S);
+    const unsigned seg_cap = (unsigned)S / 2u / NW;
+    uint16_t* segs = reinterpret_cast<uint16_t*>(vals + S);
+    __shared__ __align__(8) uint64_t mbar[kStages];
+    __shared__ Tile tiles[2 * kStages];
+    __shared__ RowMeta batch[kRowBatch];
+    __shared__ ProdState prod;
+    __shared__ unsigned wpre[33];
+    __shared__ uint32_t red_key[32], red_tie[32], winner;
+    __shared__ unsigned long long red_bp[32];
+    __shared__ int overflow, abort_flag;
+
+    const unsigned lane = lane_id();
+    const int wib = threadIdx.x >> 5;
+    uint16_t* my_seg = segs + (size_t)wib * seg_cap;
+    unsigned wfill = 0;
+    for (int q = threadIdx.x; q < S; q += NT) {
+        keys[q] = kEmptyKey;
+        vals[q] = (T)0;
+    }
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < kStages; ++b) mbar_init(&mbar[b], 1);
+        fence_mbar_init();
+        overflow = 0;
+        abort_flag = 0;
+        prod.pe = prod.pen = 0;
+        prod.bpos = kRowBatch;
+        prod.prow = -1;
+        prod.exhausted = 0;
+    }
+
+    const BinView bv = bin_view(s, bin);
+    const Labels L = labels_of(s);
+    const bool marks = marks_on(s, flag_neighbours);
+    const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
+    bool ident = identity_sweep<ASYNC, BATCH>(s);
+    if constexpr (ASYNC && !BATCH) ident = bin == kBins - 1 && s.rows_distinct && s.ctrl->iter == 0 && L.dense;
+    const bool po = ASYNC && s.ctrl->prune_other != 0;               // FLPA's pruning rule
+    const int log_S = ceil_log2((unsigned)S);
+    const unsigned cnt = bv.cnt;
+    const int64_t E_al = s.E & ~(int64_t)3;                          // end of the 16-byte aligned part of idx
+
+    // ---- producer (warp 0) -----------------------------------------------------
+    // Rows come from the bin's counter in batches of kRowBatch.  The list
+    // entries of the next batch (nxt_v, one per lane) and the counter value of
+    // the one after (nn_base, lane 0) are fetched a batch ahead; when a batch
+    // starts, its rows' offsets and labels are loaded into `batch`.
+    int32_t nxt_v = -1;
+    unsigned nxt_base = 0, nn_base = 0;
+    unsigned produced = 0;          // tiles produced by this block (index of the next one)
+
+    auto list_at = [&](unsigned base) -> int32_t {
+        const unsigned k = base + lane;
+        return (base < cnt && k < cnt) ? bv.list[k] : -1;
+    };
+    auto start_batch = [&]() {      // warp 0: the batch at nxt_base becomes current
+        RowMeta m;
+        m.v = nxt_v;
+        m.k = nxt_base + lane;
+        m.st = m.en = 0;
+        m.own = 0;
+        m.skip = 0;
+        if (m.v >= 0) {
+            m.st = s.off[m.v];
+            m.en = s.off_end[m.v];
+            m.own = ASYNC ? __ldcg(L.C + m.v) : L.C[m.v];
+            if constexpr (BATCH) m.skip = s.done[s.gid[m.v]] ? 1 : 0;
+        }
+        batch[lane] = m;
+        nxt_base = __shfl_sync(kFull, nn_base, 0);
+        nxt_v = list_at(nxt_base);
+        if (lane == 0) nn_base = atomicAdd(&s.ctrl->row_next[bin], (unsigned)kRowBatch);
+        __syncwarp();
+        if (lane == 0) {
+            prod.bpos = 0;
+            if (batch[0].v < 0) prod.exhausted = 1;
+        }
+        __syncwarp();
+    };
+    // Warp 0: writes the descriptor of the next tile into tiles[produced % 8]
+    // and starts its copy into buffer produced % kStages.  All 32 lanes call.
+    auto produce = [&]() {
+        for (;;) {                                     // warp-uniform: every lane reads the same state
+            if (prod.exhausted || prod.pe < prod.pen) break;
+            if (prod.bpos >= kRowBatch) {
+                start_batch();
+                if (prod.exhausted) break;
+            }
+            if (lane == 0) {
+                const RowMeta& r = batch[prod.bpos];
+                if (r.v < 0) {
+                    prod.exhausted = 1;
+                } else {
+                    prod.prow = prod.bpos;
+                    prod.pe = r.st;
+                    prod.pen = r.en;
+                }
+                ++prod.bpos;
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            Tile t;
+            t.v = -1;
+            const int b = (int)(produced % kStages);
+            if (!prod.exhausted) {
+                const RowMeta& r = batch[prod.prow];
+                t.v = r.v;
+                t.own = r.own;
+                t.skip = r.skip;
+                t.k = r.k;
+                t.st = r.st;
+                t.en = r.en;
+                t.e0 = prod.pe;
+                t.e1 = min(prod.pe + (int64_t)Sh::TILE, prod.pen);
+                t.last = t.e1 >= prod.pen ? 1 : 0;
+                t.a0 = t.e0 & ~(int64_t)3;
+                prod.pe = t.e1;
+            }
+            tiles[produced % (2 * kStages)] = t;
+            if (t.v >= 0) {
+                int64_t a1 = (t.e1 + 3) & ~(int64_t)3;
+                if (a1 > E_al) a1 = E_al;
+                const int64_t bytes = a1 > t.a0 ? (a1 - t.a0) * 4 : 0;
+                int32_t* dst = ibuf + b * Sh::BUF;
+                // entries past the aligned end of idx (at most 3, at the end of
+                // the array) are copied with plain loads
+                for (int64_t e = a1 > t.a0 ? a1 : t.a0; e < t.e1; ++e) dst[e - t.a0] = s.idx[e];
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&mbar[b], (unsigned)bytes);
+                if (bytes > 0) bulk_copy_g2s(dst, s.idx + t.a0, (unsigned)bytes, &mbar[b]);
+            }
+        }
+        ++produced;
+        __syncwarp();
+    };
+
+    if (wib == 0) {
+        unsigned b0 = 0;
+        if (lane == 0) b0 = atomicAdd(&s.ctrl->row_next[bin], (unsigned)kRowBatch);
+        nxt_base = __shfl_sync(kFull, b0, 0);
+        nxt_v = list_at(nxt_base);
+        if (lane == 0) nn_base = atomicAdd(&s.ctrl->row_next[bin], (unsigned)kRowBatch);
+    }
+    __syncthreads();                                   // mbarriers initialised, table clear
+    if (wib == 0) {
+        for (int q = 0; q < kStages; ++q) produce();
+    }
+    __syncthreads();
+
+    // ---- consumer state ------------------------------------------------------
+    int32_t lab_cur[P], lab_nxt[P];
+    T w_cur[P], w_nxt[P];
+    // max-over-row path: this thread's best candidate of the row so far
+    unsigned long long bp_row = 0ull;
+    __shared__ unsigned long long blk_changed, blk_changed_entries;   // this block's changes (thread 0)
+    if (threadIdx.x == 0) blk_changed = blk_changed_entries = 0ull;
+
+    // Reads tile t's ids (buffer b, phase `par`) and issues their gathers; on
+    // the max-over-row path it keeps the ids themselves (the labels).  The
+    // descriptor is read into registers once.
+    auto load_tile = [&](const Tile& t, int b, unsigned par, int32_t (&lab)[P], T (&w)[P]) -> bool {
+        const int64_t e0 = t.e0;
+        const int32_t n = (int32_t)(t.e1 - e0);
+        const int32_t* src = ibuf + b * Sh::BUF + (int32_t)(e0 - t.a0);
+        const int32_t v = t.v;
+        const bool on = !t.skip;
+        if (!mbar_wait_bounded(&mbar[b], par)) return false;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const int r = p * NT + (int)threadIdx.x;
+            const bool in = on && r < n;
+            const int32_t j = in ? src[r] : v;
+            const bool ok = in && j != v;
+            lab[p] = ok ? (ident ? j : load_label<ASYNC>(L.C, j)) : kEmptyKey;
+            if constexpr (WK == W_UNIT) w[p] = ok ? (T)1 : (T)0;
+            else w[p] = ok ? load_weight<WK>(s.w, e0 + r) : (T)0;
+        }
+        return true;
+    };
+
+    bool alive = true;
+    {
+        const Tile& t0 = tiles[0];
+        if (t0.v >= 0 && !load_tile(t0, 0, 0u, lab_cur, w_cur)) {
+            atomicExch(&s.ctrl->error, 5);
+            abort_flag = 1;
+        }
+    }
+
+    for (unsigned k = 0;; ++k) {
+        __syncthreads();                               // step k-1 done: buffer k % kStages is free
+        if (abort_flag) {
+            alive = false;
+            break;
+        }
+        const Tile& tk = tiles[k % (2 * kStages)];
+        if (tk.v < 0) break;
+        if (wib == 0) produce();                       // tile k + kStages into buffer k % kStages
+        const Tile& tn = tiles[(k + 1) % (2 * kStages)];
+        if (tn.v >= 0 &&
+            !load_tile(tn, (int)((k + 1) % kStages), ((k + 1) / kStages) & 1u, lab_nxt, w_nxt)) {
+            atomicExch(&s.ctrl->error, 5);
+            abort_flag = 1;
+        }
+
+        // aggregate tile k into the table (its descriptor read once)
+        const int32_t v = tk.v;
+        const int32_t k_n = (int32_t)(tk.e1 - tk.e0);
+        const bool k_skip = tk.skip != 0;
+        const int64_t d = tk.en - tk.st;
+        const int log_full = ceil_log2((unsigned)(2 * d < ((int64_t)1 << 30) ? 2 * d : ((int64_t)1 << 30)));
+        const bool fits = log_full <= log_S;
+        const int log_s = fits ? log_full : log_S;
+        // one (label, weight) into the table; returns the slot it filled, or -1
+        auto insert = [&](int32_t label, T wsum) -> int {
+            int created = -1;
+            if (fits) {
+                if (!table_insert<T>(keys, vals, log_s, label, wsum, 1u << log_s, created))
+                    atomicExch(&s.ctrl->error, 3);
+            } else if (!overflow && !table_insert<T>(keys, vals, log_s, label, wsum, kSharedProbes, created)) {
+                overflow = 1;
+            }
+            return created;
+        };
+        auto list_created = [&](int created) {
+            const unsigned nm = __ballot_sync(kFull, created >= 0);
+            if (created >= 0) {
+                const unsigned pos = wfill + __popc(nm & lanes_below());
+                if (pos < seg_cap) my_seg[pos] = (uint16_t)created;
+            }
+            wfill += __popc(nm);
+        };
+        if (ident && !k_skip) {
+            // labels are the neighbour ids and occur once: a max over the row
+            const TieRule tr = tie_rule(s, NS, sweep, v);
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                if (lab_cur[p] != kEmptyKey) {
+                    const unsigned long long c = pack_candidate(sum_key(w_cur[p]), tr.key(lab_cur[p]));
+                    bp_row = c > bp_row ? c : bp_row;
+                }
+            }
+        }
+        if (!ident && !k_skip && (int)(wib * 32) < k_n) {
+            // Fast path: every entry this warp holds in the tile carries one
+            // label (after the first sweeps nearly every neighbour of a hub
+            // does) -- one reduction and one insert for the warp's share.
+            int32_t mine = kEmptyKey;
+            bool uni = true;
+            T tw = (T)0;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                if (lab_cur[p] != kEmptyKey) {
+                    uni = uni && (mine == kEmptyKey || mine == lab_cur[p]);
+                    mine = lab_cur[p];
+                    tw += w_cur[p];
+                }
+            }
+            const int32_t wl = __reduce_max_sync(kFull, mine);
+            if (__all_sync(kFull, uni && (mine == kEmptyKey || mine == wl))) {
+                if (wl != kEmptyKey) {
+                    T tot;
+                    if constexpr (WK == W_F32) {
+                        tot = tw;
+                        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(kFull, tot, o);
+                    } else {
+                        tot = __reduce_add_sync(kFull, tw);
+                    }
+                    list_created(lane == 0 ? insert(wl, tot) : -1);
+                }
+            } else {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    if (p * NT + (int)(wib * 32) >= k_n) break;       // warp-uniform
+                    const bool ok = lab_cur[p] != kEmptyKey;
+                    T wsum = w_cur[p];
+                    bool lead = ok;
+                    if constexpr (WK != W_F32) {
+                        const unsigned peers = __match_any_sync(kFull, lab_cur[p]);
+                        if constexpr (WK == W_UNIT) {
+                            wsum = (T)__popc(peers);
+                        } else {
+                            wsum = __reduce_add_sync(peers, wsum);
+                        }
+                        lead = ok && lane == (unsigned)(__ffs(peers) - 1);
+                    }
+                    list_created(lead ? insert(lab_cur[p], wsum) : -1);
+                }
+            }
+        }
+
+        if (tk.last) {
+            // ---- the row is complete: pick, record, mark --------------------
+            const TieRule tr = tie_rule(s, NS, sweep, v);
+            int32_t best_lab = -1;
+            int ovf = 0;
+            if (tk.skip) {
+                // a done graph's vertex keeps its label (batches)
+            } else if (ident) {
+                unsigned long long bp = warp_max_u64(bp_row);
+                bp_row = 0ull;
+                if (lane == 0) red_bp[wib] = bp;
+                __syncthreads();
+                bp = 0ull;
+#pragma unroll
+                for (int q = 0; q < NW; ++q) bp = red_bp[q] > bp ? red_bp[q] : bp;
+                best_lab = bp == 0ull ? -1 : tr.label(~(uint32_t)bp);
+            } else {
+                if (lane == 0) wpre[wib + 1] = wfill;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    unsigned acc = 0, mx = 0;
+                    wpre[0] = 0;
+                    for (int q = 1; q <= NW; ++q) {
+                        mx = wpre[q] > mx ? wpre[q] : mx;
+                        acc += wpre[q];
+                        wpre[q] = acc;
+                    }
+                    wpre[32] = mx;
+                }
+                wfill = 0;
+                __syncthreads();
+                const bool lists = wpre[32] <= seg_cap;
+                ovf = overflow;
+                // this thread's best candidate among the row's slots; clears them
+                bool any = false;
+                T best_w = 0;
+                uint32_t best_k = 0xffffffffu;
+                auto visit = [&](int q) {
+                    const int32_t kq = keys[q];
+                    if (kq != kEmptyKey) {
+                        const T vq = vals[q];
+                        const uint32_t tq = tr.key(kq);
+                        if (!any || vq > best_w || (vq == best_w && tq < best_k)) {
+                            any = true;
+                            best_w = vq;
+                            best_k = tq;
+                        }
+                        keys[q] = kEmptyKey;
+                        vals[q] = (T)0;
+                    }
+                };
+                if (lists) {
+                    const unsigned total = wpre[NW];
+                    for (unsigned f = threadIdx.x; f < total; f += NT) {
+                        int q = 0;
+                        while (q + 1 < NW && wpre[q + 1] <= f) ++q;
+                        visit(segs[(size_t)q * seg_cap + (f - wpre[q])]);
+                    }
+                } else {
+                    for (int q = threadIdx.x; q < (1 << log_s); q += NT) visit(q);
+                }
+                const uint32_t best_tie =
+                    rows_block_argmax(any ? sum_key(best_w) : 0u, best_k, red_key, red_tie, &winner);
+                best_lab = best_tie == 0xffffffffu ? -1 : tr.label(best_tie);
+            }
+            if (ovf) {
+                // hand the row to the partitioned kernels (last bin only)
+                if (threadIdx.x == 0) {
+                    Overflow& o = s.ovf[atomicAdd(&s.ctrl->ovf_count, 1ull)];
+                    o.v = v;
+                    o.slot = tk.k;
+                    o.st = tk.st;
+                    o.d = (int32_t)d;
+                    o.own = tk.own;
+                    o.parts = (uint32_t)((2 * d + S - 1) / S);
+                    o.best = 0ull;
+                    o.done = 0u;
+                    overflow = 0;
+                }
+            } else {
+                const bool changed = best_lab >= 0 && best_lab != tk.own;     // block-uniform
+                if (threadIdx.x == 0) record_label<ASYNC>(L, bv.chg + tk.k, v, tk.own, tk.skip ? tk.own : best_lab,
+                                                          changed);
+                if (changed) {
+                    if (threadIdx.x == 0) {
+                        ++blk_changed;
+                        blk_changed_entries += (unsigned long long)d;
+                        if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
+                    }
+                    if (marks) {
+                        for (int64_t e = tk.st + threadIdx.x; e < tk.en; e += NT) {
+                            const int32_t j = s.idx[e];
+                            if (j != v && !(po && load_label<ASYNC>(L.C, j) == best_lab)) mark_unprocessed(s.flags, j);
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            lab_cur[p] = lab_nxt[p];
+            w_cur[p] = w_nxt[p];
+        }
+
+    }
+    if (!alive && threadIdx.x == 0) {
+        // let the copies this block started land before it leaves
+        for (unsigned q = produced >= kStages ? produced - kStages : 0; q < produced; ++q)
+            if (tiles[q % (2 * kStages)].v >= 0) (void)mbar_wait_bounded(&mbar[q % kStages], (q / kStages) & 1u);
+    }
+    __syncthreads();
+    flush_bin_counts(s, bin, threadIdx.x == 0 ? blk_changed : 0ull, threadIdx.x == 0 ? blk_changed_entries : 0ull);
+}
+
+// Dynamic shared memory: two index buffers, the table (S keys, S values) and
+// the filled-slot lists (S / 2 two-byte entries).
+template <int NT, int WK>
+static size_t rows_smem(int S) {
+    return (size_t)kStages * RowsShape<NT, WK>::BUF * 4 + (size_t)S * 8 + (size_t)S;
+}
+
+template <bool ASYNC, int WK, bool BATCH, bool NS, int NT>
+static cudaError_t launch_rows_nt(const DevState& s, int bin, int flag, int sms, cudaStream_t st, int* blocks_out) {
+    const size_t smem = rows_smem<NT, WK>(s.block_slots[bin - 2]);
+    auto kern = k_sweep_rows<ASYNC, WK, BATCH, NS, NT>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = sms * (per_sm > 0 ? per_sm : 1);
+    *blocks_out = blocks;
+    kern<<<blocks, NT, smem, st>>>(s, bin, flag);
+    return cudaGetLastError();
+}
+
+template <bool ASYNC, int WK, bool BATCH, bool NS>
+cudaError_t launch_rows(const DevState& s, int bin, int flag, int sms, cudaStream_t st, int* blocks_out) {
+    switch (bin) {
+        case 2: return launch_rows_nt<ASYNC, WK, BATCH, NS, 128>(s, bin, flag, sms, st, blocks_out);
+        case 3: return launch_rows_nt<ASYNC, WK, BATCH, NS, 256>(s, bin, flag, sms, st, blocks_out);
+        default: return launch_rows_nt<ASYNC, WK, BATCH, NS, 512>(s, bin, flag, sms, st, blocks_out);
+    }
+}
+
+#define LPA_ROWS_INST(A, W, B, N) \
+    template cudaError_t launch_rows<A, W, B, N>(const DevState&, int, int, int, cudaStream_t, int*);
+#define LPA_ROWS_INST_W(A, B, N) \
+    LPA_ROWS_INST(A, W_UNIT, B, N) LPA_ROWS_INST(A, W_U32, B, N) LPA_ROWS_INST(A, W_U8, B, N) LPA_ROWS_INST(A, W_F32, B, N)
+LPA_ROWS_INST_W(false, false, false)
+LPA_ROWS_INST_W(false, false, true)
+LPA_ROWS_INST_W(false, true, false)
+LPA_ROWS_INST_W(false, true, true)
+LPA_ROWS_INST_W(true, false, false)
+LPA_ROWS_INST_W(true, false, true)
+LPA_ROWS_INST_W(true, true, false)
+LPA_ROWS_INST_W(true, true, true)
+#undef LPA_ROWS_INST_W
+#undef LPA_ROWS_INST
+
+}  // namespace lpa

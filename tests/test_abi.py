@@ -48,6 +48,7 @@ def test_pure_host_entry_points(lib_path):
     lpa.load(lib_path)
     assert lpa.lpa_version().startswith("lpa-gb300")
     assert lpa.lpa_status_string(lpa.LPA_ERR_INVALID_GRAPH) == "invalid graph"
+    lpa.lpa_autotune_cache_clear()                      # host only
     # argument checks happen before any CUDA call
     with pytest.raises(lpa.LpaError) as e:
         lpa.lpa_graph_create(-5, 0, None, None)
@@ -111,7 +112,7 @@ def test_struct_layouts_match_c(lib_path):
 
 _C_STRUCTS = {"LpaRunInfo": "lpa_run_info", "LpaGraphProps": "lpa_graph_props", "LpaConfig": "lpa_config",
               "LpaProfile": "lpa_profile", "LpaServeConfig": "lpa_serve_config",
-              "LpaServeStats": "lpa_serve_stats_t"}
+              "LpaServeStats": "lpa_serve_stats_t", "LpaAutotuneInfo": "lpa_autotune_info"}
 
 
 def test_header_is_plain_c_and_layouts_match_the_binding(lib_path, tmp_path):

@@ -30,7 +30,7 @@ def test_sync_bytes_by_hand():
     assert out["k_sweep_small"]["bytes"] == small
     assert out["k_sweep_small"]["launches"] == 2 and out["k_sweep_small"]["ms"] == 1.5
     # statically empty bins are never launched: no bytes, time or launches
-    for b in ("k_sweep_block128", "k_sweep_block256"):
+    for b in ("k_sweep_rows<128>", "k_sweep_rows<256>"):
         assert out[b] == {"bytes": 0.0, "ms": 0.0, "launches": 0}
 
 
@@ -38,7 +38,7 @@ def test_first_sync_sweep_of_repeat_free_graph_reads_no_labels():
     plain = bench.kernel_bytes(_profile(), wbytes=0, sync=True, passes=1)
     rf = bench.kernel_bytes(_profile(), wbytes=0, sync=True, passes=1, rows_distinct=True)
     # only sweep 0 drops the 4 B label gather per entry
-    for b, e0 in (("k_sweep_small", 30), ("k_sweep_warp", 100), ("k_sweep_block512", 5000)):
+    for b, e0 in (("k_sweep_small", 30), ("k_sweep_warp", 100), ("k_sweep_rows<512>", 5000)):
         assert plain[b]["bytes"] - rf[b]["bytes"] == 4 * e0
 
 
@@ -109,3 +109,18 @@ def test_both_arms_share_modes_and_config():
     for mode, (C, it, ch) in want.items():
         C2, it2, ch2 = bench.oracle_run(g, mode, 20)
         assert C2.tolist() == C.tolist() and it2 == it and ch2.tolist() == ch.tolist(), mode
+
+
+def test_oracle_row_sample_times_the_sampled_rows():
+    """The CPU baseline of a graph too large for a whole oracle sweep times
+    the oracle's first sweep over a contiguous range of rows: the entries it
+    reports are exactly those rows' entries, and the range starts where asked."""
+    import lpa_inputs as L
+    g = L.rmat(13, 16, seed=2)
+    for mode in ("async", "sync"):
+        e, t, (v0, v1) = bench.oracle_rows_sample(g, mode, 1000, 20_000)
+        assert v0 == 1000 and e == int(g.off[v1] - g.off[v0]) >= 20_000 and t > 0
+    e, t, (v0, v1) = bench.oracle_rows_baseline(g, "async", target_s=0.05)
+    assert e == int(g.off[v1] - g.off[v0]) and v0 == g.n // 3
+    info = bench.host_cpu()
+    assert info["nproc"] >= 1

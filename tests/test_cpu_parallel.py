@@ -1,14 +1,15 @@
 """The multi-core CPU baseline (cpu_parallel, the paper's OpenMP design):
 its synchronous runs must equal the oracle's exactly (pruning and thread
 interleaving cannot change a Jacobi sweep with the strict tie-break), and its
-asynchronous runs must meet the invariants and modularity floor the GPU's do,
-and on one thread equal the serial ascending run."""
+asynchronous runs must meet the invariants, reach the serial ascending run's
+modularity (the order its chunks are walked in) less 0.02, and on one thread
+equal the serial ascending run."""
 import numpy as np
 
 import cpu_parallel as CP
 import lpa_inputs as L
 import oracle as O
-from async_bounds import async_floor
+from async_bounds import SLACK, ascending_q, serial_qs
 
 
 def _graphs():
@@ -29,8 +30,12 @@ def test_async_invariants():
         got, it, _ = CP.run(g.off, g.idx, g.w, "async", n_threads=4)
         assert 1 <= it <= 20
         assert O.count_labels_outside_component(g.off, g.idx, got) == 0
-        # the paper's chunked ascending design can end like a monotone serial run
-        assert O.modularity(g.off, g.idx, g.w, got) >= async_floor(g, include_monotone=True), g.n
+        # the paper's design walks contiguous chunks in ascending order, so it
+        # is held to the serial ascending run (or to the random-order runs
+        # where those are lower): on id-ordered planted partitions the
+        # ascending run ends as one community
+        floor = min(ascending_q(g), min(serial_qs(g))) - SLACK
+        assert O.modularity(g.off, g.idx, g.w, got) >= floor, g.n
 
 
 def test_async_on_one_thread_is_the_serial_ascending_run():

@@ -111,3 +111,20 @@ def test_road_grid_drop_and_shortcut_rates():
     assert abs(kept / n_lattice - 0.90) < 0.01
     shortcuts = int((~lattice).sum())
     assert abs(shortcuts - 0.001 * kept) <= max(5, 0.2 * 0.001 * kept)
+
+
+def test_row_range_sample_keeps_the_rows_in_order():
+    """The sample holds exactly rows [v0, v1) with their neighbours relabelled
+    in increasing order of their ids (so comparisons of ids, and with them the
+    smallest-id tie-break, are unchanged), and at least the asked-for entries."""
+    g = L.rmat(12, 16, seed=3)
+    v0 = 700
+    s, v1, ids = L.row_range_sample(g, v0, 5000)
+    assert s.nnz == g.off[v1] - g.off[v0] >= 5000 and g.off[v1 - 1] - g.off[v0] < 5000
+    assert np.all(np.diff(ids) > 0)
+    for v in (v0, (v0 + v1) // 2, v1 - 1):
+        k = int(np.searchsorted(ids, v))
+        assert ids[k] == v
+        assert np.array_equal(ids[s.idx[s.off[k]:s.off[k + 1]]], g.idx[g.off[v]:g.off[v + 1]])
+    sampled = np.isin(ids, np.arange(v0, v1))
+    assert np.all(np.diff(s.off)[~sampled] == 0)
