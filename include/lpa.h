@@ -98,6 +98,28 @@ typedef enum {
                                16-byte aligned are copied all the same (the sweeps move index rows
                                with 16-byte bulk copies) */
 
+/* Storage order of the vertices (lpa_graph_create / lpa_batch_create flags,
+ * at most one).  The library may store a graph's vertices in an order of its
+ * own; labels in and out are always the caller's vertex ids, initial labels
+ * are the ids (Algorithm 1) and ties go by id, so results are those of the
+ * caller's graph: LPA_MODE_SYNC gives the same labels in every order, and
+ * the asynchronous modes differ only in the order the parallel sweep meets
+ * the vertices (Algorithm 1 leaves that order open).  A reordered graph is a
+ * library copy even when LPA_BORROW is given.
+ *   LPA_REORDER_DEGREE   single graphs: vertices by decreasing degree bucket
+ *                        ceil(log2 d), then by id -- the labels that most
+ *                        gathers read sit together in memory and in L2
+ *   LPA_REORDER_SHUFFLE  each graph's vertices in a pseudo-random order of
+ *                        their own (a Feistel permutation of its id range):
+ *                        the asynchronous sweep, which walks stored vertices
+ *                        in order, then meets a graph's vertices in a random
+ *                        order even when the graph spans many waves of warps.
+ *                        The default of lpa_batch_create.
+ *   LPA_KEEP_ORDER       lpa_batch_create: keep the caller's order. */
+#define LPA_REORDER_DEGREE  4u
+#define LPA_REORDER_SHUFFLE 8u
+#define LPA_KEEP_ORDER      16u
+
 /* Per-sweep history kept in lpa_run_info (sweeps beyond this are still run). */
 #define LPA_MAX_RECORDED_ITERS 64
 /* Degree bins of lpa_config (thread, warp, three block sizes). */
@@ -131,10 +153,10 @@ typedef struct {
     int64_t scanned_total; /* CSR entries scanned by those sweeps */
     int64_t launches_total;/* kernel launches of the lpa_run calls on this handle */
     int32_t rows_distinct; /* 1: a single graph whose every row lists its neighbours in strictly
-                              increasing order (so none twice); the first LPA_MODE_SYNC sweep then
-                              reads no labels (each still equals its vertex id) and takes the
-                              heaviest entry of each row.  0 for batches and other graphs. */
-    int32_t reserved;
+                              increasing order as given (so none twice); the first LPA_MODE_SYNC
+                              sweep then reads no labels (each is still its vertex's id) and takes
+                              the heaviest entry of each row.  0 for batches and other graphs. */
+    int32_t storage_order; /* 0: the caller's order, 1: LPA_REORDER_DEGREE, 2: LPA_REORDER_SHUFFLE */
 } lpa_graph_props;
 
 /* Launch parameters of the sweep.  Vertices are binned by degree d:
@@ -214,7 +236,8 @@ lpa_status lpa_tolerance_threshold(double tolerance, int64_t n, int64_t *out);
  *   weights   float32[nnz] finite and >= 0, or NULL for unit weights (the
  *             paper's setting, Table 1).  Symmetry is the caller's contract
  *             and is not checked.
- *   flags     LPA_HOST_PTRS | LPA_DEVICE_PTRS, optionally | LPA_BORROW
+ *   flags     LPA_HOST_PTRS | LPA_DEVICE_PTRS, optionally | LPA_BORROW, optionally one storage
+ *             order (LPA_REORDER_DEGREE, LPA_REORDER_SHUFFLE)
  * Validates the CSR on the device (returns LPA_ERR_INVALID_GRAPH on failure)
  * and synchronises `stream` before returning.  Device memory: the CSR copy
  * (unless borrowed) plus about 21 bytes per vertex of working state (two
@@ -337,7 +360,9 @@ lpa_status lpa_modularity_noalloc(int64_t n, int64_t nnz, const int64_t *offsets
  *   indices         int32[E], LOCAL vertex ids of the entry's own graph
  *   weights         float32[E] or NULL
  *   flags           as lpa_graph_create (LPA_BORROW is not accepted: indices
- *                   are rewritten to global ids in the library's copy)
+ *                   are rewritten to global ids in the library's copy); each
+ *                   graph's vertices are stored shuffled (LPA_REORDER_SHUFFLE)
+ *                   unless LPA_KEEP_ORDER is given
  * Synchronises `stream`. */
 lpa_status lpa_batch_create(int32_t G, const int64_t *graph_vtx_off, const int64_t *graph_edge_off,
                             const int64_t *offsets, const int32_t *indices, const float *weights,

@@ -39,6 +39,9 @@ MODES = {"sync": LPA_MODE_SYNC, "async": LPA_MODE_ASYNC, "sync_full": LPA_MODE_S
 LPA_HOST_PTRS = 0
 LPA_DEVICE_PTRS = 1
 LPA_BORROW = 2
+LPA_REORDER_DEGREE = 4
+LPA_REORDER_SHUFFLE = 8
+LPA_KEEP_ORDER = 16
 LPA_NONSTRICT = 0x100
 LPA_PRUNE_OTHER = 0x200
 
@@ -65,7 +68,8 @@ class LpaGraphProps(ctypes.Structure):
                 ("weighted", ctypes.c_int32), ("exact", ctypes.c_int32), ("weight_bytes", ctypes.c_int32),
                 ("max_degree", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("sweeps_total", ctypes.c_int64), ("scanned_total", ctypes.c_int64),
-                ("launches_total", ctypes.c_int64), ("rows_distinct", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("launches_total", ctypes.c_int64), ("rows_distinct", ctypes.c_int32),
+                ("storage_order", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblpa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lpa_sweep_small.cu", "lpa_sweep_warp.cu", "lpa_sweep_block.cu", "lpa_sweep_rows.cu", "lpa_frontier.cu",
-           "lpa_api.cu", "lpa_noalloc.cu", "lpa_serve.cu"]
+           "lpa_reorder.cu", "lpa_api.cu", "lpa_noalloc.cu", "lpa_serve.cu"]
 HEADERS = ["lpa_internal.h", "lpa_device.cuh"]
 
 

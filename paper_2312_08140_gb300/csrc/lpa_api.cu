@@ -150,6 +150,7 @@ struct Engine {
     std::vector<int64_t> vtx_off_host;
     std::vector<int64_t> edge_off_host;
     unsigned long long* hist_d = nullptr;          // degree histogram scratch (autotuner)
+    int order = kOrderCaller;                      // storage order of the vertices (StorageOrder)
     int32_t* tune_out = nullptr;                   // labels of the autotuner's timed runs
     int64_t runs_total = 0;          // lpa_run calls that launched the device loop
 };
@@ -289,13 +290,71 @@ lpa_status alloc_state(Engine& E, cudaStream_t st) {
     return LPA_OK;
 }
 
+// Frees one of the engine's own allocations before the engine is destroyed.
+void release_owned(Engine& E, void* p, int64_t bytes) {
+    auto it = std::find(E.owned.begin(), E.owned.end(), p);
+    if (it == E.owned.end()) return;
+    E.owned.erase(it);
+    std::vector<void*> one{p};
+    pool_free_all(E.device, one);
+    E.device_bytes -= bytes;
+}
+
+// Stores the vertices in `kind` order (lpa_reorder.cu): orig, and the CSR
+// rewritten in that order, replace the engine's arrays (the caller's arrays
+// of a borrowed graph are left as they are); the static lists are rebuilt.
+lpa_status apply_order(Engine& E, int kind, cudaStream_t st) {
+    const int64_t n = E.s.N, nnz = E.s.E;
+    lpa_status rs;
+    int32_t *orig = nullptr, *inv = nullptr, *idx2 = nullptr;
+    unsigned* scr = nullptr;
+    int64_t* off2 = nullptr;
+    void* w2 = nullptr;
+    const int wbytes = E.s.weight_kind == W_UNIT ? 0 : E.s.weight_kind == W_U8 ? 1 : 4;
+    const int64_t scr_words = reorder_scratch_words(n);
+    if ((rs = dalloc_t(E, &orig, (size_t)n)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &inv, (size_t)n)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &scr, (size_t)scr_words)) != LPA_OK) return rs;
+    LPA_CUDA(reorder_positions(kind, E.s.off, E.s.vtx_off, E.s.gid, E.s.G, n, 0x5EEDC0DE2312ull, orig, inv, scr, st,
+                               E.sms));
+    if ((rs = dalloc_t(E, &off2, (size_t)n + 1)) != LPA_OK) return rs;
+    if ((rs = dalloc_t(E, &idx2, (size_t)std::max<int64_t>(nnz, 1))) != LPA_OK) return rs;
+    if (wbytes && (rs = dalloc(E, &w2, (size_t)std::max<int64_t>(nnz, 1) * wbytes)) != LPA_OK) return rs;
+    LPA_CUDA(reorder_rows(orig, inv, E.s.off, E.s.idx, E.s.w, wbytes, n, off2, idx2, w2,
+                          reinterpret_cast<unsigned long long*>(scr), st, E.sms));
+    release_owned(E, inv, n * 4);
+    release_owned(E, scr, scr_words * 4);
+    // the library's own copies of the caller's order (borrowed arrays are not
+    // among the engine's allocations and stay untouched)
+    release_owned(E, const_cast<int64_t*>(E.s.off), (n + 1) * 8);
+    release_owned(E, const_cast<int32_t*>(E.s.idx), nnz * 4);
+    if (E.s.w) release_owned(E, const_cast<void*>(E.s.w), nnz * wbytes);
+    E.s.off = off2;
+    E.s.off_end = off2 + 1;
+    E.s.idx = idx2;
+    E.s.w = w2;
+    E.s.orig = orig;
+    E.order = kind;
+    LPA_CUDA(build_static_lists(E.s, st, E.static_counts, E.static_ents));
+    return LPA_OK;
+}
+
 // Common creation path: G graphs (G == 1 for lpa_graph_create).
 lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const int64_t* edge_off_h, int64_t n,
                          int64_t nnz, const int64_t* offsets, const int32_t* indices, const float* weights,
                          uint32_t flags, cudaStream_t st) {
     const bool dev = (flags & LPA_DEVICE_PTRS) != 0;
     const bool borrow = (flags & LPA_BORROW) != 0;
-    if (flags & ~(LPA_DEVICE_PTRS | LPA_BORROW)) return fail(LPA_ERR_INVALID_ARG, "unknown flag bits");
+    const uint32_t known = LPA_DEVICE_PTRS | LPA_BORROW | LPA_REORDER_DEGREE | LPA_REORDER_SHUFFLE | LPA_KEEP_ORDER;
+    if (flags & ~known) return fail(LPA_ERR_INVALID_ARG, "unknown flag bits");
+    const int n_orders = ((flags & LPA_REORDER_DEGREE) ? 1 : 0) + ((flags & LPA_REORDER_SHUFFLE) ? 1 : 0) +
+                         ((flags & LPA_KEEP_ORDER) ? 1 : 0);
+    if (n_orders > 1) return fail(LPA_ERR_INVALID_ARG, "at most one storage-order flag");
+    if ((flags & LPA_REORDER_DEGREE) && G > 1)
+        return fail(LPA_ERR_INVALID_ARG, "LPA_REORDER_DEGREE is for single graphs");
+    int order = kOrderCaller;
+    if (flags & LPA_REORDER_DEGREE) order = kOrderDegree;
+    else if ((flags & LPA_REORDER_SHUFFLE) || (G > 1 && !(flags & LPA_KEEP_ORDER))) order = kOrderShuffle;
     if (borrow && !dev) return fail(LPA_ERR_INVALID_ARG, "LPA_BORROW needs LPA_DEVICE_PTRS");
     if (borrow && G > 1) return fail(LPA_ERR_INVALID_ARG, "LPA_BORROW is not accepted for batches");
     if (n < 0 || n > 0x7fffffffLL) return fail(LPA_ERR_INVALID_ARG, "n out of range [0, 2^31-1]");
@@ -447,6 +506,7 @@ lpa_status engine_create(Engine& E, int32_t G, const int64_t* vtx_off_h, const i
         E.s.weight_kind = W_F32;
     }
     E.s.w = w_d;
+    if (order != kOrderCaller && n > 0 && (rs = apply_order(E, order, st)) != LPA_OK) return rs;
     if ((rs = setup_blocks(E, st)) != LPA_OK) return rs;
     LPA_CUDA(cudaStreamSynchronize(st));
     return LPA_OK;
@@ -801,6 +861,7 @@ lpa_status fill_props(const Engine& E, lpa_graph_props* p) {
     p->exact = E.exact ? 1 : 0;
     p->max_degree = E.max_degree;
     p->rows_distinct = E.s.rows_distinct;
+    p->storage_order = E.order;
     p->device_bytes = E.device_bytes + (int64_t)std::max<size_t>(E.s.bin_static[kBins - 1], 1) * sizeof(Overflow);
     return LPA_OK;
 }

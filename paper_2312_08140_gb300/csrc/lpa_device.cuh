@@ -80,6 +80,13 @@ __device__ __forceinline__ bool identity_sweep(const DevState& s) {
     }
 }
 
+// The label vertex v starts with (Algorithm 1: C_i = i): its original id.
+// Vertices may be stored in another order (lpa_graph_create's storage
+// orders); labels are original ids whatever the order.
+__device__ __forceinline__ int32_t initial_label(const DevState& s, int32_t v) {
+    return s.orig ? __ldg(s.orig + v) : v;
+}
+
 // One candidate packed for a 64-bit max: sum key above, complemented tie key
 // below, so the larger sum wins and then the smaller tie key.  0 = none.
 __device__ __forceinline__ unsigned long long pack_candidate(uint32_t key, uint32_t tie) {
@@ -156,9 +163,9 @@ struct TieRule {
     }
 };
 
-// Rule for vertex v; ns and sweep (the single graph's 1-based sweep) are read
-// from the control block once per kernel.  In a batch each graph counts its
-// own sweeps.
+// Rule for (stored) vertex v, drawn with its original id; ns and sweep (the
+// single graph's 1-based sweep) are read from the control block once per
+// kernel.  In a batch each graph counts its own sweeps.
 __device__ __forceinline__ TieRule tie_rule(const DevState& s, bool ns, uint32_t sweep, int32_t v) {
     TieRule t;
     t.r = 0;
@@ -175,7 +182,8 @@ __device__ __forceinline__ TieRule tie_rule(const DevState& s, bool ns, uint32_t
     }
     t.v0 = (int32_t)v0;
     t.n = (uint32_t)n;
-    t.r = (uint32_t)(splitmix64(((uint64_t)sweep << 32) | (uint64_t)(v - v0)) % (uint64_t)n);
+    const int32_t vid = initial_label(s, v);       // the vertex's original id
+    t.r = (uint32_t)(splitmix64(((uint64_t)sweep << 32) | (uint64_t)(vid - v0)) % (uint64_t)n);
     return t;
 }
 

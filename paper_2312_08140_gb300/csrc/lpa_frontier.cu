@@ -40,8 +40,9 @@ __global__ void k_init(DevState s) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = tid; i < s.N; i += stride) {
-        s.lab[0][i] = (int32_t)i;      // C <- [0 .. |V|) (Algorithm 1), in both buffers
-        s.lab[1][i] = (int32_t)i;
+        const int32_t c0 = initial_label(s, (int32_t)i);   // C <- [0 .. |V|) (Algorithm 1), in both buffers
+        s.lab[0][i] = c0;
+        s.lab[1][i] = c0;
         s.flags[i] = 0;
     }
     Ctrl* c = s.ctrl;
@@ -628,7 +629,7 @@ __global__ void k_finalize(DevState s) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s.N; i += stride) {
         int32_t c = C[i];
         if (local && s.G > 1) c -= (int32_t)s.g_begin[s.gid[i]];
-        out[i] = c;
+        out[initial_label(s, (int32_t)i)] = c;      // back to the caller's vertex order
     }
 }
 
@@ -913,8 +914,11 @@ __global__ void k_mod_rows(DevState s, int64_t v0, int64_t v1, const int32_t* la
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double my_two_m = 0.0, my_sigma = 0.0;
+    // labels are given in the caller's vertex order: stored vertex u holds
+    // the label of its original id
+    auto label_of = [&](int64_t u) -> int32_t { return labels[(int64_t)initial_label(s, (int32_t)u) - v0]; };
     for (int64_t i = warp; i < nloc; i += nwarps) {
-        const int32_t ci = labels[i];
+        const int32_t ci = label_of(v0 + i);
         if (ci < 0 || ci >= nloc) {
             if (lane == 0) atomicAdd(&acc->bad_label, 1u);
             continue;
@@ -925,7 +929,7 @@ __global__ void k_mod_rows(DevState s, int64_t v0, int64_t v1, const int32_t* la
             const double w = weight_f64(s, e);
             K += w;
             const int64_t j = (int64_t)s.idx[e] - v0;
-            if (j >= 0 && j < nloc && labels[j] == ci) sg += w;
+            if (j >= 0 && j < nloc && label_of(v0 + j) == ci) sg += w;
         }
         for (int o = 16; o > 0; o >>= 1) {
             K += __shfl_xor_sync(kFull, K, o);

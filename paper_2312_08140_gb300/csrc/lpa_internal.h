@@ -135,6 +135,8 @@ struct DevState {
     const int32_t* idx;        // [E] global vertex ids
     const void* w;             // [E] uint8 (W_U8), uint32 (W_U32), float (W_F32) or null (W_UNIT)
     const int32_t* gid;        // [N] graph of each vertex, null when G == 1
+    const int32_t* orig;       // [N] original (global) id of each stored vertex, null when the vertices
+                               // are stored in the caller's order.  Labels are always original ids.
     const int64_t* vtx_off;    // [G+1] (batches)
     const int64_t* g_begin;    // [G] first vertex of graph g (vtx_off for batches)
     const int64_t* g_end;      // [G] one past its last vertex (vtx_off + 1 for batches)
@@ -225,6 +227,22 @@ cudaError_t launch_rows(const DevState& s, int bin, int flag, int sms, cudaStrea
 // kDegBuckets], cleared here).
 constexpr int kDegBuckets = 40;
 cudaError_t launch_degree_hist(const DevState& s, unsigned long long* hist, cudaStream_t st, int sms);
+
+// Storage orders (lpa_reorder.cu): the vertices of a graph may be stored in
+// an order of their own while labels stay original ids.
+enum StorageOrder : int { kOrderCaller = 0, kOrderDegree = 1, kOrderShuffle = 2 };
+// orig[p] (original id of stored vertex p) and inv[v] (stored position of
+// original vertex v) for the order; scratch: reorder_scratch_words(N)
+// unsigned words.  Synchronises st.
+cudaError_t reorder_positions(int kind, const int64_t* off, const int64_t* vtx_off, const int32_t* gid, int32_t G,
+                              int64_t N, uint64_t seed, int32_t* orig, int32_t* inv, unsigned* scratch,
+                              cudaStream_t st, int sms);
+int64_t reorder_scratch_words(int64_t N);
+// The CSR in stored order: new_off[N+1], new_idx (neighbours renumbered
+// through inv), new_w (wbytes 0, 1 or 4 per entry).  Synchronises st.
+cudaError_t reorder_rows(const int32_t* orig, const int32_t* inv, const int64_t* off, const int32_t* idx,
+                         const void* w, int wbytes, int64_t N, int64_t* new_off, int32_t* new_idx, void* new_w,
+                         unsigned long long* scratch, cudaStream_t st, int sms);
 
 // Graph validation (row-wise).  Results accumulate into *res (device).
 struct ValidateResult {

@@ -1,33 +1,21 @@
-// lpa_sweep_block.cu -- sweep for vertices with degree above warp_max: one
-// thread block per frontier vertex, the block size growing with the degree
-// bin (128 threads up to mid_max, 256 up to large_max, 512 above) so that the
-// shared table (2^ceil(log2(2d)) slots) per warp stays about constant and the
-// SM keeps enough warps in flight.
+// lpa_sweep_block.cu -- the rows of the last degree bin whose distinct labels
+// overflow the shared table of the block-per-row kernel (lpa_sweep_rows.cu),
+// and the launcher of the block bins.
 //
-// Warps read the row in 32-entry chunks and group equal labels with
-// __match_any_sync as in the warp kernel; group leaders add their sums into a
-// shared-memory open-addressing table and list the slots they fill; the block
-// then scans the listed slots and reduces (sum, smallest label) to the winner
-// (Eq. 2; Section 4.1.5) and, on change, marks the neighbours unprocessed
-// (Section 4.1.4).
-//
-// Last bin (d > large_max): the table has kLargeSlots slots.  Rows longer than
-// kLargeSlots / 2 may carry more distinct labels than it holds; their inserts
-// probe a bounded number of slots and, if one fails, the block stops and
-// appends the row to an overflow list.  The row's labels are then split over parts = ceil(2d / kLargeSlots) hash
-// partitions (about d / parts distinct labels each at most, half of the
+// An overflowing row's labels are split over parts = ceil(2d / kLargeSlots)
+// hash partitions (about d / parts distinct labels each at most, half of the
 // table, so an insert always finds a slot): the row is read once in slices
 // grouped by partition (k_ovf_slices) and aggregated by one block per
-// partition (k_ovf_parts); rows beyond the sliced path's limits are rescanned
-// by one block per partition (k_sweep_parts).
-// Each partition's winner is folded into a 64-bit atomicMax of
-// (sum << 32 | ~tie key) -- larger sum first, then the tie-break -- and the
-// block that completes the row applies the result.  No block waits on another.
+// partition (k_ovf_parts); rows beyond that path's limits are rescanned by one
+// block per partition (k_sweep_parts).  Each partition's winner is folded
+// into a 64-bit atomicMax of (sum << 32 | ~tie key) -- larger sum first, then
+// the tie-break (Eq. 2; Section 4.1.5) -- and the block that completes the
+// row applies the result and marks the neighbours (Section 4.1.4).  No block
+// waits on another.
 #include "lpa_device.cuh"
 
 namespace lpa {
 
-constexpr int kSharedProbes = 16;
 constexpr int kUnroll = 4;          // chunks of 32 entries in flight per warp
 constexpr int kSliceThreads = 512;  // blocks of the sliced overflow path
 
@@ -54,19 +42,6 @@ __device__ __forceinline__ uint32_t block_argmax(uint32_t key, uint32_t tie, uin
     }
     __syncthreads();
     return *winner;
-}
-
-// Each warp lists the table slots it fills for the current row in its own
-// segment of `seg_cap` entries (no atomics: the count is the same register in
-// every lane).  All 32 lanes call; entries past the segment are dropped (the
-// count still grows, which sends the scan to the whole table).
-__device__ __forceinline__ void list_filled(int created, uint16_t* seg, unsigned seg_cap, unsigned& wfill) {
-    const unsigned nm = __ballot_sync(kFull, created >= 0);
-    if (created >= 0) {
-        const unsigned pos = wfill + __popc(nm & lanes_below());
-        if (pos < seg_cap) seg[pos] = (uint16_t)created;
-    }
-    wfill += __popc(nm);
 }
 
 // This thread's best candidate of the row's table under the row's tie rule
@@ -118,219 +93,6 @@ __device__ __forceinline__ void mark_neighbours(const DevState& s, int32_t v, in
         const int32_t j = s.idx[e];
         if (j != v && !(po && load_label<ASYNC>(C, j) == best)) mark_unprocessed(s.flags, j);
     }
-}
-
-// LAST selects the last bin's variant:
-//  * chunks in flight per warp U: 4 in the last bin, whose rows span many
-//    chunks per warp; 1 in the middle bins, where the SM's 64 warps already
-//    overlap the few chunks of each row;
-//  * middle bins list the table slots each warp fills and scan only those;
-//    the last bin's rows fill many slots, and its table is scanned whole;
-//  * the last bin takes rows one at a time from a counter, so a block holding
-//    a long row does not also hold a fixed share of the others (a static split
-//    left the busiest R-MAT block with 2.4x the mean work); the middle bins'
-//    rows are short and bounded, and are split statically.
-template <bool ASYNC, int WK, bool BATCH, bool NS, bool LAST>
-__global__ void __launch_bounds__(512, 4) k_sweep_block(DevState s, int bin, int flag_neighbours) {
-    constexpr int U = LAST ? kUnroll : 1;
-    constexpr bool LISTS = !LAST;
-    using T = typename Acc<WK>::T;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int S = s.block_slots[bin - 2];
-    int32_t* keys = reinterpret_cast<int32_t*>(smem_raw);
-    T* vals = reinterpret_cast<T*>(keys + S);
-    // per-warp lists of the slots a row filled: S / 2 entries in nw segments
-    const unsigned seg_cap = (unsigned)S / 2u / (blockDim.x >> 5);
-    uint16_t* segs = reinterpret_cast<uint16_t*>(vals + S);
-    uint16_t* my_seg = segs + (size_t)(threadIdx.x >> 5) * seg_cap;
-    unsigned wfill = 0;
-    __shared__ unsigned wpre[33];      // [0, nw]: prefix sums of the warps' counts; [32]: the largest count
-    static_assert(kBlockThreads[kBlockBins - 1] / 32 < 32, "wpre holds nw + 1 prefix sums and the maximum");
-    __shared__ uint32_t red_key[32];
-    __shared__ uint32_t red_tie[32];
-    __shared__ int overflow;
-    __shared__ uint32_t winner;
-    __shared__ unsigned long long red_bp[32];
-    __shared__ unsigned long long win_bp;
-
-    const unsigned lane = lane_id();
-    const int wib = threadIdx.x >> 5;
-    const int nw = blockDim.x >> 5;
-    for (int q = threadIdx.x; q < S; q += blockDim.x) {
-        keys[q] = kEmptyKey;
-        vals[q] = (T)0;
-    }
-    if (threadIdx.x == 0) overflow = 0;
-    __syncthreads();
-
-    const BinView bv = bin_view(s, bin);
-    const Labels L = labels_of(s);
-    const bool marks = marks_on(s, flag_neighbours);
-    const uint32_t sweep = NS ? (uint32_t)s.ctrl->iter + 1u : 0u;   // non-strict tie-break (Section 4.1.5)
-    // Max-over-row path: the first synchronous sweep of a repeat-free graph;
-    // and in the asynchronous mode, the last bin of the first sweep's main
-    // pass, which runs before every other bin (its rows then read initial
-    // labels, as if processed before their neighbours).
-    bool ident = identity_sweep<ASYNC, BATCH>(s);
-    if constexpr (ASYNC && !BATCH && LAST) ident = s.rows_distinct && s.ctrl->iter == 0 && L.dense;
-    const bool po = ASYNC && s.ctrl->prune_other != 0;               // FLPA's pruning rule
-    const unsigned cnt = bv.cnt;
-    const int log_S = ceil_log2((unsigned)S);
-    unsigned long long my_changed = 0, my_changed_entries = 0;
-    // Last bin: thread 0 fetches the next row's position while the block works
-    // on the current row and publishes it at the top of the next iteration
-    // (two slots: a slot is rewritten only after every thread read it).
-    __shared__ unsigned next_k[2];
-    unsigned fetched = 0;
-    if (LAST && threadIdx.x == 0) fetched = atomicAdd(&s.ctrl->row_next[bin], 1u);
-    for (unsigned it = 0;; ++it) {
-        unsigned k = blockIdx.x + it * gridDim.x;
-        if constexpr (LAST) {
-            if (threadIdx.x == 0) next_k[it & 1u] = fetched;
-            __syncthreads();
-            k = next_k[it & 1u];
-            if (k < cnt && threadIdx.x == 0) fetched = atomicAdd(&s.ctrl->row_next[bin], 1u);
-        }
-        if (k >= cnt) break;
-        const int32_t v = bv.list[k];
-        const int32_t own = ASYNC ? __ldcg(L.C + v) : L.C[v];
-        if constexpr (BATCH) {
-            if (s.done[s.gid[v]]) {             // block-uniform
-                if (threadIdx.x == 0) record_label<ASYNC>(L, bv.chg + k, v, own, own, false);
-                continue;
-            }
-        }
-        const int64_t st = s.off[v];
-        const int64_t en = s.off_end[v];
-        const int64_t d = en - st;
-        const TieRule tr = tie_rule(s, NS, sweep, v);
-        int32_t best_lab;
-        if (ident) {
-            // labels are the neighbour ids and occur once: a max over the row
-            unsigned long long bp = 0ull;
-#pragma unroll 4
-            for (int64_t e = st + threadIdx.x; e < en; e += blockDim.x) {
-                const int32_t j = load_index_keep(s.idx, e);
-                if (j != v) {
-                    const unsigned long long c = pack_candidate(sum_key(load_weight<WK>(s.w, e)), tr.key(j));
-                    bp = c > bp ? c : bp;
-                }
-            }
-            bp = warp_max_u64(bp);
-            if (lane == 0) red_bp[wib] = bp;
-            __syncthreads();
-            if (wib == 0) {
-                bp = warp_max_u64((int)lane < nw ? red_bp[lane] : 0ull);
-                if (lane == 0) win_bp = bp;
-            }
-            __syncthreads();
-            bp = win_bp;
-            best_lab = bp == 0ull ? -1 : tr.label(~(uint32_t)bp);
-        } else {
-            const int log_full = ceil_log2((unsigned)(2 * d));
-            const bool fits = log_full <= log_S;
-            const int log_s = fits ? log_full : log_S;
-            // Each warp takes U chunks per step (chunk c = wib + (u + U*it)*nw):
-            // their index loads, then their label gathers and weights, are issued
-            // together so the latencies overlap; then the chunks are aggregated.
-            const int64_t step = (int64_t)nw * 32;
-            for (int64_t e0 = st + (int64_t)wib * 32; e0 < en; e0 += step * U) {
-                if (!fits && *(volatile int*)&overflow) break;     // warp-uniform
-                int32_t jj[U], lab[U];
-                T ww[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t e = e0 + u * step + lane;
-                    jj[u] = e < en ? load_index_keep(s.idx, e) : v;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t e = e0 + u * step + lane;
-                    const bool ok = jj[u] != v;                      // also false past the row end
-                    lab[u] = ok ? load_label<ASYNC>(L.C, jj[u]) : kEmptyKey;
-                    ww[u] = ok ? load_weight<WK>(s.w, e) : (T)0;
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if (e0 + u * step >= en) break;                 // warp-uniform
-                    const bool ok = jj[u] != v;
-                    T w = ww[u];
-                    bool lead = ok;
-                    if constexpr (WK != W_F32) {
-                        const unsigned peers = __match_any_sync(kFull, lab[u]);
-                        if constexpr (WK == W_UNIT) {
-                            w = (T)__popc(peers);
-                        } else {
-                            w = __reduce_add_sync(peers, w);
-                        }
-                        lead = ok && lane == (unsigned)(__ffs(peers) - 1);
-                    }
-                    int created = -1;
-                    if (lead) {
-                        if (fits) {
-                            if (!table_insert<T>(keys, vals, log_s, lab[u], w, 1u << log_s, created))
-                                atomicExch(&s.ctrl->error, 3);
-                        } else if (!table_insert<T>(keys, vals, log_s, lab[u], w, kSharedProbes, created)) {
-                            overflow = 1;
-                        }
-                    }
-                    if constexpr (LISTS) list_filled(created, my_seg, seg_cap, wfill);
-                }
-            }
-            bool lists = false;
-            if constexpr (LISTS) {
-                if (lane == 0) wpre[wib + 1] = wfill;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    unsigned acc = 0, mx = 0;
-                    wpre[0] = 0;
-                    for (int w = 1; w <= nw; ++w) {
-                        mx = wpre[w] > mx ? wpre[w] : mx;
-                        acc += wpre[w];
-                        wpre[w] = acc;
-                    }
-                    wpre[32] = mx;
-                }
-                wfill = 0;
-            }
-            __syncthreads();
-            if constexpr (LISTS) lists = wpre[32] <= seg_cap;
-            uint32_t key, tie;
-            scan_table<T>(keys, vals, 1 << log_s, lists, segs, seg_cap, wpre, nw, tr, key, tie);   // and clears
-            const int ovf = overflow;
-            const uint32_t best_tie = block_argmax(key, tie, red_key, red_tie, &winner);
-            best_lab = best_tie == 0xffffffffu ? -1 : tr.label(best_tie);
-            if (ovf) {
-                // hand the row to the partitioned rescan
-                if (threadIdx.x == 0) {
-                    Overflow& o = s.ovf[atomicAdd(&s.ctrl->ovf_count, 1ull)];
-                    o.v = v;
-                    o.slot = k;
-                    o.st = st;
-                    o.d = (int32_t)d;
-                    o.own = own;
-                    o.parts = (uint32_t)((2 * d + S - 1) / S);
-                    o.best = 0ull;
-                    o.done = 0u;
-                    overflow = 0;
-                }
-                __syncthreads();
-                continue;
-            }
-        }
-        const bool changed = best_lab >= 0 && best_lab != own;   // block-uniform
-        if (threadIdx.x == 0) record_label<ASYNC>(L, bv.chg + k, v, own, best_lab, changed);
-        if (changed) {
-            if (threadIdx.x == 0) {
-                ++my_changed;
-                my_changed_entries += (unsigned long long)d;
-                if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
-            }
-            if (marks) mark_neighbours<ASYNC>(s, v, st, en, po, best_lab, L.C);
-        }
-        __syncthreads();    // `winner` / `win_bp` consumed before the next vertex
-    }
-    flush_bin_counts(s, bin, my_changed, my_changed_entries);
 }
 
 __device__ __forceinline__ uint32_t part_of(int32_t label, uint32_t parts) {
@@ -832,12 +594,6 @@ cudaError_t ovf_capacity(const DevState& s, cudaStream_t st, int sms, int64_t* p
     *counts = (int64_t)h[1];
     *rows = (int64_t)h[2];
     return cudaSuccess;
-}
-
-// Dynamic shared memory of a block-bin kernel: the table (S keys, S values)
-// and, in the middle bins, the lists of filled slots (S / 2 two-byte entries).
-static size_t block_smem(const DevState& s, int bin) {
-    return (size_t)s.block_slots[bin - 2] * (bin == kBins - 1 ? 8 : 9);
 }
 
 template <bool ASYNC, int WK, bool BATCH, bool NS>

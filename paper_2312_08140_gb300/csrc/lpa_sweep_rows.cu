@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
             const bool in = on && r < n;
             const int32_t j = in ? src[r] : v;
             const bool ok = in && j != v;
-            lab[p] = ok ? (ident ? j : load_label<ASYNC>(L.C, j)) : kEmptyKey;
+            lab[p] = ok ? (ident ? initial_label(s, j) : load_label<ASYNC>(L.C, j)) : kEmptyKey;
             if constexpr (WK == W_UNIT) w[p] = ok ? (T)1 : (T)0;
             else w[p] = ok ? load_weight<WK>(s.w, e0 + r) : (T)0;
         }

@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_sweep_small(DevState s, int f
 #pragma unroll
         for (int q = 0; q < MAXD; ++q) {
             const bool ok = act && q < cur.d && cur.nb[q] != v;
-            lab[q] = ok ? (ident ? cur.nb[q] : load_label<false>(L.C, cur.nb[q])) : kEmptyKey;
+            lab[q] = ok ? (ident ? initial_label(s, cur.nb[q]) : load_label<false>(L.C, cur.nb[q])) : kEmptyKey;
             wt[q] = ok ? cur.wt[q] : (T)0;
         }
         // the next stages, issued before this slot's labels are consumed

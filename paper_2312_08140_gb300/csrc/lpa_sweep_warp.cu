@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
             const int32_t vq = __shfl_sync(kFull, vl, q);
             const int64_t sq = __shfl_sync(kFull, stl, q);
             const bool ok = j != kEmptyKey && j != vq;
-            lab = ok ? (ident ? j : load_label<ASYNC>(L.C, j)) : kEmptyKey;
+            lab = ok ? (ident ? initial_label(s, j) : load_label<ASYNC>(L.C, j)) : kEmptyKey;
             w = ok ? load_weight<WK>(s.w, sq + lane) : (T)0;
         };
         int32_t j_cur = first_index(0), j_nxt = first_index(1);
@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                 for (int64_t e = st + 32 + lane; e < en; e += 32) {
                     const int32_t jj = load_index_keep(s.idx, e);
                     if (jj != v) {
-                        const unsigned long long c = pack_candidate(sum_key(load_weight<WK>(s.w, e)), tr.key(jj));
+                        const unsigned long long c =
+                            pack_candidate(sum_key(load_weight<WK>(s.w, e)), tr.key(initial_label(s, jj)));
                         bp = c > bp ? c : bp;
                     }
                 }
