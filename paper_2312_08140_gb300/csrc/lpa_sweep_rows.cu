@@ -26,10 +26,11 @@
 //
 // Rows whose distinct labels overflow the last bin's table (bounded probing
 // fails) are appended to the overflow list and finished by the partitioned
-// kernels of lpa_sweep_block.cu, as before.  The first synchronous sweep of a
+// kernels of lpa_sweep_block.cu.  The first synchronous sweep of a
 // repeat-free graph, and the last bin of the first asynchronous sweep, take
-// the max-over-row path (every label is still its vertex's id): no gathers,
-// a max of (weight key, tie key) over the ids in shared memory.
+// the max-over-row pass instead (every label is still its vertex's id): no
+// gathers, so each warp streams whole rows with plain loads, eight per lane
+// in flight, and reduces them to the max of (weight key, tie key).
 //
 // Every wait on an mbarrier is bounded (2 s of GPU time); a wait that gives
 // up sets error code 5 in the control block and the block leaves after its
@@ -202,7 +203,6 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     __shared__ ProdState prod;
     __shared__ unsigned wpre[33];
     __shared__ uint32_t red_key[32], red_tie[32], winner;
-    __shared__ unsigned long long red_bp[32];
     __shared__ int overflow, abort_flag;
 
     const unsigned lane = lane_id();
@@ -234,6 +234,63 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     const int log_S = ceil_log2((unsigned)S);
     const unsigned cnt = bv.cnt;
     const int64_t E_al = s.E & ~(int64_t)3;                          // end of the 16-byte aligned part of idx
+
+    if (ident) {
+        // ---- max-over-row pass: every label is still its vertex's id, so each
+        // row's pick is the max of (weight key, tie key) over its entries.  No
+        // gathers to hide, so no tiles: each warp takes whole rows from the
+        // bin's counter (the largest first, as the list holds them) and
+        // streams them with plain loads, kIdentUnroll per lane in flight;
+        // NW rows per block are in flight at once and no block barrier runs.
+        constexpr int kIdentUnroll = 8;
+        unsigned long long n_changed = 0, n_changed_entries = 0;
+        for (;;) {
+            unsigned k = 0;
+            if (lane == 0) k = atomicAdd(&s.ctrl->row_next[bin], 1u);
+            k = __shfl_sync(kFull, k, 0);
+            if (k >= cnt) break;
+            const int32_t v = bv.list[k];
+            const int64_t st = s.off[v], en = s.off_end[v];
+            const int32_t own = ASYNC ? __ldcg(L.C + v) : L.C[v];
+            const TieRule tr = tie_rule(s, NS, sweep, v);
+            unsigned long long bp = 0ull;
+            for (int64_t e0 = st + lane; e0 < en; e0 += 32 * kIdentUnroll) {
+                int32_t jj[kIdentUnroll];
+                T ww[kIdentUnroll];
+#pragma unroll
+                for (int u = 0; u < kIdentUnroll; ++u) {
+                    const int64_t e = e0 + 32 * u;
+                    jj[u] = e < en ? load_index(s.idx, e) : v;
+                    ww[u] = e < en ? load_weight<WK>(s.w, e) : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < kIdentUnroll; ++u) {
+                    if (jj[u] != v) {
+                        const unsigned long long c = pack_candidate(sum_key(ww[u]), tr.key(initial_label(s, jj[u])));
+                        bp = c > bp ? c : bp;
+                    }
+                }
+            }
+            bp = warp_max_u64(bp);
+            const int32_t best_lab = bp == 0ull ? -1 : tr.label(~(uint32_t)bp);
+            const bool changed = best_lab >= 0 && best_lab != own;   // warp-uniform
+            if (lane == 0) record_label<ASYNC>(L, bv.chg + k, v, own, best_lab, changed);
+            if (changed) {
+                if (lane == 0) {
+                    ++n_changed;
+                    n_changed_entries += (unsigned long long)(en - st);
+                }
+                if (marks) {
+                    for (int64_t e = st + lane; e < en; e += 32) {
+                        const int32_t j = s.idx[e];
+                        if (j != v && !(po && load_label<ASYNC>(L.C, j) == best_lab)) mark_unprocessed(s.flags, j);
+                    }
+                }
+            }
+        }
+        flush_bin_counts(s, bin, n_changed, n_changed_entries);
+        return;
+    }
 
     // ---- producer (warp 0) -----------------------------------------------------
     // Rows come from the bin's counter in batches of kRowBatch.  The list
@@ -346,14 +403,11 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     // ---- consumer state ------------------------------------------------------
     int32_t lab_cur[P], lab_nxt[P];
     T w_cur[P], w_nxt[P];
-    // max-over-row path: this thread's best candidate of the row so far
-    unsigned long long bp_row = 0ull;
     __shared__ unsigned long long blk_changed, blk_changed_entries;   // this block's changes (thread 0)
     if (threadIdx.x == 0) blk_changed = blk_changed_entries = 0ull;
 
-    // Reads tile t's ids (buffer b, phase `par`) and issues their gathers; on
-    // the max-over-row path it keeps the ids themselves (the labels).  The
-    // descriptor is read into registers once.
+    // Reads tile t's ids (buffer b, phase `par`) and issues their gathers.
+    // The descriptor is read into registers once.
     auto load_tile = [&](const Tile& t, int b, unsigned par, int32_t (&lab)[P], T (&w)[P]) -> bool {
         const int64_t e0 = t.e0;
         const int32_t n = (int32_t)(t.e1 - e0);
@@ -367,7 +421,7 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
             const bool in = on && r < n;
             const int32_t j = in ? src[r] : v;
             const bool ok = in && j != v;
-            lab[p] = ok ? (ident ? initial_label(s, j) : load_label<ASYNC>(L.C, j)) : kEmptyKey;
+            lab[p] = ok ? load_label<ASYNC>(L.C, j) : kEmptyKey;
             if constexpr (WK == W_UNIT) w[p] = ok ? (T)1 : (T)0;
             else w[p] = ok ? load_weight<WK>(s.w, e0 + r) : (T)0;
         }
@@ -426,18 +480,7 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
             }
             wfill += __popc(nm);
         };
-        if (ident && !k_skip) {
-            // labels are the neighbour ids and occur once: a max over the row
-            const TieRule tr = tie_rule(s, NS, sweep, v);
-#pragma unroll
-            for (int p = 0; p < P; ++p) {
-                if (lab_cur[p] != kEmptyKey) {
-                    const unsigned long long c = pack_candidate(sum_key(w_cur[p]), tr.key(lab_cur[p]));
-                    bp_row = c > bp_row ? c : bp_row;
-                }
-            }
-        }
-        if (!ident && !k_skip && (int)(wib * 32) < k_n) {
+        if (!k_skip && (int)(wib * 32) < k_n) {
             // Fast path: every entry this warp holds in the tile carries one
             // label (after the first sweeps nearly every neighbour of a hub
             // does) -- one reduction and one insert for the warp's share.
@@ -492,15 +535,6 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
             int ovf = 0;
             if (tk.skip) {
                 // a done graph's vertex keeps its label (batches)
-            } else if (ident) {
-                unsigned long long bp = warp_max_u64(bp_row);
-                bp_row = 0ull;
-                if (lane == 0) red_bp[wib] = bp;
-                __syncthreads();
-                bp = 0ull;
-#pragma unroll
-                for (int q = 0; q < NW; ++q) bp = red_bp[q] > bp ? red_bp[q] : bp;
-                best_lab = bp == 0ull ? -1 : tr.label(~(uint32_t)bp);
             } else {
                 if (lane == 0) wpre[wib + 1] = wfill;
                 __syncthreads();
@@ -575,9 +609,20 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                         if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
                     }
                     if (marks) {
-                        for (int64_t e = tk.st + threadIdx.x; e < tk.en; e += NT) {
-                            const int32_t j = s.idx[e];
-                            if (j != v && !(po && load_label<ASYNC>(L.C, j) == best_lab)) mark_unprocessed(s.flags, j);
+                        // mark the neighbours unprocessed (Section 4.1.4), four
+                        // entries per thread in flight: their ids, then their flags
+                        const int64_t st = tk.st, en = tk.en;
+                        for (int64_t e0 = st + threadIdx.x; e0 < en; e0 += 4 * NT) {
+                            int32_t j[4];
+                            uint8_t f[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) j[u] = e0 + u * NT < en ? s.idx[e0 + u * NT] : v;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) f[u] = j[u] != v ? __ldcg(s.flags + j[u]) : (uint8_t)1;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                if (f[u] == 0 && !(po && load_label<ASYNC>(L.C, j[u]) == best_lab)) s.flags[j[u]] = 1;
+                            }
                         }
                     }
                 }

@@ -12,6 +12,10 @@
 //            table in shared memory sized 2^ceil(log2(2d)) slots (so it can
 //            never fill) and list the slots they fill; the warp then scans
 //            the listed slots for the argmax and clears them.
+// A chunk whose labels all agree (after the first sweeps nearly every chunk)
+// skips the grouping: a row of one chunk takes that label's total directly,
+// and in a longer row such chunks extend a run of one label held in
+// registers, which reaches the table once.
 // Ties go to the smallest label id (Section 4.1.5); self-loops are skipped
 // (Algorithm 1).  On change, the warp re-reads the row and marks the
 // neighbours unprocessed (Section 4.1.4).
@@ -48,7 +52,7 @@ __device__ __forceinline__ typename Acc<WK>::T group_sum(unsigned peers, typenam
 }
 
 template <bool ASYNC, int WK, bool BATCH, bool NS>
-__global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int flag_neighbours) {
+__global__ void __launch_bounds__(kWarpThreads, 4) k_sweep_warp(DevState s, int flag_neighbours) {
     using T = typename Acc<WK>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int wslots = s.warp_slots;
@@ -156,11 +160,29 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
             int32_t cand = 0;
             if (act && d <= 32) {
                 const bool ok = lab_cur != kEmptyKey;
-                const unsigned peers = __match_any_sync(kFull, lab_cur);
-                const T sum = group_sum<WK>(peers, w_cur, lab_cur, ok);
-                if (ok && lane == (unsigned)(__ffs(peers) - 1)) {
-                    key = sum_key(sum);
-                    cand = lab_cur;
+                // all of the row's labels agree (after the first sweeps the
+                // usual case): the row's total weight is that label's sum
+                const int32_t lmax = __reduce_max_sync(kFull, lab_cur);
+                if (__all_sync(kFull, !ok || lab_cur == lmax)) {
+                    T sum;
+                    if constexpr (WK == W_UNIT) {
+                        sum = (T)__popc(__ballot_sync(kFull, ok));
+                    } else if constexpr (WK == W_F32) {
+                        sum = group_sum<WK>(kFull, w_cur, lab_cur, ok);
+                    } else {
+                        sum = __reduce_add_sync(kFull, w_cur);
+                    }
+                    if (lane == 0 && lmax != kEmptyKey) {
+                        key = sum_key(sum);
+                        cand = lmax;
+                    }
+                } else {
+                    const unsigned peers = __match_any_sync(kFull, lab_cur);
+                    const T sum = group_sum<WK>(peers, w_cur, lab_cur, ok);
+                    if (ok && lane == (unsigned)(__ffs(peers) - 1)) {
+                        key = sum_key(sum);
+                        cand = lab_cur;
+                    }
                 }
             } else if (act && ident) {
                 // labels are the neighbour ids and occur once: a max over the row
@@ -181,8 +203,48 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                 }
             } else if (act) {
                 const int log_slots = ceil_log2(2u * (unsigned)d);
+                // one (label, weight) into the warp's table by `lane`, its
+                // newly filled slot listed
+                auto insert_listed = [&](bool ins, int32_t lab, T add) {
+                    int created = -1;
+                    if (ins && !table_insert<T>(keys, vals, log_slots, lab, add, 1u << log_slots, created))
+                        atomicExch(&s.ctrl->error, 2);
+                    const unsigned nm = __ballot_sync(kFull, created >= 0);
+                    if (created >= 0) filled_slots[filled + __popc(nm & lanes_below())] = (uint16_t)created;
+                    filled += __popc(nm);
+                };
+                // Chunks whose labels all agree extend a run held in registers
+                // (same value in every lane); the run reaches the table once,
+                // when a chunk with another label or mixed labels ends it, or
+                // at the end of the row.
+                int32_t run_lab = kEmptyKey;
+                T run_w = (T)0;
+                auto flush_run = [&]() {
+                    if (run_lab != kEmptyKey) insert_listed(lane == 0, run_lab, run_w);
+                    run_lab = kEmptyKey;
+                    run_w = (T)0;
+                };
                 auto add_chunk = [&](int32_t lab, T w) {
                     const bool ok = lab != kEmptyKey;
+                    const int32_t lmax = __reduce_max_sync(kFull, lab);
+                    if (__all_sync(kFull, !ok || lab == lmax)) {
+                        if (lmax == kEmptyKey) return;
+                        T sum;
+                        if constexpr (WK == W_UNIT) {
+                            sum = (T)__popc(__ballot_sync(kFull, ok));
+                        } else if constexpr (WK == W_F32) {
+                            sum = group_sum<WK>(kFull, w, lab, ok);
+                        } else {
+                            sum = __reduce_add_sync(kFull, w);
+                        }
+                        if (lmax != run_lab) {
+                            flush_run();
+                            run_lab = lmax;
+                        }
+                        run_w += sum;
+                        return;
+                    }
+                    flush_run();
                     bool ins = ok;
                     T add = w;
                     if constexpr (WK != W_F32) {
@@ -190,12 +252,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                         add = group_sum<WK>(peers, w, lab, ok);
                         ins = ok && lane == (unsigned)(__ffs(peers) - 1);
                     }
-                    int created = -1;
-                    if (ins && !table_insert<T>(keys, vals, log_slots, lab, add, 1u << log_slots, created))
-                        atomicExch(&s.ctrl->error, 2);
-                    const unsigned nm = __ballot_sync(kFull, created >= 0);
-                    if (created >= 0) filled_slots[filled + __popc(nm & lanes_below())] = (uint16_t)created;
-                    filled += __popc(nm);
+                    insert_listed(ins, lab, add);
                 };
                 add_chunk(lab_cur, w_cur);                 // first chunk, prefetched
                 for (int64_t e0 = st + 32; e0 < en; e0 += 32 * kWarpUnroll) {
@@ -218,6 +275,7 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                         add_chunk(ll[u], wq[u]);
                     }
                 }
+                flush_run();
                 __syncwarp();
                 bool any = false;
                 T best_w = 0;
@@ -261,9 +319,17 @@ __global__ void __launch_bounds__(kWarpThreads, 5) k_sweep_warp(DevState s, int 
                     if (d <= 32) {                   // this row's indices are still in j
                         if ((int)lane < d && j != v && !(po && lab_row == best)) mark_unprocessed(s.flags, j);
                     } else {
-                        for (int64_t e = st + lane; e < en; e += 32) {
-                            const int32_t jj = s.idx[e];
-                            if (jj != v && !(po && load_label<ASYNC>(L.C, jj) == best)) mark_unprocessed(s.flags, jj);
+                        // up to four chunks of the row in flight: ids, then flags
+                        for (int64_t e0 = st + lane; e0 < en; e0 += 128) {
+                            int32_t jj[4];
+                            uint8_t f[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) jj[u] = e0 + 32 * u < en ? s.idx[e0 + 32 * u] : v;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) f[u] = jj[u] != v ? __ldcg(s.flags + jj[u]) : (uint8_t)1;
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+                                if (f[u] == 0 && !(po && load_label<ASYNC>(L.C, jj[u]) == best)) s.flags[jj[u]] = 1;
                         }
                     }
                 }

@@ -5,8 +5,9 @@ order it leaves open, so serial runs in different orders are all executions
 of it, and their modularity (Eq. 1) differs -- on small planted-partition
 graphs by several tenths.  A parallel run is one more interleaving.  The
 tests hold the GPU to the oracle's serial runs in seeded random vertex orders
-(six by default), with the 0.02 absolute tolerance stated for the
-asynchronous mode:
+(sixteen by default: the lowest of only six is a poor estimate of how low a
+serial run goes -- one graph's six gave 0.661 where sixteen reach 0.630),
+with the 0.02 absolute tolerance stated for the asynchronous mode:
 
   * the median modularity over >= 5 GPU runs must reach the median of the
     serial runs less 0.02;
@@ -48,12 +49,12 @@ def _serial_q(args):
 def _get_pool():
     global _pool
     if _pool is None:
-        _pool = cf.ProcessPoolExecutor(max_workers=max(1, min(6, os.cpu_count() or 1)),
+        _pool = cf.ProcessPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)),
                                        mp_context=mp.get_context("spawn"))
     return _pool
 
 
-def serial_qs(g, tau=0.05, iters=20, orders=6, seed=0, prune_other=False):
+def serial_qs(g, tau=0.05, iters=20, orders=16, seed=0, prune_other=False):
     """Modularity of the oracle's serial runs of Algorithm 1 on g in `orders`
     seeded random vertex orders (with prune_other: under FLPA's pruning rule)."""
     rng = np.random.default_rng(seed)
