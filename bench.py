@@ -668,6 +668,9 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=10_000, help="0 skips the serving sample")
     ap.add_argument("--serving-big-every", type=int, default=500,
                     help="an R-MAT scale 24 request every this many requests (0: none)")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="create the workload's graphs, run each mode once through the host-launched profiled "
+                         "path (every kernel a separate launch, as ncu needs) and print the per-bin times")
     ap.add_argument("--tie", default="strict", choices=["strict", "nonstrict"],
                     help="tie-break among the most weighted labels (Section 4.1.5)")
     ap.add_argument("--prune", default="paper", choices=["paper", "other"],
@@ -703,6 +706,17 @@ def main():
     stream = torch.cuda.current_stream()
     handles = [lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS, stream) for g in graphs]
     outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    if args.profile_only:
+        for (name, _), h, o in zip(wl, handles, outs):
+            for m in modes:
+                ri, prof = lpa.lpa_run_profiled(h, m, TAU, MAX_ITERS, o, stream)
+                p = prof.as_dict()
+                print(json.dumps({"graph": name, "mode": m, "iterations": ri.iterations,
+                                  "bins": list(BIN_KERNELS), "sweep_ms": p["sweep_ms"],
+                                  "finish_ms": p["finish_ms"], "bin_vertices": p["bin_vertices"],
+                                  "bin_entries": p["bin_entries"]}), flush=True)
+        release(lpa, torch, handles)
+        return
 
     def step():
         for h, g, o in zip(handles, graphs, outs):

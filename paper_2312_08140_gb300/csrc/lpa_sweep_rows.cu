@@ -160,28 +160,6 @@ struct ProdState {
     int32_t pad;
 };
 
-// Block-wide argmax of (sum key, tie key), as in lpa_sweep_block.cu.
-__device__ __forceinline__ uint32_t rows_block_argmax(uint32_t key, uint32_t tie, uint32_t* red_key,
-                                                      uint32_t* red_tie, uint32_t* winner) {
-    const unsigned lane = lane_id();
-    const int wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t m = __reduce_max_sync(kFull, key);
-    const uint32_t c = __reduce_min_sync(kFull, (m != 0 && key == m) ? tie : 0xffffffffu);
-    if (lane == 0) {
-        red_key[wib] = m;
-        red_tie[wib] = c;
-    }
-    __syncthreads();
-    if (wib == 0) {
-        const uint32_t kk = (int)lane < nw ? red_key[lane] : 0u;
-        const uint32_t tt = (int)lane < nw ? red_tie[lane] : 0xffffffffu;
-        const uint32_t w = warp_argmax_tie(kk, tt);
-        if (lane == 0) *winner = w;
-    }
-    __syncthreads();
-    return *winner;
-}
-
 template <bool ASYNC, int WK, bool BATCH, bool NS, int NT>
 __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(DevState s, int bin,
                                                                             int flag_neighbours) {
@@ -201,8 +179,8 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     __shared__ Tile tiles[2 * kStages];
     __shared__ RowMeta batch[kRowBatch];
     __shared__ ProdState prod;
-    __shared__ unsigned wpre[33];
-    __shared__ uint32_t red_key[32], red_tie[32], winner;
+    __shared__ unsigned wcnt[32];                  // slots each warp filled for the current row
+    __shared__ uint32_t red_key[32], red_tie[32];
     __shared__ int overflow, abort_flag;
 
     const unsigned lane = lane_id();
@@ -536,21 +514,23 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
             if (tk.skip) {
                 // a done graph's vertex keeps its label (batches)
             } else {
-                if (lane == 0) wpre[wib + 1] = wfill;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    unsigned acc = 0, mx = 0;
-                    wpre[0] = 0;
-                    for (int q = 1; q <= NW; ++q) {
-                        mx = wpre[q] > mx ? wpre[q] : mx;
-                        acc += wpre[q];
-                        wpre[q] = acc;
-                    }
-                    wpre[32] = mx;
-                }
+                // two barriers per row: after the first the table, the slot
+                // lists and their per-warp counts are complete; every thread
+                // forms the count prefixes itself and, after the second, the
+                // block's winner from the per-warp candidates
+                if (lane == 0) wcnt[wib] = wfill;
                 wfill = 0;
                 __syncthreads();
-                const bool lists = wpre[32] <= seg_cap;
+                unsigned pre[NW + 1];
+                pre[0] = 0;
+                unsigned mx = 0;
+#pragma unroll
+                for (int q = 0; q < NW; ++q) {
+                    const unsigned c = wcnt[q];
+                    mx = c > mx ? c : mx;
+                    pre[q + 1] = pre[q] + c;
+                }
+                const bool lists = mx <= seg_cap;
                 ovf = overflow;
                 // this thread's best candidate among the row's slots; clears them
                 bool any = false;
@@ -571,18 +551,34 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                     }
                 };
                 if (lists) {
-                    const unsigned total = wpre[NW];
+                    const unsigned total = pre[NW];
                     for (unsigned f = threadIdx.x; f < total; f += NT) {
                         int q = 0;
-                        while (q + 1 < NW && wpre[q + 1] <= f) ++q;
-                        visit(segs[(size_t)q * seg_cap + (f - wpre[q])]);
+#pragma unroll
+                        for (int r = 1; r < NW; ++r) q += pre[r] <= f ? 1 : 0;
+                        visit(segs[(size_t)q * seg_cap + (f - pre[q])]);
                     }
                 } else {
                     for (int q = threadIdx.x; q < (1 << log_s); q += NT) visit(q);
                 }
-                const uint32_t best_tie =
-                    rows_block_argmax(any ? sum_key(best_w) : 0u, best_k, red_key, red_tie, &winner);
-                best_lab = best_tie == 0xffffffffu ? -1 : tr.label(best_tie);
+                const uint32_t key = any ? sum_key(best_w) : 0u;
+                const uint32_t m = __reduce_max_sync(kFull, key);
+                const uint32_t c = __reduce_min_sync(kFull, (m != 0 && key == m) ? best_k : 0xffffffffu);
+                if (lane == 0) {
+                    red_key[wib] = m;
+                    red_tie[wib] = c;
+                }
+                __syncthreads();
+                uint32_t bk = 0, bt = 0xffffffffu;
+#pragma unroll
+                for (int q = 0; q < NW; ++q) {
+                    const uint32_t kq = red_key[q], tq = red_tie[q];
+                    if (kq > bk || (kq == bk && tq < bt)) {
+                        bk = kq;
+                        bt = tq;
+                    }
+                }
+                best_lab = (bk == 0u || bt == 0xffffffffu) ? -1 : tr.label(bt);
             }
             if (ovf) {
                 // hand the row to the partitioned kernels (last bin only)
