@@ -138,6 +138,36 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
     return z ^ (z >> 31);
 }
 
+// A Feistel network on 2m-bit values (four rounds of SplitMix64): a
+// pseudo-random bijection of [0, 2^(2m)).
+__device__ __forceinline__ uint32_t feistel(uint32_t x, int m, uint64_t seed) {
+    const uint32_t mask = (m >= 32) ? 0xffffffffu : ((1u << m) - 1u);
+    uint32_t L = x >> m, R = x & mask;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const uint32_t f = (uint32_t)splitmix64(seed + ((uint64_t)r << 40) + R) & mask;
+        const uint32_t t = L ^ f;
+        L = R;
+        R = t;
+    }
+    return (L << m) | R;
+}
+
+// Position of i in a pseudo-random permutation of [0, n) (n >= 1).  The
+// network permutes [0, 2^(2m)) with 2^(2m) < 4n, so the walk (apply the
+// permutation until the value falls below n) ends after a few steps.
+__device__ __forceinline__ uint32_t shuffle_pos(uint32_t i, uint32_t n, uint64_t seed) {
+    if (n <= 1) return 0;
+    int k = 32 - __clz(n - 1);                 // bits of n - 1
+    if (k & 1) ++k;
+    const int m = k / 2;
+    uint32_t x = i;
+    do {
+        x = feistel(x, m, seed);
+    } while (x >= n);
+    return x;
+}
+
 // Tie-break among the most weighted labels of one vertex (Section 4.1.5).
 // Strict: the smallest label id.  Non-strict (a pseudo-random choice through a
 // modulo of the label id, read as a rotation of the label space):

@@ -31,35 +31,7 @@ constexpr int kReorderPerThread = 16;
 constexpr int kReorderChunk = kReorderThreads * kReorderPerThread;
 constexpr int kOrderKeys = 32;                 // degree buckets 0..31 (d < 2^31)
 
-// ---- shuffle: a Feistel network on 2m-bit values, walked onto [0, n) ------
-__device__ __forceinline__ uint32_t feistel(uint32_t x, int m, uint64_t seed) {
-    const uint32_t mask = (m >= 32) ? 0xffffffffu : ((1u << m) - 1u);
-    uint32_t L = x >> m, R = x & mask;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const uint32_t f = (uint32_t)splitmix64(seed + ((uint64_t)r << 40) + R) & mask;
-        const uint32_t t = L ^ f;
-        L = R;
-        R = t;
-    }
-    return (L << m) | R;
-}
-
-// Position of i in a pseudo-random permutation of [0, n) (n >= 1).  The
-// network permutes [0, 2^(2m)) with 2^(2m) < 4n, so the walk (apply the
-// permutation until the value falls below n) ends after a few steps.
-__device__ __forceinline__ uint32_t shuffle_pos(uint32_t i, uint32_t n, uint64_t seed) {
-    if (n <= 1) return 0;
-    int k = 32 - __clz(n - 1);                 // bits of n - 1
-    if (k & 1) ++k;
-    const int m = k / 2;
-    uint32_t x = i;
-    do {
-        x = feistel(x, m, seed);
-    } while (x >= n);
-    return x;
-}
-
+// ---- shuffle: shuffle_pos (lpa_device.cuh) per graph ---------------------
 __global__ void k_shuffle_inv(const int64_t* vtx_off, const int32_t* gid, int32_t G, int64_t N, uint64_t seed,
                               int32_t* inv) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;

@@ -13,7 +13,7 @@
     graphs bit-exact against the synchronous oracle (labels, sweep count,
     per-sweep changed counts), and the asynchronous batch held to the
     component invariant, the off-local-argmax bound and the modularity bound
-    of async_bounds (five batch runs against six random-order serial runs)
+    of async_bounds (five batch runs against sixteen random-order serial runs)
     on the sampled graphs.
 
 The component invariant needs a union-find over every entry, minutes on the
