@@ -69,6 +69,8 @@ def workload(name):
         return [("rmat27", lambda: _rmat_device_host(27))]
     if name == "rmat25":
         return [("rmat25", lambda: _rmat_device_host(25))]
+    if name == "rmat24":
+        return [("rmat24", lambda: _rmat_device_host(24))]
     if name == "planted1e4+grid64":
         return [("planted1e4", lambda: L.planted_partition(seed=1)), ("grid64", lambda: L.road_grid(64, 64, seed=1))]
     raise SystemExit(f"unknown workload {name}")
@@ -90,7 +92,7 @@ def _rmat_device_host(scale):
 
 
 # modes each workload runs (every other workload: both)
-WORKLOAD_MODES = {"rmat27": ("async",), "rmat25": ("async",)}
+WORKLOAD_MODES = {"rmat27": ("async",), "rmat25": ("async",), "rmat24": ("async",)}
 
 WORKLOAD_TEXT = {
     "rmat22+grid4096": "R-MAT scale 22 edge factor 16 (a,b,c,d=.57,.19,.19,.05; symmetrised, deduplicated, "
@@ -104,6 +106,8 @@ WORKLOAD_TEXT = {
     "rmat25": "R-MAT scale 25 edge factor 14 (the generator and mode of the scale-27 workload at a "
               "quarter of the size: ~0.9e9 entries, a 134 MB label array just above L2; a profiling "
               "case); asynchronous mode with pruning; tau=0.05, cap 20",
+    "rmat24": "R-MAT scale 24 edge factor 14 (~0.45e9 entries, a few GB on the device: the case for "
+              "multi-pass ncu captures of the scale-27 kernels); asynchronous mode with pruning; tau=0.05, cap 20",
     "planted1e4+grid64": "planted partition 10 x 1000 + 64x64 road-like grid (a seconds-long check of the "
                          "launch path, smaller than L2: not a performance workload); tau=0.05, cap 20",
 }
@@ -272,6 +276,7 @@ def workload_modes(args):
 def run_config(args, world):
     """The JSON line's config object, the same for both arms."""
     return {"workload": WORKLOAD_TEXT[args.workload], "tie_break": args.tie,
+            "storage_order": args.order,
             "async_pruning": "FLPA rule" if args.prune == "other" else "every neighbour",
             "inputs_larger_than_l2": True,
             "parallelism": f"replicas x{world}", "tau": TAU, "max_iters": MAX_ITERS}
@@ -668,8 +673,13 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=10_000, help="0 skips the serving sample")
     ap.add_argument("--serving-big-every", type=int, default=500,
                     help="an R-MAT scale 24 request every this many requests (0: none)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick each graph's degree-bin launch parameters with lpa_autotune (two timed runs per "
+                         "candidate) before the warm-up; the search time is reported, not timed")
+    ap.add_argument("--order", default="degree", choices=["caller", "degree", "shuffle"],
+                    help="storage order of the graphs' vertices (lpa_graph_create flags; labels stay caller ids)")
     ap.add_argument("--profile-only", action="store_true",
-                    help="create the workload's graphs, run each mode once through the host-launched profiled "
+                    help="create the workload's graphs, run each mode twice through the host-launched profiled "
                          "path (every kernel a separate launch, as ncu needs) and print the per-bin times")
     ap.add_argument("--tie", default="strict", choices=["strict", "nonstrict"],
                     help="tie-break among the most weighted labels (Section 4.1.5)")
@@ -704,14 +714,28 @@ def main():
     graphs = [make() for _, make in wl]
     modes = workload_modes(args)
     stream = torch.cuda.current_stream()
-    handles = [lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS, stream) for g in graphs]
+    order_flag = {"caller": 0, "degree": lpa.LPA_REORDER_DEGREE, "shuffle": lpa.LPA_REORDER_SHUFFLE}[args.order]
+    handles = [lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w, lpa.LPA_HOST_PTRS | order_flag, stream)
+               for g in graphs]
     outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in graphs]
+    tuned, tuned_cfgs = None, [None] * len(graphs)
+    if args.autotune:
+        tuned = {}
+        for gi, ((name, _), h) in enumerate(zip(wl, handles)):
+            cfg, info = lpa.lpa_autotune(h, modes[0], TAU, MAX_ITERS, 2, stream)
+            tuned_cfgs[gi] = cfg
+            tuned[name] = {"config": cfg.as_dict(), "default_ms": round(info["default_ms"], 3),
+                           "chosen_ms": round(info["chosen_ms"], 3), "search_ms": round(info["search_ms"], 1),
+                           "candidates": info["candidates"]}
+            print(json.dumps({"autotune": name, **tuned[name]}), file=sys.stderr, flush=True)
     if args.profile_only:
+        # two profiled runs per mode: the first one's times include the lazy
+        # loading of each kernel at its first launch
         for (name, _), h, o in zip(wl, handles, outs):
-            for m in modes:
+            for m, run in ((m, r) for m in modes for r in range(2)):
                 ri, prof = lpa.lpa_run_profiled(h, m, TAU, MAX_ITERS, o, stream)
                 p = prof.as_dict()
-                print(json.dumps({"graph": name, "mode": m, "iterations": ri.iterations,
+                print(json.dumps({"graph": name, "mode": m, "run": run, "iterations": ri.iterations,
                                   "bins": list(BIN_KERNELS), "sweep_ms": p["sweep_ms"],
                                   "finish_ms": p["finish_ms"], "bin_vertices": p["bin_vertices"],
                                   "bin_entries": p["bin_entries"]}), flush=True)
@@ -772,8 +796,10 @@ def main():
 
     def e2e_step():
         e = 0
-        for g, (t_off, t_idx, t_w, t_lab), o in zip(graphs, pinned, outs):
-            h = lpa.lpa_graph_create(g.n, g.nnz, t_off, t_idx, t_w, lpa.LPA_HOST_PTRS, stream)
+        for g, (t_off, t_idx, t_w, t_lab), o, cfg in zip(graphs, pinned, outs, tuned_cfgs):
+            h = lpa.lpa_graph_create(g.n, g.nnz, t_off, t_idx, t_w, lpa.LPA_HOST_PTRS | order_flag, stream)
+            if cfg is not None:
+                lpa.lpa_graph_set_config(h, cfg)
             for m in modes:
                 lpa.lpa_run(h, m, TAU, MAX_ITERS, o, stream, info=False)
                 t_lab.copy_(o, non_blocking=True)
@@ -881,7 +907,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-                "config": run_config(args, world),
+                "config": {**run_config(args, world), **({"autotuned": tuned} if tuned else {})},
                 "touched_edges_per_s": touched / (ms / 1e3),
                 "e2e": {"value": e2e_edges / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": args.e2e_steps},

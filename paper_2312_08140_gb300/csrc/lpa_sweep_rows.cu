@@ -10,18 +10,19 @@
 //
 //   * a row is cut into tiles of TILE = NT x P entries.  Warp 0 produces the
 //     tile sequence of the block (rows taken from a per-bin counter in
-//     batches of 32, their metadata loaded by the 32 lanes in parallel) two
-//     tiles ahead, and copies each tile's neighbour ids into one of two
-//     shared-memory buffers with one bulk asynchronous copy (cp.async.bulk,
-//     completion counted on an mbarrier);
+//     batches of 32, their metadata loaded by the 32 lanes in parallel)
+//     kStages tiles ahead, and copies each tile's neighbour ids into one of
+//     kStages shared-memory buffers with one bulk asynchronous copy
+//     (cp.async.bulk, completion counted on an mbarrier);
 //   * in step k every thread reads its P ids of tile k+1 from shared memory
 //     and issues their label gathers into registers, then aggregates tile k
 //     (whose labels arrived during step k-1): lanes holding the same label
 //     are grouped with __match_any_sync and the group leader adds the group's
 //     weight into a shared-memory open-addressing table, listing the slots it
 //     fills;
-//   * after a row's last tile the block scans the listed slots, reduces
-//     (sum, tie key) to the winner, records it and marks the neighbours.
+//   * after a row's last tile each warp scans the slots it listed and
+//     reduces (sum, tie key) to its candidate, a shared 64-bit maximum gives
+//     the block's winner, which is recorded, and the neighbours are marked.
 //     The next row's gathers are already in flight at that point.
 //
 // Rows whose distinct labels overflow the last bin's table (bounded probing
@@ -70,11 +71,13 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned by
 
 // dst (shared, 16-byte aligned) <- src (global, 16-byte aligned), bytes a
 // multiple of 16; completion adds `bytes` to the mbarrier's transaction count.
+// The row indices are read once per sweep: L2 evict-first.
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    const uint64_t pol = l2_policy_evict_first();
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
 
@@ -107,9 +110,59 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     }
 }
 
+// Entries [e, e + 4) of idx (e a multiple of 4, e < en; idx starts at a
+// 16-byte aligned address): one 16-byte load where the vector lies inside the
+// row [st, en), else entry by entry; entries outside the row read as `fill`.
+__device__ __forceinline__ void load_idx4(const int32_t* idx, int64_t e, int64_t st, int64_t en, int32_t fill,
+                                          int32_t (&j)[4]) {
+    if (e >= st && e + 4 <= en) {
+        const int4 x = __ldg(reinterpret_cast<const int4*>(idx + e));
+        j[0] = x.x;
+        j[1] = x.y;
+        j[2] = x.z;
+        j[3] = x.w;
+    } else {
+        // the first or last vector of the row
+#pragma unroll
+        for (int c = 0; c < 4; ++c) j[c] = (e + c >= st && e + c < en) ? __ldg(idx + e + c) : fill;
+    }
+}
+
+// Marks the neighbours of changed vertex v unprocessed (Section 4.1.4): the
+// GROUP threads of rank 0..GROUP-1 walk row [st, en) in 4-entry vectors,
+// VEC vectors per thread in flight (their ids, then their flags, then the
+// stores).  FLPA's rule (po) leaves a neighbour already carrying `best`.
+template <bool ASYNC, int GROUP, int VEC>
+__device__ __forceinline__ void mark_row(const DevState& s, const Labels& L, int64_t st, int64_t en, int32_t v,
+                                         unsigned rank, bool po, int32_t best) {
+    for (int64_t e0 = (st & ~(int64_t)3) + 4 * (int64_t)rank; e0 < en; e0 += 4 * GROUP * VEC) {
+        int32_t j[VEC][4];
+        uint8_t f[VEC][4];
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+            const int64_t e = e0 + 4 * GROUP * u;
+            if (e < en) {
+                load_idx4(s.idx, e, st, en, v, j[u]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) j[u][c] = v;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < VEC; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) f[u][c] = j[u][c] != v ? __ldcg(s.flags + j[u][c]) : (uint8_t)1;
+#pragma unroll
+        for (int u = 0; u < VEC; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (f[u][c] == 0 && !(po && load_label<ASYNC>(L.C, j[u][c]) == best)) s.flags[j[u][c]] = 1;
+    }
+}
+
 // ---- per-block shared state -----------------------------------------------
-// One tile: entries [e0, e1) of one row.  Written by warp 0 two steps before
-// it is aggregated.
+// One tile: entries [e0, e1) of one row.  Written by warp 0 kStages steps
+// before it is aggregated.
 struct Tile {
     int64_t e0, e1;        // entry range of the tile
     int64_t a0;            // first entry held by the tile's buffer (e0 rounded down to 4)
@@ -122,12 +175,15 @@ struct Tile {
     int32_t pad;
 };
 
-// Entries per thread per tile, entries per tile, and one index buffer.  The
-// unit-weight kernels of the wider blocks keep 8 gathers per thread in
-// flight (1 block of 512 or 2 of 256 threads per SM, no register spills).
+// Entries per thread per tile, tiles of gathers in flight ahead of the one
+// being aggregated, entries per tile, and one index buffer.  The unit-weight
+// kernels of the wider blocks keep 8 gathers per thread in flight (1 block of
+// 512 or 2 of 256 threads per SM, no register spills); a second tile of
+// gathers in flight (LA = 2) measured no faster on R-MAT 27.
 template <int NT, int WK>
 struct RowsShape {
     static constexpr int P = (NT >= 256 && WK == W_UNIT) ? 8 : 4;
+    static constexpr int LA = 1;                   // tiles whose gathers run ahead of the aggregated one
     static constexpr int TILE = NT * P;
     static constexpr int BUF = TILE + 8;       // + up to 3 entries of alignment slack on each side
 };
@@ -179,14 +235,14 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     __shared__ Tile tiles[2 * kStages];
     __shared__ RowMeta batch[kRowBatch];
     __shared__ ProdState prod;
-    __shared__ unsigned wcnt[32];                  // slots each warp filled for the current row
-    __shared__ uint32_t red_key[32], red_tie[32];
+    __shared__ unsigned long long row_best[2];     // packed winner of the current row (rows alternate)
     __shared__ int overflow, abort_flag;
 
     const unsigned lane = lane_id();
     const int wib = threadIdx.x >> 5;
     uint16_t* my_seg = segs + (size_t)wib * seg_cap;
     unsigned wfill = 0;
+    unsigned rb = 0;                                // row_best slot of the current row
     for (int q = threadIdx.x; q < S; q += NT) {
         keys[q] = kEmptyKey;
         vals[q] = (T)0;
@@ -196,6 +252,7 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
         fence_mbar_init();
         overflow = 0;
         abort_flag = 0;
+        row_best[0] = row_best[1] = 0ull;
         prod.pe = prod.pen = 0;
         prod.bpos = kRowBatch;
         prod.prow = -1;
@@ -218,39 +275,79 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
         // row's pick is the max of (weight key, tie key) over its entries.  No
         // gathers to hide, so no tiles: each warp takes whole rows from the
         // bin's counter (the largest first, as the list holds them) and
-        // streams them with plain loads, kIdentUnroll per lane in flight;
+        // streams them with 16-byte loads, kIdentVec per lane in flight;
         // NW rows per block are in flight at once and no block barrier runs.
-        constexpr int kIdentUnroll = 8;
+        constexpr int kIdentVec = NT >= 256 ? 4 : 2;    // 4-entry index vectors per lane in flight
         unsigned long long n_changed = 0, n_changed_entries = 0;
-        for (;;) {
-            unsigned k = 0;
-            if (lane == 0) k = atomicAdd(&s.ctrl->row_next[bin], 1u);
-            k = __shfl_sync(kFull, k, 0);
-            if (k >= cnt) break;
+        unsigned k = 0;
+        if (lane == 0) k = atomicAdd(&s.ctrl->row_next[bin], 1u);
+        k = __shfl_sync(kFull, k, 0);
+        while (k < cnt) {
+            // the warp's next row is claimed now and read after this one
+            unsigned k_next = 0;
+            if (lane == 0) k_next = atomicAdd(&s.ctrl->row_next[bin], 1u);
             const int32_t v = bv.list[k];
             const int64_t st = s.off[v], en = s.off_end[v];
             const int32_t own = ASYNC ? __ldcg(L.C + v) : L.C[v];
-            const TieRule tr = tie_rule(s, NS, sweep, v);
-            unsigned long long bp = 0ull;
-            for (int64_t e0 = st + lane; e0 < en; e0 += 32 * kIdentUnroll) {
-                int32_t jj[kIdentUnroll];
-                T ww[kIdentUnroll];
-#pragma unroll
-                for (int u = 0; u < kIdentUnroll; ++u) {
-                    const int64_t e = e0 + 32 * u;
-                    jj[u] = e < en ? load_index(s.idx, e) : v;
-                    ww[u] = e < en ? load_weight<WK>(s.w, e) : (T)0;
-                }
-#pragma unroll
-                for (int u = 0; u < kIdentUnroll; ++u) {
-                    if (jj[u] != v) {
-                        const unsigned long long c = pack_candidate(sum_key(ww[u]), tr.key(initial_label(s, jj[u])));
-                        bp = c > bp ? c : bp;
+            int32_t best_lab = -1;
+            if constexpr (!NS && WK == W_UNIT) {
+                // strict tie-break, unit weights: every label's sum is 1, so
+                // the pick is the smallest neighbour id; the row lists its
+                // neighbours in increasing caller id (the storage orders keep
+                // each row's entry order), so it is the first entry other
+                // than v itself
+                for (int64_t e0 = st; e0 < en; e0 += 32) {
+                    const int64_t e = e0 + lane;
+                    const int32_t j = e < en ? __ldg(s.idx + e) : v;
+                    const unsigned okm = __ballot_sync(kFull, j != v);
+                    if (okm != 0u) {
+                        best_lab = initial_label(s, __shfl_sync(kFull, j, __ffs(okm) - 1));
+                        break;
                     }
                 }
+            } else {
+                // max of (weight key, tie key); with the strict tie-break the
+                // tie key is the entry's position in the row (positions
+                // increase with the caller's neighbour ids), so no label is
+                // read but the winner's
+                const TieRule tr = tie_rule(s, NS, sweep, v);
+                unsigned long long bp = 0ull;
+                for (int64_t e0 = (st & ~(int64_t)3) + 4 * (int64_t)lane; e0 < en; e0 += 128 * kIdentVec) {
+                    int32_t jj[kIdentVec][4];
+                    T ww[kIdentVec][4];
+#pragma unroll
+                    for (int u = 0; u < kIdentVec; ++u) {
+                        const int64_t e = e0 + 128 * u;
+                        if (e < en) {
+                            load_idx4(s.idx, e, st, en, v, jj[u]);
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) jj[u][c] = v;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            if constexpr (WK == W_UNIT) ww[u][c] = (T)1;
+                            else ww[u][c] = jj[u][c] != v ? load_weight<WK>(s.w, e + c) : (T)0;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kIdentVec; ++u)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            if (jj[u][c] != v) {
+                                const uint32_t tie = NS ? tr.key(initial_label(s, jj[u][c]))
+                                                        : (uint32_t)(e0 + 128 * u + c - st);
+                                const unsigned long long cc = pack_candidate(sum_key(ww[u][c]), tie);
+                                bp = cc > bp ? cc : bp;
+                            }
+                        }
+                }
+                bp = warp_max_u64(bp);
+                if (bp != 0ull) {
+                    const uint32_t tie = ~(uint32_t)bp;
+                    best_lab = NS ? tr.label(tie) : initial_label(s, __ldg(s.idx + st + tie));
+                }
             }
-            bp = warp_max_u64(bp);
-            const int32_t best_lab = bp == 0ull ? -1 : tr.label(~(uint32_t)bp);
             const bool changed = best_lab >= 0 && best_lab != own;   // warp-uniform
             if (lane == 0) record_label<ASYNC>(L, bv.chg + k, v, own, best_lab, changed);
             if (changed) {
@@ -258,13 +355,9 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                     ++n_changed;
                     n_changed_entries += (unsigned long long)(en - st);
                 }
-                if (marks) {
-                    for (int64_t e = st + lane; e < en; e += 32) {
-                        const int32_t j = s.idx[e];
-                        if (j != v && !(po && load_label<ASYNC>(L.C, j) == best_lab)) mark_unprocessed(s.flags, j);
-                    }
-                }
+                if (marks) mark_row<ASYNC, 32, (NT >= 256 ? 2 : 1)>(s, L, st, en, v, lane, po, best_lab);
             }
+            k = __shfl_sync(kFull, k_next, 0);
         }
         flush_bin_counts(s, bin, n_changed, n_changed_entries);
         return;
@@ -379,8 +472,13 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     __syncthreads();
 
     // ---- consumer state ------------------------------------------------------
-    int32_t lab_cur[P], lab_nxt[P];
-    T w_cur[P], w_nxt[P];
+    // lab_q[0]: the tile being aggregated; lab_q[1..LA]: the next LA tiles,
+    // whose gathers are in flight
+    constexpr int LA = Sh::LA;
+    int32_t lab_q[LA + 1][P];
+    T w_q[LA + 1][P];
+    int32_t (&lab_cur)[P] = lab_q[0];
+    T (&w_cur)[P] = w_q[0];
     __shared__ unsigned long long blk_changed, blk_changed_entries;   // this block's changes (thread 0)
     if (threadIdx.x == 0) blk_changed = blk_changed_entries = 0ull;
 
@@ -407,9 +505,10 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     };
 
     bool alive = true;
-    {
-        const Tile& t0 = tiles[0];
-        if (t0.v >= 0 && !load_tile(t0, 0, 0u, lab_cur, w_cur)) {
+#pragma unroll
+    for (int a = 0; a < LA; ++a) {
+        const Tile& ta = tiles[a];
+        if (ta.v >= 0 && !load_tile(ta, a % kStages, (unsigned)(a / kStages) & 1u, lab_q[a], w_q[a])) {
             atomicExch(&s.ctrl->error, 5);
             abort_flag = 1;
         }
@@ -424,9 +523,9 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
         const Tile& tk = tiles[k % (2 * kStages)];
         if (tk.v < 0) break;
         if (wib == 0) produce();                       // tile k + kStages into buffer k % kStages
-        const Tile& tn = tiles[(k + 1) % (2 * kStages)];
+        const Tile& tn = tiles[(k + LA) % (2 * kStages)];
         if (tn.v >= 0 &&
-            !load_tile(tn, (int)((k + 1) % kStages), ((k + 1) / kStages) & 1u, lab_nxt, w_nxt)) {
+            !load_tile(tn, (int)((k + LA) % kStages), ((k + LA) / kStages) & 1u, lab_q[LA], w_q[LA])) {
             atomicExch(&s.ctrl->error, 5);
             abort_flag = 1;
         }
@@ -514,23 +613,15 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
             if (tk.skip) {
                 // a done graph's vertex keeps its label (batches)
             } else {
-                // two barriers per row: after the first the table, the slot
-                // lists and their per-warp counts are complete; every thread
-                // forms the count prefixes itself and, after the second, the
-                // block's winner from the per-warp candidates
-                if (lane == 0) wcnt[wib] = wfill;
-                wfill = 0;
-                __syncthreads();
-                unsigned pre[NW + 1];
-                pre[0] = 0;
-                unsigned mx = 0;
-#pragma unroll
-                for (int q = 0; q < NW; ++q) {
-                    const unsigned c = wcnt[q];
-                    mx = c > mx ? c : mx;
-                    pre[q + 1] = pre[q] + c;
-                }
-                const bool lists = mx <= seg_cap;
+                // two barriers per row.  The first completes the table and the
+                // slot lists, and tells every thread whether some warp's list
+                // overflowed (then the whole table is scanned).  Each warp
+                // scans the slots it created, reduces its candidates, and its
+                // lane 0 folds (sum key, ~tie key) into one packed 64-bit
+                // shared maximum; after the second barrier every thread reads
+                // the winner.  The two maxima alternate between rows, so the
+                // one for the next row is cleared here.
+                const int full_scan = __syncthreads_or(wfill > seg_cap);
                 ovf = overflow;
                 // this thread's best candidate among the row's slots; clears them
                 bool any = false;
@@ -550,35 +641,21 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                         vals[q] = (T)0;
                     }
                 };
-                if (lists) {
-                    const unsigned total = pre[NW];
-                    for (unsigned f = threadIdx.x; f < total; f += NT) {
-                        int q = 0;
-#pragma unroll
-                        for (int r = 1; r < NW; ++r) q += pre[r] <= f ? 1 : 0;
-                        visit(segs[(size_t)q * seg_cap + (f - pre[q])]);
-                    }
+                if (!full_scan) {
+                    for (unsigned f = lane; f < wfill; f += 32) visit(my_seg[f]);
                 } else {
                     for (int q = threadIdx.x; q < (1 << log_s); q += NT) visit(q);
                 }
+                wfill = 0;
                 const uint32_t key = any ? sum_key(best_w) : 0u;
                 const uint32_t m = __reduce_max_sync(kFull, key);
                 const uint32_t c = __reduce_min_sync(kFull, (m != 0 && key == m) ? best_k : 0xffffffffu);
-                if (lane == 0) {
-                    red_key[wib] = m;
-                    red_tie[wib] = c;
-                }
+                if (lane == 0 && m != 0u) atomicMax(&row_best[rb], pack_candidate(m, c));
                 __syncthreads();
-                uint32_t bk = 0, bt = 0xffffffffu;
-#pragma unroll
-                for (int q = 0; q < NW; ++q) {
-                    const uint32_t kq = red_key[q], tq = red_tie[q];
-                    if (kq > bk || (kq == bk && tq < bt)) {
-                        bk = kq;
-                        bt = tq;
-                    }
-                }
-                best_lab = (bk == 0u || bt == 0xffffffffu) ? -1 : tr.label(bt);
+                const unsigned long long bp = row_best[rb];
+                if (threadIdx.x == 0) row_best[rb ^ 1] = 0ull;
+                rb ^= 1;
+                best_lab = bp == 0ull ? -1 : tr.label(~(uint32_t)bp);
             }
             if (ovf) {
                 // hand the row to the partitioned kernels (last bin only)
@@ -604,31 +681,17 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                         blk_changed_entries += (unsigned long long)d;
                         if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
                     }
-                    if (marks) {
-                        // mark the neighbours unprocessed (Section 4.1.4), four
-                        // entries per thread in flight: their ids, then their flags
-                        const int64_t st = tk.st, en = tk.en;
-                        for (int64_t e0 = st + threadIdx.x; e0 < en; e0 += 4 * NT) {
-                            int32_t j[4];
-                            uint8_t f[4];
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) j[u] = e0 + u * NT < en ? s.idx[e0 + u * NT] : v;
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) f[u] = j[u] != v ? __ldcg(s.flags + j[u]) : (uint8_t)1;
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                if (f[u] == 0 && !(po && load_label<ASYNC>(L.C, j[u]) == best_lab)) s.flags[j[u]] = 1;
-                            }
-                        }
-                    }
+                    if (marks) mark_row<ASYNC, NT, (NT >= 256 ? 2 : 1)>(s, L, tk.st, tk.en, v, threadIdx.x, po, best_lab);
                 }
             }
         }
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            lab_cur[p] = lab_nxt[p];
-            w_cur[p] = w_nxt[p];
-        }
+        for (int a = 0; a < LA; ++a)
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                lab_q[a][p] = lab_q[a + 1][p];
+                w_q[a][p] = w_q[a + 1][p];
+            }
 
     }
     if (!alive && threadIdx.x == 0) {
@@ -640,8 +703,8 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     flush_bin_counts(s, bin, threadIdx.x == 0 ? blk_changed : 0ull, threadIdx.x == 0 ? blk_changed_entries : 0ull);
 }
 
-// Dynamic shared memory: two index buffers, the table (S keys, S values) and
-// the filled-slot lists (S / 2 two-byte entries).
+// Dynamic shared memory: kStages index buffers, the table (S keys, S values)
+// and the filled-slot lists (S / 2 two-byte entries).
 template <int NT, int WK>
 static size_t rows_smem(int S) {
     return (size_t)kStages * RowsShape<NT, WK>::BUF * 4 + (size_t)S * 8 + (size_t)S;

@@ -15,11 +15,25 @@ with the 0.02 absolute tolerance stated for the asynchronous mode:
     serial random orders (a run recovers a block or floods it: one batched
     graph gives 0.02-0.14 in seven orders of sixteen and 0.32-0.45 in nine),
     and a sixteen-run median then sits in either mode by chance; there the
-    GPU median must reach the serial lower quartile less 0.02;
+    GPU median must reach the serial lower quartile less 0.02, over 15 GPU
+    runs instead of 5 (a five-run median swings between the modes from one
+    box to the next: the 3000-vertex planted partition under FLPA's rule gave
+    GPU medians 0.49 and 0.04 with the same kernels, against serial runs
+    spread from 0 to 0.71);
   * every GPU run must reach the lowest serial run less 0.02;
-  * at an exit by tolerance at most floor(tau N) vertices may sit off their
-    local argmax (Algorithm 1 stops once at most a tau share of vertices
-    change in a sweep).
+  * at an exit by tolerance, the vertices off their local argmax are
+    neighbours of the vertices that changed in the last sweep (a vertex
+    scanned in that sweep picked its argmax from the labels it read, so only
+    a later change of a neighbour can move it off; a vertex not scanned had
+    no neighbour change since its last scan, or it would have been marked --
+    under FLPA's rule an unmarked neighbour already carries the new label,
+    which only adds to its own label's weight).  Their number is therefore at
+    most the sum of the dN largest degrees, dN the last sweep's changes.  The
+    tempting reading "at most floor(tau N), since the run stops once at most
+    tau N vertices change" does not follow (one change can move several
+    neighbours off): serial runs stay below 0.7% of N on the test graphs, but
+    a GPU batch run left 8 of 135 vertices off (floor(tau N) = 6) on a graph
+    whose serial runs reach 6.  The share is printed.
 
 Serial runs in monotone id order (ascending or descending) are not reference
 orders: with the smallest-id tie-break a monotone visit lets the smallest ids
@@ -75,12 +89,27 @@ def ascending_q(g, tau=0.05, iters=20):
     return _serial_q((g.off, g.idx, g.w, tau, iters, None, False))
 
 
+MULTIMODAL_RUNS = 15
+
+
+def concentrated(qs_serial):
+    """Whether the serial runs' interquartile range is at most SPREAD."""
+    q1, q3 = (float(x) for x in np.percentile(qs_serial, [25, 75]))
+    return q3 - q1 <= SPREAD
+
+
+def gpu_runs(qs_serial, runs=5):
+    """GPU runs to take against these serial runs: `runs`, or MULTIMODAL_RUNS
+    where the serial runs are not concentrated."""
+    return runs if concentrated(qs_serial) else max(runs, MULTIMODAL_RUNS)
+
+
 def quality_reference(qs_serial):
     """The serial statistic the GPU median is held to: the median when the
     serial runs are concentrated (interquartile range <= SPREAD), else the
     lower quartile."""
-    q1, med, q3 = (float(x) for x in np.percentile(qs_serial, [25, 50, 75]))
-    return (med, "median") if q3 - q1 <= SPREAD else (q1, "lower quartile")
+    q1, med = (float(x) for x in np.percentile(qs_serial, [25, 50]))
+    return (med, "median") if concentrated(qs_serial) else (q1, "lower quartile")
 
 
 def assert_async_quality(q_runs, qs_serial, what=""):
@@ -94,12 +123,31 @@ def assert_async_quality(q_runs, qs_serial, what=""):
     assert min(q_runs) >= lo_ser - SLACK, (what, min(q_runs), lo_ser)
 
 
-def assert_local_max_bound(g, labels, exit_reason, tau=0.05, what=""):
-    """At an exit by tolerance (exit_reason 0), at most floor(tau N) vertices
-    are off their local argmax (tie-insensitive: a vertex whose label has the
-    largest weight among its neighbours' labels, or with no other neighbour,
-    is at its local argmax).  Returns the count."""
+def _field(info, name):
+    return info[name] if isinstance(info, dict) else getattr(info, name)
+
+
+def neighbourhood_bound(g, changed_last):
+    """Sum of the changed_last largest degrees of g (at most N)."""
+    if changed_last <= 0:
+        return 0
+    deg = np.sort(np.diff(g.off))[::-1]
+    return int(min(g.n, deg[:changed_last].sum()))
+
+
+def assert_local_max_bound(g, labels, info, tau=0.05, what=""):
+    """At an exit by tolerance (exit_reason 0), the vertices off their local
+    argmax (tie-insensitive: a vertex whose label has the largest weight among
+    its neighbours' labels, or with no other neighbour, is at its local
+    argmax) number at most neighbourhood_bound(g, last sweep's changes).
+    `info` is a run's info (dict or LpaRunInfo).  Returns the count."""
     off = O.count_not_local_max(g.off, g.idx, g.w, labels)
-    if exit_reason == 0:
-        assert off <= int(np.floor(tau * g.n)), (what, off, g.n)
+    it = int(_field(info, "iterations"))
+    if int(_field(info, "exit_reason")) == 0 and it >= 1:
+        changed_last = int(_field(info, "changed")[it - 1])
+        bound = neighbourhood_bound(g, changed_last)
+        assert off <= bound, (what, off, bound, changed_last)
+        if off > np.floor(tau * g.n):
+            print(f"{what}: {off} of {g.n} vertices off their local argmax, above floor(tau N) "
+                  f"= {int(np.floor(tau * g.n))} (last sweep changed {changed_last}, bound {bound})")
     return off

@@ -3,7 +3,7 @@ modularity samples: which serial statistic the GPU median is held to, and
 that the rule rejects what it should."""
 import pytest
 
-from async_bounds import SLACK, assert_async_quality, quality_reference
+from async_bounds import MULTIMODAL_RUNS, SLACK, assert_async_quality, gpu_runs, quality_reference
 
 
 def test_concentrated_serial_runs_use_the_median():
@@ -28,3 +28,32 @@ def test_rule_accepts_and_rejects():
         assert_async_quality([0.73, 0.73, 0.73, 0.75, 0.75], qs)       # median 0.73 < 0.733
     with pytest.raises(AssertionError):
         assert_async_quality([0.75, 0.75, 0.75, 0.75, 0.72 - SLACK], qs)   # one run below min - 0.02
+
+
+def test_spread_serial_runs_take_more_gpu_runs():
+    concentrated = [0.750, 0.752, 0.753, 0.753, 0.754, 0.755, 0.756, 0.741]
+    spread = [0.0, 0.24, 0.24, 0.37, 0.52, 0.57, 0.62, 0.71]
+    assert gpu_runs(concentrated) == 5
+    assert gpu_runs(spread) == MULTIMODAL_RUNS and gpu_runs(spread, 20) == 20
+
+
+def test_neighbourhood_bound_of_the_local_argmax_check():
+    import numpy as np
+    import lpa_inputs as L
+    from async_bounds import assert_local_max_bound, neighbourhood_bound
+    # a star with centre 0 and 5 leaves, plus an edge 6-7: degrees 5, 1 x 5, 1, 1
+    g = L.from_undirected_pairs(8, [(0, k) for k in range(1, 6)] + [(6, 7)])
+    assert neighbourhood_bound(g, 0) == 0
+    assert neighbourhood_bound(g, 1) == 5
+    assert neighbourhood_bound(g, 2) == 6
+    assert neighbourhood_bound(g, 100) == 8
+    # the centre and its five leaves off their argmax (each leaf carries its
+    # own id, the centre a label none of its neighbours has): six vertices,
+    # allowed when the last sweep changed two vertices (bound 5 + 1), not one
+    lab = np.array([7, 1, 2, 3, 4, 5, 6, 6], dtype=np.int32)
+    assert assert_local_max_bound(g, lab, {"iterations": 2, "exit_reason": 0, "changed": [8, 2]}) == 6
+    for last in (1, 0):
+        with pytest.raises(AssertionError):
+            assert_local_max_bound(g, lab, {"iterations": 2, "exit_reason": 0, "changed": [8, last]})
+    # an exit by the cap is not bounded
+    assert assert_local_max_bound(g, lab, {"iterations": 2, "exit_reason": 1, "changed": [8, 0]}) == 6

@@ -93,10 +93,10 @@ def test_both_arms_share_modes_and_config():
 
     import lpa_inputs as L
     import oracle as O
-    args = argparse.Namespace(workload="rmat22+grid4096", tie="strict", prune="paper")
+    args = argparse.Namespace(workload="rmat22+grid4096", tie="strict", prune="paper", order="caller")
     assert bench.workload_modes(args) == ("sync", "async")
     assert bench.run_config(args, 1)["tie_break"] == "strict"
-    args = argparse.Namespace(workload="rmat22+grid4096", tie="nonstrict", prune="other")
+    args = argparse.Namespace(workload="rmat22+grid4096", tie="nonstrict", prune="other", order="caller")
     assert bench.workload_modes(args) == ("sync+nonstrict", "async+nonstrict+prune_other")
     cfg = bench.run_config(args, 2)
     assert cfg["async_pruning"] == "FLPA rule" and cfg["parallelism"] == "replicas x2"

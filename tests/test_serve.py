@@ -10,7 +10,7 @@ import pytest
 
 import lpa_inputs as L
 import oracle as O
-from async_bounds import assert_async_quality, assert_local_max_bound, serial_qs
+from async_bounds import assert_async_quality, assert_local_max_bound, gpu_runs, serial_qs
 
 
 def test_serve_config_is_validated_before_any_device_call():
@@ -110,17 +110,19 @@ def test_serve_busy_then_admitted_and_solo_lane():
 
 @pytest.mark.gpu
 def test_serve_async_invariants():
-    """Asynchronous requests served in the mix, each graph five times: labels
-    inside components, the off-local-argmax bound at a tolerance exit, and the
-    modularity bound of async_bounds per graph over its five results."""
+    """Asynchronous requests served in the mix, each graph five times (fifteen
+    if a graph's serial runs are not concentrated): labels inside components,
+    the off-local-argmax bound at a tolerance exit, and the modularity bound
+    of async_bounds per graph over its results."""
     import paper_2312_08140_gb300 as lpa
     lpa.load()
     graphs = [L.batched_sbm_graph(g, n_max=5000) for g in range(50, 70)]
     srv = lpa.lpa_serve_create(hbm_budget_bytes=4 << 30, arena_vertices=200_000, arena_entries=10_000_000,
                                max_slots=32, mode="async")
     try:
+        serial = [serial_qs(g) for g in graphs]
         qs = [[] for _ in graphs]
-        for r in range(5):
+        for r in range(max(gpu_runs(sq) for sq in serial)):
             tickets = {lpa.lpa_serve_submit(srv, g.n, g.nnz, g.off, g.idx, g.w): k for k, g in enumerate(graphs)}
             _drain(lpa, srv, tickets)
             for t, k in tickets.items():
@@ -129,10 +131,10 @@ def test_serve_async_invariants():
                 lpa.lpa_serve_release(srv, t)
                 assert O.count_labels_outside_component(g.off, g.idx, lab) == 0
                 assert 1 <= info.iterations <= 20
-                assert_local_max_bound(g, lab, info.exit_reason, 0.05, f"served graph {k}")
+                assert_local_max_bound(g, lab, info, 0.05, f"served graph {k}")
                 qs[k].append(O.modularity(g.off, g.idx, g.w, lab))
         for k, g in enumerate(graphs):
-            assert_async_quality(qs[k], serial_qs(g), f"served graph {k}")
+            assert_async_quality(qs[k], serial[k], f"served graph {k}")
     finally:
         lpa.lpa_serve_destroy(srv)
 
