@@ -676,7 +676,7 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="pick each graph's degree-bin launch parameters with lpa_autotune (two timed runs per "
                          "candidate) before the warm-up; the search time is reported, not timed")
-    ap.add_argument("--order", default="degree", choices=["caller", "degree", "shuffle"],
+    ap.add_argument("--order", default="caller", choices=["caller", "degree", "shuffle"],
                     help="storage order of the graphs' vertices (lpa_graph_create flags; labels stay caller ids)")
     ap.add_argument("--profile-only", action="store_true",
                     help="create the workload's graphs, run each mode twice through the host-launched profiled "

@@ -57,3 +57,30 @@ def test_neighbourhood_bound_of_the_local_argmax_check():
             assert_local_max_bound(g, lab, {"iterations": 2, "exit_reason": 0, "changed": [8, last]})
     # an exit by the cap is not bounded
     assert assert_local_max_bound(g, lab, {"iterations": 2, "exit_reason": 1, "changed": [8, 0]}) == 6
+
+
+def test_tolerance_fraction_of_the_local_argmax_check():
+    import numpy as np
+    import lpa_inputs as L
+    from async_bounds import LOCAL_MAX_MIN_N, assert_local_max_bound
+    # a path of 2000 vertices in pairs (0-1, 2-3, ...) joined in a chain; the
+    # pair partner labels make every vertex its pair's label -> at argmax
+    n = 2000
+    assert n >= LOCAL_MAX_MIN_N
+    pairs = [(2 * i, 2 * i + 1) for i in range(n // 2)]
+    g = L.from_undirected_pairs(n, pairs)
+    lab = np.repeat(np.arange(0, n, 2), 2).astype(np.int32)
+    info = {"iterations": 1, "exit_reason": 0, "changed": [200]}
+    assert assert_local_max_bound(g, lab, info) == 0
+    # 101 pairs split: 202 vertices off, above floor(0.05 * 2000) = 100
+    bad = lab.copy()
+    bad[1:404:4] = np.arange(1, 404, 4)[: bad[1:404:4].size]
+    assert O_count(g, bad) > 100
+    # within the neighbourhood bound (every vertex changed last), above tau N
+    with pytest.raises(AssertionError, match="off|202"):
+        assert_local_max_bound(g, bad, {"iterations": 1, "exit_reason": 0, "changed": [n]})
+
+
+def O_count(g, lab):
+    import oracle as O
+    return O.count_not_local_max(g.off, g.idx, g.w, lab)

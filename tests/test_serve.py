@@ -134,7 +134,7 @@ def test_serve_async_invariants():
                 assert_local_max_bound(g, lab, info, 0.05, f"served graph {k}")
                 qs[k].append(O.modularity(g.off, g.idx, g.w, lab))
         for k, g in enumerate(graphs):
-            assert_async_quality(qs[k], serial[k], f"served graph {k}")
+            assert_async_quality(qs[k][:gpu_runs(serial[k])], serial[k], f"served graph {k}")
     finally:
         lpa.lpa_serve_destroy(srv)
 
