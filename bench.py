@@ -441,9 +441,9 @@ def batched_sample_full(lpa, torch, stream, G=4096, reps=3):
     nnz = np.diff(eo)
     res = {"graphs": G, "vertices": N, "entries": int(eo[-1]), "inputs": "drawn on the device"}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for m in MODES:
-        infos = lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=True)
-        edges = int(sum(int(nnz[k]) * infos[k].iterations for k in range(G)))
+    default_cfg = lpa.lpa_batch_get_config(b)
+
+    def timed(m):
         lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=False)
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -451,8 +451,23 @@ def batched_sample_full(lpa, torch, stream, G=4096, reps=3):
             lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=False)
         ev1.record(stream)
         torch.cuda.synchronize()
-        sec = ev0.elapsed_time(ev1) / 1e3 / reps
-        res[m] = {"batched_graphs_per_s": G / sec, "batched_edges_per_s": edges / sec, "batched_ms": sec * 1e3}
+        return ev0.elapsed_time(ev1) / 1e3 / reps
+
+    for m in MODES:
+        lpa.lpa_batch_set_config(b, default_cfg)
+        infos = lpa.lpa_batch_run(b, G, m, TAU, MAX_ITERS, out, stream, info=True)
+        edges = int(sum(int(nnz[k]) * infos[k].iterations for k in range(G)))
+        sec = timed(m)
+        res[m] = {"batched_graphs_per_s": G / sec, "batched_edges_per_s": edges / sec, "batched_ms": sec * 1e3,
+                  "config": default_cfg.as_dict()}
+        # the batched autotuner: a search timed on a sampled sub-batch (1/8 of
+        # the entries), its pick then timed on the whole batch
+        cfg, tinfo = lpa.lpa_batch_autotune(b, m, TAU, MAX_ITERS, 2, 125, stream)
+        sec_t = timed(m)
+        res[m]["autotuned"] = {"config": cfg.as_dict(), "batched_graphs_per_s": G / sec_t,
+                               "batched_ms": sec_t * 1e3, "search_ms": tinfo["search_ms"],
+                               "candidates": tinfo["candidates"], "sample_graphs": tinfo["sample_graphs"]}
+    lpa.lpa_batch_set_config(b, default_cfg)
     lpa.lpa_batch_destroy(b)
     handles, outs = [], []
     for k in range(G):

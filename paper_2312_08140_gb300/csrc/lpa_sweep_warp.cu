@@ -27,6 +27,7 @@ constexpr int kWarpThreads = 256;
 constexpr int kWarpsPerBlock = kWarpThreads / 32;
 constexpr int kWarpUnroll = 3;      // chunks of 32 entries in flight per warp beyond the first
 constexpr unsigned kAsyncMinBatch = 16;       // async: at least this many consecutive visits per warp batch
+constexpr unsigned kAsyncMaxRunBatches = 8;   // async: batches a warp walks in one run
 constexpr unsigned kScatterWindow = 4096;   // batches per scattered window (a power of two)
 
 // Combined weight of the lanes in `peers` (all hold the same label).
@@ -102,12 +103,23 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_sweep_warp(DevState s, int 
     // blocks.  The windows keep the labels being gathered at a time to a few
     // graphs' worth (L2-resident) in large batches.
     const unsigned nbatch = (cnt + B - 1) / B;
-    const unsigned full_windows = nbatch / kScatterWindow;
+    // Asynchronous mode: a warp walks K consecutive batches in order (a run
+    // of K x B vertices), K as large as 8 while the bin still gives every
+    // warp at least two runs; fewer runs in flight at once means fewer
+    // vertices reading labels their neighbours are about to change (a
+    // 140K-vertex planted partition inside a 4096-graph batch: median Q 0.645
+    // with single batches, 0.750 with runs of 8, serial runs 0.745).
+    unsigned K = 1;
+    if (ASYNC)
+        while (K < kAsyncMaxRunBatches && (unsigned long long)nbatch >= 2ull * (2u * K) * nwarps) K *= 2u;
+    const unsigned nruns = (nbatch + K - 1) / K;
+    const unsigned full_windows = nruns / kScatterWindow;
     unsigned long long my_changed = 0, my_changed_entries = 0;
-    for (unsigned bi = blockIdx.x * kWarpsPerBlock + wib; bi < nbatch; bi += nwarps) {
-        unsigned pb = bi;
-        if (ASYNC && bi / kScatterWindow < full_windows)
-            pb = (bi & ~(kScatterWindow - 1u)) | ((bi * 0x9E3779B1u) & (kScatterWindow - 1u));
+    for (unsigned ri = blockIdx.x * kWarpsPerBlock + wib; ri < nruns; ri += nwarps) {
+        unsigned pr = ri;
+        if (ASYNC && ri / kScatterWindow < full_windows)
+            pr = (ri & ~(kScatterWindow - 1u)) | ((ri * 0x9E3779B1u) & (kScatterWindow - 1u));
+      for (unsigned pb = pr * K; pb < pr * K + K && pb < nbatch; ++pb) {
         const unsigned base = pb * B;
         // Metadata of up to B consecutive frontier entries, one per lane, loaded
         // together so their latencies overlap.
@@ -345,6 +357,7 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_sweep_warp(DevState s, int 
                 }
             }
         }
+      }
     }
     flush_bin_counts(s, 1, my_changed, my_changed_entries);
 }
