@@ -118,15 +118,18 @@ WORKLOAD_TEXT = {
 # the kernel in one step of the profiled run path), valid only while the
 # kernel's sources are unchanged (sha1 of the files below).
 TRAFFIC = {
-    "k_sweep_small": {"bytes_per_launch": 399.2e6, "sha1": "fc00dc6ef1ef77ae301905acedb1714e310d8f24",
-                      "files": ["lpa_sweep_small.cu", "lpa_device.cuh", "lpa_internal.h"]},
+    # R-MAT 27, asynchronous, caller's storage order: 83.05 GB over the six
+    # launches of one run (profiles/dram_traffic_rmat27_async.md)
+    "k_sweep_rows<512>": {"bytes_per_launch": 13.842e9, "sha1": "895dc1413ca3130d534dd653f68e4a13308a462f",
+                          "workload": "rmat27", "order": "caller",
+                          "files": ["lpa_sweep_rows.cu", "lpa_device.cuh", "lpa_internal.h"]},
 }
 
 
-def measured_traffic(kernel):
+def measured_traffic(kernel, args):
     import hashlib
     t = TRAFFIC.get(kernel)
-    if not t:
+    if not t or t["workload"] != args.workload or t["order"] != args.order:
         return None
     h = hashlib.sha1()
     for f in t["files"]:
@@ -857,9 +860,13 @@ def main():
         dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
         d = kernels[dom]
         roofline = {"bound": "hbm", "kernel": dom, "achieved": d["GB_per_s"], "peak": hbm, "unit": "GB/s",
-                    "frac": d["GB_per_s"] / hbm, "peak_kind": hbm_kind, "traffic": measured_traffic(dom),
+                    "frac": d["GB_per_s"] / hbm, "peak_kind": hbm_kind, "traffic": measured_traffic(dom, args),
                     "bytes_per_launch": d["bytes_per_launch"],
                     "mean_launch_ms": d["ms_per_step"] / d["launches_per_step"]}
+        if roofline["traffic"]:
+            # the DRAM bytes ncu counted per launch, at this run's launch time
+            roofline["traffic_GB_per_s"] = roofline["traffic"] / (roofline["mean_launch_ms"] / 1e3) / 1e9
+            roofline["traffic_frac"] = roofline["traffic_GB_per_s"] / hbm
         tot_b = sum(a["bytes"] for a in agg.values())
         tot_ms = sum(a["ms"] for a in agg.values())
         if tot_ms > 0:

@@ -50,14 +50,20 @@ def test_async_counts_two_passes_and_4_byte_changes():
 
 
 def test_traffic_is_reported_only_for_the_captured_sources(monkeypatch):
-    """The ncu DRAM bytes stand for the kernel sources they were captured
-    from: any edit to those files (another sha1) turns them into null."""
-    assert bench.measured_traffic("k_no_such_kernel") is None
-    rec = dict(bench.TRAFFIC["k_sweep_small"])
-    got = bench.measured_traffic("k_sweep_small")
+    """The ncu DRAM bytes stand for the kernel sources, workload and storage
+    order they were captured from: another sha1 (any edit to those files),
+    workload or order turns them into null."""
+    import argparse
+    args = argparse.Namespace(workload="rmat27", order="caller")
+    assert bench.measured_traffic("k_no_such_kernel", args) is None
+    k = "k_sweep_rows<512>"
+    rec = dict(bench.TRAFFIC[k])
+    got = bench.measured_traffic(k, args)
     assert got is None or got == rec["bytes_per_launch"]
-    monkeypatch.setitem(bench.TRAFFIC, "k_sweep_small", dict(rec, sha1="0" * 40))
-    assert bench.measured_traffic("k_sweep_small") is None
+    assert bench.measured_traffic(k, argparse.Namespace(workload="rmat27", order="degree")) is None
+    assert bench.measured_traffic(k, argparse.Namespace(workload="rmat25", order="caller")) is None
+    monkeypatch.setitem(bench.TRAFFIC, k, dict(rec, sha1="0" * 40))
+    assert bench.measured_traffic(k, args) is None
 
 
 def test_clock_summary_takes_the_median_and_every_active_reason():
