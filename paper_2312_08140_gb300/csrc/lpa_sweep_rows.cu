@@ -8,12 +8,18 @@
 // 4.1.4).  The gathers are random 4-byte reads, so the kernel is bound by how
 // many of them are in flight.  It keeps them in flight across the whole pass:
 //
-//   * a row is cut into tiles of TILE = NT x P entries.  Warp 0 produces the
-//     tile sequence of the block (rows taken from a per-bin counter in
-//     batches of 32, their metadata loaded by the 32 lanes in parallel)
-//     kStages tiles ahead, and copies each tile's neighbour ids into one of
-//     kStages shared-memory buffers with one bulk asynchronous copy
-//     (cp.async.bulk, completion counted on an mbarrier);
+//   * a row is cut into tiles of TILE = NC x P entries, NC the aggregating
+//     threads.  One warp produces the tile sequence of the block (rows taken
+//     from a per-bin counter in batches of 32, their metadata loaded by the
+//     32 lanes in parallel) up to kStages tiles ahead, and copies each tile's
+//     neighbour ids into one of kStages shared-memory buffers with one bulk
+//     asynchronous copy (cp.async.bulk, completion counted on an mbarrier).
+//     In the 256- and 512-thread kernels the last warp only produces: it
+//     refills a buffer once the other warps have signalled (a second
+//     mbarrier per buffer) that they read it, and those warps synchronise on
+//     a named barrier of their own, so the producer's work never holds up a
+//     step.  In the 128-thread kernel warp 0 produces between its own
+//     aggregation steps;
 //   * in step k every thread reads its P ids of tile k+1 from shared memory
 //     and issues their label gathers into registers, then aggregates tile k
 //     (whose labels arrived during step k-1): lanes holding the same label
@@ -81,6 +87,29 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
         : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Named barrier 1 over the first `count` threads of the block (a multiple
+// of 32): the consumer warps of the row kernels with a producer warp.
+__device__ __forceinline__ void named_sync(unsigned count) {
+    asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+
+__device__ __forceinline__ int named_sync_or(unsigned count, bool pred) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)pred), "r"(count)
+        : "memory");
+    return (int)r;
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     unsigned ok;
     asm volatile(
@@ -107,6 +136,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity
     for (unsigned polls = 1;; ++polls) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((polls & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// The same wait, also giving up once *stop is set.
+__device__ __forceinline__ bool mbar_wait_bounded_or(uint64_t* bar, unsigned parity, const volatile int* stop) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned polls = 1;; ++polls) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((polls & 63u) == 0 && (*stop || global_ns() - t0 > kWaitNs)) return false;
     }
 }
 
@@ -182,9 +221,11 @@ struct Tile {
 // gathers in flight (LA = 2) measured no faster on R-MAT 27.
 template <int NT, int WK>
 struct RowsShape {
+    static constexpr bool SPEC = NT >= 256;        // the last warp only produces tiles
+    static constexpr int NC = SPEC ? NT - 32 : NT; // threads that aggregate
     static constexpr int P = (NT >= 256 && WK == W_UNIT) ? 8 : 4;
     static constexpr int LA = 1;                   // tiles whose gathers run ahead of the aggregated one
-    static constexpr int TILE = NT * P;
+    static constexpr int TILE = NC * P;
     static constexpr int BUF = TILE + 8;       // + up to 3 entries of alignment slack on each side
 };
 
@@ -223,15 +264,20 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     using Sh = RowsShape<NT, WK>;
     constexpr int P = Sh::P;
     constexpr int NW = NT / 32;
+    constexpr bool SPEC = Sh::SPEC;            // the last warp produces, the others aggregate
+    constexpr int NC = Sh::NC;                 // aggregating threads
+    constexpr int NWC = NC / 32;
+    constexpr int PW = SPEC ? NW - 1 : 0;      // the producing warp
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // layout: kStages index buffers | table keys | table values | filled-slot lists
     int32_t* ibuf = reinterpret_cast<int32_t*>(smem_raw);                   // [kStages][BUF]
     const int S = s.block_slots[bin - 2];
     int32_t* keys = ibuf + kStages * Sh::BUF;
     T* vals = reinterpret_cast<T*>(keys + S);
-    const unsigned seg_cap = (unsigned)S / 2u / NW;
+    const unsigned seg_cap = (unsigned)S / 2u / NWC;
     uint16_t* segs = reinterpret_cast<uint16_t*>(vals + S);
-    __shared__ __align__(8) uint64_t mbar[kStages];
+    __shared__ __align__(8) uint64_t mbar[kStages];        // full: a tile's indices (and descriptor) landed
+    __shared__ __align__(8) uint64_t mbar_empty[kStages];  // producer warp only: a buffer was read
     __shared__ Tile tiles[2 * kStages];
     __shared__ RowMeta batch[kRowBatch];
     __shared__ ProdState prod;
@@ -240,7 +286,7 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
 
     const unsigned lane = lane_id();
     const int wib = threadIdx.x >> 5;
-    uint16_t* my_seg = segs + (size_t)wib * seg_cap;
+    uint16_t* my_seg = segs + (size_t)(wib < NWC ? wib : 0) * seg_cap;
     unsigned wfill = 0;
     unsigned rb = 0;                                // row_best slot of the current row
     for (int q = threadIdx.x; q < S; q += NT) {
@@ -248,7 +294,10 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
         vals[q] = (T)0;
     }
     if (threadIdx.x == 0) {
-        for (int b = 0; b < kStages; ++b) mbar_init(&mbar[b], 1);
+        for (int b = 0; b < kStages; ++b) {
+            mbar_init(&mbar[b], 1);
+            mbar_init(&mbar_empty[b], 1);
+        }
         fence_mbar_init();
         overflow = 0;
         abort_flag = 0;
@@ -400,8 +449,9 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
         }
         __syncwarp();
     };
-    // Warp 0: writes the descriptor of the next tile into tiles[produced % 8]
-    // and starts its copy into buffer produced % kStages.  All 32 lanes call.
+    // The producing warp: writes the descriptor of the next tile into
+    // tiles[produced % 8] and starts its copy into buffer produced % kStages.
+    // All 32 lanes call.
     auto produce = [&]() {
         for (;;) {                                     // warp-uniform: every lane reads the same state
             if (prod.exhausted || prod.pe < prod.pen) break;
@@ -452,13 +502,15 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&mbar[b], (unsigned)bytes);
                 if (bytes > 0) bulk_copy_g2s(dst, s.idx + t.a0, (unsigned)bytes, &mbar[b]);
+            } else if (SPEC) {
+                mbar_arrive(&mbar[b]);                 // the end of the sequence, for the waiting consumers
             }
         }
         ++produced;
         __syncwarp();
     };
 
-    if (wib == 0) {
+    if (wib == PW) {
         unsigned b0 = 0;
         if (lane == 0) b0 = atomicAdd(&s.ctrl->row_next[bin], (unsigned)kRowBatch);
         nxt_base = __shfl_sync(kFull, b0, 0);
@@ -466,10 +518,41 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
         if (lane == 0) nn_base = atomicAdd(&s.ctrl->row_next[bin], (unsigned)kRowBatch);
     }
     __syncthreads();                                   // mbarriers initialised, table clear
-    if (wib == 0) {
-        for (int q = 0; q < kStages; ++q) produce();
+    __shared__ unsigned long long blk_changed, blk_changed_entries;   // this block's changes (thread 0)
+    if (threadIdx.x == 0) blk_changed = blk_changed_entries = 0ull;
+    if constexpr (!SPEC) {
+        if (wib == 0) {
+            for (int q = 0; q < kStages; ++q) produce();
+        }
+        __syncthreads();
+    } else if (wib == PW) {
+        // ---- the producing warp: tile t goes into buffer t % kStages once the
+        // aggregating warps have read tile t - kStages from it (mbar_empty),
+        // up to and including the end of the sequence (v = -1)
+        for (unsigned t = 0;; ++t) {
+            const unsigned b = t % kStages;
+            if (t >= kStages) {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait_bounded_or(&mbar_empty[b], ((t / kStages) - 1u) & 1u, &abort_flag);
+                ok = __shfl_sync(kFull, ok, 0) != 0;
+                if (!ok) {
+                    if (lane == 0 && !abort_flag) {
+                        atomicExch(&s.ctrl->error, 5);
+                        abort_flag = 1;
+                    }
+                    break;
+                }
+            }
+            produce();
+            if (tiles[t % (2 * kStages)].v < 0) break;
+        }
+        // after an abort, let the copies still in flight land before the
+        // block can leave
+        if (lane == 0 && abort_flag)
+            for (unsigned q = produced >= kStages ? produced - kStages : 0; q < produced; ++q)
+                if (tiles[q % (2 * kStages)].v >= 0) (void)mbar_wait_bounded(&mbar[q % kStages], (q / kStages) & 1u);
     }
-    __syncthreads();
+    if (!(SPEC && wib == PW)) {
 
     // ---- consumer state ------------------------------------------------------
     // lab_q[0]: the tile being aggregated; lab_q[1..LA]: the next LA tiles,
@@ -479,21 +562,24 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     T w_q[LA + 1][P];
     int32_t (&lab_cur)[P] = lab_q[0];
     T (&w_cur)[P] = w_q[0];
-    __shared__ unsigned long long blk_changed, blk_changed_entries;   // this block's changes (thread 0)
-    if (threadIdx.x == 0) blk_changed = blk_changed_entries = 0ull;
 
-    // Reads tile t's ids (buffer b, phase `par`) and issues their gathers.
-    // The descriptor is read into registers once.
-    auto load_tile = [&](const Tile& t, int b, unsigned par, int32_t (&lab)[P], T (&w)[P]) -> bool {
+    // Waits for tile t (buffer t % kStages, phase (t / kStages) & 1; with a
+    // producing warp, its descriptor lands with it), then reads the tile's
+    // ids and issues their gathers.  Returns false if the wait gave up.
+    auto load_tile = [&](unsigned t_idx, int32_t (&lab)[P], T (&w)[P]) -> bool {
+        const int b = (int)(t_idx % kStages);
+        const Tile& t = tiles[t_idx % (2 * kStages)];
+        if (!SPEC && t.v < 0) return true;               // no copy: nothing to wait for
+        if (!mbar_wait_bounded(&mbar[b], (t_idx / kStages) & 1u)) return false;
+        if (t.v < 0) return true;
         const int64_t e0 = t.e0;
         const int32_t n = (int32_t)(t.e1 - e0);
         const int32_t* src = ibuf + b * Sh::BUF + (int32_t)(e0 - t.a0);
         const int32_t v = t.v;
         const bool on = !t.skip;
-        if (!mbar_wait_bounded(&mbar[b], par)) return false;
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const int r = p * NT + (int)threadIdx.x;
+            const int r = p * NC + (int)threadIdx.x;
             const bool in = on && r < n;
             const int32_t j = in ? src[r] : v;
             const bool ok = in && j != v;
@@ -507,25 +593,30 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
     bool alive = true;
 #pragma unroll
     for (int a = 0; a < LA; ++a) {
-        const Tile& ta = tiles[a];
-        if (ta.v >= 0 && !load_tile(ta, a % kStages, (unsigned)(a / kStages) & 1u, lab_q[a], w_q[a])) {
+        if (!load_tile((unsigned)a, lab_q[a], w_q[a])) {
             atomicExch(&s.ctrl->error, 5);
             abort_flag = 1;
         }
     }
 
     for (unsigned k = 0;; ++k) {
-        __syncthreads();                               // step k-1 done: buffer k % kStages is free
-        if (abort_flag) {
+        // step k-1 done: buffer k % kStages is free
+        int stop;
+        if constexpr (SPEC) {
+            stop = named_sync_or(NC, abort_flag != 0);   // the producer may set the flag at any time
+            if (threadIdx.x == 0) mbar_arrive(&mbar_empty[k % kStages]);
+        } else {
+            __syncthreads();
+            stop = abort_flag;
+        }
+        if (stop) {
             alive = false;
             break;
         }
         const Tile& tk = tiles[k % (2 * kStages)];
         if (tk.v < 0) break;
-        if (wib == 0) produce();                       // tile k + kStages into buffer k % kStages
-        const Tile& tn = tiles[(k + LA) % (2 * kStages)];
-        if (tn.v >= 0 &&
-            !load_tile(tn, (int)((k + LA) % kStages), ((k + LA) / kStages) & 1u, lab_q[LA], w_q[LA])) {
+        if (!SPEC && wib == 0) produce();              // tile k + kStages into buffer k % kStages
+        if (!load_tile(k + LA, lab_q[LA], w_q[LA])) {
             atomicExch(&s.ctrl->error, 5);
             abort_flag = 1;
         }
@@ -587,7 +678,7 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
             } else {
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    if (p * NT + (int)(wib * 32) >= k_n) break;       // warp-uniform
+                    if (p * NC + (int)(wib * 32) >= k_n) break;       // warp-uniform
                     const bool ok = lab_cur[p] != kEmptyKey;
                     T wsum = w_cur[p];
                     bool lead = ok;
@@ -621,7 +712,9 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                 // shared maximum; after the second barrier every thread reads
                 // the winner.  The two maxima alternate between rows, so the
                 // one for the next row is cleared here.
-                const int full_scan = __syncthreads_or(wfill > seg_cap);
+                int full_scan;
+                if constexpr (SPEC) full_scan = named_sync_or(NC, wfill > seg_cap);
+                else full_scan = __syncthreads_or(wfill > seg_cap);
                 ovf = overflow;
                 // this thread's best candidate among the row's slots; clears them
                 bool any = false;
@@ -644,14 +737,15 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                 if (!full_scan) {
                     for (unsigned f = lane; f < wfill; f += 32) visit(my_seg[f]);
                 } else {
-                    for (int q = threadIdx.x; q < (1 << log_s); q += NT) visit(q);
+                    for (int q = threadIdx.x; q < (1 << log_s); q += NC) visit(q);
                 }
                 wfill = 0;
                 const uint32_t key = any ? sum_key(best_w) : 0u;
                 const uint32_t m = __reduce_max_sync(kFull, key);
                 const uint32_t c = __reduce_min_sync(kFull, (m != 0 && key == m) ? best_k : 0xffffffffu);
                 if (lane == 0 && m != 0u) atomicMax(&row_best[rb], pack_candidate(m, c));
-                __syncthreads();
+                if constexpr (SPEC) named_sync(NC);
+                else __syncthreads();
                 const unsigned long long bp = row_best[rb];
                 if (threadIdx.x == 0) row_best[rb ^ 1] = 0ull;
                 rb ^= 1;
@@ -681,7 +775,7 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                         blk_changed_entries += (unsigned long long)d;
                         if constexpr (BATCH) atomicAdd(&s.dN[s.gid[v]], 1ull);
                     }
-                    if (marks) mark_row<ASYNC, NT, (NT >= 256 ? 2 : 1)>(s, L, tk.st, tk.en, v, threadIdx.x, po, best_lab);
+                    if (marks) mark_row<ASYNC, NC, (NT >= 256 ? 2 : 1)>(s, L, tk.st, tk.en, v, threadIdx.x, po, best_lab);
                 }
             }
         }
@@ -694,11 +788,12 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
             }
 
     }
-    if (!alive && threadIdx.x == 0) {
+    if (!SPEC && !alive && threadIdx.x == 0) {
         // let the copies this block started land before it leaves
         for (unsigned q = produced >= kStages ? produced - kStages : 0; q < produced; ++q)
             if (tiles[q % (2 * kStages)].v >= 0) (void)mbar_wait_bounded(&mbar[q % kStages], (q / kStages) & 1u);
     }
+    }  // the aggregating warps
     __syncthreads();
     flush_bin_counts(s, bin, threadIdx.x == 0 ? blk_changed : 0ull, threadIdx.x == 0 ? blk_changed_entries : 0ull);
 }

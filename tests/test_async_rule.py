@@ -12,13 +12,23 @@ def test_concentrated_serial_runs_use_the_median():
     assert kind == "median" and ref == pytest.approx(0.753)
 
 
+def test_wide_serial_runs_keep_only_the_range_rule():
+    # serial runs from 0 to 0.61: a block floods or not by the order alone
+    qs = [0.0, 0.0, 0.25, 0.26, 0.26, 0.36, 0.37, 0.47, 0.47, 0.51, 0.54, 0.58, 0.58, 0.61, 0.26, 0.26]
+    ref, kind = quality_reference(qs)
+    assert ref is None and kind == "range"
+    assert_async_quality([0.14, 0.14, 0.0, 0.14, 0.0], qs)
+    with pytest.raises(AssertionError):
+        assert_async_quality([0.14, 0.14, -0.03, 0.14, 0.0], qs)
+
+
 def test_bimodal_serial_runs_use_the_lower_quartile():
-    # seven runs flood a block, nine recover it
-    qs = [0.14, 0.05, 0.44, 0.09, 0.32, 0.11, 0.02, 0.44, 0.45, 0.44, 0.13, 0.44, 0.43, 0.42, 0.14, 0.45]
+    # seven runs flood a block, nine recover it (a range of 0.23)
+    qs = [0.34, 0.25, 0.44, 0.29, 0.42, 0.31, 0.22, 0.44, 0.45, 0.44, 0.33, 0.44, 0.43, 0.42, 0.34, 0.45]
     ref, kind = quality_reference(qs)
     assert kind == "lower quartile"
-    # sorted runs 0.02, 0.05, 0.09, 0.11, 0.13, ...: position 15 / 4 = 3.75 -> 0.11 + 0.75 * 0.02
-    assert ref == pytest.approx(0.125)
+    # sorted runs 0.22, 0.25, 0.29, 0.31, 0.33, ...: position 15 / 4 = 3.75 -> 0.31 + 0.75 * 0.02
+    assert ref == pytest.approx(0.325)
 
 
 def test_rule_accepts_and_rejects():
