@@ -637,7 +637,7 @@ def release(lpa, torch, handles):
 
 
 def run_extras(lpa, torch, stream, tie, prune, reps=5):
-    """R-MAT 22 + the road-like 4096^2 grid (config 2) in both modes: device
+    """R-MAT 22 + the road-like 4096^2 grid in both modes: device
     edges/s per (graph, mode), the paper's multi-core CPU design on the host
     cores, and the tolerance / cap sweep per graph class."""
     args = argparse.Namespace(workload="rmat22+grid4096", tie=tie, prune=prune)
