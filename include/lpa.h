@@ -265,6 +265,15 @@ lpa_status lpa_graph_props_get(lpa_graph_t g, lpa_graph_props *out);
 lpa_status lpa_graph_get_config(lpa_graph_t g, lpa_config *out);
 lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config *cfg);
 
+/* Test hook for the bounded device-side waits (no counterpart in the paper).
+ * block_threads 128, 256 or 512: in the next run that launches the row
+ * kernel of that block size past its first-sweep shortcut, the first block to
+ * produce a tile leaves that tile's index copy unissued, once; the warps
+ * waiting on it give up after 2 s and the run returns LPA_ERR_TIMEOUT,
+ * leaving the context usable (the next run starts clean).  0 cancels a
+ * pending request.  Other values: LPA_ERR_INVALID_ARG. */
+lpa_status lpa_graph_debug_stall(lpa_graph_t g, int32_t block_threads);
+
 /* Run label propagation (Algorithm 1, lpa()): C <- [0..N), then sweeps until
  * dN/N <= tolerance (Section 4.1.3; the paper uses 0.05) or max_iters sweeps
  * (Section 4.1.2; the paper uses 20).

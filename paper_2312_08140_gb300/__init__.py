@@ -154,6 +154,7 @@ _SIGS = {
     "lpa_graph_props_get": ([_V, _P(LpaGraphProps)], ctypes.c_int),
     "lpa_graph_get_config": ([_V, _P(LpaConfig)], ctypes.c_int),
     "lpa_graph_set_config": ([_V, _P(LpaConfig)], ctypes.c_int),
+    "lpa_graph_debug_stall": ([_V, ctypes.c_int32], ctypes.c_int),
     "lpa_tolerance_threshold": ([_D, _I64, _P(_I64)], ctypes.c_int),
     "lpa_run": ([_V, ctypes.c_int, _D, _I32, _V, _V, _P(LpaRunInfo)], ctypes.c_int),
     "lpa_run_profiled": ([_V, ctypes.c_int, _D, _I32, _V, _V, _P(LpaRunInfo), _P(LpaProfile)], ctypes.c_int),
@@ -279,6 +280,13 @@ def lpa_graph_get_config(g) -> LpaConfig:
     c = LpaConfig()
     _check(load().lpa_graph_get_config(g, ctypes.byref(c)))
     return c
+
+
+def lpa_graph_debug_stall(g, block_threads):
+    """Test hook: the first block of the next row kernel of `block_threads`
+    threads to produce a tile skips that tile's index copy, once (its waits
+    give up: LPA_ERR_TIMEOUT)."""
+    _check(load().lpa_graph_debug_stall(g, block_threads))
 
 
 def lpa_graph_set_config(g, cfg: LpaConfig):

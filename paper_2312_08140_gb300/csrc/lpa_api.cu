@@ -1171,6 +1171,16 @@ lpa_status lpa_graph_set_config(lpa_graph_t g, const lpa_config* cfg) {
     return set_config(g->e, cfg);
 }
 
+lpa_status lpa_graph_debug_stall(lpa_graph_t g, int32_t block_threads) {
+    if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");
+    if (block_threads != 0 && block_threads != 128 && block_threads != 256 && block_threads != 512)
+        return fail(LPA_ERR_INVALID_ARG, "block_threads must be 0, 128, 256 or 512");
+    Engine& E = g->e;
+    LPA_CUDA(cudaSetDevice(E.device));
+    LPA_CUDA(cudaMemcpy(&E.s.ctrl->stall_copy, &block_threads, sizeof(int32_t), cudaMemcpyHostToDevice));
+    return LPA_OK;
+}
+
 lpa_status lpa_run(lpa_graph_t g, lpa_mode mode, double tolerance, int32_t max_iters, int32_t* labels_out,
                    void* stream, lpa_run_info* info) {
     if (!g) return fail(LPA_ERR_INVALID_ARG, "graph is NULL");

@@ -90,7 +90,8 @@ struct Ctrl {
     unsigned int ovf_slice_items;        // work items of the overflow kernels (set by k_ovf_plan)
     unsigned int ovf_part_items;
     unsigned int ovf_rescan_items;
-    unsigned int ovf_pad;
+    int32_t stall_copy;                  // test hook (lpa_graph_debug_stall): the block size of the
+                                         // row kernel whose block 0 skips its first index copy, once
     unsigned int row_next[kBins];        // block bins: next list position to take in this pass
     unsigned int row_next_pad[8 - kBins];
 };

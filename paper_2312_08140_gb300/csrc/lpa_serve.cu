@@ -149,6 +149,7 @@ __global__ void k_ctrl_init(Ctrl* c, double tau, int max_iters, int mode) {
     c->skip_marks = 0;
     c->cbuf = 0;
     c->rd = 0;
+    c->stall_copy = 0;
 }
 
 // ---------------------------------------------------------------- allocator

@@ -491,7 +491,14 @@ __global__ void __launch_bounds__(NT, RowsOccupancy<NT>::kBlocks) k_sweep_rows(D
                 prod.pe = t.e1;
             }
             tiles[produced % (2 * kStages)] = t;
-            if (t.v >= 0) {
+            // test hook: the first block of the kernel named by
+            // ctrl->stall_copy to produce a tile leaves that tile's copy
+            // unissued (once), so the waits on it run out
+            const bool stall = t.v >= 0 && produced == 0 && s.ctrl->stall_copy == NT &&
+                               atomicCAS(&s.ctrl->stall_copy, NT, 0) == NT;
+            if (stall) {
+                // neither the copy nor the arrival that would complete it
+            } else if (t.v >= 0) {
                 int64_t a1 = (t.e1 + 3) & ~(int64_t)3;
                 if (a1 > E_al) a1 = E_al;
                 const int64_t bytes = a1 > t.a0 ? (a1 - t.a0) * 4 : 0;
