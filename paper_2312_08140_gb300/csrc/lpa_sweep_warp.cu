@@ -120,6 +120,14 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_sweep_warp(DevState s, int 
     if (ASYNC && nbatch <= nwarps) K = kAsyncSmallRunBatches;
     const unsigned nruns = (nbatch + K - 1) / K;
     const unsigned full_windows = nruns / kScatterWindow;
+    // Graphs kept in the caller's order inside a batch (the serving arena,
+    // LPA_KEEP_ORDER): their vertices come in id order, and on id-ordered
+    // communities a run of consecutive vertices acts as a short ascending
+    // sweep, so the entries of a run are drawn at pseudo-random positions of
+    // the frontier instead (a Feistel permutation, redrawn every sweep) --
+    // what the shuffled storage order of batches gives the others.
+    const bool scatter_entries = ASYNC && BATCH && s.orig == nullptr;
+    const uint64_t visit_seed = 0x2312081405ull + 0x9E3779B97F4A7C15ull * (uint64_t)s.ctrl->iter;
     unsigned long long my_changed = 0, my_changed_entries = 0;
     for (unsigned ri = blockIdx.x * kWarpsPerBlock + wib; ri < nruns; ri += nwarps) {
         unsigned pr = ri;
@@ -131,7 +139,8 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_sweep_warp(DevState s, int 
         // together so their latencies overlap.
         const unsigned kl = base + lane;
         const bool okl = lane < B && kl < cnt;
-        const int32_t vl = okl ? bv.list[kl] : 0;
+        const unsigned pl = (scatter_entries && okl) ? shuffle_pos(kl, cnt, visit_seed) : kl;   // frontier slot
+        const int32_t vl = okl ? bv.list[pl] : 0;
         int64_t stl = 0, enl = 0;
         int32_t ownl = 0;
         int actl = okl;
@@ -330,7 +339,8 @@ __global__ void __launch_bounds__(kWarpThreads, 4) k_sweep_warp(DevState s, int 
             const uint32_t best_key = warp_argmax_tie(key, key ? tr.key(cand) : 0xffffffffu);
             const int32_t best = best_key == 0xffffffffu ? -1 : tr.label(best_key);
             const bool changed = act && best >= 0 && best != own;   // warp-uniform
-            if (lane == 0) record_label<ASYNC>(L, bv.chg + base + i, v, own, best, changed);
+            const unsigned slot = __shfl_sync(kFull, pl, i);
+            if (lane == 0) record_label<ASYNC>(L, bv.chg + slot, v, own, best, changed);
             if constexpr (ASYNC) {
                 // the next vertex's first-chunk labels were read before this
                 // update: lanes holding v as neighbour take its new label
