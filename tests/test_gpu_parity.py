@@ -430,7 +430,7 @@ def check_async(lpa, g, tau=0.05, iters=20, cfg=None, runs=5, mode="async"):
     most the sum of the largest degrees, as many as the last sweep changed);
     and over `runs` runs (15 where the
     serial runs are not concentrated) the modularity bound of async_bounds
-    against the oracle's serial runs in sixteen random
+    against the oracle's serial runs in seeded random
     vertex orders (median within 0.02 of their median, or of their lower
     quartile where they are not concentrated; every run within 0.02 of their
     lowest)."""
