@@ -36,12 +36,17 @@
 // kernels of lpa_sweep_block.cu.  The first synchronous sweep of a
 // repeat-free graph, and the last bin of the first asynchronous sweep, take
 // the max-over-row pass instead (every label is still its vertex's id): no
-// gathers, so each warp streams whole rows with plain loads, eight per lane
-// in flight, and reduces them to the max of (weight key, tie key).
+// gathers, so each warp streams whole rows with 16-byte loads and reduces
+// them to the max of (weight key, tie key); under the strict tie-break the
+// tie key is the entry's position (rows list their neighbours in increasing
+// caller id), and with unit weights the pick is the row's first entry other
+// than the vertex itself.
 //
 // Every wait on an mbarrier is bounded (2 s of GPU time); a wait that gives
-// up sets error code 5 in the control block and the block leaves after its
-// copies in flight have landed (again waited for with a bound).
+// up sets error code 5 in the control block and the abort flag, the
+// aggregating warps leave together at their next barrier, and the producing
+// warp leaves after its copies in flight have landed (again waited for with
+// a bound).  lpa_graph_debug_stall makes one copy go missing, to test this.
 #include "lpa_device.cuh"
 
 namespace lpa {
