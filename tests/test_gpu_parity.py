@@ -109,6 +109,34 @@ def test_rmat_bins_and_spill_sync(lpa, cfg):
     assert_sync_parity(lpa, g, cfg=cfg)
 
 
+def test_profiled_path_matches_oracle(lpa):
+    """lpa_run_profiled launches every sweep kernel from the host (the path
+    the benchmark's roofline pass and ncu see) instead of the device loop; on
+    R-MAT scale 16 (all five degree bins, rows that overflow the last bin's
+    table) its synchronous labels, sweep count and per-sweep changed counts
+    are the oracle's, and its asynchronous labels stay inside components."""
+    import torch
+    g = L.rmat(16, 16, seed=3)
+    ref, it, changed = O.lpa_sync(g.off, g.idx, g.w, 0.05, 20)
+    h = lpa.lpa_graph_create(g.n, g.nnz, g.off, g.idx, g.w)
+    try:
+        out = torch.full((g.n,), -7, dtype=torch.int32, device="cuda")
+        for mode in ("sync", "sync_full"):
+            ri, prof = lpa.lpa_run_profiled(h, mode, 0.05, 20, out)
+            got = out.cpu().numpy()
+            mism = np.flatnonzero(got != ref)
+            assert mism.size == 0, f"{mode}: {mism.size} labels differ, first at {mism[:5]}"
+            assert ri.iterations == it and prof.iterations == it, (mode, ri.iterations, prof.iterations, it)
+            assert list(ri.changed[:it]) == changed.tolist(), mode
+        ri, prof = lpa.lpa_run_profiled(h, "async", 0.05, 20, out)
+        got = out.cpu().numpy()
+        assert np.all((got >= 0) & (got < g.n))
+        assert O.count_labels_outside_component(g.off, g.idx, got) == 0
+        assert prof.iterations == ri.iterations
+    finally:
+        lpa.lpa_graph_destroy(h)
+
+
 def test_rmat_raw_duplicates_selfloops_sync(lpa):
     g = L.rmat(12, 8, seed=5, dedup=False, drop_self=False)
     assert_sync_parity(lpa, g)
