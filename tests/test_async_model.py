@@ -7,6 +7,7 @@ consecutive frontier vertices.
   per-sweep changed counts exactly (random graphs, with and without weights).
 * On the twenty test graphs of the batched distribution (graphs 50-69, up to
   5,000 vertices), batches of 16, the kernel's smallest asynchronous batch,
+  and of 32 (a graph of one wave of warps: runs of two 16-vertex batches)
   meet the asynchronous acceptance rule of tests/async_bounds.py against the
   serial runs of Algorithm 1, while one vertex per batch (a Jacobi sweep)
   falls below it on several graphs: the reason the kernel does not scan a
@@ -34,16 +35,17 @@ def _meets_rule(q, serial):
     return q >= min(serial) - SLACK and (ref is None or q >= ref - SLACK)
 
 
-def test_batches_of_16_meet_the_rule_where_jacobi_sweeps_do_not():
-    ok16, ok1, worst1 = 0, 0, []
+def test_batches_of_16_and_32_meet_the_rule_where_jacobi_sweeps_do_not():
+    ok16, ok32, ok1, worst1 = 0, 0, 0, []
     for gi in range(50, 70):
         g = L.batched_sbm_graph(gi, n_max=5000)
         serial = serial_qs(g, 0.05, 20)
-        q16, q1 = lockstep_q(g, 16), lockstep_q(g, 1)
+        q16, q32, q1 = lockstep_q(g, 16), lockstep_q(g, 32), lockstep_q(g, 1)
         ok16 += _meets_rule(q16, serial)
+        ok32 += _meets_rule(q32, serial)
         ok1 += _meets_rule(q1, serial)
         worst1.append((q1 - float(np.median(serial)), gi))
-    assert ok16 == 20, ok16
+    assert ok16 == 20 and ok32 == 20, (ok16, ok32)
     assert ok1 <= 17, ok1
-    # the 509-vertex graph 66: a Jacobi sweep ends far below every serial run
+    # graphs 66 (509 vertices) and 67: a Jacobi sweep ends far below every serial run
     assert min(worst1)[0] < -0.3, min(worst1)
