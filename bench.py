@@ -120,7 +120,7 @@ WORKLOAD_TEXT = {
 TRAFFIC = {
     # R-MAT 27, asynchronous, caller's storage order: 83.1 GB over the six
     # launches of one run (profiles/dram_traffic_rmat27_async.md)
-    "k_sweep_rows<512>": {"bytes_per_launch": 13.845e9, "sha1": "a4b1898b68993817b0a26e212a97fca6ac402374",
+    "k_sweep_rows<512>": {"bytes_per_launch": 13.845e9, "sha1": "65d8471627fce658f1fa91866f02670ef6ea9178",
                           "workload": "rmat27", "order": "caller",
                           "files": ["lpa_sweep_rows.cu", "lpa_device.cuh", "lpa_internal.h"]},
 }

@@ -91,7 +91,8 @@ struct Ctrl {
     unsigned int ovf_part_items;
     unsigned int ovf_rescan_items;
     int32_t stall_copy;                  // test hook (lpa_graph_debug_stall): the block size of the
-                                         // row kernel whose block 0 skips its first index copy, once
+                                         // row kernel whose first block to produce a tile leaves that
+                                         // tile's index copy unissued, once
     unsigned int row_next[kBins];        // block bins: next list position to take in this pass
     unsigned int row_next_pad[8 - kBins];
 };
