@@ -101,9 +101,9 @@ def test_planted_partition_sync(lpa):
 @pytest.mark.parametrize("cfg", [None, (4, 64, 512, 1024, 0), (8, 256, 2048, 4096, 1001),
                                  (1, 33, 100, 200, 200)])
 def test_rmat_bins_and_spill_sync(lpa, cfg):
-    """R-MAT scale 16 has vertices in all five degree bins; rows above 4096
-    entries overflow the 8192-slot shared table of the last bin and use its
-    global spill table."""
+    """R-MAT scale 16 has vertices in all five degree bins, and rows above
+    4096 entries, whose inserts into the last bin's 8192-slot table are
+    bounded (they would go to the overflow path if they failed)."""
     g = L.rmat(16, 16, seed=3)
     assert int(np.diff(g.off).max()) > 4096
     assert_sync_parity(lpa, g, cfg=cfg)
@@ -112,8 +112,8 @@ def test_rmat_bins_and_spill_sync(lpa, cfg):
 def test_profiled_path_matches_oracle(lpa):
     """lpa_run_profiled launches every sweep kernel from the host (the path
     the benchmark's roofline pass and ncu see) instead of the device loop; on
-    R-MAT scale 16 (all five degree bins, rows that overflow the last bin's
-    table) its synchronous labels, sweep count and per-sweep changed counts
+    R-MAT scale 16 (all five degree bins, rows above 4096 entries) its
+    synchronous labels, sweep count and per-sweep changed counts
     are the oracle's, and its asynchronous labels stay inside components."""
     import torch
     g = L.rmat(16, 16, seed=3)
@@ -335,22 +335,45 @@ def test_async_small_sbm_graphs(lpa):
         check_async(lpa, L.batched_sbm_graph(gi, n_max=5000))
 
 
-def hub_graph(leaves, seed=0):
+def hub_graph(leaves, repeat=False):
     """A hub joined to `leaves` vertices that are paired into triangles with it
     (every leaf pair also linked), so the hub's row holds `leaves` distinct
-    labels in the first sweep: more than the last bin's shared table holds."""
+    labels in the first sweep: more than the last bin's shared table holds.
+    With `repeat` the hub-leaf 1 edge is listed twice (adjacent entries in
+    both rows), so the graph is not repeat-free."""
     pairs = [(0, k) for k in range(1, leaves + 1)]
     pairs += [(k, k + 1) for k in range(1, leaves, 2)]
+    if repeat:
+        pairs.append((0, 1))
     return L.from_undirected_pairs(leaves + 1, pairs)
 
 
-def test_hub_rows_that_overflow_the_shared_table(lpa):
-    """Rows with more distinct labels than the 8192-slot table take the
-    overflow path (slices grouped by label partition, then one block per
-    partition); labels, sweep counts and changed counts stay exact."""
+def test_repeat_free_hub_rows(lpa):
+    """Hub rows of 5,001 to 40,001 entries in repeat-free graphs: the first
+    sweep picks each row's first heaviest entry without a table, and the
+    later sweeps see few distinct labels; labels, sweep counts and changed
+    counts stay exact, and the asynchronous runs meet the acceptance rule."""
     for leaves in (5000, 9000, 40000):
         assert_sync_parity(lpa, hub_graph(leaves))
     check_async(lpa, hub_graph(40000))
+
+
+def test_hub_rows_through_the_sliced_overflow_path(lpa):
+    """A hub whose row lists a leaf twice makes the graph not repeat-free, so
+    the first sweep takes the general path: the hub's row then holds `leaves`
+    distinct labels, more than the 8192 slots of the last bin's table, and
+    goes through the sliced overflow path (slices grouped by label partition,
+    then one block per partition).  Synchronous labels, sweep counts and
+    changed counts equal the oracle's; asynchronous labels stay inside the
+    component."""
+    for leaves in (9000, 40000):
+        g = hub_graph(leaves, repeat=True)
+        assert _props_rows_distinct(lpa, g) == 0
+        assert_sync_parity(lpa, g)
+        got, info, h = run_gpu(lpa, g, "async")
+        lpa.lpa_graph_destroy(h)
+        assert np.all((got >= 0) & (got < g.n))
+        assert O.count_labels_outside_component(g.off, g.idx, got) == 0
 
 
 def test_nonstrict_sync_matches_oracle(lpa):
